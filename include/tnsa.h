@@ -1,0 +1,206 @@
+/*
+ * tnsa.h -- C ABI of the GB300 engine that contracts a quantum-circuit tensor network split into
+ * k partitions (arXiv 2507.20667, "Optimizing tensor network partitioning using Simulated
+ * Annealing").  Plain C types only: host or device pointers, sizes, status codes.
+ *
+ * Conventions used by every entry point
+ *   - Status codes only; no exceptions cross the ABI.  On any status other than TN_OK the
+ *     out-parameters are left untouched and tn_last_error() returns a message for this thread.
+ *   - Handles (tn_net, tn_plan, tn_ctx, tn_program) are owned by the caller and released with the
+ *     matching *_free.  Nets and plans are immutable after creation and may be shared between
+ *     threads; a tn_ctx (and every tn_program made from it) is bound to one device and one CUDA
+ *     stream and is not thread-safe.
+ *   - Complex numbers are interleaved (re, im).  Tensors are row-major: axis 0 is the slowest.
+ *   - Amplitudes are returned as a mantissa and a power of two: value = (re + i im) * 2^exp2.
+ *   - Operation counts can exceed 2^64, so they are returned as unsigned 128-bit integers.
+ *   - No entry point falls back to the CPU: compute entry points fail with TN_ECUDA when no
+ *     usable sm_103a device is present.
+ */
+#ifndef TNSA_H
+#define TNSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TN_OK = 0,
+    TN_EINVAL = 1,        /* malformed network, plan, option or argument */
+    TN_ENOMEM = 2,        /* host or device allocation failed */
+    TN_EBUDGET = 3,       /* the plan's device footprint exceeds the context's budget */
+    TN_ECUDA = 4,         /* a CUDA call failed or no usable device */
+    TN_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    TN_EUNSUPPORTED = 6   /* valid request outside what this build supports */
+} tn_status;
+
+/* Arithmetic used for the pairwise contractions.
+ *   TN_C128        complex128 everywhere (correctness variant, CUDA cores).
+ *   TN_C64         complex64 storage and arithmetic (CUDA cores).
+ *   TN_TF32_SPLIT  complex64 storage; dense steps on tensor cores with a 3-term TF32 hi/lo split.
+ *   TN_BF16_SPLIT  complex64 storage; dense steps on tensor cores with a 3-term BF16 hi/lo split,
+ *                  FP32 accumulation.
+ * In every mode the last, scalar-producing contraction accumulates in FP64. */
+typedef enum { TN_C128 = 0, TN_C64 = 1, TN_TF32_SPLIT = 2, TN_BF16_SPLIT = 3 } tn_precision;
+
+/* Target selection of the simulated-annealing move (Algorithm 2). */
+typedef enum { TN_SA_NAIVE = 0, TN_SA_DIRECTED = 1 } tn_sa_mode;
+
+/* One edge ((u, a), (v, b)) of Eq. 2.1, 0-based axes.  v = -1 is the dummy vertex (an open leg);
+ * b is then ignored. */
+typedef struct { int32_t u, a, v, b; } tn_edge;
+
+typedef struct { uint64_t lo, hi; } tn_u128;
+
+typedef struct tn_net tn_net;
+typedef struct tn_plan tn_plan;
+typedef struct tn_ctx tn_ctx;
+typedef struct tn_program tn_program;
+
+/* ------------------------------------------------------------------ networks (Section 2.1) */
+
+/* Build a network (Eq. 2.1-2.3).
+ *   n_tensors  number of tensors |V| >= 1
+ *   degree     [n_tensors] degree d_v >= 0 of each tensor (0 = scalar)
+ *   dims       concatenation of every tensor's dims n_v (sum of degree entries, each >= 1)
+ *   data       concatenation of every tensor's entries, complex128 interleaved (re, im),
+ *              row-major; 2 * sum_v |T_v| doubles
+ *   n_edges, edges  the edge list; every (u, a) slot must be named exactly once, the dims at both
+ *              ends must agree (n_{u,a} = n_{v,b}), and u != v (no self-loops).  Several edges
+ *              between the same two tensors are allowed.
+ * The arrays are copied; the caller keeps ownership of its buffers.
+ * Errors: TN_EINVAL for any violation above or an element count above 2^62; TN_ENOMEM. */
+tn_status tn_build(int32_t n_tensors, const int32_t *degree, const int64_t *dims,
+                   const double *data, int32_t n_edges, const tn_edge *edges, tn_net **out);
+
+/* Replace the entries of tensor t (same shape), e.g. a new bitstring's bra tensors.
+ * data: |T_t| complex128 interleaved.  Programs built from this net pick the change up at their
+ * next run (the leaves are re-uploaded).  Errors: TN_EINVAL. */
+tn_status tn_net_set_tensor(tn_net *net, int32_t t, const double *data);
+
+/* Number of tensors, edges, and whether every leg is bound (a closed network). */
+tn_status tn_net_info(const tn_net *net, int32_t *n_tensors, int32_t *n_edges, int32_t *closed);
+void tn_net_free(tn_net *net);
+
+/* ------------------------------------------------------------------ planning (Sections 3-4) */
+
+typedef struct {
+    int32_t k;                  /* number of partitions, 1 <= k <= n_tensors */
+    int32_t mode;               /* tn_sa_mode; default TN_SA_DIRECTED */
+    double T0, Tf;              /* initial / final temperature of Eq. 4.3-4.4 (log-cost units) */
+    int32_t steps_per_temp;     /* N of Algorithm 1 (split as ceil(N/p) per thread) */
+    int32_t threads;            /* p of Algorithm 1 (division algorithm); >= 1 */
+    double time_limit_s;        /* > 0: time-based cooling, t = elapsed / limit */
+    int32_t iterations;         /* used when time_limit_s <= 0: t = i / iterations */
+    int32_t restart_threshold;  /* RestartThreshold of Algorithm 1 */
+    int32_t fanin_samples;      /* RandomGreedy samples for the fan-in tree (k > 4) */
+    uint64_t seed;
+    const int32_t *initial_part;/* nullable: [n_tensors] initial partition in [0, k); NULL = a
+                                   balanced breadth-first split.  Read during tn_plan only. */
+} tn_plan_opts;
+
+/* Fill opts with the defaults: k = 1, DIRECTED, T0 = 0.1, Tf = 0.001, N = 8, p = 1,
+ * iterations = 200, RestartThreshold = 50, 32 fan-in samples, seed = 0, initial_part = NULL. */
+void tn_plan_opts_default(tn_plan_opts *opts);
+
+/* Plan a contraction (Section 4): initial partition, simulated-annealing refinement
+ * (Algorithms 1 and 2) minimising con_dist (Eq. 3.5 with con = con_serial and no communication
+ * term, Section 4.4 and 5.2), a Greedy tree per partition and a fan-in tree over the partition
+ * results (exhaustive for k <= 4, RandomGreedy above).  With k = 1 the plan is the Greedy tree.
+ * Deterministic for a given seed when time_limit_s <= 0.
+ * Errors: TN_EINVAL (bad k or options, invalid initial_part), TN_ENOMEM. */
+tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **out);
+
+/* Wrap a caller-chosen tree as a plan.  steps: [n_steps][2] (left, right) node ids, where leaves
+ * are 0..n-1 and step s creates node n + s; n_steps must be n - 1.  part: [n] partition of each
+ * tensor in [0, k) (NULL means k = 1).  Errors: TN_EINVAL if the steps do not form one binary
+ * tree over all tensors or the tree does not accept the partition (Eq. 2.7). */
+tn_status tn_plan_import(const tn_net *net, int32_t k, const int32_t *part, int32_t n_steps,
+                         const int32_t *steps, tn_plan **out);
+
+/* Exact counts of the plan's tree B (Section 3):
+ *   total_ops = con_serial(B) (Eq. 3.2), crit_ops = con_dist(B, K) (Eq. 3.5, con = con_serial,
+ *   comm = 0), mem_elems = mem(B) (Eq. 3.1).  Any pointer may be NULL. */
+tn_status tn_plan_counts(const tn_plan *plan, tn_u128 *total_ops, tn_u128 *crit_ops,
+                         tn_u128 *mem_elems);
+
+typedef struct {
+    tn_u128 con_serial, con_dist, con_par, mem; /* Eq. 3.2, 3.5, 3.4, 3.1 */
+    tn_u128 initial_con_dist;                   /* con_dist of the initial partition */
+    int32_t k, n_steps;
+    int32_t sa_iterations, sa_accepted, sa_restarts;
+    double plan_seconds;
+} tn_plan_info;
+tn_status tn_plan_get_info(const tn_plan *plan, tn_plan_info *info);
+
+/* Export the plan.  part_of_tensor: [n_tensors]; steps: [n_steps][3] (left, right, out) with the
+ * node numbering of tn_plan_import (partition 0's steps first, ..., fan-in steps last);
+ * step_part: [n_steps] partition of each step, -1 for fan-in steps.  Any array may be NULL;
+ * *n_steps receives n_tensors - 1. */
+tn_status tn_plan_export(const tn_plan *plan, int32_t *part_of_tensor, int32_t *steps,
+                         int32_t *step_part, int32_t *n_steps);
+void tn_plan_free(tn_plan *plan);
+
+/* ------------------------------------------------------------------ contraction on the GPU */
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  hbm_budget_bytes bounds the device memory a program may use (0 = no bound).
+ * Errors: TN_ECUDA (no sm_103a device), TN_ENOMEM. */
+tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_bytes, tn_ctx **out);
+void tn_ctx_free(tn_ctx *ctx);
+
+/* Block until all work enqueued on the context's stream has finished.  Errors: TN_ECUDA. */
+tn_status tn_ctx_synchronize(tn_ctx *ctx);
+
+typedef struct {
+    double device_ms;          /* device time of the contraction (CUDA events) */
+    int32_t launches;          /* kernels launched */
+    int32_t n_gather, n_tile, n_dot, n_tc;  /* steps per kernel class */
+    double flops;              /* algorithmic flops, 8 * con_serial */
+    double bytes;              /* algorithmic bytes: sum over steps of (|A|+|B|+|C|) * element size */
+    size_t arena_bytes;        /* device memory held for intermediates */
+} tn_run_info;
+
+/* Compile (net, plan, precision) into a device program: per-step layouts, index maps, kernel
+ * classes, a static memory plan for all intermediates, the leaves uploaded to the device.
+ * Errors: TN_EBUDGET (footprint above the budget), TN_EUNSUPPORTED (open network), TN_ECUDA. */
+tn_status tn_program_create(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
+                            tn_program **out);
+
+/* Enqueue one contraction on the context's stream without waiting.  d_result is DEVICE memory of
+ * at least 32 bytes, receiving {double re, double im, int32 exp2, int32 status}.  The program's
+ * leaves and intermediates stay resident between runs.  Errors: TN_ECUDA. */
+tn_status tn_program_run(tn_program *prog, void *d_result);
+
+/* Bytes of device memory the program holds (leaves + intermediates + descriptors). */
+tn_status tn_program_footprint(const tn_program *prog, size_t *bytes);
+tn_status tn_program_last_info(const tn_program *prog, tn_run_info *info);
+void tn_program_free(tn_program *prog);
+
+/* One contraction end to end: upload the leaves from the host net, run, read the amplitude back.
+ * out_amp: host double[2]; out_exp2: host int32.  info may be NULL.  Blocks until done.
+ * Errors: as tn_program_create / tn_program_run. */
+tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
+                      double out_amp[2], int32_t *out_exp2, tn_run_info *info);
+
+/* Permute the axes of a row-major DEVICE tensor (the transposition of the TTGT scheme realising
+ * Eq. 2.4, Section 5.1): output axis t is input axis perm[t], so out has dims[perm[t]] at axis t.
+ *   d_in, d_out   device buffers of prod(dims) elements, not overlapping
+ *   elem_bytes    1, 2, 4, 8 or 16 (the payload is moved bit for bit)
+ *   rank          0..32; dims[rank] >= 1; perm a permutation of 0..rank-1
+ * Enqueued on the context's stream, returns without waiting.  Errors: TN_EINVAL, TN_ECUDA. */
+tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_bytes, int32_t rank,
+                     const int64_t *dims, const int32_t *perm);
+
+/* ------------------------------------------------------------------ diagnostics */
+
+const char *tn_status_str(tn_status s);
+const char *tn_last_error(void);   /* thread-local message of the last failure */
+const char *tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNSA_H */

@@ -1,0 +1,684 @@
+// Host planner: Greedy trees, the cost model, the fan-in tree and the simulated-annealing
+// refinement of the partitioning (Sections 2.3-4.4 of arXiv 2507.20667).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <queue>
+#include <thread>
+
+#include "tn_internal.hpp"
+
+namespace tn {
+
+static const u128 kSizeCap = ((u128)1) << 120;
+
+u128 legs_size(const Legs &l, const std::vector<int64_t> &edim, bool &ovf) {
+    u128 p = 1;
+    for (int32_t e : l) {
+        p *= (u128)edim[e];
+        if (p > kSizeCap) { ovf = true; p = kSizeCap; }
+    }
+    return p;
+}
+
+// Product of n(e) over legs(a) U legs(b): 2^vc of Eq. 3.3 as an integer product.
+u128 union_size(const Legs &a, const Legs &b, const std::vector<int64_t> &edim, bool &ovf) {
+    u128 p = 1;
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {
+        int32_t e;
+        if (j == b.size() || (i < a.size() && a[i] < b[j])) e = a[i++];
+        else if (i == a.size() || b[j] < a[i]) e = b[j++];
+        else { e = a[i]; ++i; ++j; }
+        p *= (u128)edim[e];
+        if (p > kSizeCap) { ovf = true; p = kSizeCap; }
+    }
+    return p;
+}
+
+// Eq. 2.6: the legs of a contracted pair are the symmetric difference of the children's legs.
+void legs_symdiff(const Legs &a, const Legs &b, Legs &out) {
+    out.clear();
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {
+        if (j == b.size() || (i < a.size() && a[i] < b[j])) out.push_back(a[i++]);
+        else if (i == a.size() || b[j] < a[i]) out.push_back(b[j++]);
+        else { ++i; ++j; }
+    }
+}
+
+bool legs_intersect(const Legs &a, const Legs &b) {
+    size_t i = 0, j = 0;
+    while (i < a.size() && j < b.size()) {
+        if (a[i] == b[j]) return true;
+        if (a[i] < b[j]) ++i; else ++j;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------ Greedy
+// The Greedy rule (Section 2.3 with the memory-reduction objective of Eq. 4.5): repeatedly
+// contract the pair sharing a leg with the largest |A| + |B| - |A*B|; ties go to the
+// lexicographically smallest (i, j) in local ids; new nodes take the next id; a set with no
+// connected pair joins its two smallest tensors (by size, then id) by an outer product.
+namespace {
+struct Cand {
+    i128 obj;
+    int32_t i, j;
+};
+struct CandLess {  // priority_queue pops the "largest": higher obj, then smaller i, smaller j
+    bool operator()(const Cand &x, const Cand &y) const {
+        if (x.obj != y.obj) return x.obj < y.obj;
+        if (x.i != y.i) return x.i > y.i;
+        return x.j > y.j;
+    }
+};
+}  // namespace
+
+GreedyTree greedy_tree(const std::vector<const Legs *> &init, const std::vector<int64_t> &edim,
+                       bool &ovf) {
+    GreedyTree out;
+    const int32_t s = (int32_t)init.size();
+    if (s == 0) return out;
+    std::vector<Legs> legs(2 * s - 1);
+    std::vector<u128> size(2 * s - 1, 0);
+    std::vector<char> alive(2 * s - 1, 0);
+    for (int32_t i = 0; i < s; ++i) {
+        legs[i] = *init[i];
+        size[i] = legs_size(legs[i], edim, ovf);
+        alive[i] = 1;
+    }
+    if (s == 1) {
+        out.root_legs = legs[0];
+        out.root_size = size[0];
+        return out;
+    }
+    // holders: which (at most two) live nodes carry each edge
+    std::vector<int32_t> touched;
+    std::vector<std::array<int32_t, 2>> hold;
+    std::vector<int32_t> slot(edim.size(), -1);
+    auto add_holder = [&](int32_t e, int32_t v) {
+        if (slot[e] < 0) {
+            slot[e] = (int32_t)hold.size();
+            hold.push_back({-1, -1});
+            touched.push_back(e);
+        }
+        auto &h = hold[slot[e]];
+        if (h[0] < 0) h[0] = v; else h[1] = v;
+    };
+    auto drop_holder = [&](int32_t e, int32_t v) {
+        auto &h = hold[slot[e]];
+        if (h[0] == v) { h[0] = h[1]; h[1] = -1; }
+        else if (h[1] == v) h[1] = -1;
+    };
+    for (int32_t i = 0; i < s; ++i)
+        for (int32_t e : legs[i]) add_holder(e, i);
+
+    std::priority_queue<Cand, std::vector<Cand>, CandLess> pq;
+    auto objective = [&](int32_t i, int32_t j) -> i128 {
+        Legs r;
+        legs_symdiff(legs[i], legs[j], r);
+        return (i128)size[i] + (i128)size[j] - (i128)legs_size(r, edim, ovf);
+    };
+    auto push_pair = [&](int32_t a, int32_t b) {
+        int32_t i = std::min(a, b), j = std::max(a, b);
+        pq.push(Cand{objective(i, j), i, j});
+    };
+    for (int32_t e : touched) {
+        auto &h = hold[slot[e]];
+        if (h[0] >= 0 && h[1] >= 0) push_pair(h[0], h[1]);   // duplicates are harmless
+    }
+    int32_t next = s, n_alive = s;
+    while (n_alive > 1) {
+        int32_t i = -1, j = -1;
+        while (!pq.empty()) {
+            Cand c = pq.top();
+            pq.pop();
+            if (alive[c.i] && alive[c.j]) { i = c.i; j = c.j; break; }
+        }
+        if (i < 0) {  // no connected pair: outer product of the two smallest by (size, id)
+            int32_t a = -1, b = -1;
+            for (int32_t v = 0; v < next; ++v) {
+                if (!alive[v]) continue;
+                if (a < 0 || size[v] < size[a]) { b = a; a = v; }
+                else if (b < 0 || size[v] < size[b]) b = v;
+            }
+            i = std::min(a, b);
+            j = std::max(a, b);
+        }
+        const int32_t o = next++;
+        legs_symdiff(legs[i], legs[j], legs[o]);
+        size[o] = legs_size(legs[o], edim, ovf);
+        u128 c = union_size(legs[i], legs[j], edim, ovf);
+        out.con += c;
+        if (out.con > kSizeCap) { ovf = true; out.con = kSizeCap; }
+        u128 m = size[o] + size[i] + size[j];
+        if (m > out.mem) out.mem = m;
+        out.steps.emplace_back(i, j);
+        alive[i] = alive[j] = 0;
+        alive[o] = 1;
+        --n_alive;
+        for (int32_t e : legs[i]) drop_holder(e, i);
+        for (int32_t e : legs[j]) drop_holder(e, j);
+        for (int32_t e : legs[o]) add_holder(e, o);
+        for (int32_t e : legs[o]) {
+            auto &h = hold[slot[e]];
+            int32_t other = (h[0] == o) ? h[1] : h[0];
+            if (other >= 0 && other != o) push_pair(o, other);
+        }
+    }
+    out.root_legs = legs[next - 1];
+    out.root_size = size[next - 1];
+    return out;
+}
+
+// ------------------------------------------------------------------------------------ fan-in
+namespace {
+struct Rng {  // xoshiro256** seeded through splitmix64
+    uint64_t s[4];
+    explicit Rng(uint64_t seed) {
+        for (int i = 0; i < 4; ++i) {
+            seed += 0x9E3779B97F4A7C15ull;
+            uint64_t z = seed;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            s[i] = z ^ (z >> 31);
+        }
+    }
+    static uint64_t rotl(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
+    uint64_t next() {
+        uint64_t r = rotl(s[1] * 5, 7) * 9, t = s[1] << 17;
+        s[2] ^= s[0]; s[3] ^= s[1]; s[1] ^= s[2]; s[0] ^= s[3]; s[2] ^= t; s[3] = rotl(s[3], 45);
+        return r;
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+    uint32_t below(uint32_t n) { return (uint32_t)(((next() >> 32) * (uint64_t)n) >> 32); }
+};
+
+uint64_t mix64(uint64_t h, uint64_t v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h * 0xff51afd7ed558ccdull;
+}
+
+// Evaluate a fan-in merge sequence: con_dist (Eq. 3.5, comm = 0) and the fan-in con / mem.
+FanIn eval_fanin(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
+                 const std::vector<std::pair<int32_t, int32_t>> &steps,
+                 const std::vector<int64_t> &edim, bool &ovf) {
+    const int32_t k = (int32_t)roots.size();
+    std::vector<Legs> legs(roots);
+    legs.resize(2 * k - 1);
+    std::vector<u128> cost(2 * k - 1, 0), size(2 * k - 1, 0);
+    std::vector<int32_t> parent(2 * k - 1, -1);
+    FanIn f;
+    f.steps = steps;
+    for (int32_t i = 0; i < k; ++i) size[i] = legs_size(legs[i], edim, ovf);
+    for (size_t s = 0; s < steps.size(); ++s) {
+        int32_t a = steps[s].first, b = steps[s].second, o = k + (int32_t)s;
+        legs_symdiff(legs[a], legs[b], legs[o]);
+        size[o] = legs_size(legs[o], edim, ovf);
+        cost[o] = union_size(legs[a], legs[b], edim, ovf);
+        parent[a] = parent[b] = o;
+        f.con += cost[o];
+        u128 m = size[o] + size[a] + size[b];
+        if (m > f.mem) f.mem = m;
+    }
+    for (int32_t i = 0; i < k; ++i) {
+        u128 c = part_con[i];
+        for (int32_t v = parent[i]; v >= 0; v = parent[v]) c += cost[v];
+        if (c > f.con_dist) f.con_dist = c;
+    }
+    return f;
+}
+
+bool fanin_better(const FanIn &a, const FanIn &b) {
+    if (a.con_dist != b.con_dist) return a.con_dist < b.con_dist;
+    return a.con < b.con;
+}
+
+void enumerate_fanin(std::vector<int32_t> &alive, int32_t next,
+                     std::vector<std::pair<int32_t, int32_t>> &cur, const std::vector<Legs> &roots,
+                     const std::vector<u128> &part_con, const std::vector<int64_t> &edim,
+                     FanIn &best, bool &have, bool &ovf) {
+    if (alive.size() == 1) {
+        FanIn f = eval_fanin(roots, part_con, cur, edim, ovf);
+        if (!have || fanin_better(f, best)) { best = f; have = true; }
+        return;
+    }
+    for (size_t x = 0; x < alive.size(); ++x)
+        for (size_t y = x + 1; y < alive.size(); ++y) {
+            int32_t a = alive[x], b = alive[y];
+            std::vector<int32_t> rest;
+            for (int32_t v : alive) if (v != a && v != b) rest.push_back(v);
+            rest.push_back(next);
+            cur.emplace_back(std::min(a, b), std::max(a, b));
+            enumerate_fanin(rest, next + 1, cur, roots, part_con, edim, best, have, ovf);
+            cur.pop_back();
+        }
+}
+
+// One (possibly noisy) Greedy pass over the partition results (RandomGreedy sample).
+std::vector<std::pair<int32_t, int32_t>> noisy_greedy(const std::vector<Legs> &roots,
+                                                      const std::vector<int64_t> &edim,
+                                                      double tau, Rng *rng, bool &ovf) {
+    const int32_t k = (int32_t)roots.size();
+    std::vector<Legs> legs(roots);
+    legs.resize(2 * k - 1);
+    std::vector<u128> size(2 * k - 1, 0);
+    std::vector<char> alive(2 * k - 1, 0);
+    for (int32_t i = 0; i < k; ++i) { size[i] = legs_size(legs[i], edim, ovf); alive[i] = 1; }
+    std::vector<std::pair<int32_t, int32_t>> steps;
+    int32_t next = k;
+    for (int32_t it = 0; it < k - 1; ++it) {
+        double best = 0;
+        int32_t bi = -1, bj = -1;
+        for (int32_t i = 0; i < next; ++i) {
+            if (!alive[i]) continue;
+            for (int32_t j = i + 1; j < next; ++j) {
+                if (!alive[j] || !legs_intersect(legs[i], legs[j])) continue;
+                Legs r;
+                legs_symdiff(legs[i], legs[j], r);
+                i128 obj = (i128)size[i] + (i128)size[j] - (i128)legs_size(r, edim, ovf);
+                double sc = (double)obj;
+                if (rng) {
+                    double u = rng->uniform();
+                    double g = -std::log(-std::log(u + 1e-300) + 1e-300);  // Gumbel(0, 1)
+                    sc += tau * std::max(std::fabs(sc), 1.0) * g;
+                }
+                if (bi < 0 || sc > best) { best = sc; bi = i; bj = j; }
+            }
+        }
+        if (bi < 0) {
+            int32_t a = -1, b = -1;
+            for (int32_t v = 0; v < next; ++v) {
+                if (!alive[v]) continue;
+                if (a < 0 || size[v] < size[a]) { b = a; a = v; }
+                else if (b < 0 || size[v] < size[b]) b = v;
+            }
+            bi = std::min(a, b);
+            bj = std::max(a, b);
+        }
+        legs_symdiff(legs[bi], legs[bj], legs[next]);
+        size[next] = legs_size(legs[next], edim, ovf);
+        alive[bi] = alive[bj] = 0;
+        alive[next] = 1;
+        steps.emplace_back(bi, bj);
+        ++next;
+    }
+    return steps;
+}
+}  // namespace
+
+// The fan-in (reduction) tree of Section 4.4: for k <= 4 every merge order is tried; above that
+// RandomGreedy keeps the best of `samples` Greedy paths (sample 0 noiseless, the others with
+// Gumbel noise on the objective).  Best = smallest con_dist, then smallest fan-in con, then first.
+FanIn fanin_tree(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
+                 const std::vector<int64_t> &edim, int samples, uint64_t seed, bool &ovf) {
+    const int32_t k = (int32_t)roots.size();
+    if (k == 1) {
+        FanIn f;
+        f.con_dist = part_con[0];
+        return f;
+    }
+    FanIn best;
+    bool have = false;
+    if (k <= 4) {
+        std::vector<int32_t> alive(k);
+        for (int32_t i = 0; i < k; ++i) alive[i] = i;
+        std::vector<std::pair<int32_t, int32_t>> cur;
+        enumerate_fanin(alive, k, cur, roots, part_con, edim, best, have, ovf);
+        return best;
+    }
+    Rng rng(seed);
+    for (int s = 0; s < std::max(samples, 1); ++s) {
+        auto steps = noisy_greedy(roots, edim, 0.5, s == 0 ? nullptr : &rng, ovf);
+        FanIn f = eval_fanin(roots, part_con, steps, edim, ovf);
+        if (!have || fanin_better(f, best)) { best = f; have = true; }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------------------------ counts
+tn_status plan_finalize(const Net &net, Plan &p) {
+    const int32_t n = net.n;
+    if ((int32_t)p.steps.size() != n - 1) return fail(TN_EINVAL, "a plan needs n_tensors - 1 steps");
+    const int32_t nn = 2 * n - 1;
+    std::vector<Legs> legs(nn);
+    std::vector<u128> cost(nn, 0), sub(nn, 0), acc(nn, 0), size(nn, 0);
+    std::vector<int32_t> parent(nn, -1), label(nn, -1), count(nn, 0);
+    std::vector<int32_t> part_size(p.k, 0);
+    bool ovf = false;
+    for (int32_t t = 0; t < n; ++t) {
+        legs[t] = net.legs[t];
+        size[t] = legs_size(legs[t], net.edim, ovf);
+        label[t] = p.part[t];
+        count[t] = 1;
+        if (p.part[t] < 0 || p.part[t] >= p.k) return fail(TN_EINVAL, "partition index out of range");
+        part_size[p.part[t]]++;
+    }
+    for (int32_t k = 0; k < p.k; ++k)
+        if (part_size[k] == 0) return fail(TN_EINVAL, "empty partition");
+    u128 con = 0, mem = 0;
+    for (int32_t s = 0; s < n - 1; ++s) {
+        int32_t l = p.steps[s][0], r = p.steps[s][1], o = n + s;
+        if (l < 0 || r < 0 || l >= o || r >= o || l == r || parent[l] >= 0 || parent[r] >= 0)
+            return fail(TN_EINVAL, "steps do not form a binary contraction tree");
+        p.steps[s][2] = o;
+        parent[l] = parent[r] = o;
+        legs_symdiff(legs[l], legs[r], legs[o]);
+        size[o] = legs_size(legs[o], net.edim, ovf);
+        cost[o] = union_size(legs[l], legs[r], net.edim, ovf);
+        sub[o] = cost[o] + sub[l] + sub[r];
+        con += cost[o];
+        u128 m = size[o] + size[l] + size[r];
+        if (m > mem) mem = m;
+        count[o] = count[l] + count[r];
+        label[o] = (label[l] >= 0 && label[l] == label[r]) ? label[l] : -1;
+    }
+    if (ovf) return fail(TN_EINVAL, "operation count exceeds 2^120");
+    // acc(v): sum of 2^vc over the ancestors of v (v excluded), top-down.
+    for (int32_t v = nn - 1; v >= 0; --v)
+        acc[v] = parent[v] >= 0 ? acc[parent[v]] + cost[parent[v]] : 0;
+    u128 cpar = 0;
+    for (int32_t t = 0; t < n; ++t) cpar = std::max(cpar, acc[t]);     // Eq. 3.4
+    // Eq. 2.7: each partition must be the leaf set of a subtree (a pure node covering it).
+    p.part_root.assign(p.k, -1);
+    for (int32_t v = 0; v < nn; ++v)
+        if (label[v] >= 0 && count[v] == part_size[label[v]]) p.part_root[label[v]] = v;
+    u128 cdist = 0;
+    for (int32_t k = 0; k < p.k; ++k) {
+        if (p.part_root[k] < 0) return fail(TN_EINVAL, "the tree does not accept the partitioning");
+        int32_t r = p.part_root[k];
+        cdist = std::max(cdist, sub[r] + acc[r]);                        // Eq. 3.5, comm = 0
+    }
+    p.step_part.assign(n - 1, -1);
+    for (int32_t s = 0; s < n - 1; ++s) p.step_part[s] = label[n + s];
+    p.con_serial = con;
+    p.con_par = cpar;
+    p.con_dist = cdist;
+    p.mem = mem;
+    return TN_OK;
+}
+
+// ------------------------------------------------------------------------------------ SA
+namespace {
+struct PartState {
+    std::vector<int32_t> members;   // global tensor ids, increasing
+    GreedyTree tree;
+};
+
+struct State {
+    std::vector<int32_t> part;
+    std::vector<PartState> parts;
+    FanIn fan;
+    u128 cost = 0;                  // con_dist
+};
+
+struct Ctx {
+    const Net &net;
+    int32_t k;
+    int32_t samples;
+    bool ovf = false;
+};
+
+void rebuild_part(const Ctx &c, PartState &ps, bool &ovf) {
+    std::vector<const Legs *> init;
+    init.reserve(ps.members.size());
+    for (int32_t t : ps.members) init.push_back(&c.net.legs[t]);
+    ps.tree = greedy_tree(init, c.net.edim, ovf);
+}
+
+// EvaluateState (Section 4.4): Greedy trees are kept per partition; the fan-in tree and con_dist
+// follow from the partition results.  The fan-in sampling seed is a hash of the partition roots,
+// so the cost is a function of the state alone.
+void evaluate(const Ctx &c, State &s, bool &ovf) {
+    std::vector<Legs> roots(c.k);
+    std::vector<u128> pc(c.k);
+    uint64_t h = 0x1234567ull;
+    for (int32_t k = 0; k < c.k; ++k) {
+        roots[k] = s.parts[k].tree.root_legs;
+        pc[k] = s.parts[k].tree.con;
+        for (int32_t e : roots[k]) h = mix64(h, (uint64_t)e * 131 + (uint64_t)k);
+        h = mix64(h, (uint64_t)pc[k] ^ (uint64_t)(pc[k] >> 64));
+    }
+    s.fan = fanin_tree(roots, pc, c.net.edim, c.samples, h, ovf);
+    s.cost = s.fan.con_dist;
+}
+
+// Rebalance (Algorithm 2): pick a source partition with at least two tensors, a node v of its tree
+// other than the root (so the source never empties), the tensors under v, and a target partition
+// (uniform for NAIVE; for DIRECTED the argmax of Eq. 4.5 between legs(v) and the target's root,
+// ties to the lowest index); move the tensors and rebuild both Greedy trees and the fan-in tree.
+bool rebalance(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rng, bool &ovf) {
+    std::vector<int32_t> cand;
+    for (int32_t k = 0; k < c.k; ++k)
+        if (cur.parts[k].members.size() >= 2) cand.push_back(k);
+    if (cand.empty()) return false;
+    const int32_t src = cand[rng.below((uint32_t)cand.size())];
+    const PartState &ps = cur.parts[src];
+    const int32_t s = (int32_t)ps.members.size();
+    const int32_t v = (int32_t)rng.below((uint32_t)(2 * s - 2));   // any node but the root
+    // leaves under v
+    std::vector<std::pair<int32_t, int32_t>> ch(2 * s - 1, {-1, -1});
+    for (size_t t = 0; t < ps.tree.steps.size(); ++t) ch[s + t] = ps.tree.steps[t];
+    std::vector<int32_t> moved, stack{v};
+    while (!stack.empty()) {
+        int32_t x = stack.back();
+        stack.pop_back();
+        if (x < s) moved.push_back(ps.members[x]);
+        else { stack.push_back(ch[x].first); stack.push_back(ch[x].second); }
+    }
+    int32_t dst;
+    if (mode == TN_SA_NAIVE) {
+        dst = (int32_t)rng.below((uint32_t)(c.k - 1));
+        if (dst >= src) ++dst;
+    } else {
+        // legs(v) = edges with exactly one end among the moved tensors (Eq. 2.6 applied up the
+        // subtree), open legs included.
+        Legs lv;
+        {
+            std::vector<int32_t> all;
+            for (int32_t t : moved) all.insert(all.end(), c.net.legs[t].begin(), c.net.legs[t].end());
+            std::sort(all.begin(), all.end());
+            for (size_t i = 0; i < all.size();) {
+                size_t j = i;
+                while (j < all.size() && all[j] == all[i]) ++j;
+                if ((j - i) % 2 == 1) lv.push_back(all[i]);
+                i = j;
+            }
+        }
+        u128 sv = legs_size(lv, c.net.edim, ovf);
+        dst = -1;
+        i128 best = 0;
+        for (int32_t k = 0; k < c.k; ++k) {
+            if (k == src) continue;
+            const Legs &rl = cur.parts[k].tree.root_legs;
+            Legs r;
+            legs_symdiff(lv, rl, r);
+            i128 obj = (i128)sv + (i128)cur.parts[k].tree.root_size - (i128)legs_size(r, c.net.edim, ovf);
+            if (dst < 0 || obj > best) { best = obj; dst = k; }
+        }
+    }
+    nxt = cur;
+    std::sort(moved.begin(), moved.end());
+    for (int32_t t : moved) nxt.part[t] = dst;
+    auto &sm = nxt.parts[src].members;
+    std::vector<int32_t> keep;
+    std::set_difference(sm.begin(), sm.end(), moved.begin(), moved.end(), std::back_inserter(keep));
+    sm.swap(keep);
+    auto &dm = nxt.parts[dst].members;
+    std::vector<int32_t> merged;
+    std::merge(dm.begin(), dm.end(), moved.begin(), moved.end(), std::back_inserter(merged));
+    dm.swap(merged);
+    rebuild_part(c, nxt.parts[src], ovf);
+    rebuild_part(c, nxt.parts[dst], ovf);
+    evaluate(c, nxt, ovf);
+    return true;
+}
+
+double log_ratio(u128 cn, u128 cc) {
+    if (cc == 0) return cn == 0 ? 0.0 : INFINITY;
+    return std::log((double)cn) - std::log((double)cc);
+}
+
+struct StepResult {
+    State s;
+    int32_t accepted = 0;
+};
+
+// DoSteps of Algorithm 1 with the acceptance rule of Eq. 4.2.
+void do_steps(const Ctx &c, int32_t nsteps, const State &start, double T, int32_t mode,
+              uint64_t seed, StepResult &res, bool &ovf) {
+    Rng rng(seed);
+    res.s = start;
+    State cand;
+    for (int32_t j = 0; j < nsteps; ++j) {
+        if (!rebalance(c, res.s, cand, mode, rng, ovf)) break;
+        double p = std::exp(-log_ratio(cand.cost, res.s.cost) / T);
+        if (p >= rng.uniform()) {
+            res.s = std::move(cand);
+            res.accepted++;
+        }
+    }
+}
+}  // namespace
+
+tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
+    auto t_start = std::chrono::steady_clock::now();
+    const int32_t n = net.n;
+    if (o.k < 1 || o.k > n) return fail(TN_EINVAL, "k must satisfy 1 <= k <= n_tensors");
+    if (o.threads < 1 || o.steps_per_temp < 1 || o.restart_threshold < 1)
+        return fail(TN_EINVAL, "threads, steps_per_temp and restart_threshold must be >= 1");
+    if (!(o.T0 > 0) || !(o.Tf > 0)) return fail(TN_EINVAL, "temperatures must be positive");
+    if (o.time_limit_s <= 0 && o.iterations < 0) return fail(TN_EINVAL, "iterations must be >= 0");
+    if (o.mode != TN_SA_NAIVE && o.mode != TN_SA_DIRECTED) return fail(TN_EINVAL, "unknown SA mode");
+    Ctx c{net, o.k, o.fanin_samples};
+    bool ovf = false;
+
+    // initial partitioning
+    State init;
+    init.part.assign(n, 0);
+    if (o.k > 1) {
+        if (o.initial_part) {
+            for (int32_t t = 0; t < n; ++t) {
+                if (o.initial_part[t] < 0 || o.initial_part[t] >= o.k)
+                    return fail(TN_EINVAL, "initial_part entry out of range");
+                init.part[t] = o.initial_part[t];
+            }
+        } else {
+            // balanced breadth-first split: BFS order from tensor 0 (restarting in unvisited
+            // components), cut into k contiguous chunks of near-equal size
+            std::vector<std::vector<int32_t>> nb(n);
+            for (const tn_edge &e : net.edges)
+                if (e.v >= 0) { nb[e.u].push_back(e.v); nb[e.v].push_back(e.u); }
+            std::vector<int32_t> order, seen(n, 0);
+            for (int32_t r = 0; r < n; ++r) {
+                if (seen[r]) continue;
+                seen[r] = 1;
+                size_t head = order.size();
+                order.push_back(r);
+                while (head < order.size()) {
+                    int32_t x = order[head++];
+                    for (int32_t y : nb[x]) if (!seen[y]) { seen[y] = 1; order.push_back(y); }
+                }
+            }
+            for (int32_t i = 0; i < n; ++i) init.part[order[i]] = (int32_t)((int64_t)i * o.k / n);
+        }
+    }
+    init.parts.resize(o.k);
+    for (int32_t t = 0; t < n; ++t) init.parts[init.part[t]].members.push_back(t);
+    for (int32_t k = 0; k < o.k; ++k)
+        if (init.parts[k].members.empty()) return fail(TN_EINVAL, "initial partition has an empty part");
+    // Sizes and costs saturate at 2^120 during the search: a saturated state is merely very
+    // expensive, so the annealing can still move away from it.  Only the final plan must fit.
+    for (int32_t k = 0; k < o.k; ++k) rebuild_part(c, init.parts[k], ovf);
+    evaluate(c, init, ovf);
+
+    // Algorithm 1 (SimulatedAnnealing) with the division algorithm over p threads
+    State best = init, cur = init;
+    int64_t i = -1, i_best = -1;
+    int32_t accepted = 0, restarts = 0, iters = 0;
+    if (o.k > 1) {
+        const double alpha = o.Tf / o.T0;
+        const int32_t p = o.threads;
+        const int32_t np = (o.steps_per_temp + p - 1) / p;
+        auto now = [&] {
+            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        };
+        const bool timed = o.time_limit_s > 0;
+        double t0 = now();
+        while (true) {
+            double elapsed = now() - t0;
+            if (timed ? elapsed >= o.time_limit_s : (i + 1) >= o.iterations) break;
+            ++i;
+            double t = timed ? elapsed / o.time_limit_s : (double)i / (double)o.iterations;
+            double T = o.T0 * std::pow(alpha, t);
+            std::vector<StepResult> res(p);
+            std::vector<char> ovfs(p, 0);
+            auto work = [&](int32_t th) {
+                bool lo = false;
+                uint64_t sd = mix64(mix64(o.seed, (uint64_t)i), (uint64_t)th + 1);
+                do_steps(c, np, cur, T, o.mode, sd, res[th], lo);
+                ovfs[th] = lo;
+            };
+            if (p == 1) work(0);
+            else {
+                std::vector<std::thread> ts;
+                for (int32_t th = 0; th < p; ++th) ts.emplace_back(work, th);
+                for (auto &t : ts) t.join();
+            }
+            int32_t w = 0;   // parmin, ties to the lowest thread index
+            for (int32_t th = 0; th < p; ++th) {
+                accepted += res[th].accepted;
+                if (res[th].s.cost < res[w].s.cost) w = th;
+            }
+            cur = std::move(res[w].s);
+            ++iters;
+            if (cur.cost < best.cost) {
+                i_best = i;
+                best = cur;
+            } else if (i - i_best >= o.restart_threshold) {
+                i_best = i;
+                cur = best;
+                ++restarts;
+            }
+        }
+    }
+    // assemble the plan from the best state
+    out = Plan();
+    out.n = n;
+    out.k = o.k;
+    out.part = best.part;
+    std::vector<int32_t> root_id(o.k);
+    for (int32_t k = 0; k < o.k; ++k) {
+        const PartState &ps = best.parts[k];
+        std::vector<int32_t> gid(ps.members.begin(), ps.members.end());
+        for (auto &st : ps.tree.steps) {
+            int32_t a = gid[st.first], b = gid[st.second];
+            int32_t oid = n + (int32_t)out.steps.size();
+            out.steps.push_back({std::min(a, b), std::max(a, b), oid});
+            gid.push_back(oid);
+        }
+        root_id[k] = gid.back();
+    }
+    {
+        std::vector<int32_t> gid(root_id);
+        for (auto &st : best.fan.steps) {
+            int32_t a = gid[st.first], b = gid[st.second];
+            int32_t oid = n + (int32_t)out.steps.size();
+            out.steps.push_back({std::min(a, b), std::max(a, b), oid});
+            gid.push_back(oid);
+        }
+    }
+    tn_status s = plan_finalize(net, out);
+    if (s != TN_OK) return s;
+    out.init_con_dist = init.cost;
+    out.sa_iterations = iters;
+    out.sa_accepted = accepted;
+    out.sa_restarts = restarts;
+    out.plan_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return TN_OK;
+}
+
+}  // namespace tn

@@ -1,0 +1,294 @@
+"""Python binding of the C ABI in include/tnsa.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no arithmetic of the
+method: planning happens in the library's C++ planner and contraction in its CUDA kernels.  If the
+shared library is missing the import fails loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnsa.so")
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_EBUDGET, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(7)
+PRECISIONS = {"c128": 0, "c64": 1, "tf32": 2, "bf16": 3}
+MODES = {"naive": 0, "directed": 1}
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class tn_edge(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_int32), ("a", ctypes.c_int32), ("v", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+class tn_u128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+    def value(self) -> int:
+        return int(self.lo) | (int(self.hi) << 64)
+
+
+class tn_plan_opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("mode", ctypes.c_int32), ("T0", ctypes.c_double),
+                ("Tf", ctypes.c_double), ("steps_per_temp", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("time_limit_s", ctypes.c_double), ("iterations", ctypes.c_int32),
+                ("restart_threshold", ctypes.c_int32), ("fanin_samples", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("initial_part", ctypes.POINTER(ctypes.c_int32))]
+
+
+class tn_plan_info(ctypes.Structure):
+    _fields_ = [("con_serial", tn_u128), ("con_dist", tn_u128), ("con_par", tn_u128), ("mem", tn_u128),
+                ("initial_con_dist", tn_u128), ("k", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("sa_iterations", ctypes.c_int32), ("sa_accepted", ctypes.c_int32),
+                ("sa_restarts", ctypes.c_int32), ("plan_seconds", ctypes.c_double)]
+
+
+class tn_run_info(ctypes.Structure):
+    _fields_ = [("device_ms", ctypes.c_double), ("launches", ctypes.c_int32), ("n_gather", ctypes.c_int32),
+                ("n_tile", ctypes.c_int32), ("n_dot", ctypes.c_int32), ("n_tc", ctypes.c_int32),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: (getattr(self, f)) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_SIGS = {
+    "tn_build": (_I32, [_I32, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)]),
+    "tn_net_set_tensor": (_I32, [_P, _I32, _P]),
+    "tn_net_info": (_I32, [_P, _P, _P, _P]),
+    "tn_net_free": (None, [_P]),
+    "tn_plan_opts_default": (None, [ctypes.POINTER(tn_plan_opts)]),
+    "tn_plan_create": (_I32, [_P, ctypes.POINTER(tn_plan_opts), ctypes.POINTER(_P)]),
+    "tn_plan_import": (_I32, [_P, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
+    "tn_plan_counts": (_I32, [_P, ctypes.POINTER(tn_u128), ctypes.POINTER(tn_u128), ctypes.POINTER(tn_u128)]),
+    "tn_plan_get_info": (_I32, [_P, ctypes.POINTER(tn_plan_info)]),
+    "tn_plan_export": (_I32, [_P, _P, _P, _P, _P]),
+    "tn_plan_free": (None, [_P]),
+    "tn_ctx_create": (_I32, [_I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "tn_ctx_free": (None, [_P]),
+    "tn_ctx_synchronize": (_I32, [_P]),
+    "tn_program_create": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "tn_program_run": (_I32, [_P, _P]),
+    "tn_program_footprint": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tn_program_last_info": (_I32, [_P, ctypes.POINTER(tn_run_info)]),
+    "tn_program_free": (None, [_P]),
+    "tn_contract": (_I32, [_P, _P, _P, _I32, _P, _P, ctypes.POINTER(tn_run_info)]),
+    "tn_permute": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "tn_status_str": (ctypes.c_char_p, [_I32]),
+    "tn_last_error": (ctypes.c_char_p, []),
+    "tn_version": (ctypes.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2507_20667_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != TN_OK:
+        raise TnError(status, lib.tn_last_error().decode() or lib.tn_status_str(status).decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ptr, keep=()):
+        self.ptr = ptr
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self._free is not None:
+            getattr(lib, self._free)(self.ptr)
+            self.ptr = None
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+class Net(_Handle):
+    _free = "tn_net_free"
+
+
+class Plan(_Handle):
+    _free = "tn_plan_free"
+
+
+class Ctx(_Handle):
+    _free = "tn_ctx_free"
+
+
+class Program(_Handle):
+    _free = "tn_program_free"
+
+
+def tn_build(network) -> Net:
+    """network: any object with degrees, dims, data (float64 interleaved) and edges ([E,4])."""
+    degrees = np.ascontiguousarray(network.degrees, dtype=np.int32)
+    dims = np.ascontiguousarray(network.dims, dtype=np.int64)
+    data = np.ascontiguousarray(network.data, dtype=np.float64)
+    edges = np.ascontiguousarray(np.asarray(network.edges, dtype=np.int32).reshape(-1, 4))
+    out = ctypes.c_void_p()
+    _check(lib.tn_build(len(degrees), _ptr(degrees), _ptr(dims), _ptr(data), len(edges), _ptr(edges),
+                        ctypes.byref(out)))
+    return Net(out.value)
+
+
+def tn_net_set_tensor(net: Net, t: int, values) -> None:
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.complex128)).view(np.float64)
+    _check(lib.tn_net_set_tensor(net, int(t), _ptr(v)))
+
+
+def tn_net_info(net: Net):
+    n, e, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.tn_net_info(net, ctypes.byref(n), ctypes.byref(e), ctypes.byref(c)))
+    return n.value, e.value, bool(c.value)
+
+
+def tn_plan_opts_default() -> tn_plan_opts:
+    o = tn_plan_opts()
+    lib.tn_plan_opts_default(ctypes.byref(o))
+    return o
+
+
+def tn_plan_create(net: Net, k=1, mode="directed", T0=None, Tf=None, steps_per_temp=None, threads=None,
+                   time_limit_s=None, iterations=None, restart_threshold=None, fanin_samples=None,
+                   seed=None, initial_part=None) -> Plan:
+    o = tn_plan_opts_default()
+    o.k = int(k)
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    for name, val in (("T0", T0), ("Tf", Tf), ("steps_per_temp", steps_per_temp), ("threads", threads),
+                      ("time_limit_s", time_limit_s), ("iterations", iterations),
+                      ("restart_threshold", restart_threshold), ("fanin_samples", fanin_samples),
+                      ("seed", seed)):
+        if val is not None:
+            setattr(o, name, val)
+    keep = None
+    if initial_part is not None:
+        keep = np.ascontiguousarray(initial_part, dtype=np.int32)
+        o.initial_part = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    out = ctypes.c_void_p()
+    _check(lib.tn_plan_create(net, ctypes.byref(o), ctypes.byref(out)))
+    return Plan(out.value)
+
+
+def tn_plan_import(net: Net, steps, part=None, k=None) -> Plan:
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.int32).reshape(-1, 2))
+    if part is None:
+        pa, kk = None, 1
+    else:
+        pa = np.ascontiguousarray(part, dtype=np.int32)
+        kk = int(k if k is not None else pa.max() + 1)
+    out = ctypes.c_void_p()
+    _check(lib.tn_plan_import(net, kk, _ptr(pa) if pa is not None else None, len(st), _ptr(st),
+                              ctypes.byref(out)))
+    return Plan(out.value)
+
+
+def tn_plan_counts(plan: Plan):
+    t, c, m = tn_u128(), tn_u128(), tn_u128()
+    _check(lib.tn_plan_counts(plan, ctypes.byref(t), ctypes.byref(c), ctypes.byref(m)))
+    return t.value(), c.value(), m.value()
+
+
+def tn_plan_get_info(plan: Plan) -> dict:
+    i = tn_plan_info()
+    _check(lib.tn_plan_get_info(plan, ctypes.byref(i)))
+    out = {}
+    for f, _ in tn_plan_info._fields_:
+        v = getattr(i, f)
+        out[f] = v.value() if isinstance(v, tn_u128) else v
+    return out
+
+
+def tn_plan_export(plan: Plan, n_tensors: int):
+    part = np.zeros(n_tensors, np.int32)
+    steps = np.zeros((max(n_tensors - 1, 0), 3), np.int32)
+    sp = np.zeros(max(n_tensors - 1, 0), np.int32)
+    ns = ctypes.c_int32()
+    _check(lib.tn_plan_export(plan, _ptr(part), _ptr(steps), _ptr(sp), ctypes.byref(ns)))
+    return part, steps[: ns.value], sp[: ns.value]
+
+
+def tn_ctx_create(device=0, stream=None, hbm_budget_bytes=0) -> Ctx:
+    out = ctypes.c_void_p()
+    _check(lib.tn_ctx_create(int(device), ctypes.c_void_p(stream) if stream else None,
+                             int(hbm_budget_bytes), ctypes.byref(out)))
+    return Ctx(out.value)
+
+
+def tn_ctx_synchronize(ctx: Ctx) -> None:
+    _check(lib.tn_ctx_synchronize(ctx))
+
+
+def tn_program_create(ctx: Ctx, net: Net, plan: Plan, precision="c64") -> Program:
+    out = ctypes.c_void_p()
+    _check(lib.tn_program_create(ctx, net, plan, PRECISIONS[precision], ctypes.byref(out)))
+    # the program refers to ctx, net and plan: keep them alive as long as it lives
+    return Program(out.value, keep=(ctx, net, plan))
+
+
+def tn_program_run(prog: Program, d_result: int) -> None:
+    _check(lib.tn_program_run(prog, ctypes.c_void_p(d_result)))
+
+
+def tn_program_footprint(prog: Program) -> int:
+    b = ctypes.c_size_t()
+    _check(lib.tn_program_footprint(prog, ctypes.byref(b)))
+    return b.value
+
+
+def tn_program_last_info(prog: Program) -> dict:
+    i = tn_run_info()
+    _check(lib.tn_program_last_info(prog, ctypes.byref(i)))
+    return i.as_dict()
+
+
+def tn_contract(ctx: Ctx, net: Net, plan: Plan, precision="c64"):
+    """Returns (amplitude mantissa as complex, exp2, run info); amplitude = mantissa * 2**exp2."""
+    amp = np.zeros(2, np.float64)
+    e = ctypes.c_int32()
+    info = tn_run_info()
+    _check(lib.tn_contract(ctx, net, plan, PRECISIONS[precision], _ptr(amp), ctypes.byref(e),
+                           ctypes.byref(info)))
+    return complex(amp[0], amp[1]), e.value, info.as_dict()
+
+
+def tn_permute(ctx: Ctx, d_in: int, d_out: int, elem_bytes: int, dims, perm) -> None:
+    d = np.ascontiguousarray(dims, dtype=np.int64)
+    p = np.ascontiguousarray(perm, dtype=np.int32)
+    _check(lib.tn_permute(ctx, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), int(elem_bytes), len(d),
+                          _ptr(d), _ptr(p)))
+
+
+def tn_version() -> str:
+    return lib.tn_version().decode()
+
+
+def amplitude(mantissa: complex, exp2: int) -> complex:
+    """value = mantissa * 2**exp2 (a representation change of the returned pair, for callers)."""
+    return complex(mantissa) * (2.0 ** exp2)

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the complex128 oracle.
+
+Tolerances (relative error of the amplitude): complex128 1e-12 (against the state vector / oracle),
+complex64 1e-5, split-TF32 1e-5 and split-BF16 1e-4 -- the bounds the workload definition states
+for the single-amplitude results.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import contract as oc
+from oracle import costs as ocost
+from oracle import greedy as og
+from oracle import statevector as sv
+from paper_2507_20667_gb300 import inputs as tni
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 1e-5, "tf32": 1e-5, "bf16": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def tnsa():
+    from paper_2507_20667_gb300 import tnsa as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(tnsa):
+    return tnsa.tn_ctx_create(0)
+
+
+def oracle_amp(net):
+    steps = og.greedy_steps(list(ocost.leaf_legs(net)), ocost.edge_dims(net))
+    return oc.contract_scalar(net, steps)
+
+
+def gpu_amp(tnsa, ctx, net, plan=None, prec="c64", k=1, **kw):
+    h = tnsa.tn_build(net)
+    if plan is None:
+        plan = tnsa.tn_plan_create(h, k=k, **kw)
+    m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
+    return tnsa.amplitude(m, e), info
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64", "tf32", "bf16"])
+def test_cfg1_all_precisions(tnsa, ctx, prec):
+    circ, x = tni.cfg1()
+    net = tni.amplitude_tn(circ, x)
+    ref = sv.amplitude(circ, x)
+    assert rel(oracle_amp(net), ref) < 1e-13
+    got, info = gpu_amp(tnsa, ctx, net, prec=prec)
+    assert rel(got, ref) <= TOL[prec], (got, ref)
+    assert info["launches"] >= 1
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_closed_forms(tnsa, ctx, prec):
+    n = 9
+    g = tni.ghz(n)
+    for bits, want in (([0] * n, 1 / math.sqrt(2)), ([1] * n, 1 / math.sqrt(2))):
+        got, _ = gpu_amp(tnsa, ctx, tni.amplitude_tn(g, bits), prec=prec)
+        assert abs(got - want) <= TOL[prec] * want
+    got, _ = gpu_amp(tnsa, ctx, tni.amplitude_tn(g, [0, 1] + [0] * (n - 2)), prec=prec)
+    assert abs(got) <= 1e-6
+    circ = tni.brickwork_1d(8, 6, seed=31)
+    for net in (tni.inverse_tn(circ), tni.norm_tn(circ)):
+        got, _ = gpu_amp(tnsa, ctx, net, prec=prec, k=2, iterations=20,
+                         initial_part=tni.qubit_block_partition(net, 8, 2))
+        assert abs(got - 1) <= 10 * TOL[prec]
+    zz = sv.zz_expectation(circ, 2, 6)
+    got, _ = gpu_amp(tnsa, ctx, tni.zz_tn(circ, 2, 6), prec=prec)
+    assert abs(got - zz) <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_partition_and_order_invariance(tnsa, ctx, k):
+    """The amplitude does not depend on the tree or the partitioning (Section 2.3)."""
+    circ = tni.brickwork_1d(12, 10, seed=40)
+    x = tni.random_bitstring(12, 41)
+    net = tni.amplitude_tn(circ, x)
+    ref = sv.amplitude(circ, x)
+    init = tni.qubit_block_partition(net, 12, k) if k > 1 else None
+    for mode in ("directed", "naive"):
+        got, _ = gpu_amp(tnsa, ctx, net, prec="c128", k=k, mode=mode, iterations=30, seed=k,
+                         initial_part=init)
+        assert rel(got, ref) <= 1e-12
+        got, _ = gpu_amp(tnsa, ctx, net, prec="c64", k=k, mode=mode, iterations=30, seed=k,
+                         initial_part=init)
+        assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_networks_mixed_dims(tnsa, ctx, seed):
+    """Non-power-of-two dimensions exercise the general (div/mod) index maps."""
+    net = tni.random_network(14, 10, (1, 2, 3, 5, 6), seed=seed)
+    ref = oracle_amp(net)
+    for prec in ("c128", "c64"):
+        got, _ = gpu_amp(tnsa, ctx, net, prec=prec)
+        assert rel(got, ref) <= TOL[prec] * 10
+
+
+def test_random_tree_import(tnsa, ctx):
+    """Arbitrary imported trees, with larger intermediates and the tiled kernel class."""
+    net = tni.random_network(10, 12, (2, 3, 4), seed=77)
+    ref = oracle_amp(net)
+    rng = np.random.default_rng(5)
+    n = net.n_tensors
+    for trial in range(3):
+        alive, steps, nxt = list(range(n)), [], n
+        while len(alive) > 1:
+            i, j = sorted(rng.choice(len(alive), 2, replace=False))
+            a, b = alive[i], alive[j]
+            steps.append((min(a, b), max(a, b)))
+            alive = [t for t in alive if t not in (a, b)] + [nxt]
+            nxt += 1
+        h = tnsa.tn_build(net)
+        plan = tnsa.tn_plan_import(h, steps)
+        for prec in ("c128", "c64"):
+            m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
+            assert rel(tnsa.amplitude(m, e), ref) <= TOL[prec] * 10
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64", "tf32", "bf16"])
+def test_cfg3_oracle_instance(tnsa, ctx, prec):
+    """2D grid 4x5, depth 8, k = 8 partitions: against the 2^20 state vector."""
+    circ, x = tni.cfg3(small=True)
+    net = tni.amplitude_tn(circ, x)
+    ref = sv.amplitude(circ, x)
+    got, info = gpu_amp(tnsa, ctx, net, prec=prec, k=8, iterations=200, steps_per_temp=8, seed=7,
+                        initial_part=tni.qubit_block_partition(net, 20, 8))
+    assert rel(got, ref) <= TOL[prec], (got, ref)
+
+
+def test_cfg2_full_size(tnsa, ctx):
+    """24-qubit brickwork, depth 14, k = 4 SA partitions, complex64; the oracle contracts the
+    same network along its own Greedy tree."""
+    circ, x = tni.cfg2()
+    net = tni.amplitude_tn(circ, x)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=4, iterations=2000, steps_per_temp=8, seed=7,
+                               initial_part=tni.qubit_block_partition(net, 24, 4))
+    ref = oracle_amp(net)
+    for prec in ("c64", "c128"):
+        m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
+        assert rel(tnsa.amplitude(m, e), ref) <= TOL[prec] * (10 if prec == "c128" else 1)
+
+
+def test_new_bitstring_reuploads_leaves(tnsa, ctx):
+    circ, x = tni.cfg1()
+    net = tni.amplitude_tn(circ, x)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=1)
+    y = 1 - np.asarray(x)
+    n = circ.n_qubits
+    for q in range(n):  # bra tensors are the last n tensors
+        v = np.zeros(2, np.complex128)
+        v[y[q]] = 1
+        tnsa.tn_net_set_tensor(h, net.n_tensors - n + q, v)
+    m, e, _ = tnsa.tn_contract(ctx, h, plan, "c128")
+    assert rel(tnsa.amplitude(m, e), sv.amplitude(circ, y)) <= 1e-12
+
+
+def test_degenerate_networks(tnsa, ctx):
+    class Net:
+        pass
+    # a single scalar tensor
+    s = Net()
+    s.degrees = np.array([0], np.int32)
+    s.dims = np.zeros(0, np.int64)
+    s.data = np.array([0.25, -0.5])
+    s.edges = np.zeros((0, 4), np.int32)
+    h = tnsa.tn_build(s)
+    plan = tnsa.tn_plan_create(h, k=1)
+    for prec in ("c128", "c64"):
+        m, e, _ = tnsa.tn_contract(ctx, h, plan, prec)
+        assert tnsa.amplitude(m, e) == complex(0.25, -0.5)
+    # two disconnected closed components: the outer product of their amplitudes
+    c1, c2 = tni.brickwork_1d(4, 3, seed=1), tni.brickwork_1d(5, 3, seed=2)
+    n1 = tni.amplitude_tn(c1, [0, 1, 1, 0])
+    n2 = tni.amplitude_tn(c2, [1, 1, 0, 0, 1])
+    both = Net()
+    both.tensors = n1.tensors + n2.tensors
+    both.degrees = np.concatenate([n1.degrees, n2.degrees])
+    both.dims = np.concatenate([n1.dims, n2.dims])
+    both.data = np.concatenate([n1.data, n2.data])
+    e2 = n2.edges.copy()
+    e2[:, 0] += n1.n_tensors
+    e2[:, 2] += n1.n_tensors
+    both.edges = np.concatenate([n1.edges, e2])
+    want = sv.amplitude(c1, [0, 1, 1, 0]) * sv.amplitude(c2, [1, 1, 0, 0, 1])
+    h = tnsa.tn_build(both)
+    for k in (1, 2, 3):
+        plan = tnsa.tn_plan_create(h, k=k, iterations=10)
+        m, e, _ = tnsa.tn_contract(ctx, h, plan, "c128")
+        assert rel(tnsa.amplitude(m, e), want) <= 1e-12
+    # an open network is refused by the scalar entry point
+    o = tni.random_network(5, 2, (2,), seed=1, n_open=1)
+    h = tnsa.tn_build(o)
+    plan = tnsa.tn_plan_create(h, k=1)
+    with pytest.raises(tnsa.TnError) as ei:
+        tnsa.tn_contract(ctx, h, plan, "c64")
+    assert ei.value.status == tnsa.TN_EUNSUPPORTED
+
+
+def test_budget_rejection(tnsa):
+    ctx = tnsa.tn_ctx_create(0, hbm_budget_bytes=1024)
+    net = tni.amplitude_tn(*tni.cfg1())
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=1)
+    with pytest.raises(tnsa.TnError) as ei:
+        tnsa.tn_contract(ctx, h, plan, "c64")
+    assert ei.value.status == tnsa.TN_EBUDGET
