@@ -1,5 +1,6 @@
 // Host-side entry points of the C ABI: networks, plans, diagnostics.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -15,6 +16,11 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 tn_status fail(tn_status s, const std::string &msg) {
     g_last_error = msg;
     return s;
+}
+
+uint64_t next_uid() {
+    static std::atomic<uint64_t> counter{1};
+    return counter.fetch_add(1);
 }
 
 }  // namespace tn
@@ -137,6 +143,7 @@ tn_status tn_build(int32_t n_tensors, const int32_t *degree, const int64_t *dims
         delete h;
         return fail(TN_ENOMEM, "allocating the network");
     }
+    h->impl.uid = next_uid();
     *out = h;
     return TN_OK;
 }
@@ -189,6 +196,7 @@ tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **
         s = fail(TN_ENOMEM, "planner allocation");
     }
     if (s != TN_OK) { delete p; return s; }
+    p->impl.uid = next_uid();
     *out = p;
     return TN_OK;
 }
@@ -213,6 +221,7 @@ tn_status tn_plan_import(const tn_net *net, int32_t k, const int32_t *part, int3
     tn_status s = plan_finalize(nt, pl);
     if (s != TN_OK) { delete p; return s; }
     pl.init_con_dist = pl.con_dist;
+    pl.uid = next_uid();
     *out = p;
     return TN_OK;
 }

@@ -21,9 +21,8 @@ struct tn_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0;
-    tn_program *cached = nullptr;      // program reused by tn_contract
-    const tn_net *cached_net = nullptr;
-    const tn_plan *cached_plan = nullptr;
+    tn_program *cached = nullptr;      // program reused by tn_contract, keyed by the unique ids
+    uint64_t cached_net = 0, cached_plan = 0;   // of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
 };
 
@@ -480,7 +479,8 @@ tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_pr
                       double out_amp[2], int32_t *out_exp2, tn_run_info *info) {
     if (!ctx || !net || !plan || !out_amp || !out_exp2) return fail(TN_EINVAL, "NULL argument");
     CK(cudaSetDevice(ctx->device));
-    if (!(ctx->cached && ctx->cached_net == net && ctx->cached_plan == plan && ctx->cached_prec == prec)) {
+    if (!(ctx->cached && ctx->cached_net == net->impl.uid && ctx->cached_plan == plan->impl.uid &&
+          ctx->cached_prec == prec)) {
         if (ctx->cached) {
             cudaStreamSynchronize(ctx->stream);
             program_destroy(ctx->cached);
@@ -490,11 +490,12 @@ tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_pr
         tn_status s = tn_program_create(ctx, net, plan, prec, &p);
         if (s != TN_OK) return s;
         ctx->cached = p;
-        ctx->cached_net = net;
-        ctx->cached_plan = plan;
+        ctx->cached_net = net->impl.uid;
+        ctx->cached_plan = plan->impl.uid;
         ctx->cached_prec = prec;
     }
     tn_program *p = ctx->cached;
+    p->net = net;                  // the same net (by id); refresh the address
     p->uploaded_version = ~0ull;   // end to end: the leaves are copied from the host every call
     tn_status s = tn_program_run(p, p->d_res);
     if (s != TN_OK) return s;

@@ -37,6 +37,7 @@ struct Net {
     std::vector<Legs> legs;              // sorted legs of each tensor
     bool closed = true;
     uint64_t version = 0;                // bumped by tn_net_set_tensor
+    uint64_t uid = 0;                    // unique per created net (addresses can be reused)
 };
 
 // Saturating products of edge dimensions; `ovf` is set on overflow of 2^120.
@@ -75,7 +76,10 @@ struct Plan {
     u128 con_serial = 0, con_dist = 0, con_par = 0, mem = 0, init_con_dist = 0;
     int32_t sa_iterations = 0, sa_accepted = 0, sa_restarts = 0;
     double plan_seconds = 0;
+    uint64_t uid = 0;                    // unique per created plan
 };
+
+uint64_t next_uid();
 
 // Recompute all counts of a plan from its steps (Eq. 3.1-3.5); checks tree and acceptance.
 tn_status plan_finalize(const Net &net, Plan &plan);
