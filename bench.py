@@ -1,0 +1,316 @@
+"""Benchmark: contraction throughput of the partitioned tensor-network engine on one GB300.
+
+Workload (one "step"): a batch of B single amplitudes <x|C|0^n> of one 24-qubit 1D brickwork
+circuit of depth 14 (seed 2), each a closed network of 569 tensors split into k = 4 partitions by
+the simulated-annealing planner (DIRECTED targets, 2000 temperature iterations, seed 7, qubit-block
+initial partition), with B distinct random bitstrings x.  All B contractions -- every partition's
+steps and the fan-in -- run in one persistent dataflow launch, complex64 arithmetic with the FP64
+final reduction.
+
+  value  contraction TFLOP/s = (B * 8 * con_serial) / device time of the timed steps, inputs
+         resident in HBM (con_serial is the plan's exact Eq. 3.2 count: 8 real flops per complex
+         multiply-add).
+  e2e    the same metric through the C ABI with host buffers: each step uploads the B networks'
+         leaves (new bitstrings every step) from pinned host memory and reads the B results back.
+  roofline  the persistent kernel against the measured HBM copy bandwidth.
+  cpu_baseline / --impl reference  the oracle (complex128 C contractor) on the host cores.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contraction TFLOP/s, % roofline; amps/s, p99 latency vs plain c64 at err<=1e-4"
+N_QUBITS, DEPTH, K_PARTS = 24, 14, 4
+PLAN_ITERS, PLAN_SEED = 2000, 7
+
+
+def workload_config(batch):
+    return {"workload": f"24-qubit 1D brickwork depth {DEPTH} (seed 2), single amplitudes, "
+                        f"k={K_PARTS} SA partitions (directed, {PLAN_ITERS} iterations, seed {PLAN_SEED}), "
+                        f"batch of {batch} bitstrings per step",
+            "n_qubits": N_QUBITS, "depth": DEPTH, "k": K_PARTS, "batch": batch,
+            "precision": "complex64, FP64 final reduction",
+            "l2": "per-step working set larger than the 129 MB L2 (no flush needed)"}
+
+
+def make_workload(batch, seed0=5000):
+    from paper_2507_20667_gb300 import inputs as tni
+    circ = tni.brickwork_1d(N_QUBITS, DEPTH, seed=2)
+    xs = [tni.random_bitstring(N_QUBITS, seed0 + i) for i in range(batch)]
+    nets = [tni.amplitude_tn(circ, x) for x in xs]
+    return circ, xs, nets
+
+
+def plan_for(tnsa, tni, net_py, net_h):
+    return tnsa.tn_plan_create(net_h, k=K_PARTS, mode="directed", iterations=PLAN_ITERS, steps_per_temp=8,
+                               seed=PLAN_SEED,
+                               initial_part=tni.qubit_block_partition(net_py, N_QUBITS, K_PARTS))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample(nets, plan_steps, con_serial, budget_s=12.0, min_amps=1):
+    """The oracle as it stands on the host cores: whole amplitudes of the same workload until the
+    time budget is used."""
+    from oracle import contract as oc
+    t0 = time.perf_counter()
+    done = 0
+    while done < min_amps or (time.perf_counter() - t0 < budget_s and done < len(nets)):
+        oc.contract_scalar(nets[done % len(nets)], plan_steps)
+        done += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done * 8 * con_serial / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} whole amplitudes of the step's workload (complex128 C contractor, "
+                      f"same trees), {dt:.1f} s", "amps_per_s": done / dt}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args):
+    """--impl reference: the oracle, unmodified, on the host cores (rank 0 only)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    circ, xs, nets = make_workload(max(args.steps + args.warmup, 1))
+    h = tnsa.tn_build(nets[0])
+    plan = plan_for(tnsa, tni, nets[0], h)
+    con_serial, _, _ = tnsa.tn_plan_counts(plan)
+    part, steps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+    tree = [(int(l), int(r)) for l, r, o in steps]
+    from oracle import contract as oc
+    for i in range(args.warmup):
+        oc.contract_scalar(nets[i], tree)
+    t0 = time.perf_counter()
+    for i in range(args.steps):  # one step = one whole amplitude (a bounded sample of the batch)
+        oc.contract_scalar(nets[args.warmup + i], tree)
+    dt = time.perf_counter() - t0
+    value = args.steps * 8 * con_serial / dt / 1e12
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": workload_config(1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} whole amplitudes, one per step"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "amps_per_s": args.steps / dt}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+
+    B = args.batch
+    circ, xs, nets = make_workload(B, seed0=5000 + 100000 * rank)
+    handles = [tnsa.tn_build(n) for n in nets]
+    plan = plan_for(tnsa, tni, nets[0], handles[0])
+    con_serial, con_dist, mem = tnsa.tn_plan_counts(plan)
+    stream = torch.cuda.Stream()
+    ctx = tnsa.tn_ctx_create(local, stream=stream.cuda_stream)
+    batch = tnsa.tn_batch_create(ctx, handles, [plan] * B, args.precision)
+    info = tnsa.tn_batch_last_info(batch)
+    flops_per_step = B * 8.0 * con_serial
+    bytes_per_step = info["bytes"]  # algorithmic bytes of all B contractions
+
+    # parity spot check of the timed configuration: a few jobs against the oracle
+    tnsa.tn_batch_run(batch)
+    mant, e2, st = tnsa.tn_batch_results(batch, B)
+    assert (st == 0).all(), "a device wait timed out"
+    if rank == 0 and not args.skip_check:
+        from oracle import contract as oc
+        part, steps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+        tree = [(int(l), int(r)) for l, r, o in steps]
+        for i in sorted({0, B // 2, B - 1}):
+            ref = oc.contract_scalar(nets[i], tree)
+            got = complex(mant[i]) * 2.0 ** int(e2[i])
+            err = abs(got - ref) / abs(ref)
+            assert err <= 1e-5, f"job {i}: relative error {err:.2e}"
+
+    # device-resident timing: K steps bracketed by barrier + synchronize, CUDA events on the stream
+    for _ in range(args.warmup):
+        tnsa.tn_batch_run(batch)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            tnsa.tn_batch_run(batch)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1)
+    kernel_ms = tnsa.tn_batch_kernel_ms(batch, min(args.steps, 256))
+    ms = reduce_max(ms, ws)
+    ms_per_step = ms / args.steps
+    value = ws * flops_per_step / (ms_per_step * 1e-3) / 1e12
+
+    # end to end through the C ABI with host buffers: every step B new bitstrings are written into
+    # pinned host memory, copied to the device with the step, and the B results are read back
+    n = N_QUBITS
+    n_t = nets[0].n_tensors
+    rng = np.random.default_rng(77 + rank)
+    e2e_steps = max(1, min(args.steps, 20))
+    jobs = np.repeat(np.arange(B, dtype=np.int32), n)
+    tensors = np.tile(np.arange(n_t - n, n_t, dtype=np.int32), B)
+    eye = np.eye(2, dtype=np.complex128)
+    h2d = 0
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bits = rng.integers(0, 2, B * n)
+        tnsa.tn_batch_set_tensors(batch, jobs, tensors, eye[bits])
+        tnsa.tn_batch_run(batch)
+        h2d = tnsa.tn_batch_last_info(batch)["h2d_bytes"]
+        m2, ee, st2 = tnsa.tn_batch_results(batch, B)
+    dt = reduce_max(time.perf_counter() - t0, ws)
+    e2e_value = ws * e2e_steps * flops_per_step / dt / 1e12
+    d2h = 32 * B
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_step / (kernel_ms * 1e-3) / 1e9
+    cpu = oracle_sample(nets, [(int(l), int(r)) for l, r, o in tnsa.tn_plan_export(plan, n_t)[1]],
+                        con_serial, budget_s=args.cpu_seconds) if not args.skip_cpu else None
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": workload_config(B),
+            "amps_per_s": ws * B / (ms_per_step * 1e-3),
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+                    "amps_per_s": ws * e2e_steps * B / dt, "steps": e2e_steps},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_persist<float> (persistent dataflow contraction)",
+                         "kernel_ms": kernel_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks.summary(),
+            "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--precision", default="c64")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -58,6 +58,7 @@ typedef struct tn_net tn_net;
 typedef struct tn_plan tn_plan;
 typedef struct tn_ctx tn_ctx;
 typedef struct tn_program tn_program;
+typedef struct tn_batch tn_batch;
 
 /* ------------------------------------------------------------------ networks (Section 2.1) */
 
@@ -154,6 +155,15 @@ void tn_ctx_free(tn_ctx *ctx);
 /* Block until all work enqueued on the context's stream has finished.  Errors: TN_ECUDA. */
 tn_status tn_ctx_synchronize(tn_ctx *ctx);
 
+/* How programs and batches made from the context execute their steps.
+ *   TN_EXEC_PERSISTENT (default)  one persistent dataflow kernel per run: every step is cut into
+ *       work tiles; resident blocks claim tiles in dependency-level order across all jobs, wait
+ *       (bounded, ~4 s) for the steps producing their operands, run the tile and publish it.
+ *   TN_EXEC_GRAPH  one kernel launch per step and job, recorded once into a CUDA graph.
+ * Takes effect for programs and batches created afterwards.  Errors: TN_EINVAL. */
+typedef enum { TN_EXEC_PERSISTENT = 0, TN_EXEC_GRAPH = 1 } tn_exec_mode;
+tn_status tn_ctx_set_exec_mode(tn_ctx *ctx, int32_t mode);
+
 typedef struct {
     double device_ms;          /* device time of the contraction (CUDA events) */
     int32_t launches;          /* kernels launched */
@@ -161,10 +171,13 @@ typedef struct {
     double flops;              /* algorithmic flops, 8 * con_serial */
     double bytes;              /* algorithmic bytes: sum over steps of (|A|+|B|+|C|) * element size */
     size_t arena_bytes;        /* device memory held for intermediates */
+    double h2d_bytes;          /* host-to-device bytes copied by the last run (leaf uploads) */
 } tn_run_info;
 
 /* Compile (net, plan, precision) into a device program: per-step layouts, index maps, kernel
  * classes, a static memory plan for all intermediates, the leaves uploaded to the device.
+ * The net and plan must outlive the program; tn_net_set_tensor changes are uploaded by the next
+ * tn_program_run.
  * Errors: TN_EBUDGET (footprint above the budget), TN_EUNSUPPORTED (open network), TN_ECUDA. */
 tn_status tn_program_create(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
                             tn_program **out);
@@ -181,9 +194,51 @@ void tn_program_free(tn_program *prog);
 
 /* One contraction end to end: upload the leaves from the host net, run, read the amplitude back.
  * out_amp: host double[2]; out_exp2: host int32.  info may be NULL.  Blocks until done.
- * Errors: as tn_program_create / tn_program_run. */
+ * The compiled program is cached in the context for the next call with the same net and plan.
+ * Errors: as tn_program_create / tn_program_run; TN_ETIMEOUT if a device wait gave up. */
 tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
                       double out_amp[2], int32_t *out_exp2, tn_run_info *info);
+
+/* ------------------------------------------------------------------ batches (many contractions) */
+
+/* A batch holds n independent contractions ("jobs") resident on the device and runs them all in
+ * one persistent launch (the k partitions of every job are independent step lists, so they and
+ * all the jobs proceed concurrently).  Jobs whose nets have the same structure and share a plan
+ * share one compiled step list; they differ only in their leaves (for example one circuit with
+ * many bitstrings).  nets[i] and plans[i] must outlive the batch.
+ * Errors: TN_EINVAL, TN_EBUDGET, TN_EUNSUPPORTED (open network), TN_ENOMEM, TN_ECUDA. */
+tn_status tn_batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets,
+                          const tn_plan *const *plans, tn_precision prec, tn_batch **out);
+
+/* Enqueue one run of every job on the context's stream (leaves re-uploaded first for nets changed
+ * by tn_net_set_tensor).  d_results: NULL, or DEVICE memory of n * 32 bytes that receives one
+ * {double re, double im, int32 exp2, int32 status} record per job.  Errors: TN_ECUDA. */
+tn_status tn_batch_run(tn_batch *b, void *d_results);
+
+/* Replace the entries of tensor tensor[i] of job job[i] (same shape) for i < count, in the batch's
+ * resident copy only (the nets are not modified).  data: the new entries back to back, complex128
+ * interleaved.  The values are staged on the host and applied on the device by the next
+ * tn_batch_run, in one copy and one scatter kernel.  Errors: TN_EINVAL (nothing is staged). */
+tn_status tn_batch_set_tensors(tn_batch *b, int32_t count, const int32_t *job, const int32_t *tensor,
+                               const double *data);
+
+/* Wait for the last run and copy its results to the host: amps [n][2], exp2 [n], status [n]
+ * (0 ok, TN_ETIMEOUT if a device wait gave up); any pointer may be NULL.  With status == NULL a
+ * timed-out job makes the call return TN_ETIMEOUT.  Errors: TN_ECUDA, TN_ETIMEOUT. */
+tn_status tn_batch_results(tn_batch *b, double *amps, int32_t *exp2, int32_t *status);
+tn_status tn_batch_footprint(const tn_batch *b, size_t *bytes);
+tn_status tn_batch_last_info(const tn_batch *b, tn_run_info *info);
+
+/* Mean device duration (CUDA events recorded around the launch on the context's stream) of the
+ * persistent contraction kernel over the last n_runs runs, 1 <= n_runs <= 256; waits for them.
+ * Errors: TN_EINVAL, TN_EUNSUPPORTED (graph mode), TN_ECUDA. */
+tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms);
+void tn_batch_free(tn_batch *b);
+
+/* One-shot: create a batch, run it once, return the results on the host, free it. */
+tn_status tn_batch_contract(tn_ctx *ctx, int32_t n, const tn_net *const *nets,
+                            const tn_plan *const *plans, tn_precision prec, double *out_amps,
+                            int32_t *out_exp2);
 
 /* Permute the axes of a row-major DEVICE tensor (the transposition of the TTGT scheme realising
  * Eq. 2.4, Section 5.1): output axis t is input axis perm[t], so out has dims[perm[t]] at axis t.

@@ -1,12 +1,20 @@
-// Program compiler and runtime: turns (network, plan, precision) into a device program -- per-step
-// layouts and fused index maps, kernel classes, a static memory plan for every intermediate --
-// and runs it as one CUDA graph on the context's stream.
+// Program compiler and runtime.
+//
+// compile(): turns (network structure, plan, precision) into a device step list -- per-step
+// layouts and fused index maps, kernel class, work tiles, dependencies, a static memory plan for
+// every intermediate (offsets into one arena).  Nets with the same structure that use the same
+// plan share one compiled list and differ only in their leaves.
+//
+// A batch is a set of jobs (independent contractions).  It is executed either by the persistent
+// dataflow kernel (one cooperative launch for all jobs; the default) or, as a reference mode, by
+// one launch per step and job recorded into a CUDA graph.  A program is a batch of one job.
 #include <algorithm>
 #include <array>
 #include <cstring>
 #include <map>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -16,47 +24,87 @@
 
 using namespace tn;
 
+namespace {
+
+struct Compiled {
+    std::vector<StepDesc> steps;
+    std::vector<int64_t> leaf_off;   // [n + 1] element offsets of the leaves
+    int32_t n = 0, n_nodes = 0;
+    size_t arena_bytes = 0;
+    int64_t n_partials = 0;          // double2 entries
+    int64_t total_tiles = 0;
+    double flops = 0, bytes = 0;
+    int32_t counts[5] = {0, 0, 0, 0, 0};
+    uint64_t plan_uid = 0, shape_hash = 0;
+    // device copies (inside the batch's allocation)
+    StepDesc *d_steps = nullptr;
+    int64_t *d_leaf_off = nullptr;
+};
+
+}  // namespace
+
 struct tn_ctx {
     int32_t device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0;
-    tn_program *cached = nullptr;      // program reused by tn_contract, keyed by the unique ids
-    uint64_t cached_net = 0, cached_plan = 0;   // of the net and plan (never by address)
+    int32_t mode = 0;                 // tn_exec_mode
+    tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
+    uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
 };
 
-struct tn_program {
+struct tn_batch {
     tn_ctx *ctx = nullptr;
-    const tn_net *net = nullptr;
-    uint64_t uploaded_version = ~0ull;
     tn_precision prec = TN_C64;
     bool c128 = false;
-    int32_t n = 0, n_nodes = 0;
     int32_t elem = 8;
-    // device memory (one allocation, carved)
+    int32_t mode = 0;
+    int32_t n_jobs = 0;
+    std::vector<const tn_net *> nets;
+    std::vector<uint64_t> uploaded;
+    std::vector<Compiled> comp;
+    std::vector<int32_t> job_comp;
+    std::vector<JobPtrs> jobs;
+    std::vector<int64_t> leaf64_off;  // per job, element offset into d_leaf64
+    int64_t leaf_elems_total = 0;
+    int32_t max_leaves = 0;
+    // device memory: one allocation, carved
     void *d_block = nullptr;
-    double *d_leaf64 = nullptr;
-    void *d_leaf = nullptr;
-    int64_t *d_leaf_off = nullptr;
-    char *d_arena = nullptr;
-    StepDesc *d_desc = nullptr;
-    int32_t *d_exp2 = nullptr;
-    uint32_t *d_maxbits = nullptr;
-    double *d_partials = nullptr;
+    double2 *d_leaf64 = nullptr;
+    JobPtrs *d_jobs = nullptr;
+    WorkItem *d_work = nullptr;
+    int64_t n_work = 0;
+    uint32_t *d_counter = nullptr;
     DeviceResult *d_res = nullptr;
-    size_t footprint = 0, arena_bytes = 0;
+    char *d_reset = nullptr;          // results, maxbits, done, counter: zeroed before every run
+    size_t reset_bytes = 0;
+    size_t footprint = 0, arena_total = 0;
+    int32_t grid = 0;
     // host
-    std::vector<StepDesc> desc;
-    std::vector<std::array<int64_t, 3>> where;   // operand locations: leaf index (< 0: -1 - t) or
-                                                 // arena byte offset (>= 0); C of the root: unused
-    std::vector<int64_t> leaf_off;
     double *h_pinned = nullptr;
     DeviceResult *h_res = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // ring of event pairs around the dominant kernel (persistent mode), one pair per run
+    static constexpr int kRing = 256;
+    cudaEvent_t kev[kRing][2] = {};
+    int64_t runs = 0;
+    // pending tensor updates (tn_batch_set_tensors): headers {dst element offset, count, src
+    // element offset} and complex128 values, staged in pinned memory, applied on the device
+    std::vector<int64_t> upd_hdr;
+    std::vector<double> upd_val;
+    char *h_upd = nullptr;
+    size_t h_upd_cap = 0;
+    char *d_upd = nullptr;
+    size_t d_upd_cap = 0;
+    size_t last_h2d = 0;
     tn_run_info info{};
     bool ran = false;
+};
+
+struct tn_program {
+    tn_batch *b = nullptr;
 };
 
 namespace {
@@ -76,6 +124,19 @@ int32_t ilog2(int64_t x) {
     int32_t r = 0;
     while ((((int64_t)1) << r) < x) ++r;
     return r;
+}
+
+uint64_t shape_hash(const Net &net) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)net.n);
+    for (int32_t d : net.degree) mix((uint64_t)d);
+    for (int64_t d : net.dims) mix((uint64_t)d);
+    for (const tn_edge &e : net.edges) {
+        mix((uint64_t)(uint32_t)e.u); mix((uint64_t)(uint32_t)e.a);
+        mix((uint64_t)(uint32_t)e.v); mix((uint64_t)(uint32_t)e.b);
+    }
+    return h;
 }
 
 // Build a fused group list from legs listed outermost -> innermost with their strides.
@@ -146,31 +207,34 @@ struct FreeList {
     }
 };
 
-tn_status compile(tn_program *p, const Net &net, const Plan &plan) {
+int32_t rows_per_tile(int64_t M) {
+    if (M <= (1 << 14)) return 256;
+    if (M <= (1 << 20)) return 1024;
+    return 4096;
+}
+
+tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
     const int32_t n = net.n, nn = 2 * n - 1;
-    p->n = n;
-    p->n_nodes = nn;
+    c.n = n;
+    c.n_nodes = nn;
     std::vector<std::vector<int32_t>> layout(nn);
     std::vector<int64_t> size(nn, 1);
     for (int32_t t = 0; t < n; ++t) {
         layout[t] = net.axis_edge[t];
         size[t] = net.data_off[t + 1] - net.data_off[t];
     }
-    p->leaf_off.assign(net.data_off.begin(), net.data_off.end());
-    const size_t esz = (size_t)p->elem;
-    std::vector<size_t> arena_off(nn, (size_t)-1);
+    c.leaf_off.assign(net.data_off.begin(), net.data_off.end());
+    const size_t esz = (size_t)elem;
+    std::vector<size_t> arena_off(nn, 0);
+    std::vector<int32_t> producer(nn, -1), level(nn, 0);   // step index producing each node
     FreeList fl;
-    p->desc.assign(n - 1, StepDesc{});
-    double flops = 0, bytes = 0;
-    int32_t counts[4] = {0, 0, 0, 0};
+    c.steps.clear();
+    c.steps.reserve(n);
     for (int32_t s = 0; s < n - 1; ++s) {
         const int32_t l = plan.steps[s][0], r = plan.steps[s][1], o = n + s;
         const bool root = (s == n - 2);
         const int32_t a = size[l] >= size[r] ? l : r, b = (a == l) ? r : l;
         const auto &LA = layout[a], &LB = layout[b];
-        auto in = [](const std::vector<int32_t> &v, int32_t e) {
-            return std::find(v.begin(), v.end(), e) != v.end();
-        };
         std::vector<int64_t> strA(LA.size()), strB(LB.size());
         int64_t acc = 1;
         for (int32_t i = (int32_t)LA.size() - 1; i >= 0; --i) { strA[i] = acc; acc *= net.edim[LA[i]]; }
@@ -180,7 +244,7 @@ tn_status compile(tn_program *p, const Net &net, const Plan &plan) {
         std::vector<int32_t> out;
         int64_t M = 1, N = 1, K = 1;
         for (size_t i = 0; i < LA.size(); ++i) {
-            int32_t e = LA[i];
+            const int32_t e = LA[i];
             auto jt = std::find(LB.begin(), LB.end(), e);
             if (jt == LB.end()) {
                 md.push_back(net.edim[e]); ms.push_back(strA[i]); out.push_back(e); M *= net.edim[e];
@@ -190,87 +254,127 @@ tn_status compile(tn_program *p, const Net &net, const Plan &plan) {
             }
         }
         for (size_t i = 0; i < LB.size(); ++i) {
-            int32_t e = LB[i];
-            if (!in(LA, e)) {
+            const int32_t e = LB[i];
+            if (std::find(LA.begin(), LA.end(), e) == LA.end()) {
                 nd.push_back(net.edim[e]); ns.push_back(strB[i]); out.push_back(e); N *= net.edim[e];
             }
         }
         layout[o] = out;
         size[o] = M * N;
-        StepDesc &d = p->desc[s];
-        d.M = M;
-        d.N = N;
-        d.K = K;
-        d.node_a = a;
-        d.node_b = b;
-        d.node_c = o;
-        d.is_root = root ? 1 : 0;
+        if (root && M * N != 1) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+        StepDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.M = M; d.N = N; d.K = K;
+        d.node_a = a; d.node_b = b; d.node_c = o;
         if (!make_groups(md, ms, none, false, d.m) || !make_groups(nd, ns, none, false, d.n) ||
             !make_groups(kd, ksa, ksb, true, d.k))
             return fail(TN_EUNSUPPORTED, "step " + std::to_string(s) + " has more than 32 leg groups");
-        if (root) {
-            if (M * N != 1) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
-            d.kind = STEP_DOT;
-        } else if (M * N <= 16 && K > 64) {
-            d.kind = STEP_DOT;
-        } else if (N <= 16 && K <= 64 && K * N <= 1024) {
+        // memory plan: place the output, then release the inputs
+        if (!root) arena_off[o] = fl.alloc(align_up((size_t)size[o] * esz, 256));
+        auto where = [&](int32_t v, int64_t &off) -> bool {
+            if (v < n) { off = c.leaf_off[v]; return true; }
+            off = (int64_t)(arena_off[v] / esz);
+            return false;
+        };
+        if (where(a, d.a_off)) d.flags |= FLAG_A_LEAF;
+        if (where(b, d.b_off)) d.flags |= FLAG_B_LEAF;
+        d.c_off = (int64_t)(arena_off[o] / esz);
+        d.dep0 = producer[a];
+        d.dep1 = producer[b];
+        d.level = 1 + std::max(level[a], level[b]);
+        c.flops += 8.0 * (double)M * (double)N * (double)K;
+        c.bytes += (double)(size[a] + size[b] + size[o]) * (double)esz;
+        const bool dot = root || (M * N <= kDotMaxOut && K > kRowsMaxK);
+        if (dot) {
+            StepDesc p = d;
+            p.kind = STEP_DOTP;
+            p.flags |= FLAG_NO_C;
+            p.tile_rows = kDotChunk;
+            p.ntiles = (int32_t)((K + kDotChunk - 1) / kDotChunk);
+            p.part_off = (int32_t)c.n_partials;
+            c.n_partials += (int64_t)p.ntiles * kDotMaxOut;
+            c.steps.push_back(p);
+            StepDesc f = d;
+            f.kind = STEP_DOTF;
+            f.ntiles = 1;
+            f.tile_rows = p.ntiles;
+            f.part_off = p.part_off;
+            f.dep0 = (int32_t)c.steps.size() - 1;
+            f.dep1 = -1;
+            f.level = d.level + 1;
+            if (root) f.flags |= FLAG_ROOT | FLAG_NO_C;
+            c.steps.push_back(f);
+            c.counts[STEP_DOTP]++;
+        } else if (N <= kRowsMaxN && K <= kRowsMaxK && K * N <= kRowsMaxKN) {
             d.kind = STEP_ROWS;
+            d.tile_rows = rows_per_tile(M);
+            d.ntiles = (int32_t)((M + d.tile_rows - 1) / d.tile_rows);
+            c.steps.push_back(d);
+            c.counts[STEP_ROWS]++;
         } else {
             d.kind = STEP_TILE;
+            const int64_t tiles = ((M + kTileM - 1) / kTileM) * ((N + kTileN - 1) / kTileN);
+            if (tiles > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "step too large");
+            d.ntiles = (int32_t)tiles;
+            c.steps.push_back(d);
+            c.counts[STEP_TILE]++;
         }
-        counts[d.kind]++;
-        flops += 8.0 * (double)M * (double)N * (double)K;
-        bytes += (double)(size[a] + size[b] + size[o]) * (double)esz;
-        // memory plan: allocate the output, then release the inputs
-        if (!root) arena_off[o] = fl.alloc(align_up((size_t)size[o] * esz, 256));
+        producer[o] = (int32_t)c.steps.size() - 1;
+        level[o] = c.steps.back().level;
         for (int32_t x : {l, r})
             if (x >= n) fl.release(arena_off[x], align_up((size_t)size[x] * esz, 256));
     }
-    p->arena_bytes = std::max(fl.high, (size_t)256);
-    p->info.n_gather = counts[STEP_ROWS];
-    p->info.n_tile = counts[STEP_TILE];
-    p->info.n_dot = counts[STEP_DOT];
-    p->info.n_tc = counts[STEP_TC];
-    p->info.flops = flops;
-    p->info.bytes = bytes;
-    p->info.arena_bytes = p->arena_bytes;
-    // operand locations, resolved to device addresses once the arena exists
-    p->where.resize(n - 1);
-    for (int32_t s = 0; s < n - 1; ++s) {
-        const StepDesc &d = p->desc[s];
-        auto loc = [&](int32_t v) -> int64_t { return v < n ? -1 - (int64_t)v : (int64_t)arena_off[v]; };
-        p->where[s] = {loc(d.node_a), loc(d.node_b), d.is_root ? 0 : loc(d.node_c)};
-    }
+    c.arena_bytes = std::max(fl.high, (size_t)256);
+    c.total_tiles = 0;
+    for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
 }
 
-tn_status upload_leaves(tn_program *p) {
-    const Net &net = p->net->impl;
+tn_status upload_leaves(tn_batch *b, int32_t job) {
+    const Net &net = b->nets[job]->impl;
     const size_t bytes = sizeof(double) * net.data.size();
+    double *stage = b->h_pinned + 2 * b->leaf64_off[job];
     if (bytes) {
-        std::memcpy(p->h_pinned, net.data.data(), bytes);
-        CK(cudaMemcpyAsync(p->d_leaf64, p->h_pinned, bytes, cudaMemcpyHostToDevice, p->ctx->stream));
+        std::memcpy(stage, net.data.data(), bytes);
+        CK(cudaMemcpyAsync(b->d_leaf64 + b->leaf64_off[job], stage, bytes, cudaMemcpyHostToDevice,
+                           b->ctx->stream));
     }
-    p->uploaded_version = net.version;
+    b->uploaded[job] = net.version;
     return TN_OK;
 }
 
-tn_status record_graph(tn_program *p) {
-    cudaStream_t st = p->ctx->stream;
-    ScaleState sc{p->d_exp2, p->d_maxbits};
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int32_t launches = 0;
-    cudaError_t err = cudaMemsetAsync(p->d_maxbits, 0, sizeof(uint32_t) * p->n_nodes, st);
-    if (err == cudaSuccess)
-        err = launch_leaf_convert(p->c128, p->d_leaf64, p->d_leaf, p->d_leaf_off, p->n, sc, st);
-    launches += 1;
-    for (size_t s = 0; err == cudaSuccess && s < p->desc.size(); ++s)
-        err = launch_step(p->c128, p->d_desc + s, p->desc[s], sc, p->d_partials,
-                          dot_partial_blocks(), p->d_res, st, &launches);
-    if (err == cudaSuccess && p->n == 1) {
-        err = launch_finish_leaf(p->c128, p->d_leaf, 0, sc, p->d_res, st);
-        launches += 1;
+cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
+    if (e == cudaSuccess) e = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+    if (e != cudaSuccess) return e;
+    if (b->mode == TN_EXEC_PERSISTENT) {
+        cudaEvent_t *ev = b->kev[b->runs % tn_batch::kRing];
+        if (!ev[0]) {
+            e = cudaEventCreate(&ev[0]);
+            if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess)
+            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        b->runs++;
+    } else {
+        for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb) {
+            const Compiled &c = b->comp[b->job_comp[jb]];
+            for (size_t s = 0; e == cudaSuccess && s < c.steps.size(); ++s)
+                e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], st);
+        }
     }
+    for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb)
+        if (b->comp[b->job_comp[jb]].n == 1) e = launch_finish_leaf(b->c128, b->jobs[jb], st);
+    return e;
+}
+
+tn_status record_graph(tn_batch *b) {
+    cudaStream_t st = b->ctx->stream;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = enqueue_run(b, st);
     cudaGraph_t g = nullptr;
     cudaError_t err2 = cudaStreamEndCapture(st, &g);
     if (err != cudaSuccess) {
@@ -278,22 +382,311 @@ tn_status record_graph(tn_program *p) {
         return fail(TN_ECUDA, std::string("recording the program: ") + cudaGetErrorString(err));
     }
     if (err2 != cudaSuccess) return fail(TN_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(err2));
-    err = cudaGraphInstantiate(&p->gexec, g, 0);
+    err = cudaGraphInstantiate(&b->gexec, g, 0);
     cudaGraphDestroy(g);
     if (err != cudaSuccess) return fail(TN_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(err));
-    p->info.launches = launches;
     return TN_OK;
 }
 
-void program_destroy(tn_program *p) {
-    if (!p) return;
-    if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    if (p->ev0) cudaEventDestroy(p->ev0);
-    if (p->ev1) cudaEventDestroy(p->ev1);
-    if (p->d_block) cudaFree(p->d_block);
-    if (p->h_pinned) cudaFreeHost(p->h_pinned);
-    if (p->h_res) cudaFreeHost(p->h_res);
-    delete p;
+void batch_destroy(tn_batch *b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto &pair : b->kev)
+        for (cudaEvent_t e : pair)
+            if (e) cudaEventDestroy(e);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->d_block) cudaFree(b->d_block);
+    if (b->h_pinned) cudaFreeHost(b->h_pinned);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    if (b->h_upd) cudaFreeHost(b->h_upd);
+    if (b->d_upd) cudaFree(b->d_upd);
+    delete b;
+}
+
+tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
+                       tn_precision prec, tn_batch **out) {
+    if (!ctx || !out || n < 1 || !nets || !plans) return fail(TN_EINVAL, "NULL argument or empty batch");
+    if (prec < TN_C128 || prec > TN_BF16_SPLIT) return fail(TN_EINVAL, "unknown precision");
+    for (int32_t i = 0; i < n; ++i) {
+        if (!nets[i] || !plans[i]) return fail(TN_EINVAL, "NULL net or plan in the batch");
+        if (plans[i]->impl.n != nets[i]->impl.n) return fail(TN_EINVAL, "plan and network do not match");
+        if (!nets[i]->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+    }
+    CK(cudaSetDevice(ctx->device));
+    tn_batch *b = new (std::nothrow) tn_batch;
+    if (!b) return fail(TN_ENOMEM, "allocating the batch");
+    b->ctx = ctx;
+    b->prec = prec;
+    b->c128 = (prec == TN_C128);
+    b->elem = b->c128 ? 16 : 8;
+    b->mode = ctx->mode;
+    b->n_jobs = n;
+    b->nets.assign(nets, nets + n);
+    b->uploaded.assign(n, ~0ull);
+    b->job_comp.assign(n, -1);
+    // compile every distinct (structure, plan) once
+    std::unordered_map<std::string, int32_t> seen;
+    for (int32_t i = 0; i < n; ++i) {
+        const Net &net = nets[i]->impl;
+        const uint64_t h = shape_hash(net);
+        const std::string key = std::to_string(plans[i]->impl.uid) + ":" + std::to_string(h);
+        auto it = seen.find(key);
+        if (it != seen.end()) { b->job_comp[i] = it->second; continue; }
+        Compiled c;
+        tn_status s = compile(c, net, plans[i]->impl, b->elem);
+        if (s != TN_OK) { batch_destroy(b); return s; }
+        c.plan_uid = plans[i]->impl.uid;
+        c.shape_hash = h;
+        b->job_comp[i] = (int32_t)b->comp.size();
+        seen[key] = b->job_comp[i];
+        b->comp.push_back(std::move(c));
+    }
+    // device layout
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max(bytes, (size_t)16), 256); return o; };
+    std::vector<size_t> o_steps(b->comp.size()), o_loff(b->comp.size());
+    for (size_t ci = 0; ci < b->comp.size(); ++ci) {
+        o_steps[ci] = carve(sizeof(StepDesc) * b->comp[ci].steps.size());
+        o_loff[ci] = carve(sizeof(int64_t) * b->comp[ci].leaf_off.size());
+    }
+    b->leaf64_off.assign(n, 0);
+    int64_t leaf_total = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        b->leaf64_off[i] = leaf_total;
+        leaf_total += b->comp[b->job_comp[i]].leaf_off.back();
+        b->max_leaves = std::max(b->max_leaves, b->comp[b->job_comp[i]].n);
+    }
+    b->leaf_elems_total = leaf_total;
+    const size_t o_leaf64 = carve(sizeof(double2) * (size_t)leaf_total);
+    const size_t o_leaf = carve((size_t)b->elem * (size_t)leaf_total);
+    std::vector<size_t> o_arena(n), o_part(n), o_exp(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const Compiled &c = b->comp[b->job_comp[i]];
+        o_arena[i] = carve(c.arena_bytes);
+        o_part[i] = carve(sizeof(double2) * (size_t)c.n_partials);
+        o_exp[i] = carve(sizeof(int32_t) * (size_t)c.n_nodes);
+        b->arena_total += c.arena_bytes;
+    }
+    const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
+    // work list: (job, step, tile) in (level, job, step, tile) order
+    std::vector<WorkItem> work;
+    if (b->mode == TN_EXEC_PERSISTENT) {
+        int64_t total = 0;
+        for (int32_t i = 0; i < n; ++i) total += b->comp[b->job_comp[i]].total_tiles;
+        if (total >= 0xffffffffLL) { batch_destroy(b); return fail(TN_EUNSUPPORTED, "too many work tiles"); }
+        std::vector<std::array<int32_t, 3>> order;   // level, job, step
+        for (int32_t i = 0; i < n; ++i) {
+            const Compiled &c = b->comp[b->job_comp[i]];
+            for (size_t s = 0; s < c.steps.size(); ++s) order.push_back({c.steps[s].level, i, (int32_t)s});
+        }
+        std::sort(order.begin(), order.end());
+        work.reserve((size_t)total);
+        for (auto &o : order) {
+            const StepDesc &d = b->comp[b->job_comp[o[1]]].steps[o[2]];
+            for (int32_t t = 0; t < d.ntiles; ++t) work.push_back({(uint32_t)o[1], (uint32_t)o[2], (uint32_t)t});
+        }
+    }
+    b->n_work = (int64_t)work.size();
+    const size_t o_work = carve(sizeof(WorkItem) * work.size());
+    // reset region: results, maxbits, done, counter
+    const size_t o_reset = off;
+    const size_t o_res = carve(sizeof(DeviceResult) * (size_t)n);
+    std::vector<size_t> o_max(n), o_done(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const Compiled &c = b->comp[b->job_comp[i]];
+        o_max[i] = carve(sizeof(uint32_t) * (size_t)c.n_nodes);
+        o_done[i] = carve(sizeof(int32_t) * c.steps.size());
+    }
+    const size_t o_counter = carve(sizeof(uint32_t));
+    b->reset_bytes = off - o_reset;
+    b->footprint = off;
+    if (ctx->budget && b->footprint > ctx->budget) {
+        batch_destroy(b);
+        return fail(TN_EBUDGET, "the batch needs " + std::to_string(off) + " bytes of device memory");
+    }
+    cudaError_t e = cudaMalloc(&b->d_block, off);
+    if (e != cudaSuccess) {
+        batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA, cudaGetErrorString(e));
+    }
+    char *base = static_cast<char *>(b->d_block);
+    for (size_t ci = 0; ci < b->comp.size(); ++ci) {
+        b->comp[ci].d_steps = reinterpret_cast<StepDesc *>(base + o_steps[ci]);
+        b->comp[ci].d_leaf_off = reinterpret_cast<int64_t *>(base + o_loff[ci]);
+    }
+    b->d_leaf64 = reinterpret_cast<double2 *>(base + o_leaf64);
+    char *d_leaf = base + o_leaf;
+    b->d_jobs = reinterpret_cast<JobPtrs *>(base + o_jobs);
+    b->d_work = reinterpret_cast<WorkItem *>(base + o_work);
+    b->d_reset = base + o_reset;
+    b->d_res = reinterpret_cast<DeviceResult *>(base + o_res);
+    b->d_counter = reinterpret_cast<uint32_t *>(base + o_counter);
+    b->jobs.resize(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const Compiled &c = b->comp[b->job_comp[i]];
+        JobPtrs &j = b->jobs[i];
+        j.leaf64 = b->d_leaf64 + b->leaf64_off[i];
+        j.leaf_off = c.d_leaf_off;
+        j.leaf = d_leaf + (size_t)b->elem * (size_t)b->leaf64_off[i];
+        j.arena = base + o_arena[i];
+        j.partials = reinterpret_cast<double2 *>(base + o_part[i]);
+        j.exp2 = reinterpret_cast<int32_t *>(base + o_exp[i]);
+        j.maxbits = reinterpret_cast<uint32_t *>(base + o_max[i]);
+        j.done = reinterpret_cast<int32_t *>(base + o_done[i]);
+        j.result = b->d_res + i;
+        j.steps = c.d_steps;
+        j.n_steps = (int32_t)c.steps.size();
+        j.n_leaves = c.n;
+    }
+    if (cudaMallocHost(&b->h_pinned, std::max((size_t)16, sizeof(double2) * (size_t)leaf_total)) != cudaSuccess ||
+        cudaMallocHost(&b->h_res, sizeof(DeviceResult) * (size_t)n) != cudaSuccess) {
+        batch_destroy(b);
+        return fail(TN_ENOMEM, "pinned host buffers");
+    }
+    cudaStream_t st = ctx->stream;
+    for (size_t ci = 0; ci < b->comp.size() && e == cudaSuccess; ++ci) {
+        const Compiled &c = b->comp[ci];
+        if (!c.steps.empty())
+            e = cudaMemcpyAsync(c.d_steps, c.steps.data(), sizeof(StepDesc) * c.steps.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c.d_leaf_off, c.leaf_off.data(), sizeof(int64_t) * c.leaf_off.size(),
+                                cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(JobPtrs) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !work.empty())
+        e = cudaMemcpyAsync(b->d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
+    b->grid = persistent_grid(b->c128);
+    if (b->grid <= 0) { batch_destroy(b); return fail(TN_ECUDA, "occupancy query failed"); }
+    tn_status s = TN_OK;
+    for (int32_t i = 0; i < n && s == TN_OK; ++i) s = upload_leaves(b, i);
+    if (s == TN_OK && b->mode == TN_EXEC_GRAPH) s = record_graph(b);
+    if (s == TN_OK) {
+        e = cudaStreamSynchronize(st);   // the uploads read host buffers that must stay alive
+        if (e != cudaSuccess) s = fail(TN_ECUDA, cudaGetErrorString(e));
+    }
+    if (s != TN_OK) { batch_destroy(b); return s; }
+    // run statistics
+    b->info = tn_run_info{};
+    for (int32_t i = 0; i < n; ++i) {
+        const Compiled &c = b->comp[b->job_comp[i]];
+        b->info.flops += c.flops;
+        b->info.bytes += c.bytes;
+        b->info.n_gather += c.counts[STEP_ROWS];
+        b->info.n_tile += c.counts[STEP_TILE];
+        b->info.n_dot += c.counts[STEP_DOTP];
+        b->info.n_tc += c.counts[STEP_TC];
+    }
+    b->info.arena_bytes = b->arena_total;
+    if (b->mode == TN_EXEC_PERSISTENT) {
+        b->info.launches = 2;   // leaf conversion + the persistent kernel
+    } else {
+        int32_t l = 1;
+        for (int32_t i = 0; i < n; ++i) l += (int32_t)b->comp[b->job_comp[i]].steps.size();
+        b->info.launches = l;
+    }
+    for (int32_t i = 0; i < n; ++i)
+        if (b->comp[b->job_comp[i]].n == 1) b->info.launches++;
+    *out = b;
+    return TN_OK;
+}
+
+// Copy the pending tensor updates to the device in one transfer and scatter them into the
+// resident complex128 leaves.
+tn_status apply_updates(tn_batch *b, cudaStream_t st) {
+    const size_t n_upd = b->upd_hdr.size() / 3;
+    if (n_upd == 0) return TN_OK;
+    const size_t hdr_bytes = align_up(sizeof(int64_t) * b->upd_hdr.size(), 16);
+    const size_t bytes = hdr_bytes + sizeof(double) * b->upd_val.size();
+    CK(cudaStreamSynchronize(st));   // the staging buffers may still be read by a previous copy
+    if (bytes > b->h_upd_cap) {
+        if (b->h_upd) cudaFreeHost(b->h_upd);
+        b->h_upd = nullptr;
+        b->h_upd_cap = 0;
+        CK(cudaMallocHost(&b->h_upd, bytes));
+        b->h_upd_cap = bytes;
+    }
+    if (bytes > b->d_upd_cap) {
+        if (b->d_upd) cudaFree(b->d_upd);
+        b->d_upd = nullptr;
+        b->d_upd_cap = 0;
+        cudaError_t e = cudaMalloc(&b->d_upd, bytes);
+        if (e != cudaSuccess) return fail(TN_ENOMEM, cudaGetErrorString(e));
+        b->d_upd_cap = bytes;
+    }
+    std::memcpy(b->h_upd, b->upd_hdr.data(), sizeof(int64_t) * b->upd_hdr.size());
+    std::memcpy(b->h_upd + hdr_bytes, b->upd_val.data(), sizeof(double) * b->upd_val.size());
+    CK(cudaMemcpyAsync(b->d_upd, b->h_upd, bytes, cudaMemcpyHostToDevice, st));
+    CK(launch_scatter_updates(reinterpret_cast<const int64_t *>(b->d_upd),
+                              reinterpret_cast<const double2 *>(b->d_upd + hdr_bytes), (int64_t)n_upd,
+                              b->d_leaf64, st));
+    b->last_h2d += bytes;
+    b->upd_hdr.clear();
+    b->upd_val.clear();
+    return TN_OK;
+}
+
+tn_status batch_run(tn_batch *b, void *d_results) {
+    CK(cudaSetDevice(b->ctx->device));
+    cudaStream_t st = b->ctx->stream;
+    bool synced = false;
+    b->last_h2d = 0;
+    for (int32_t i = 0; i < b->n_jobs; ++i)
+        if (b->uploaded[i] != b->nets[i]->impl.version) {
+            if (!synced) { CK(cudaStreamSynchronize(st)); synced = true; }   // staging in flight
+            tn_status s = upload_leaves(b, i);
+            if (s != TN_OK) return s;
+            b->last_h2d += sizeof(double) * b->nets[i]->impl.data.size();
+        }
+    {
+        tn_status s = apply_updates(b, st);
+        if (s != TN_OK) return s;
+    }
+    CK(cudaEventRecord(b->ev0, st));
+    if (b->mode == TN_EXEC_GRAPH) CK(cudaGraphLaunch(b->gexec, st));
+    else CK(enqueue_run(b, st));
+    CK(cudaEventRecord(b->ev1, st));
+    if (d_results && d_results != (void *)b->d_res)
+        CK(cudaMemcpyAsync(d_results, b->d_res, sizeof(DeviceResult) * (size_t)b->n_jobs,
+                           cudaMemcpyDeviceToDevice, st));
+    b->ran = true;
+    return TN_OK;
+}
+
+tn_status batch_info(tn_batch *b, tn_run_info *info) {
+    b->info.h2d_bytes = (double)b->last_h2d;
+    if (b->ran) {
+        CK(cudaSetDevice(b->ctx->device));
+        CK(cudaEventSynchronize(b->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        b->info.device_ms = ms;
+    }
+    *info = b->info;
+    return TN_OK;
+}
+
+// Copy the results to the host (blocking).
+tn_status batch_results(tn_batch *b, double *amps, int32_t *exp2, int32_t *status) {
+    CK(cudaSetDevice(b->ctx->device));
+    cudaStream_t st = b->ctx->stream;
+    CK(cudaMemcpyAsync(b->h_res, b->d_res, sizeof(DeviceResult) * (size_t)b->n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool timeout = false;
+    for (int32_t i = 0; i < b->n_jobs; ++i) {
+        const DeviceResult &r = b->h_res[i];
+        if (amps) { amps[2 * i] = r.re; amps[2 * i + 1] = r.im; }
+        if (exp2) exp2[i] = r.exp2;
+        if (status) status[i] = r.status;
+        if (r.status != 0) timeout = true;
+    }
+    if (timeout && !status) return fail(TN_ETIMEOUT, "a device-side wait gave up");
+    return TN_OK;
 }
 
 }  // namespace
@@ -310,11 +703,15 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
     if (prop.major != 10 || prop.minor != 3)
         return fail(TN_ECUDA, "this build targets sm_103a (GB300); device is sm_" +
                                   std::to_string(prop.major) + std::to_string(prop.minor));
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    if (!coop) return fail(TN_ECUDA, "device does not support cooperative launches");
     CK(cudaSetDevice(device));
     tn_ctx *c = new (std::nothrow) tn_ctx;
     if (!c) return fail(TN_ENOMEM, "allocating the context");
     c->device = device;
     c->budget = hbm_budget_bytes;
+    c->mode = TN_EXEC_PERSISTENT;
     if (cuda_stream) {
         c->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -326,10 +723,24 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
     return TN_OK;
 }
 
+tn_status tn_ctx_set_exec_mode(tn_ctx *c, int32_t mode) {
+    if (!c) return fail(TN_EINVAL, "NULL ctx");
+    if (mode != TN_EXEC_PERSISTENT && mode != TN_EXEC_GRAPH) return fail(TN_EINVAL, "unknown mode");
+    if (c->mode != mode && c->cached) {
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+        batch_destroy(c->cached);
+        c->cached = nullptr;
+    }
+    c->mode = mode;
+    return TN_OK;
+}
+
 void tn_ctx_free(tn_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
-    program_destroy(c->cached);
+    cudaStreamSynchronize(c->stream);
+    batch_destroy(c->cached);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -344,135 +755,114 @@ tn_status tn_ctx_synchronize(tn_ctx *c) {
 tn_status tn_program_create(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
                             tn_program **out) {
     if (!ctx || !net || !plan || !out) return fail(TN_EINVAL, "NULL argument");
-    if (prec < TN_C128 || prec > TN_BF16_SPLIT) return fail(TN_EINVAL, "unknown precision");
-    const Net &nt = net->impl;
-    const Plan &pl = plan->impl;
-    if (pl.n != nt.n) return fail(TN_EINVAL, "plan and network do not match");
-    if (!nt.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
-    CK(cudaSetDevice(ctx->device));
     tn_program *p = new (std::nothrow) tn_program;
     if (!p) return fail(TN_ENOMEM, "allocating the program");
-    p->ctx = ctx;
-    p->net = net;
-    p->prec = prec;
-    p->c128 = (prec == TN_C128);
-    p->elem = p->c128 ? 16 : 8;
-    tn_status s = compile(p, nt, pl);
-    if (s != TN_OK) { program_destroy(p); return s; }
-    // one device allocation, carved into the program's buffers
-    const size_t n_el = (size_t)nt.data_off[nt.n];
-    size_t off = 0;
-    auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max(bytes, (size_t)16), 256); return o; };
-    const size_t o_leaf64 = carve(16 * n_el);
-    const size_t o_leaf = carve((size_t)p->elem * n_el);
-    const size_t o_loff = carve(sizeof(int64_t) * (nt.n + 1));
-    const size_t o_desc = carve(sizeof(StepDesc) * p->desc.size());
-    const size_t o_exp = carve(sizeof(int32_t) * p->n_nodes);
-    const size_t o_max = carve(sizeof(uint32_t) * p->n_nodes);
-    const size_t o_part = carve(sizeof(double) * 2 * 16 * (size_t)dot_partial_blocks());
-    const size_t o_res = carve(sizeof(DeviceResult));
-    const size_t o_arena = carve(p->arena_bytes);
-    p->footprint = off;
-    if (ctx->budget && p->footprint > ctx->budget) {
-        program_destroy(p);
-        return fail(TN_EBUDGET, "program needs " + std::to_string(off) + " bytes of device memory");
-    }
-    cudaError_t e = cudaMalloc(&p->d_block, off);
-    if (e != cudaSuccess) {
-        program_destroy(p);
-        return fail(e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA, cudaGetErrorString(e));
-    }
-    char *base = static_cast<char *>(p->d_block);
-    p->d_leaf64 = reinterpret_cast<double *>(base + o_leaf64);
-    p->d_leaf = base + o_leaf;
-    p->d_leaf_off = reinterpret_cast<int64_t *>(base + o_loff);
-    p->d_desc = reinterpret_cast<StepDesc *>(base + o_desc);
-    p->d_exp2 = reinterpret_cast<int32_t *>(base + o_exp);
-    p->d_maxbits = reinterpret_cast<uint32_t *>(base + o_max);
-    p->d_partials = reinterpret_cast<double *>(base + o_part);
-    p->d_res = reinterpret_cast<DeviceResult *>(base + o_res);
-    p->d_arena = base + o_arena;
-    // resolve descriptor operand addresses
-    for (size_t i = 0; i < p->desc.size(); ++i) {
-        StepDesc &d = p->desc[i];
-        auto resolve = [&](int64_t w) -> char * {
-            if (w < 0) return static_cast<char *>(p->d_leaf) + (size_t)p->elem * (size_t)p->leaf_off[-1 - w];
-            return p->d_arena + w;
-        };
-        d.A = resolve(p->where[i][0]);
-        d.B = resolve(p->where[i][1]);
-        d.C = d.is_root ? nullptr : resolve(p->where[i][2]);
-    }
-    cudaStream_t st = ctx->stream;
-    if (cudaMallocHost(&p->h_pinned, std::max((size_t)16, sizeof(double) * nt.data.size())) != cudaSuccess ||
-        cudaMallocHost(&p->h_res, sizeof(DeviceResult)) != cudaSuccess) {
-        program_destroy(p);
-        return fail(TN_ENOMEM, "pinned staging buffer");
-    }
-    e = cudaMemcpyAsync(p->d_leaf_off, p->leaf_off.data(), sizeof(int64_t) * (nt.n + 1),
-                        cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !p->desc.empty())
-        e = cudaMemcpyAsync(p->d_desc, p->desc.data(), sizeof(StepDesc) * p->desc.size(),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_exp2, 0, sizeof(int32_t) * p->n_nodes, st);
-    if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
-    if (e != cudaSuccess) { program_destroy(p); return fail(TN_ECUDA, cudaGetErrorString(e)); }
-    s = upload_leaves(p);
-    if (s == TN_OK) s = record_graph(p);
-    if (s == TN_OK) {
-        e = cudaStreamSynchronize(st);   // descriptor and leaf uploads read host buffers
-        if (e != cudaSuccess) s = fail(TN_ECUDA, cudaGetErrorString(e));
-    }
-    if (s != TN_OK) { program_destroy(p); return s; }
+    tn_status s = batch_create(ctx, 1, &net, &plan, prec, &p->b);
+    if (s != TN_OK) { delete p; return s; }
     *out = p;
     return TN_OK;
 }
 
 tn_status tn_program_run(tn_program *p, void *d_result) {
     if (!p || !d_result) return fail(TN_EINVAL, "NULL argument");
-    CK(cudaSetDevice(p->ctx->device));
-    cudaStream_t st = p->ctx->stream;
-    if (p->uploaded_version != p->net->impl.version) {
-        CK(cudaStreamSynchronize(st));   // the pinned staging buffer may still be in flight
-        tn_status s = upload_leaves(p);
-        if (s != TN_OK) return s;
-    }
-    CK(cudaEventRecord(p->ev0, st));
-    CK(cudaGraphLaunch(p->gexec, st));
-    CK(cudaEventRecord(p->ev1, st));
-    if (d_result != (void *)p->d_res)
-        CK(cudaMemcpyAsync(d_result, p->d_res, sizeof(DeviceResult), cudaMemcpyDeviceToDevice, st));
-    p->ran = true;
-    return TN_OK;
+    return batch_run(p->b, d_result);
 }
 
 tn_status tn_program_footprint(const tn_program *p, size_t *bytes) {
     if (!p || !bytes) return fail(TN_EINVAL, "NULL argument");
-    *bytes = p->footprint;
+    *bytes = p->b->footprint;
     return TN_OK;
 }
 
-tn_status tn_program_last_info(const tn_program *pc, tn_run_info *info) {
-    if (!pc || !info) return fail(TN_EINVAL, "NULL argument");
-    tn_program *p = const_cast<tn_program *>(pc);
-    if (p->ran) {
-        CK(cudaSetDevice(p->ctx->device));
-        CK(cudaEventSynchronize(p->ev1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
-        p->info.device_ms = ms;
-    }
-    *info = p->info;
-    return TN_OK;
+tn_status tn_program_last_info(const tn_program *p, tn_run_info *info) {
+    if (!p || !info) return fail(TN_EINVAL, "NULL argument");
+    return batch_info(p->b, info);
 }
 
 void tn_program_free(tn_program *p) {
     if (!p) return;
-    cudaSetDevice(p->ctx->device);
-    cudaStreamSynchronize(p->ctx->stream);
-    if (p->ctx->cached == p) p->ctx->cached = nullptr;
-    program_destroy(p);
+    cudaSetDevice(p->b->ctx->device);
+    cudaStreamSynchronize(p->b->ctx->stream);
+    batch_destroy(p->b);
+    delete p;
+}
+
+tn_status tn_batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
+                          tn_precision prec, tn_batch **out) {
+    return batch_create(ctx, n, nets, plans, prec, out);
+}
+
+tn_status tn_batch_run(tn_batch *b, void *d_results) {
+    if (!b) return fail(TN_EINVAL, "NULL batch");
+    return batch_run(b, d_results);
+}
+
+tn_status tn_batch_results(tn_batch *b, double *amps, int32_t *exp2, int32_t *status) {
+    if (!b) return fail(TN_EINVAL, "NULL batch");
+    return batch_results(b, amps, exp2, status);
+}
+
+tn_status tn_batch_set_tensors(tn_batch *b, int32_t count, const int32_t *job, const int32_t *tensor,
+                               const double *data) {
+    if (!b || (count > 0 && (!job || !tensor || !data))) return fail(TN_EINVAL, "NULL argument");
+    if (count < 0) return fail(TN_EINVAL, "count must be >= 0");
+    size_t src = 0;
+    const size_t hdr0 = b->upd_hdr.size(), val0 = b->upd_val.size();
+    for (int32_t i = 0; i < count; ++i) {
+        if (job[i] < 0 || job[i] >= b->n_jobs) {
+            b->upd_hdr.resize(hdr0); b->upd_val.resize(val0);
+            return fail(TN_EINVAL, "job index out of range");
+        }
+        const Compiled &c = b->comp[b->job_comp[job[i]]];
+        if (tensor[i] < 0 || tensor[i] >= c.n) {
+            b->upd_hdr.resize(hdr0); b->upd_val.resize(val0);
+            return fail(TN_EINVAL, "tensor index out of range");
+        }
+        const int64_t off = c.leaf_off[tensor[i]], cnt = c.leaf_off[tensor[i] + 1] - off;
+        b->upd_hdr.push_back(b->leaf64_off[job[i]] + off);
+        b->upd_hdr.push_back(cnt);
+        b->upd_hdr.push_back((int64_t)(b->upd_val.size() / 2));
+        b->upd_val.insert(b->upd_val.end(), data + src, data + src + 2 * cnt);
+        src += 2 * (size_t)cnt;
+    }
+    return TN_OK;
+}
+
+tn_status tn_batch_footprint(const tn_batch *b, size_t *bytes) {
+    if (!b || !bytes) return fail(TN_EINVAL, "NULL argument");
+    *bytes = b->footprint;
+    return TN_OK;
+}
+
+tn_status tn_batch_last_info(const tn_batch *b, tn_run_info *info) {
+    if (!b || !info) return fail(TN_EINVAL, "NULL argument");
+    return batch_info(const_cast<tn_batch *>(b), info);
+}
+
+tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms) {
+    if (!b || !mean_ms) return fail(TN_EINVAL, "NULL argument");
+    if (b->mode != TN_EXEC_PERSISTENT) return fail(TN_EUNSUPPORTED, "only the persistent mode is timed per run");
+    if (n_runs < 1 || n_runs > tn_batch::kRing || n_runs > b->runs)
+        return fail(TN_EINVAL, "n_runs must be in [1, min(256, runs so far)]");
+    CK(cudaSetDevice(b->ctx->device));
+    double total = 0;
+    for (int64_t r = b->runs - n_runs; r < b->runs; ++r) {
+        cudaEvent_t const *ev = b->kev[r % tn_batch::kRing];
+        CK(cudaEventSynchronize(ev[1]));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        total += ms;
+    }
+    *mean_ms = total / n_runs;
+    return TN_OK;
+}
+
+void tn_batch_free(tn_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    if (b->ctx->cached == b) b->ctx->cached = nullptr;
+    batch_destroy(b);
 }
 
 tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
@@ -483,34 +873,43 @@ tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_pr
           ctx->cached_prec == prec)) {
         if (ctx->cached) {
             cudaStreamSynchronize(ctx->stream);
-            program_destroy(ctx->cached);
+            batch_destroy(ctx->cached);
             ctx->cached = nullptr;
         }
-        tn_program *p = nullptr;
-        tn_status s = tn_program_create(ctx, net, plan, prec, &p);
+        tn_batch *b = nullptr;
+        tn_status s = batch_create(ctx, 1, &net, &plan, prec, &b);
         if (s != TN_OK) return s;
-        ctx->cached = p;
+        ctx->cached = b;
         ctx->cached_net = net->impl.uid;
         ctx->cached_plan = plan->impl.uid;
         ctx->cached_prec = prec;
     }
-    tn_program *p = ctx->cached;
-    p->net = net;                  // the same net (by id); refresh the address
-    p->uploaded_version = ~0ull;   // end to end: the leaves are copied from the host every call
-    tn_status s = tn_program_run(p, p->d_res);
+    tn_batch *b = ctx->cached;
+    b->nets[0] = net;               // the same net (by id); refresh the address
+    b->uploaded[0] = ~0ull;         // end to end: the leaves are copied from the host every call
+    tn_status s = batch_run(b, nullptr);
     if (s != TN_OK) return s;
-    CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(DeviceResult), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    const DeviceResult r = *p->h_res;
-    if (r.status != 0) return fail(TN_ETIMEOUT, "device reported status " + std::to_string(r.status));
-    out_amp[0] = r.re;
-    out_amp[1] = r.im;
-    *out_exp2 = r.exp2;
-    if (info) {
-        tn_status si = tn_program_last_info(p, info);
-        if (si != TN_OK) return si;
-    }
+    double amp[2];
+    int32_t e2 = 0;
+    s = batch_results(b, amp, &e2, nullptr);
+    if (s != TN_OK) return s;
+    out_amp[0] = amp[0];
+    out_amp[1] = amp[1];
+    *out_exp2 = e2;
+    if (info) return batch_info(b, info);
     return TN_OK;
+}
+
+tn_status tn_batch_contract(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
+                            tn_precision prec, double *out_amps, int32_t *out_exp2) {
+    if (!out_amps || !out_exp2) return fail(TN_EINVAL, "NULL output");
+    tn_batch *b = nullptr;
+    tn_status s = batch_create(ctx, n, nets, plans, prec, &b);
+    if (s != TN_OK) return s;
+    s = batch_run(b, nullptr);
+    if (s == TN_OK) s = batch_results(b, out_amps, out_exp2, nullptr);
+    tn_batch_free(b);
+    return s;
 }
 
 tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_bytes, int32_t rank,

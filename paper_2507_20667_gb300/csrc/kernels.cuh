@@ -1,4 +1,4 @@
-// Device step descriptors and kernel launchers of the contraction engine.
+// Device step descriptors, job tables and kernel launchers of the contraction engine.
 #pragma once
 
 #include <cstdint>
@@ -25,48 +25,81 @@ struct Groups {
     int64_t mask[kMaxGroups]; // pow2: dim - 1
 };
 
-enum StepKind : int32_t { STEP_ROWS = 0, STEP_TILE = 1, STEP_DOT = 2, STEP_TC = 3 };
+// Kernel classes.  A contraction producing at most 16 outputs from a long shared index is split
+// in two steps: DOTP reduces K-chunks into FP64 partials, DOTF sums them in a fixed order.
+enum StepKind : int32_t { STEP_ROWS = 0, STEP_TILE = 1, STEP_DOTP = 2, STEP_DOTF = 3, STEP_TC = 4 };
+
+enum StepFlags : int32_t {
+    FLAG_A_LEAF = 1,    // A lives in the job's leaf buffer (else in its arena)
+    FLAG_B_LEAF = 2,
+    FLAG_ROOT = 4,      // the step produces the network's value: write the job's result record
+    FLAG_NO_C = 8       // no tensor output (DOTP, or the root's DOTF)
+};
 
 struct StepDesc {
-    const void *A;
-    const void *B;
-    void *C;                 // may be null for the root step (result written to the scalar slot)
     int64_t M, N, K;
+    int64_t a_off, b_off, c_off;   // element offsets into the leaf buffer or the arena
     int32_t node_a, node_b, node_c;
     int32_t kind;
-    int32_t is_root;
-    int32_t pad;
+    int32_t flags;
+    int32_t ntiles;                // work tiles of this step
+    int32_t dep0, dep1;            // steps producing A and B (-1: a leaf); DOTF: dep0 = its DOTP
+    int32_t tile_rows;             // ROWS: output rows per tile; DOTP: shared indices per tile
+    int32_t part_off;              // DOTP / DOTF: offset of the step's partials (in double2)
+    int32_t level;                 // longest path from the leaves (scheduling order)
+    int32_t pad[3];
     Groups m, n, k;
 };
 
-// Per-node power-of-two scale bookkeeping (spec precision row): the stored values V of
-// node v represent V * 2^exp2[v]; maxbits[v] holds the float bit pattern of max(|Re V|, |Im V|)
-// (atomicMax on the bit pattern orders non-negative floats correctly).
-struct ScaleState {
-    int32_t *exp2;
-    uint32_t *maxbits;
+// Everything one contraction (a "job") owns on the device.  Several jobs may share one compiled
+// step list (same network structure and plan) and differ only in their leaves.
+struct JobPtrs {
+    const double2 *leaf64;   // complex128 leaves as uploaded
+    const int64_t *leaf_off; // [n_leaves + 1] element offsets of the leaves
+    const void *leaf;        // storage-type leaves
+    char *arena;             // intermediates
+    double2 *partials;       // DOTP partials
+    int32_t *exp2;           // [n_nodes] power-of-two exponent of each node's stored values
+    uint32_t *maxbits;       // [n_nodes] float bits of max(|Re|, |Im|) of each node's values
+    int32_t *done;           // [n_steps] completed tiles of each step (persistent execution)
+    void *result;            // DeviceResult
+    const StepDesc *steps;   // the job's compiled step list
+    int32_t n_steps;
+    int32_t n_leaves;
 };
 
 // Result record written to device memory at the end of a run.
 struct DeviceResult {
     double re, im;
     int32_t exp2;
-    int32_t status;
+    int32_t status;          // 0 = ok, 5 = a bounded wait gave up (TN_ETIMEOUT)
     int64_t pad;
 };
 
+// A unit of persistent work: tile `tile` of step `step` of job `job`.
+struct WorkItem {
+    uint32_t job, step, tile;
+};
+
 // Launchers (all enqueue on `stream`, return the launch error).
-cudaError_t launch_leaf_convert(bool c128, const double *src, void *dst, const int64_t *leaf_off,
-                                int32_t n_leaves, ScaleState sc, cudaStream_t stream);
-cudaError_t launch_step(bool c128, const StepDesc *d_desc, const StepDesc &h_desc, ScaleState sc,
-                        double *dot_partials, int32_t dot_blocks, DeviceResult *result,
-                        cudaStream_t stream, int32_t *launches);
-cudaError_t launch_finish_leaf(bool c128, const void *leaf, int32_t node, ScaleState sc,
-                               DeviceResult *result, cudaStream_t stream);
+cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jobs,
+                                int32_t max_leaves, cudaStream_t stream);
+cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const JobPtrs &job,
+                        cudaStream_t stream);
+cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);
+cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
+                              int64_t n_work, uint32_t *counter, int32_t grid, cudaStream_t stream);
+int32_t persistent_grid(bool c128);
+cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int64_t n_upd,
+                                   double2 *leaf64, cudaStream_t stream);
 cudaError_t launch_permute(const void *src, void *dst, int32_t elem_bytes, int32_t rank,
                            const int64_t *dims, const int32_t *perm, cudaStream_t stream);
 
-// Number of blocks of the first phase of the dot kernel (partials buffer: blocks * 16 double2).
-int32_t dot_partial_blocks();
+// Tiling constants shared by the compiler and the kernels.
+constexpr int kThreads = 256;
+constexpr int kTileM = 64, kTileN = 64, kTileK = 16;   // CUDA-core GEMM tile
+constexpr int kRowsMaxKN = 1024, kRowsMaxK = 64, kRowsMaxN = 16;
+constexpr int kDotMaxOut = 16;
+constexpr int kDotChunk = 8192;                         // shared indices per DOTP tile
 
 }  // namespace tn

@@ -1,0 +1,415 @@
+// Tile-level device functions of the contraction kernels.  One call computes one work tile of
+// one step; the per-step kernels map blocks to tiles, the persistent kernel claims tiles from a
+// global work list.  All operand loads bypass L1 (ld.global.cg): inside one persistent launch an
+// arena address is rewritten by later steps, so an SM must never see a stale L1 line.
+#pragma once
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace tn {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+template <typename T> using cx_t = typename Cx<T>::t;
+
+__device__ __forceinline__ float2 cmake(float r, float i) { return make_float2(r, i); }
+__device__ __forceinline__ double2 cmake(double r, double i) { return make_double2(r, i); }
+
+template <typename C>
+__device__ __forceinline__ void cfma(C &acc, const C &a, const C &b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+template <typename C> __device__ __forceinline__ C ldc(const C *p) { return __ldcg(p); }
+
+template <typename C> __device__ __forceinline__ C cscale(C v, decltype(C::x) s) {
+    return cmake(v.x * s, v.y * s);
+}
+
+// frexp-style exponent of the float with bit pattern `bits` (0 for zero): x = f * 2^e with f in
+// [0.5, 1).  Subnormal maxima are treated as 2^-126.
+__device__ __forceinline__ int32_t scale_exponent(uint32_t bits) {
+    if (bits == 0u) return 0;
+    int32_t e = (int32_t)((bits >> 23) & 0xffu);
+    return e == 0 ? -126 : e - 126;
+}
+
+template <typename T> __device__ __forceinline__ T pow2(int32_t e) { return (T)ldexp(1.0, e); }
+
+__device__ __forceinline__ float absmax2(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ float absmax2(double2 v) { return (float)fmax(fabs(v.x), fabs(v.y)); }
+
+// Offset contributed by the digits of `idx` over a group list (stride `sa`).
+__device__ __forceinline__ int64_t group_off(const Groups &g, int64_t idx) {
+    int64_t off = 0;
+    if (g.pow2) {
+        for (int32_t i = 0; i < g.n; ++i) off += ((idx >> g.lsb[i]) & g.mask[i]) * g.sa[i];
+    } else {
+        for (int32_t i = 0; i < g.n; ++i) {
+            int64_t d = idx % g.dim[i];
+            idx /= g.dim[i];
+            off += d * g.sa[i];
+        }
+    }
+    return off;
+}
+
+// Offsets in A and B of a shared-leg multi-index.
+__device__ __forceinline__ void group_off2(const Groups &g, int64_t idx, int64_t &oa, int64_t &ob) {
+    oa = 0;
+    ob = 0;
+    if (g.pow2) {
+        for (int32_t i = 0; i < g.n; ++i) {
+            int64_t d = (idx >> g.lsb[i]) & g.mask[i];
+            oa += d * g.sa[i];
+            ob += d * g.sb[i];
+        }
+    } else {
+        for (int32_t i = 0; i < g.n; ++i) {
+            int64_t d = idx % g.dim[i];
+            idx /= g.dim[i];
+            oa += d * g.sa[i];
+            ob += d * g.sb[i];
+        }
+    }
+}
+
+// Copy a descriptor into shared memory (all threads), followed by a barrier.
+__device__ __forceinline__ void load_desc(StepDesc &dst, const StepDesc *src) {
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(StepDesc) / sizeof(int4)); i += blockDim.x)
+        d[i] = __ldcg(s + i);
+    __syncthreads();
+}
+static_assert(sizeof(StepDesc) % sizeof(int4) == 0, "descriptor must be a multiple of 16 bytes");
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide max of non-negative values, then one atomicMax on the bit pattern (non-negative
+// floats order like their bit patterns).  Ends with a barrier.
+__device__ __forceinline__ void publish_max(float v, uint32_t *slot, float *red) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+        v = warp_max(v);
+        if (lane == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
+    }
+    __syncthreads();
+}
+
+template <typename C>
+__device__ __forceinline__ const C *operand(const StepDesc &d, const JobPtrs &j, bool is_a) {
+    const bool leaf = is_a ? (d.flags & FLAG_A_LEAF) : (d.flags & FLAG_B_LEAF);
+    const int64_t off = is_a ? d.a_off : d.b_off;
+    return leaf ? static_cast<const C *>(j.leaf) + off : reinterpret_cast<const C *>(j.arena) + off;
+}
+
+__device__ __forceinline__ void step_scales(const StepDesc &d, const JobPtrs &j, int32_t &eA, int32_t &eB) {
+    eA = scale_exponent(__ldcg(j.maxbits + d.node_a));
+    eB = scale_exponent(__ldcg(j.maxbits + d.node_b));
+}
+
+__device__ __forceinline__ void write_exponent(const StepDesc &d, const JobPtrs &j, int32_t eA, int32_t eB) {
+    j.exp2[d.node_c] = __ldcg(j.exp2 + d.node_a) + eA + __ldcg(j.exp2 + d.node_b) + eB;
+}
+
+// Shared-memory scratch needed by any tile function, per element type.
+template <typename T> struct Scratch {
+    using C = cx_t<T>;
+    static constexpr int rows = kRowsMaxKN * sizeof(C) + kRowsMaxK * sizeof(int64_t);
+    static constexpr int tile = 2 * kTileK * kTileM * sizeof(C) + (kTileM + kTileN + 2 * kTileK) * sizeof(int64_t);
+    static constexpr int dot = (kThreads / 32) * kDotMaxOut * sizeof(double2) + 2 * kDotMaxOut * sizeof(int64_t);
+    static constexpr int bytes = (rows > tile ? (rows > dot ? rows : dot) : (tile > dot ? tile : dot));
+};
+
+// ------------------------------------------------------------------------------ ROWS
+// Tiny-bond contraction (N <= NT <= 16, K <= 64): B (K x N) is staged in shared memory, each
+// thread owns output rows m, reads their K entries of A through the index map and writes N
+// consecutive outputs.  HBM traffic: one read of A, one write of C.
+template <typename T, int NT>
+__device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem, float *red) {
+    using C = cx_t<T>;
+    C *Bs = reinterpret_cast<C *>(smem);
+    int64_t *kA = reinterpret_cast<int64_t *>(smem + kRowsMaxKN * sizeof(C));
+    const int32_t N = (int32_t)d.N, K = (int32_t)d.K;
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const C *__restrict__ A = operand<C>(d, j, true);
+    const C *__restrict__ B = operand<C>(d, j, false);
+    C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
+    for (int32_t i = threadIdx.x; i < K * N; i += blockDim.x) {
+        int32_t k = i / N, n = i - k * N;
+        int64_t oa, ob;
+        group_off2(d.k, k, oa, ob);
+        ob += group_off(d.n, n);
+        Bs[i] = cscale(ldc(B + ob), sB);
+        if (n == 0) kA[k] = oa;
+    }
+    __syncthreads();
+    const int64_t m_begin = tile * (int64_t)d.tile_rows;
+    const int64_t m_end = min(d.M, m_begin + (int64_t)d.tile_rows);
+    float mx = 0.f;
+    for (int64_t m = m_begin + threadIdx.x; m < m_end; m += blockDim.x) {
+        const int64_t offA = group_off(d.m, m);
+        C acc[NT];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n] = cmake((T)0, (T)0);
+        for (int32_t k = 0; k < K; ++k) {
+            const C a = ldc(A + offA + kA[k]);
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+                if (n < N) cfma(acc[n], a, Bs[k * N + n]);
+        }
+        C *out = Cp + m * N;
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+            if (n < N) {
+                C v = cscale(acc[n], sA);
+                out[n] = v;
+                mx = fmaxf(mx, absmax2(v));
+            }
+    }
+    publish_max(mx, j.maxbits + d.node_c, red);
+    if (tile == 0 && threadIdx.x == 0) write_exponent(d, j, eA, eB);
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_rows_dispatch(const StepDesc &d, int64_t tile, const JobPtrs &j,
+                                                   char *smem, float *red) {
+    if (d.N <= 1) tile_rows<T, 1>(d, tile, j, smem, red);
+    else if (d.N <= 2) tile_rows<T, 2>(d, tile, j, smem, red);
+    else if (d.N <= 4) tile_rows<T, 4>(d, tile, j, smem, red);
+    else if (d.N <= 8) tile_rows<T, 8>(d, tile, j, smem, red);
+    else tile_rows<T, 16>(d, tile, j, smem, red);
+}
+
+// ------------------------------------------------------------------------------ TILE (GEMM)
+// General contraction on CUDA cores: a 64 x 64 output tile, K in chunks of 16, operand tiles
+// gathered through the index maps into shared memory, 4 x 4 outputs per thread.
+template <typename T>
+__device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem, float *red) {
+    using C = cx_t<T>;
+    C(*As)[kTileM] = reinterpret_cast<C(*)[kTileM]>(smem);
+    C(*Bs)[kTileN] = reinterpret_cast<C(*)[kTileN]>(smem + kTileK * kTileM * sizeof(C));
+    int64_t *rowA = reinterpret_cast<int64_t *>(smem + 2 * kTileK * kTileM * sizeof(C));
+    int64_t *colB = rowA + kTileM;
+    int64_t *kAo = colB + kTileN;
+    int64_t *kBo = kAo + kTileK;
+    const int64_t M = d.M, N = d.N, K = d.K;
+    const int64_t tiles_n = (N + kTileN - 1) / kTileN;
+    const int64_t m0 = (tile / tiles_n) * kTileM, n0 = (tile % tiles_n) * kTileN;
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const C *__restrict__ A = operand<C>(d, j, true);
+    const C *__restrict__ B = operand<C>(d, j, false);
+    C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
+    const int tid = threadIdx.x;
+    if (tid < kTileM) rowA[tid] = (m0 + tid < M) ? group_off(d.m, m0 + tid) : -1;
+    else if (tid < kTileM + kTileN) {
+        int c = tid - kTileM;
+        colB[c] = (n0 + c < N) ? group_off(d.n, n0 + c) : -1;
+    }
+    const int tx = tid & 15, ty = tid >> 4;
+    C acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cmake((T)0, (T)0);
+    for (int64_t k0 = 0; k0 < K; k0 += kTileK) {
+        __syncthreads();
+        if (tid < kTileK) {
+            int64_t oa = -1, ob = -1;
+            if (k0 + tid < K) group_off2(d.k, k0 + tid, oa, ob);
+            kAo[tid] = oa;
+            kBo[tid] = ob;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < (kTileM * kTileK) / kThreads; ++r) {
+            int i = tid + r * kThreads;
+            int row = i % kTileM, kk = i / kTileM;
+            C v = cmake((T)0, (T)0);
+            if (rowA[row] >= 0 && kAo[kk] >= 0) v = cscale(ldc(A + rowA[row] + kAo[kk]), sA);
+            As[kk][row] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < (kTileN * kTileK) / kThreads; ++r) {
+            int i = tid + r * kThreads;
+            int col = i % kTileN, kk = i / kTileN;
+            C v = cmake((T)0, (T)0);
+            if (colB[col] >= 0 && kBo[kk] >= 0) v = cscale(ldc(B + kBo[kk] + colB[col]), sB);
+            Bs[kk][col] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTileK; ++kk) {
+            C a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) b[jj] = Bs[kk][tx + 16 * jj];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) cfma(acc[i][jj], a[i], b[jj]);
+        }
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            int64_t n = n0 + tx + 16 * jj;
+            if (n < N) {
+                Cp[m * N + n] = acc[i][jj];
+                mx = fmaxf(mx, absmax2(acc[i][jj]));
+            }
+        }
+    }
+    publish_max(mx, j.maxbits + d.node_c, red);
+    if (tile == 0 && threadIdx.x == 0) write_exponent(d, j, eA, eB);
+}
+
+// ------------------------------------------------------------------------------ DOT
+// Small outputs (M * N <= 16) with a long shared index.  DOTP: each tile reduces kDotChunk shared
+// indices; products are formed in the storage precision, summed in runs of 32 in that precision
+// and then in FP64.  DOTF: one tile sums the partials in a fixed order, so results are
+// reproducible.  The root step of a closed network (M = N = 1) always takes this path: the final
+// reduction of the amplitude is FP64.
+template <typename T>
+__device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem) {
+    using C = cx_t<T>;
+    double2(*red)[kDotMaxOut] = reinterpret_cast<double2(*)[kDotMaxOut]>(smem);
+    int64_t *rowA = reinterpret_cast<int64_t *>(smem + (kThreads / 32) * kDotMaxOut * sizeof(double2));
+    int64_t *colB = rowA + kDotMaxOut;
+    const int32_t M = (int32_t)d.M, N = (int32_t)d.N;
+    const int32_t MN = M * N;
+    if (threadIdx.x < M) rowA[threadIdx.x] = group_off(d.m, threadIdx.x);
+    if (threadIdx.x < N) colB[threadIdx.x] = group_off(d.n, threadIdx.x);
+    __syncthreads();
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const C *__restrict__ A = operand<C>(d, j, true);
+    const C *__restrict__ B = operand<C>(d, j, false);
+    double2 acc[kDotMaxOut];
+    C run[kDotMaxOut];
+#pragma unroll
+    for (int i = 0; i < kDotMaxOut; ++i) { acc[i] = make_double2(0, 0); run[i] = cmake((T)0, (T)0); }
+    const int64_t k_begin = tile * (int64_t)d.tile_rows;
+    const int64_t k_end = min(d.K, k_begin + (int64_t)d.tile_rows);
+    int cnt = 0;
+    for (int64_t k = k_begin + threadIdx.x; k < k_end; k += blockDim.x) {
+        int64_t oa, ob;
+        group_off2(d.k, k, oa, ob);
+#pragma unroll
+        for (int i = 0; i < kDotMaxOut; ++i) {
+            if (i < MN) {
+                int m = i / N, n = i - m * N;
+                C a = cscale(ldc(A + oa + rowA[m]), sA), b = cscale(ldc(B + ob + colB[n]), sB);
+                cfma(run[i], a, b);
+            }
+        }
+        if (++cnt == 32) {
+#pragma unroll
+            for (int i = 0; i < kDotMaxOut; ++i) {
+                acc[i].x += (double)run[i].x;
+                acc[i].y += (double)run[i].y;
+                run[i] = cmake((T)0, (T)0);
+            }
+            cnt = 0;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kDotMaxOut; ++i) {
+        if (i >= MN) break;
+        double x = acc[i].x + (double)run[i].x, y = acc[i].y + (double)run[i].y;
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) red[warp][i] = make_double2(x, y);
+    }
+    __syncthreads();
+    if (threadIdx.x < MN) {
+        double2 s = make_double2(0, 0);
+        for (int w = 0; w < kThreads / 32; ++w) { s.x += red[w][threadIdx.x].x; s.y += red[w][threadIdx.x].y; }
+        j.partials[d.part_off + tile * kDotMaxOut + threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tile_dotf(const StepDesc &d, const JobPtrs &j, char *smem) {
+    using C = cx_t<T>;
+    double2(*red)[kDotMaxOut] = reinterpret_cast<double2(*)[kDotMaxOut]>(smem);
+    const int32_t MN = (int32_t)(d.M * d.N);
+    const int32_t nparts = d.tile_rows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < MN; ++i) {
+        double x = 0, y = 0;
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+            double2 p = __ldcg(j.partials + d.part_off + (int64_t)b * kDotMaxOut + i);
+            x += p.x;
+            y += p.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) red[warp][i] = make_double2(x, y);
+    }
+    __syncthreads();
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    const int32_t e_out = __ldcg(j.exp2 + d.node_a) + eA + __ldcg(j.exp2 + d.node_b) + eB;
+    if (threadIdx.x < MN) {
+        double2 s = make_double2(0, 0);
+        for (int w = 0; w < kThreads / 32; ++w) { s.x += red[w][threadIdx.x].x; s.y += red[w][threadIdx.x].y; }
+        if (d.flags & FLAG_ROOT) {
+            DeviceResult *r = static_cast<DeviceResult *>(j.result);
+            r->re = s.x;
+            r->im = s.y;
+            r->exp2 = e_out;
+        }
+        if (!(d.flags & FLAG_NO_C)) {
+            C v = cmake((T)s.x, (T)s.y);
+            (reinterpret_cast<C *>(j.arena) + d.c_off)[threadIdx.x] = v;
+            atomicMax(j.maxbits + d.node_c, __float_as_uint(absmax2(v)));
+        }
+    }
+    if (threadIdx.x == 0) j.exp2[d.node_c] = e_out;
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void run_tile(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
+                                         float *red) {
+    switch (d.kind) {
+        case STEP_ROWS: tile_rows_dispatch<T>(d, tile, j, smem, red); break;
+        case STEP_TILE: tile_gemm<T>(d, tile, j, smem, red); break;
+        case STEP_DOTP: tile_dotp<T>(d, tile, j, smem); break;
+        case STEP_DOTF: tile_dotf<T>(d, j, smem); break;
+        default: break;
+    }
+}
+
+}  // namespace tn

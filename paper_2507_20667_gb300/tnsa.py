@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libtnsa.so")
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_EBUDGET, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(7)
 PRECISIONS = {"c128": 0, "c64": 1, "tf32": 2, "bf16": 3}
+EXEC_MODES = {"persistent": 0, "graph": 1}
 MODES = {"naive": 0, "directed": 1}
 
 
@@ -54,7 +55,8 @@ class tn_plan_info(ctypes.Structure):
 class tn_run_info(ctypes.Structure):
     _fields_ = [("device_ms", ctypes.c_double), ("launches", ctypes.c_int32), ("n_gather", ctypes.c_int32),
                 ("n_tile", ctypes.c_int32), ("n_dot", ctypes.c_int32), ("n_tc", ctypes.c_int32),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
+                ("h2d_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: (getattr(self, f)) for f, _ in self._fields_}
@@ -77,6 +79,16 @@ _SIGS = {
     "tn_ctx_create": (_I32, [_I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "tn_ctx_free": (None, [_P]),
     "tn_ctx_synchronize": (_I32, [_P]),
+    "tn_ctx_set_exec_mode": (_I32, [_P, _I32]),
+    "tn_batch_create": (_I32, [_P, _I32, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "tn_batch_run": (_I32, [_P, _P]),
+    "tn_batch_results": (_I32, [_P, _P, _P, _P]),
+    "tn_batch_footprint": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tn_batch_last_info": (_I32, [_P, ctypes.POINTER(tn_run_info)]),
+    "tn_batch_kernel_ms": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
+    "tn_batch_set_tensors": (_I32, [_P, _I32, _P, _P, _P]),
+    "tn_batch_free": (None, [_P]),
+    "tn_batch_contract": (_I32, [_P, _I32, _P, _P, _I32, _P, _P]),
     "tn_program_create": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
     "tn_program_run": (_I32, [_P, _P]),
     "tn_program_footprint": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -144,6 +156,10 @@ class Ctx(_Handle):
 
 class Program(_Handle):
     _free = "tn_program_free"
+
+
+class Batch(_Handle):
+    _free = "tn_batch_free"
 
 
 def tn_build(network) -> Net:
@@ -243,6 +259,74 @@ def tn_ctx_create(device=0, stream=None, hbm_budget_bytes=0) -> Ctx:
 
 def tn_ctx_synchronize(ctx: Ctx) -> None:
     _check(lib.tn_ctx_synchronize(ctx))
+
+
+def tn_ctx_set_exec_mode(ctx: Ctx, mode="persistent") -> None:
+    _check(lib.tn_ctx_set_exec_mode(ctx, EXEC_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+
+def _handle_array(hs):
+    arr = (ctypes.c_void_p * len(hs))(*[h.ptr for h in hs])
+    return ctypes.cast(arr, ctypes.c_void_p), arr
+
+
+def tn_batch_create(ctx: Ctx, nets, plans, precision="c64") -> Batch:
+    if len(nets) != len(plans):
+        raise ValueError("nets and plans must have the same length")
+    pn, keep_n = _handle_array(nets)
+    pp, keep_p = _handle_array(plans)
+    out = ctypes.c_void_p()
+    _check(lib.tn_batch_create(ctx, len(nets), pn, pp, PRECISIONS[precision], ctypes.byref(out)))
+    return Batch(out.value, keep=(ctx, tuple(nets), tuple(plans)))
+
+
+def tn_batch_run(batch: Batch, d_results: int = 0) -> None:
+    _check(lib.tn_batch_run(batch, ctypes.c_void_p(d_results) if d_results else None))
+
+
+def tn_batch_results(batch: Batch, n: int):
+    """Returns (mantissas complex128 [n], exp2 int32 [n], status int32 [n])."""
+    amps = np.zeros(2 * n, np.float64)
+    e = np.zeros(n, np.int32)
+    st = np.zeros(n, np.int32)
+    _check(lib.tn_batch_results(batch, _ptr(amps), _ptr(e), _ptr(st)))
+    return amps.view(np.complex128).copy(), e, st
+
+
+def tn_batch_set_tensors(batch: Batch, jobs, tensors, data) -> None:
+    """data: complex128 entries of all (job, tensor) pairs back to back."""
+    j = np.ascontiguousarray(jobs, dtype=np.int32)
+    t = np.ascontiguousarray(tensors, dtype=np.int32)
+    d = np.ascontiguousarray(np.asarray(data, dtype=np.complex128).ravel()).view(np.float64)
+    _check(lib.tn_batch_set_tensors(batch, len(j), _ptr(j), _ptr(t), _ptr(d)))
+
+
+def tn_batch_footprint(batch: Batch) -> int:
+    b = ctypes.c_size_t()
+    _check(lib.tn_batch_footprint(batch, ctypes.byref(b)))
+    return b.value
+
+
+def tn_batch_last_info(batch: Batch) -> dict:
+    i = tn_run_info()
+    _check(lib.tn_batch_last_info(batch, ctypes.byref(i)))
+    return i.as_dict()
+
+
+def tn_batch_kernel_ms(batch: Batch, n_runs: int) -> float:
+    v = ctypes.c_double()
+    _check(lib.tn_batch_kernel_ms(batch, int(n_runs), ctypes.byref(v)))
+    return v.value
+
+
+def tn_batch_contract(ctx: Ctx, nets, plans, precision="c64"):
+    pn, keep_n = _handle_array(nets)
+    pp, keep_p = _handle_array(plans)
+    n = len(nets)
+    amps = np.zeros(2 * n, np.float64)
+    e = np.zeros(n, np.int32)
+    _check(lib.tn_batch_contract(ctx, n, pn, pp, PRECISIONS[precision], _ptr(amps), _ptr(e)))
+    return amps.view(np.complex128).copy(), e
 
 
 def tn_program_create(ctx: Ctx, net: Net, plan: Plan, precision="c64") -> Program:

@@ -1,0 +1,125 @@
+"""Batched and persistent execution on the GPU.
+
+  * the persistent dataflow kernel and the per-step graph mode compute every tile identically,
+    so their results agree bit for bit;
+  * a batch of one circuit with many bitstrings, and a mixed batch of different circuits, sizes
+    and partition counts, each match the state vector; every job's result is the same alone and
+    in the mix (bit for bit: the tiles of one job never depend on the others);
+  * bulk tensor updates (new bitstrings) are applied by the next run.
+"""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from paper_2507_20667_gb300 import inputs as tni
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tnsa():
+    from paper_2507_20667_gb300 import tnsa as mod
+    return mod
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def amps(tnsa, mant, e2):
+    return np.array([complex(m) * 2.0 ** int(e) for m, e in zip(mant, e2)])
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_persistent_equals_graph_bitwise(tnsa, prec):
+    circ, x = tni.cfg2()
+    net = tni.amplitude_tn(circ, x)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=4, iterations=300, seed=7,
+                               initial_part=tni.qubit_block_partition(net, 24, 4))
+    out = {}
+    for mode in ("persistent", "graph"):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_exec_mode(ctx, mode)
+        m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
+        out[mode] = (m, e)
+    assert out["persistent"] == out["graph"]
+
+
+def test_one_circuit_many_bitstrings(tnsa):
+    circ = tni.brickwork_1d(14, 10, seed=3)
+    xs = [tni.random_bitstring(14, 900 + i) for i in range(64)]
+    nets = [tni.amplitude_tn(circ, x) for x in xs]
+    hs = [tnsa.tn_build(n) for n in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=4, iterations=100, seed=1,
+                               initial_part=tni.qubit_block_partition(nets[0], 14, 4))
+    ctx = tnsa.tn_ctx_create(0)
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), "c64")
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+    assert (st == 0).all()
+    got = amps(tnsa, mant, e2)
+    psi = sv.simulate(circ).reshape((2,) * 14)
+    for i, x in enumerate(xs):
+        assert rel(got[i], psi[tuple(x)]) <= 1e-5
+    # bulk update: flip every bit of the first 8 jobs and rerun
+    n_t = nets[0].n_tensors
+    jobs = np.repeat(np.arange(8, dtype=np.int32), 14)
+    tensors = np.tile(np.arange(n_t - 14, n_t, dtype=np.int32), 8)
+    flipped = [1 - x for x in xs[:8]]
+    data = np.eye(2, dtype=np.complex128)[np.concatenate(flipped)]
+    tnsa.tn_batch_set_tensors(b, jobs, tensors, data)
+    tnsa.tn_batch_run(b)
+    info = tnsa.tn_batch_last_info(b)
+    assert 0 < info["h2d_bytes"] < 16384
+    mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+    got2 = amps(tnsa, mant, e2)
+    for i in range(8):
+        assert rel(got2[i], psi[tuple(flipped[i])]) <= 1e-5
+    assert np.array_equal(got2[8:], got[8:])
+    with pytest.raises(tnsa.TnError):
+        tnsa.tn_batch_set_tensors(b, [len(hs)], [0], np.zeros(2, np.complex128))
+
+
+def test_mixed_batch_alone_equals_mix(tnsa):
+    specs = [(tni.brickwork_1d(10, 8, seed=11), 2), (tni.grid_2d(3, 4, 6, seed=12), 4),
+             (tni.brickwork_1d(16, 9, seed=13), 8), (tni.grid_2d(4, 4, 5, seed=14), 2),
+             (tni.ghz(12), 1)]
+    nets, hs, plans, refs = [], [], [], []
+    for i, (circ, k) in enumerate(specs):
+        for r in range(3):
+            x = tni.random_bitstring(circ.n_qubits, 70 * i + r) if i < 4 else [r % 2] * 12
+            net = tni.amplitude_tn(circ, x)
+            h = tnsa.tn_build(net)
+            init = tni.qubit_block_partition(net, circ.n_qubits, k) if k > 1 else None
+            plans.append(tnsa.tn_plan_create(h, k=k, iterations=60, seed=i, initial_part=init))
+            nets.append(net)
+            hs.append(h)
+            refs.append(sv.amplitude(circ, x))
+    ctx = tnsa.tn_ctx_create(0)
+    for prec, tol in (("c64", 1e-5), ("c128", 1e-12)):
+        mant, e2 = tnsa.tn_batch_contract(ctx, hs, plans, prec)
+        mix = amps(tnsa, mant, e2)
+        for i, ref in enumerate(refs):
+            if abs(ref) > 1e-9:
+                assert rel(mix[i], ref) <= tol, (i, mix[i], ref)
+            else:
+                assert abs(mix[i]) <= 1e-6
+        for i in (0, 4, 8, 13):
+            m, e, _ = tnsa.tn_contract(ctx, hs[i], plans[i], prec)
+            assert complex(m) * 2.0 ** e == mix[i]      # alone == in the mix, bit for bit
+
+
+def test_batch_kernel_timing(tnsa):
+    circ, x = tni.cfg1()
+    nets = [tni.amplitude_tn(circ, tni.random_bitstring(10, i)) for i in range(32)]
+    hs = [tnsa.tn_build(n) for n in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=1)
+    ctx = tnsa.tn_ctx_create(0)
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * 32, "c64")
+    for _ in range(3):
+        tnsa.tn_batch_run(b)
+    ms = tnsa.tn_batch_kernel_ms(b, 3)
+    assert 0 < ms < 1000
+    info = tnsa.tn_batch_last_info(b)
+    assert info["launches"] == 2 and info["flops"] > 0 and info["bytes"] > 0
