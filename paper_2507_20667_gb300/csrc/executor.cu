@@ -498,7 +498,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         o_max[i] = carve(sizeof(uint32_t) * (size_t)c.n_nodes);
         o_done[i] = carve(sizeof(int32_t) * c.steps.size());
     }
-    const size_t o_counter = carve(sizeof(uint32_t));
+    const size_t o_counter = carve(2 * sizeof(uint32_t));   // claim counter, abort flag
     b->reset_bytes = off - o_reset;
     b->footprint = off;
     if (ctx->budget && b->footprint > ctx->budget) {

@@ -87,6 +87,7 @@ cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jo
 cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const JobPtrs &job,
                         cudaStream_t stream);
 cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);
+// counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
                               int64_t n_work, uint32_t *counter, int32_t grid, cudaStream_t stream);
 int32_t persistent_grid(bool c128);

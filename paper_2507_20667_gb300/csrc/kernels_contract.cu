@@ -26,18 +26,24 @@ __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
     return v;
 }
 
-// Wait until step `dep` of job `j` has completed all its tiles; false if the wait gave up.
-__device__ bool wait_step(const JobPtrs &j, int32_t dep) {
+// Wait until step `dep` of job `j` has completed all its tiles; false if the wait gave up.  The
+// first wait that gives up raises the launch-wide abort flag, after which every wait returns at
+// once, so a broken dependency costs one time-out, not one per waiting tile.
+__device__ bool wait_step(const JobPtrs &j, int32_t dep, int32_t *abort_flag) {
     if (dep < 0) return true;
     const uint32_t need = (uint32_t)__ldcg(&j.steps[dep].ntiles);
     if (ld_acquire(j.done + dep) >= need) return true;
     long long t0 = clock64();
     unsigned ns = 32;
     while (ld_acquire(j.done + dep) < need) {
+        if (ld_acquire(abort_flag)) return false;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
         // clock64 counts SM cycles; 2.07 GHz at most, so cycles / 2 is a lower bound in ns
-        if ((clock64() - t0) / 2 > kSpinLimitNs) return false;
+        if ((clock64() - t0) / 2 > kSpinLimitNs) {
+            atomicExch(abort_flag, 1);
+            return false;
+        }
     }
     return true;
 }
@@ -79,6 +85,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict__ jobs,
                                                       const WorkItem *__restrict__ work,
                                                       int64_t n_work, uint32_t *counter) {
+    int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -93,8 +100,8 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         const JobPtrs &j = jobs[it.job];
         if (threadIdx.x == 0) {
             const StepDesc *sd = j.steps + it.step;
-            bool ok = wait_step(j, __ldcg(&sd->dep0));
-            ok = wait_step(j, __ldcg(&sd->dep1)) && ok;
+            bool ok = wait_step(j, __ldcg(&sd->dep0), abort_flag);
+            ok = wait_step(j, __ldcg(&sd->dep1), abort_flag) && ok;
             if (!ok) atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
             s_ok = ok;
         }
