@@ -169,22 +169,9 @@ bool make_groups(const std::vector<int64_t> &dim, const std::vector<int64_t> &sa
     return true;
 }
 
-struct FreeList {
-    std::map<size_t, size_t> blocks;   // offset -> size
-    size_t top = 0, high = 0;
-    size_t alloc(size_t sz) {
-        for (auto it = blocks.begin(); it != blocks.end(); ++it)
-            if (it->second >= sz) {
-                size_t off = it->first, rest = it->second - sz;
-                blocks.erase(it);
-                if (rest) blocks[off + sz] = rest;
-                return off;
-            }
-        size_t off = top;
-        top += sz;
-        high = std::max(high, top);
-        return off;
-    }
+// Free blocks of the arena (offset -> size), coalescing neighbours.
+struct Pool {
+    std::map<size_t, size_t> blocks;
     void release(size_t off, size_t sz) {
         auto it = blocks.emplace(off, sz).first;
         auto nx = std::next(it);
@@ -197,15 +184,57 @@ struct FreeList {
             if (pv->first + pv->second == it->first) {
                 pv->second += it->second;
                 blocks.erase(it);
-                it = pv;
             }
         }
-        if (it->first + it->second == top) {   // give the tail back
-            top = it->first;
-            blocks.erase(it);
-        }
+    }
+    bool take(size_t sz, size_t &off) {   // best fit
+        auto best = blocks.end();
+        for (auto it = blocks.begin(); it != blocks.end(); ++it)
+            if (it->second >= sz && (best == blocks.end() || it->second < best->second)) best = it;
+        if (best == blocks.end()) return false;
+        off = best->first;
+        const size_t rest = best->second - sz;
+        blocks.erase(best);
+        if (rest) blocks[off + sz] = rest;
+        return true;
+    }
+    void absorb(Pool &o) {
+        if (o.blocks.size() > blocks.size()) std::swap(blocks, o.blocks);
+        for (auto &b : o.blocks) release(b.first, b.second);
+        o.blocks.clear();
     }
 };
+
+// Static memory plan that is valid for ANY execution order consistent with the tree's
+// dependencies: a buffer freed inside a subtree (its last reader is in that subtree) may be
+// reused only by that subtree's ancestors, which run after every step of the subtree; sibling
+// subtrees may run concurrently and so draw fresh memory from the top of the arena.  A step's
+// output never overlaps its own operands.  Returns the arena size.
+size_t plan_memory(const Plan &plan, int32_t n, const std::vector<size_t> &bytes,
+                   std::vector<size_t> &off) {
+    const int32_t nn = 2 * n - 1;
+    std::vector<Pool> pool(nn);
+    size_t top = 0;
+    off.assign(nn, 0);
+    for (int32_t s = 0; s < n - 1; ++s) {
+        const int32_t l = plan.steps[s][0], r = plan.steps[s][1], o = n + s;
+        Pool p;
+        p.absorb(pool[l]);
+        p.absorb(pool[r]);
+        if (s != n - 2) {   // the root's value goes to the result record
+            size_t at;
+            if (!p.take(bytes[o], at)) {
+                at = top;
+                top += bytes[o];
+            }
+            off[o] = at;
+        }
+        for (int32_t x : {l, r})
+            if (x >= n) p.release(off[x], bytes[x]);
+        pool[o].blocks.swap(p.blocks);
+    }
+    return top;
+}
 
 int32_t rows_per_tile(int64_t M) {
     if (M <= (1 << 14)) return 256;
@@ -225,9 +254,22 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
     }
     c.leaf_off.assign(net.data_off.begin(), net.data_off.end());
     const size_t esz = (size_t)elem;
-    std::vector<size_t> arena_off(nn, 0);
+    // first pass: sizes of all nodes (layouts follow in the main pass)
+    {
+        std::vector<std::vector<int32_t>> legs(nn);
+        for (int32_t t = 0; t < n; ++t) legs[t] = net.legs[t];
+        for (int32_t s = 0; s < n - 1; ++s) {
+            const int32_t l = plan.steps[s][0], r = plan.steps[s][1], o = n + s;
+            legs_symdiff(legs[l], legs[r], legs[o]);
+            int64_t sz = 1;
+            for (int32_t e : legs[o]) sz *= net.edim[e];
+            size[o] = sz;
+        }
+    }
+    std::vector<size_t> bytes(nn, 0), arena_off;
+    for (int32_t v = n; v < nn; ++v) bytes[v] = align_up((size_t)size[v] * esz, 256);
+    c.arena_bytes = std::max(plan_memory(plan, n, bytes, arena_off), (size_t)256);
     std::vector<int32_t> producer(nn, -1), level(nn, 0);   // step index producing each node
-    FreeList fl;
     c.steps.clear();
     c.steps.reserve(n);
     for (int32_t s = 0; s < n - 1; ++s) {
@@ -269,8 +311,6 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
         if (!make_groups(md, ms, none, false, d.m) || !make_groups(nd, ns, none, false, d.n) ||
             !make_groups(kd, ksa, ksb, true, d.k))
             return fail(TN_EUNSUPPORTED, "step " + std::to_string(s) + " has more than 32 leg groups");
-        // memory plan: place the output, then release the inputs
-        if (!root) arena_off[o] = fl.alloc(align_up((size_t)size[o] * esz, 256));
         auto where = [&](int32_t v, int64_t &off) -> bool {
             if (v < n) { off = c.leaf_off[v]; return true; }
             off = (int64_t)(arena_off[v] / esz);
@@ -321,10 +361,7 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
         }
         producer[o] = (int32_t)c.steps.size() - 1;
         level[o] = c.steps.back().level;
-        for (int32_t x : {l, r})
-            if (x >= n) fl.release(arena_off[x], align_up((size_t)size[x] * esz, 256));
     }
-    c.arena_bytes = std::max(fl.high, (size_t)256);
     c.total_tiles = 0;
     for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
