@@ -249,6 +249,26 @@ tn_status tn_batch_contract(tn_ctx *ctx, int32_t n, const tn_net *const *nets,
 tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_bytes, int32_t rank,
                      const int64_t *dims, const int32_t *perm);
 
+/* Inner product sum_i a[i] * b[i] (bilinear, no conjugation) of two DEVICE vectors of n complex
+ * numbers, accumulated in FP64, without allocating any memory.  The paper has no counterpart: it
+ * is the engine's final-reduction kernel offered to callers that cannot allocate device memory
+ * while they run -- code whose device memory belongs to a host framework's pool, or serving loops
+ * where cudaMalloc / cudaFree would synchronize the device or could fail mid-request.
+ *   device       the CUDA device of the vectors; made current by the call
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream); returns without waiting
+ *   d_a, d_b     n complex64 (prec = TN_C64) or complex128 (TN_C128) numbers, interleaved
+ *   n            0 <= n <= 2^26; larger n is rejected with TN_EINVAL (the scratch holds one FP64
+ *                partial sum per 65536 elements, 1024 of them)
+ *   d_out        DEVICE double[2] receiving (re, im)
+ * Scratch lives in a file-scope device array (16 KB) that every GPU loading the library keeps
+ * until the process exits; all calls share it, so calls whose kernels overlap on the GPU (for
+ * example on two streams) race and must be ordered by the caller.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or allocating library routine
+ * is called.  Errors: TN_EINVAL, TN_ECUDA. */
+tn_status tn_dot_noalloc(int32_t device, void *cuda_stream, const void *d_a, const void *d_b,
+                         int64_t n, tn_precision prec, double *d_out);
+
 /* ------------------------------------------------------------------ diagnostics */
 
 const char *tn_status_str(tn_status s);

@@ -96,6 +96,7 @@ _SIGS = {
     "tn_program_free": (None, [_P]),
     "tn_contract": (_I32, [_P, _P, _P, _I32, _P, _P, ctypes.POINTER(tn_run_info)]),
     "tn_permute": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "tn_dot_noalloc": (_I32, [_I32, _P, _P, _P, ctypes.c_int64, _I32, _P]),
     "tn_status_str": (ctypes.c_char_p, [_I32]),
     "tn_last_error": (ctypes.c_char_p, []),
     "tn_version": (ctypes.c_char_p, []),
@@ -367,6 +368,12 @@ def tn_permute(ctx: Ctx, d_in: int, d_out: int, elem_bytes: int, dims, perm) -> 
     p = np.ascontiguousarray(perm, dtype=np.int32)
     _check(lib.tn_permute(ctx, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), int(elem_bytes), len(d),
                           _ptr(d), _ptr(p)))
+
+
+def tn_dot_noalloc(device: int, stream: int, d_a: int, d_b: int, n: int, precision: str, d_out: int) -> None:
+    """Inner product of two device vectors into d_out (device double[2]) without allocating."""
+    _check(lib.tn_dot_noalloc(int(device), ctypes.c_void_p(stream) if stream else None, ctypes.c_void_p(d_a),
+                              ctypes.c_void_p(d_b), int(n), PRECISIONS[precision], ctypes.c_void_p(d_out)))
 
 
 def tn_version() -> str:
