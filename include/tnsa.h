@@ -164,6 +164,14 @@ tn_status tn_ctx_synchronize(tn_ctx *ctx);
 typedef enum { TN_EXEC_PERSISTENT = 0, TN_EXEC_GRAPH = 1 } tn_exec_mode;
 tn_status tn_ctx_set_exec_mode(tn_ctx *ctx, int32_t mode);
 
+/* Shared memory (bytes) a CTA-resident subtree program may use.  The compiler runs every maximal
+ * subtree of the contraction tree whose sequential working set -- its leaves plus the
+ * intermediates alive at any one time -- fits this budget inside one thread block, entirely in
+ * shared memory; only the subtree's result goes to device memory.  -1 (default): the largest
+ * budget that keeps two blocks per SM; 0: no subtree programs (every step is a global step).
+ * Takes effect for programs and batches created afterwards.  Errors: TN_EINVAL. */
+tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
+
 typedef struct {
     double device_ms;          /* device time of the contraction (CUDA events) */
     int32_t launches;          /* kernels launched */
@@ -172,6 +180,9 @@ typedef struct {
     double bytes;              /* algorithmic bytes: sum over steps of (|A|+|B|+|C|) * element size */
     size_t arena_bytes;        /* device memory held for intermediates */
     double h2d_bytes;          /* host-to-device bytes copied by the last run (leaf uploads) */
+    int32_t n_local;           /* CTA-resident subtree programs */
+    int32_t n_local_steps;     /* steps executed inside them */
+    int32_t dyn_smem;          /* dynamic shared memory per block of the contraction kernels */
 } tn_run_info;
 
 /* Compile (net, plan, precision) into a device program: per-step layouts, index maps, kernel

@@ -28,17 +28,24 @@ namespace {
 
 struct Compiled {
     std::vector<StepDesc> steps;
+    std::vector<LocalProg> progs;
+    std::vector<LocalStep> lsteps;
+    std::vector<LeafRef> leafrefs;
     std::vector<int64_t> leaf_off;   // [n + 1] element offsets of the leaves
     int32_t n = 0, n_nodes = 0;
     size_t arena_bytes = 0;
     int64_t n_partials = 0;          // double2 entries
     int64_t total_tiles = 0;
+    int32_t dyn_smem = 0;            // largest shared-memory need of a local program
     double flops = 0, bytes = 0;
-    int32_t counts[5] = {0, 0, 0, 0, 0};
+    int32_t counts[6] = {0, 0, 0, 0, 0, 0};
     uint64_t plan_uid = 0, shape_hash = 0;
     // device copies (inside the batch's allocation)
     StepDesc *d_steps = nullptr;
     int64_t *d_leaf_off = nullptr;
+    LocalProg *d_progs = nullptr;
+    LocalStep *d_lsteps = nullptr;
+    LeafRef *d_leafrefs = nullptr;
 };
 
 }  // namespace
@@ -49,6 +56,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
+    int32_t local_budget = -1;        // shared memory per subtree program: -1 auto, 0 none
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -81,6 +89,7 @@ struct tn_batch {
     size_t reset_bytes = 0;
     size_t footprint = 0, arena_total = 0;
     int32_t grid = 0;
+    int32_t dyn_smem = 0;             // dynamic shared memory of the contraction kernels
     // host
     double *h_pinned = nullptr;
     DeviceResult *h_res = nullptr;
@@ -221,7 +230,7 @@ size_t plan_memory(const Plan &plan, int32_t n, const std::vector<size_t> &bytes
         Pool p;
         p.absorb(pool[l]);
         p.absorb(pool[r]);
-        if (s != n - 2) {   // the root's value goes to the result record
+        if (s != n - 2 && bytes[o] > 0) {   // the root's value goes to the result record
             size_t at;
             if (!p.take(bytes[o], at)) {
                 at = top;
@@ -230,7 +239,7 @@ size_t plan_memory(const Plan &plan, int32_t n, const std::vector<size_t> &bytes
             off[o] = at;
         }
         for (int32_t x : {l, r})
-            if (x >= n) p.release(off[x], bytes[x]);
+            if (x >= n && bytes[x] > 0) p.release(off[x], bytes[x]);
         pool[o].blocks.swap(p.blocks);
     }
     return top;
@@ -242,7 +251,106 @@ int32_t rows_per_tile(int64_t M) {
     return 4096;
 }
 
-tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
+// Geometry of one pairwise step: which child plays A (the larger), the free / shared legs with
+// their strides (outermost first), and M, N, K.
+struct Geom {
+    int32_t a = -1, b = -1;
+    int64_t M = 1, N = 1, K = 1;
+    std::vector<int64_t> md, ms, nd, ns, kd, ksa, ksb;
+};
+
+// Local (shared-memory) form of a leg-group list; false if it needs more than kLG groups.
+bool make_lgroups(const std::vector<int64_t> &dim, const std::vector<int64_t> &sa,
+                  const std::vector<int64_t> &sb, bool two, int32_t *o_dim, int32_t *o_sa, int32_t *o_sb,
+                  uint8_t *o_lsb, uint8_t &count, bool &pow2) {
+    Groups g;
+    if (!make_groups(dim, sa, sb, two, g) || g.n > kLG) return false;
+    count = (uint8_t)g.n;
+    for (int32_t i = 0; i < g.n; ++i) {
+        if (g.dim[i] > (1 << 30) || g.sa[i] > (1 << 30) || g.sb[i] > (1 << 30)) return false;
+        o_dim[i] = (int32_t)g.dim[i];
+        o_sa[i] = (int32_t)g.sa[i];
+        if (o_sb) o_sb[i] = (int32_t)g.sb[i];
+        o_lsb[i] = (uint8_t)g.lsb[i];
+    }
+    if (!g.pow2) pow2 = false;
+    return true;
+}
+
+struct LocalPlan {
+    std::vector<int32_t> nodes;      // internal nodes, plan order
+    std::vector<int32_t> leaves;     // leaves, increasing
+    std::vector<int64_t> loc;        // per node of the subtree: shared-memory element offset
+    std::unordered_map<int32_t, int32_t> idx;   // node -> position in loc / slot
+    int64_t leaf_elems = 0, arena_elems = 0;
+    int32_t smem_bytes = 0;
+};
+
+// Can the subtree rooted at v run in one block within `budget` bytes of dynamic shared memory?
+// Simulates its sequential execution (plan order) with a best-fit allocator.
+bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &geo,
+               const std::vector<int64_t> &size, int32_t elem, int32_t budget, LocalPlan &lp) {
+    lp = LocalPlan();
+    std::vector<int32_t> stack{v};
+    while (!stack.empty()) {
+        int32_t x = stack.back();
+        stack.pop_back();
+        if (x < n) { lp.leaves.push_back(x); continue; }
+        lp.nodes.push_back(x);
+        stack.push_back(plan.steps[x - n][0]);
+        stack.push_back(plan.steps[x - n][1]);
+    }
+    std::sort(lp.nodes.begin(), lp.nodes.end());
+    std::sort(lp.leaves.begin(), lp.leaves.end());
+    const int64_t slots = (int64_t)lp.nodes.size() + (int64_t)lp.leaves.size();
+    if (slots > 32000) return false;
+    const int64_t fixed = 2 * (int64_t)sizeof(LocalStep) + (8 * slots + 15) / 16 * 16;
+    for (int32_t x : lp.nodes) {
+        const Geom &g = geo[x - n];
+        if (g.M > (1 << 30) || g.N > (1 << 30) || g.K > (1 << 30)) return false;
+    }
+    int64_t pos = 0;
+    for (int32_t t : lp.leaves) {
+        lp.idx[t] = (int32_t)lp.loc.size();
+        lp.loc.push_back(pos);
+        pos += size[t];
+    }
+    lp.leaf_elems = (pos + 1) / 2 * 2;   // keep the arena 16-byte aligned
+    if (fixed + lp.leaf_elems * elem > budget) return false;
+    Pool pool;
+    int64_t top = 0;
+    std::unordered_map<int32_t, int64_t> asz;
+    for (int32_t x : lp.nodes) {
+        const int64_t sz = (size[x] + 1) / 2 * 2;
+        size_t at;
+        if (!pool.take((size_t)sz, at)) {
+            at = (size_t)top;
+            top += sz;
+        }
+        lp.idx[x] = (int32_t)lp.loc.size();
+        lp.loc.push_back(lp.leaf_elems + (int64_t)at);
+        asz[x] = sz;
+        for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
+            if (c >= n) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
+        if (fixed + (lp.leaf_elems + top) * elem > budget) return false;
+    }
+    lp.arena_elems = top;
+    lp.smem_bytes = (int32_t)(fixed + (lp.leaf_elems + top) * elem);
+    if (lp.loc.back() + size[v] > (1LL << 30)) return false;
+    // every step must fit the compact descriptor
+    for (int32_t x : lp.nodes) {
+        const Geom &g = geo[x - n];
+        LocalStep ls;
+        bool p2 = true;
+        if (!make_lgroups(g.md, g.ms, g.ms, false, ls.m_dim, ls.m_str, nullptr, ls.m_lsb, ls.nm, p2) ||
+            !make_lgroups(g.nd, g.ns, g.ns, false, ls.n_dim, ls.n_str, nullptr, ls.n_lsb, ls.nn, p2) ||
+            !make_lgroups(g.kd, g.ksa, g.ksb, true, ls.k_dim, ls.k_sa, ls.k_sb, ls.k_lsb, ls.nk, p2))
+            return false;
+    }
+    return true;
+}
+
+tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget) {
     const int32_t n = net.n, nn = 2 * n - 1;
     c.n = n;
     c.n_nodes = nn;
@@ -254,76 +362,111 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
     }
     c.leaf_off.assign(net.data_off.begin(), net.data_off.end());
     const size_t esz = (size_t)elem;
-    // first pass: sizes of all nodes (layouts follow in the main pass)
-    {
-        std::vector<std::vector<int32_t>> legs(nn);
-        for (int32_t t = 0; t < n; ++t) legs[t] = net.legs[t];
-        for (int32_t s = 0; s < n - 1; ++s) {
-            const int32_t l = plan.steps[s][0], r = plan.steps[s][1], o = n + s;
-            legs_symdiff(legs[l], legs[r], legs[o]);
-            int64_t sz = 1;
-            for (int32_t e : legs[o]) sz *= net.edim[e];
-            size[o] = sz;
-        }
-    }
-    std::vector<size_t> bytes(nn, 0), arena_off;
-    for (int32_t v = n; v < nn; ++v) bytes[v] = align_up((size_t)size[v] * esz, 256);
-    c.arena_bytes = std::max(plan_memory(plan, n, bytes, arena_off), (size_t)256);
-    std::vector<int32_t> producer(nn, -1), level(nn, 0);   // step index producing each node
-    c.steps.clear();
-    c.steps.reserve(n);
+    // pass 1: layouts and geometry of every step
+    std::vector<Geom> geo(std::max(n - 1, 0));
     for (int32_t s = 0; s < n - 1; ++s) {
         const int32_t l = plan.steps[s][0], r = plan.steps[s][1], o = n + s;
-        const bool root = (s == n - 2);
-        const int32_t a = size[l] >= size[r] ? l : r, b = (a == l) ? r : l;
-        const auto &LA = layout[a], &LB = layout[b];
+        Geom &g = geo[s];
+        g.a = size[l] >= size[r] ? l : r;
+        g.b = (g.a == l) ? r : l;
+        const auto &LA = layout[g.a], &LB = layout[g.b];
         std::vector<int64_t> strA(LA.size()), strB(LB.size());
         int64_t acc = 1;
         for (int32_t i = (int32_t)LA.size() - 1; i >= 0; --i) { strA[i] = acc; acc *= net.edim[LA[i]]; }
         acc = 1;
         for (int32_t i = (int32_t)LB.size() - 1; i >= 0; --i) { strB[i] = acc; acc *= net.edim[LB[i]]; }
-        std::vector<int64_t> md, ms, nd, ns, kd, ksa, ksb, none;
         std::vector<int32_t> out;
-        int64_t M = 1, N = 1, K = 1;
         for (size_t i = 0; i < LA.size(); ++i) {
             const int32_t e = LA[i];
             auto jt = std::find(LB.begin(), LB.end(), e);
             if (jt == LB.end()) {
-                md.push_back(net.edim[e]); ms.push_back(strA[i]); out.push_back(e); M *= net.edim[e];
+                g.md.push_back(net.edim[e]); g.ms.push_back(strA[i]); out.push_back(e); g.M *= net.edim[e];
             } else {
-                kd.push_back(net.edim[e]); ksa.push_back(strA[i]); ksb.push_back(strB[jt - LB.begin()]);
-                K *= net.edim[e];
+                g.kd.push_back(net.edim[e]); g.ksa.push_back(strA[i]); g.ksb.push_back(strB[jt - LB.begin()]);
+                g.K *= net.edim[e];
             }
         }
         for (size_t i = 0; i < LB.size(); ++i) {
             const int32_t e = LB[i];
             if (std::find(LA.begin(), LA.end(), e) == LA.end()) {
-                nd.push_back(net.edim[e]); ns.push_back(strB[i]); out.push_back(e); N *= net.edim[e];
+                g.nd.push_back(net.edim[e]); g.ns.push_back(strB[i]); out.push_back(e); g.N *= net.edim[e];
             }
         }
         layout[o] = out;
-        size[o] = M * N;
-        if (root && M * N != 1) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+        size[o] = g.M * g.N;
+        if (s == n - 2 && g.M * g.N != 1)
+            return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+        c.flops += 8.0 * (double)g.M * (double)g.N * (double)g.K;
+        c.bytes += (double)(size[g.a] + size[g.b] + size[o]) * (double)esz;
+    }
+    // pass 2: CTA-resident subtree programs -- the maximal subtrees that fit the budget
+    std::vector<int32_t> prog_of(nn, -1);     // program index for every internal node inside one
+    std::vector<LocalPlan> lplans;
+    std::vector<int32_t> proot;
+    if (local_budget > 0 && n > 1) {
+        std::vector<int32_t> stack{nn - 1};
+        while (!stack.empty()) {
+            const int32_t v = stack.back();
+            stack.pop_back();
+            if (v < n) continue;
+            LocalPlan lp;
+            if (local_fit(v, n, plan, geo, size, elem, local_budget, lp)) {
+                for (int32_t x : lp.nodes) prog_of[x] = (int32_t)proot.size();
+                proot.push_back(v);
+                lplans.push_back(std::move(lp));
+            } else {
+                stack.push_back(plan.steps[v - n][0]);
+                stack.push_back(plan.steps[v - n][1]);
+            }
+        }
+    }
+    std::vector<char> is_proot(nn, 0);
+    for (int32_t v : proot) is_proot[v] = 1;
+    // global memory: outputs of global steps and of programs (not the intermediates of programs)
+    std::vector<size_t> bytes(nn, 0), arena_off;
+    for (int32_t v = n; v < nn; ++v)
+        if (prog_of[v] < 0 || is_proot[v]) bytes[v] = align_up((size_t)size[v] * esz, 256);
+    c.arena_bytes = std::max(plan_memory(plan, n, bytes, arena_off), (size_t)256);
+    // pass 3: the global step list (plan order), programs as single pseudo-steps
+    std::vector<int32_t> producer(nn, -1), level(nn, 0);
+    c.steps.clear();
+    for (int32_t s = 0; s < n - 1; ++s) {
+        const int32_t o = n + s;
+        if (prog_of[o] >= 0 && !is_proot[o]) continue;
+        const Geom &g = geo[s];
+        const bool root = (s == n - 2);
         StepDesc d;
         std::memset(&d, 0, sizeof(d));
-        d.M = M; d.N = N; d.K = K;
-        d.node_a = a; d.node_b = b; d.node_c = o;
-        if (!make_groups(md, ms, none, false, d.m) || !make_groups(nd, ns, none, false, d.n) ||
-            !make_groups(kd, ksa, ksb, true, d.k))
+        d.M = g.M; d.N = g.N; d.K = g.K;
+        d.node_a = g.a; d.node_b = g.b; d.node_c = o;
+        d.c_off = (int64_t)(arena_off[o] / esz);
+        if (is_proot[o]) {
+            d.kind = STEP_LOCAL;
+            d.ntiles = 1;
+            d.tile_rows = prog_of[o];
+            d.dep0 = d.dep1 = -1;
+            d.level = 1;
+            if (root) d.flags |= FLAG_ROOT | FLAG_NO_C;
+            c.steps.push_back(d);
+            c.counts[STEP_LOCAL]++;
+            producer[o] = (int32_t)c.steps.size() - 1;
+            level[o] = 1;
+            continue;
+        }
+        if (!make_groups(g.md, g.ms, g.ms, false, d.m) || !make_groups(g.nd, g.ns, g.ns, false, d.n) ||
+            !make_groups(g.kd, g.ksa, g.ksb, true, d.k))
             return fail(TN_EUNSUPPORTED, "step " + std::to_string(s) + " has more than 32 leg groups");
         auto where = [&](int32_t v, int64_t &off) -> bool {
             if (v < n) { off = c.leaf_off[v]; return true; }
             off = (int64_t)(arena_off[v] / esz);
             return false;
         };
-        if (where(a, d.a_off)) d.flags |= FLAG_A_LEAF;
-        if (where(b, d.b_off)) d.flags |= FLAG_B_LEAF;
-        d.c_off = (int64_t)(arena_off[o] / esz);
-        d.dep0 = producer[a];
-        d.dep1 = producer[b];
-        d.level = 1 + std::max(level[a], level[b]);
-        c.flops += 8.0 * (double)M * (double)N * (double)K;
-        c.bytes += (double)(size[a] + size[b] + size[o]) * (double)esz;
+        if (where(g.a, d.a_off)) d.flags |= FLAG_A_LEAF;
+        if (where(g.b, d.b_off)) d.flags |= FLAG_B_LEAF;
+        d.dep0 = producer[g.a];
+        d.dep1 = producer[g.b];
+        d.level = 1 + std::max(level[g.a], level[g.b]);
+        const int64_t M = g.M, N = g.N, K = g.K;
         const bool dot = root || (M * N <= kDotMaxOut && K > kRowsMaxK);
         if (dot) {
             StepDesc p = d;
@@ -362,6 +505,69 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem) {
         producer[o] = (int32_t)c.steps.size() - 1;
         level[o] = c.steps.back().level;
     }
+    // pass 4: the programs' compact step lists
+    c.progs.clear();
+    c.lsteps.clear();
+    c.leafrefs.clear();
+    c.dyn_smem = 0;
+    for (size_t pi = 0; pi < proot.size(); ++pi) {
+        const LocalPlan &lp = lplans[pi];
+        const int32_t v = proot[pi];
+        LocalProg P;
+        std::memset(&P, 0, sizeof(P));
+        P.first_step = (int32_t)c.lsteps.size();
+        P.n_steps = (int32_t)lp.nodes.size();
+        P.first_leaf = (int32_t)c.leafrefs.size();
+        P.n_leaves = (int32_t)lp.leaves.size();
+        P.n_slots = (int32_t)lp.loc.size();
+        P.smem_bytes = lp.smem_bytes;
+        P.root_node = v;
+        P.root_slot = lp.idx.at(v);
+        P.root_smem_off = (int32_t)lp.loc[lp.idx.at(v)];
+        P.root_size = (int32_t)size[v];
+        P.root_c_off = (int64_t)(arena_off[v] / esz);
+        P.flags = (v == nn - 1) ? LFLAG_JOB_ROOT : 0;
+        for (int32_t t : lp.leaves) {
+            LeafRef r;
+            r.global_off = (int32_t)c.leaf_off[t];
+            r.count = (int32_t)size[t];
+            r.smem_off = (int32_t)lp.loc[lp.idx.at(t)];
+            r.slot = lp.idx.at(t);
+            r.node = t;
+            c.leafrefs.push_back(r);
+        }
+        for (int32_t x : lp.nodes) {
+            const Geom &g = geo[x - n];
+            LocalStep ls;
+            std::memset(&ls, 0, sizeof(ls));
+            ls.M = (int32_t)g.M; ls.N = (int32_t)g.N; ls.K = (int32_t)g.K;
+            ls.a_off = (int32_t)lp.loc[lp.idx.at(g.a)];
+            ls.b_off = (int32_t)lp.loc[lp.idx.at(g.b)];
+            ls.c_off = (int32_t)lp.loc[lp.idx.at(x)];
+            ls.sa = (int16_t)lp.idx.at(g.a);
+            ls.sb = (int16_t)lp.idx.at(g.b);
+            ls.sc = (int16_t)lp.idx.at(x);
+            bool p2 = true;
+            make_lgroups(g.md, g.ms, g.ms, false, ls.m_dim, ls.m_str, nullptr, ls.m_lsb, ls.nm, p2);
+            make_lgroups(g.nd, g.ns, g.ns, false, ls.n_dim, ls.n_str, nullptr, ls.n_lsb, ls.nn, p2);
+            make_lgroups(g.kd, g.ksa, g.ksb, true, ls.k_dim, ls.k_sa, ls.k_sb, ls.k_lsb, ls.nk, p2);
+            ls.pow2 = p2 ? 1 : 0;
+            if (x == nn - 1) {
+                ls.mode = LMODE_REDUCE;
+                ls.flags = LFLAG_JOB_ROOT;
+            } else if (g.N <= kRowsMaxN && g.K <= kRowsMaxK) {
+                ls.mode = LMODE_ROWS;
+            } else if (g.M >= 32 && g.N >= 32) {
+                ls.mode = LMODE_GEMM;
+            } else {
+                ls.mode = LMODE_REDUCE;
+            }
+            c.lsteps.push_back(ls);
+        }
+        c.dyn_smem = std::max(c.dyn_smem, P.smem_bytes);
+        c.progs.push_back(P);
+    }
+    c.counts[5] = (int32_t)c.lsteps.size();
     c.total_tiles = 0;
     for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
@@ -393,14 +599,14 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         }
         e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess)
-            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, st);
+            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->dyn_smem, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
     } else {
         for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb) {
             const Compiled &c = b->comp[b->job_comp[jb]];
             for (size_t s = 0; e == cudaSuccess && s < c.steps.size(); ++s)
-                e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], st);
+                e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], b->dyn_smem, st);
         }
     }
     for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb)
@@ -463,6 +669,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->uploaded.assign(n, ~0ull);
     b->job_comp.assign(n, -1);
     // compile every distinct (structure, plan) once
+    const int32_t budget = ctx->local_budget >= 0 ? ctx->local_budget : local_smem_budget(b->c128, 2);
     std::unordered_map<std::string, int32_t> seen;
     for (int32_t i = 0; i < n; ++i) {
         const Net &net = nets[i]->impl;
@@ -471,7 +678,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         auto it = seen.find(key);
         if (it != seen.end()) { b->job_comp[i] = it->second; continue; }
         Compiled c;
-        tn_status s = compile(c, net, plans[i]->impl, b->elem);
+        tn_status s = compile(c, net, plans[i]->impl, b->elem, budget);
         if (s != TN_OK) { batch_destroy(b); return s; }
         c.plan_uid = plans[i]->impl.uid;
         c.shape_hash = h;
@@ -483,9 +690,14 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max(bytes, (size_t)16), 256); return o; };
     std::vector<size_t> o_steps(b->comp.size()), o_loff(b->comp.size());
+    std::vector<size_t> o_progs(b->comp.size()), o_lsteps(b->comp.size()), o_lrefs(b->comp.size());
     for (size_t ci = 0; ci < b->comp.size(); ++ci) {
         o_steps[ci] = carve(sizeof(StepDesc) * b->comp[ci].steps.size());
         o_loff[ci] = carve(sizeof(int64_t) * b->comp[ci].leaf_off.size());
+        o_progs[ci] = carve(sizeof(LocalProg) * b->comp[ci].progs.size());
+        o_lsteps[ci] = carve(sizeof(LocalStep) * b->comp[ci].lsteps.size());
+        o_lrefs[ci] = carve(sizeof(LeafRef) * b->comp[ci].leafrefs.size());
+        b->dyn_smem = std::max(b->dyn_smem, b->comp[ci].dyn_smem);
     }
     b->leaf64_off.assign(n, 0);
     int64_t leaf_total = 0;
@@ -551,6 +763,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     for (size_t ci = 0; ci < b->comp.size(); ++ci) {
         b->comp[ci].d_steps = reinterpret_cast<StepDesc *>(base + o_steps[ci]);
         b->comp[ci].d_leaf_off = reinterpret_cast<int64_t *>(base + o_loff[ci]);
+        b->comp[ci].d_progs = reinterpret_cast<LocalProg *>(base + o_progs[ci]);
+        b->comp[ci].d_lsteps = reinterpret_cast<LocalStep *>(base + o_lsteps[ci]);
+        b->comp[ci].d_leafrefs = reinterpret_cast<LeafRef *>(base + o_lrefs[ci]);
     }
     b->d_leaf64 = reinterpret_cast<double2 *>(base + o_leaf64);
     char *d_leaf = base + o_leaf;
@@ -573,6 +788,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         j.done = reinterpret_cast<int32_t *>(base + o_done[i]);
         j.result = b->d_res + i;
         j.steps = c.d_steps;
+        j.progs = c.d_progs;
+        j.lsteps = c.d_lsteps;
+        j.leafrefs = c.d_leafrefs;
         j.n_steps = (int32_t)c.steps.size();
         j.n_leaves = c.n;
     }
@@ -590,6 +808,15 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c.d_leaf_off, c.leaf_off.data(), sizeof(int64_t) * c.leaf_off.size(),
                                 cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !c.progs.empty())
+            e = cudaMemcpyAsync(c.d_progs, c.progs.data(), sizeof(LocalProg) * c.progs.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !c.lsteps.empty())
+            e = cudaMemcpyAsync(c.d_lsteps, c.lsteps.data(), sizeof(LocalStep) * c.lsteps.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !c.leafrefs.empty())
+            e = cudaMemcpyAsync(c.d_leafrefs, c.leafrefs.data(), sizeof(LeafRef) * c.leafrefs.size(),
+                                cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(JobPtrs) * (size_t)n, cudaMemcpyHostToDevice, st);
@@ -598,7 +825,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
-    b->grid = persistent_grid(b->c128);
+    b->grid = persistent_grid(b->c128, b->dyn_smem);
     if (b->grid <= 0) { batch_destroy(b); return fail(TN_ECUDA, "occupancy query failed"); }
     tn_status s = TN_OK;
     for (int32_t i = 0; i < n && s == TN_OK; ++i) s = upload_leaves(b, i);
@@ -618,7 +845,10 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->info.n_tile += c.counts[STEP_TILE];
         b->info.n_dot += c.counts[STEP_DOTP];
         b->info.n_tc += c.counts[STEP_TC];
+        b->info.n_local += c.counts[STEP_LOCAL];
+        b->info.n_local_steps += c.counts[5];
     }
+    b->info.dyn_smem = b->dyn_smem;
     b->info.arena_bytes = b->arena_total;
     if (b->mode == TN_EXEC_PERSISTENT) {
         b->info.launches = 2;   // leaf conversion + the persistent kernel
@@ -757,6 +987,19 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
         c->own_stream = true;
     }
     *out = c;
+    return TN_OK;
+}
+
+tn_status tn_ctx_set_local_budget(tn_ctx *c, int32_t bytes) {
+    if (!c) return fail(TN_EINVAL, "NULL ctx");
+    if (bytes < -1) return fail(TN_EINVAL, "bytes must be -1 (automatic), 0 (off) or positive");
+    if (c->cached) {
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+        batch_destroy(c->cached);
+        c->cached = nullptr;
+    }
+    c->local_budget = bytes;
     return TN_OK;
 }
 

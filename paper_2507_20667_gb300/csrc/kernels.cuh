@@ -27,7 +27,10 @@ struct Groups {
 
 // Kernel classes.  A contraction producing at most 16 outputs from a long shared index is split
 // in two steps: DOTP reduces K-chunks into FP64 partials, DOTF sums them in a fixed order.
-enum StepKind : int32_t { STEP_ROWS = 0, STEP_TILE = 1, STEP_DOTP = 2, STEP_DOTF = 3, STEP_TC = 4 };
+enum StepKind : int32_t {
+    STEP_ROWS = 0, STEP_TILE = 1, STEP_DOTP = 2, STEP_DOTF = 3, STEP_TC = 4,
+    STEP_LOCAL = 5      // a whole subtree run by one block in shared memory (tile_rows = program)
+};
 
 enum StepFlags : int32_t {
     FLAG_A_LEAF = 1,    // A lives in the job's leaf buffer (else in its arena)
@@ -51,6 +54,43 @@ struct StepDesc {
     Groups m, n, k;
 };
 
+// ---- CTA-resident subtree programs -------------------------------------------------------------
+// A local step is the same contraction as a StepDesc with every operand in shared memory (int32
+// element offsets) and at most kLG fused groups per index class.
+constexpr int kLG = 6;
+enum LocalMode : uint8_t { LMODE_ROWS = 0, LMODE_GEMM = 1, LMODE_REDUCE = 2 };
+enum LocalFlags : int32_t { LFLAG_JOB_ROOT = 1 };
+
+struct LocalStep {
+    int32_t M, N, K;
+    int32_t a_off, b_off, c_off;        // shared-memory element offsets
+    int16_t sa, sb, sc;                 // scale slots of A, B and C
+    uint8_t nm, nn, nk, pow2, mode, flags;
+    int32_t m_dim[kLG], m_str[kLG];     // free legs of A (stride in A)
+    int32_t n_dim[kLG], n_str[kLG];     // free legs of B (stride in B)
+    int32_t k_dim[kLG], k_sa[kLG], k_sb[kLG];
+    uint8_t m_lsb[kLG], n_lsb[kLG], k_lsb[kLG];
+    uint8_t pad[2];
+};
+static_assert(sizeof(LocalStep) == 224, "LocalStep layout");
+
+struct LocalProg {
+    int32_t first_step, n_steps;        // into the job's LocalStep array
+    int32_t first_leaf, n_leaves;       // into the job's LeafRef array
+    int32_t n_slots;                    // nodes of the subtree (leaves and intermediates)
+    int32_t smem_bytes;                 // dynamic shared memory the program needs
+    int32_t root_node, root_slot;
+    int32_t root_smem_off, root_size;   // where the subtree's value sits in shared memory
+    int64_t root_c_off;                 // and where it goes in the job's arena
+    int32_t flags;                      // LFLAG_JOB_ROOT: the subtree is the whole network
+    int32_t pad;
+};
+
+struct LeafRef {
+    int32_t global_off, count;          // element offset and size in the job's leaf buffer
+    int32_t smem_off, slot, node;
+};
+
 // Everything one contraction (a "job") owns on the device.  Several jobs may share one compiled
 // step list (same network structure and plan) and differ only in their leaves.
 struct JobPtrs {
@@ -64,6 +104,9 @@ struct JobPtrs {
     int32_t *done;           // [n_steps] completed tiles of each step (persistent execution)
     void *result;            // DeviceResult
     const StepDesc *steps;   // the job's compiled step list
+    const LocalProg *progs;  // CTA-resident subtree programs
+    const LocalStep *lsteps;
+    const LeafRef *leafrefs;
     int32_t n_steps;
     int32_t n_leaves;
 };
@@ -85,12 +128,16 @@ struct WorkItem {
 cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jobs,
                                 int32_t max_leaves, cudaStream_t stream);
 cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const JobPtrs &job,
-                        cudaStream_t stream);
+                        int32_t dyn_smem, cudaStream_t stream);
 cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
-                              int64_t n_work, uint32_t *counter, int32_t grid, cudaStream_t stream);
-int32_t persistent_grid(bool c128);
+                              int64_t n_work, uint32_t *counter, int32_t grid, int32_t dyn_smem,
+                              cudaStream_t stream);
+// Co-resident grid of the persistent kernel with `dyn_smem` bytes of dynamic shared memory.
+int32_t persistent_grid(bool c128, int32_t dyn_smem);
+// Dynamic shared memory a local program may use so that `blocks_per_sm` persistent blocks fit.
+int32_t local_smem_budget(bool c128, int32_t blocks_per_sm);
 cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int64_t n_upd,
                                    double2 *leaf64, cudaStream_t stream);
 cudaError_t launch_permute(const void *src, void *dst, int32_t elem_bytes, int32_t rank,

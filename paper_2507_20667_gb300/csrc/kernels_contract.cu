@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "local_ops.cuh"
 #include "tile_ops.cuh"
 
 namespace tn {
@@ -72,13 +73,21 @@ __global__ void __launch_bounds__(128) k_leaf_convert(const JobPtrs *__restrict_
 }
 
 template <typename T>
+__device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
+                                         float *red, char *dyn) {
+    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, reinterpret_cast<double2 *>(smem));
+    else run_tile<T>(d, tile, j, smem, red);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ steps, int32_t step,
                                                    JobPtrs job) {
+    extern __shared__ __align__(16) char dyn[];
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
     load_desc(d, steps + step);
-    run_tile<T>(d, blockIdx.x, job, smem, red);
+    run_item<T>(d, blockIdx.x, job, smem, red, dyn);
 }
 
 template <typename T>
@@ -86,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
                                                       const WorkItem *__restrict__ work,
                                                       int64_t n_work, uint32_t *counter) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
+    extern __shared__ __align__(16) char dyn[];
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         }
         __syncthreads();
         load_desc(d, j.steps + it.step);
-        if (s_ok) run_tile<T>(d, it.tile, j, smem, red);
+        if (s_ok) run_item<T>(d, it.tile, j, smem, red, dyn);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(j.done + it.step, 1);
@@ -144,11 +154,21 @@ cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jo
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtrs &job,
+// Kernels that take more than 48 KB of dynamic shared memory must opt in once per size.
+template <typename K>
+cudaError_t allow_dyn_smem(K kernel, int32_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtrs &job, int32_t dyn_smem,
                         cudaStream_t stream) {
     if (h.ntiles <= 0) return cudaErrorInvalidValue;
-    if (c128) k_step<double><<<(unsigned)h.ntiles, kThreads, 0, stream>>>(job.steps, step, job);
-    else k_step<float><<<(unsigned)h.ntiles, kThreads, 0, stream>>>(job.steps, step, job);
+    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : 0;
+    cudaError_t e = c128 ? allow_dyn_smem(k_step<double>, dyn) : allow_dyn_smem(k_step<float>, dyn);
+    if (e != cudaSuccess) return e;
+    if (c128) k_step<double><<<(unsigned)h.ntiles, kThreads, dyn, stream>>>(job.steps, step, job);
+    else k_step<float><<<(unsigned)h.ntiles, kThreads, dyn, stream>>>(job.steps, step, job);
     return cudaGetLastError();
 }
 
@@ -167,23 +187,39 @@ cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int6
     return cudaGetLastError();
 }
 
-int32_t persistent_grid(bool c128) {
+int32_t persistent_grid(bool c128, int32_t dyn_smem) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaError_t e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, 0);
+    cudaError_t e = c128 ? allow_dyn_smem(k_persist<double>, dyn_smem) : allow_dyn_smem(k_persist<float>, dyn_smem);
+    if (e != cudaSuccess) return 0;
+    e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, dyn_smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, dyn_smem);
     if (e != cudaSuccess) return 0;
     return sms * per_sm;
 }
 
+int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
+    int dev = 0, per_sm = 0, per_block = 0, reserved = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) return 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = c128 ? cudaFuncGetAttributes(&fa, k_persist<double>) : cudaFuncGetAttributes(&fa, k_persist<float>);
+    if (e != cudaSuccess) return 0;
+    int32_t b = per_sm / blocks_per_sm - reserved - (int32_t)fa.sharedSizeBytes;
+    if (b > per_block - (int32_t)fa.sharedSizeBytes) b = per_block - (int32_t)fa.sharedSizeBytes;
+    return b > 0 ? (b / 16) * 16 : 0;
+}
+
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work, int64_t n_work,
-                              uint32_t *counter, int32_t grid, cudaStream_t stream) {
+                              uint32_t *counter, int32_t grid, int32_t dyn_smem, cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
     void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter};
     const void *fn = c128 ? (const void *)k_persist<double> : (const void *)k_persist<float>;
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, 0, stream);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, (size_t)dyn_smem, stream);
 }
 
 }  // namespace tn

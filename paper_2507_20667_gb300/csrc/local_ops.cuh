@@ -1,0 +1,291 @@
+// CTA-resident subtree programs.  A subtree of the contraction tree whose sequential working set
+// (its leaves plus the intermediates alive at any one time) fits a shared-memory budget runs
+// entirely inside one thread block: the block stages the subtree's leaves into shared memory,
+// executes its pairwise steps in plan order with one barrier per step, and writes only the
+// subtree's result to global memory.  This replaces hundreds of tiny global work tiles -- each a
+// claim, a dependency wait and a global round trip -- by on-chip work.
+#pragma once
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tile_ops.cuh"
+
+namespace tn {
+
+__device__ __forceinline__ int32_t lgroup_off(int32_t n, const int32_t *dim, const int32_t *str,
+                                              const uint8_t *lsb, bool pow2, int32_t idx) {
+    int32_t off = 0;
+    if (pow2) {
+        for (int32_t i = 0; i < n; ++i) off += ((idx >> lsb[i]) & (dim[i] - 1)) * str[i];
+    } else {
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t d = idx % dim[i];
+            idx /= dim[i];
+            off += d * str[i];
+        }
+    }
+    return off;
+}
+
+__device__ __forceinline__ void lgroup_off2(const LocalStep &s, int32_t idx, int32_t &oa, int32_t &ob) {
+    oa = 0;
+    ob = 0;
+    if (s.pow2) {
+        for (int32_t i = 0; i < s.nk; ++i) {
+            const int32_t d = (idx >> s.k_lsb[i]) & (s.k_dim[i] - 1);
+            oa += d * s.k_sa[i];
+            ob += d * s.k_sb[i];
+        }
+    } else {
+        for (int32_t i = 0; i < s.nk; ++i) {
+            const int32_t d = idx % s.k_dim[i];
+            idx /= s.k_dim[i];
+            oa += d * s.k_sa[i];
+            ob += d * s.k_sb[i];
+        }
+    }
+}
+
+struct LocalSmem {
+    LocalStep *desc;     // two buffers (double-buffered descriptors)
+    uint32_t *smax;      // [n_slots] max-abs bit pattern of each node of the program
+    int32_t *sexp;       // [n_slots] power-of-two exponent of each node
+    char *data;          // leaves, then the arena of intermediates
+};
+
+__device__ __forceinline__ LocalSmem local_layout(char *dyn, int32_t n_slots) {
+    LocalSmem L;
+    L.desc = reinterpret_cast<LocalStep *>(dyn);
+    L.smax = reinterpret_cast<uint32_t *>(dyn + 2 * sizeof(LocalStep));
+    L.sexp = reinterpret_cast<int32_t *>(L.smax + n_slots);
+    L.data = dyn + 2 * sizeof(LocalStep) + ((8 * (size_t)n_slots + 15) / 16) * 16;
+    return L;
+}
+
+// One step, all operands in shared memory.  Modes:
+//   LMODE_ROWS    N <= 16, K <= 64: a thread owns output rows and keeps the N outputs in registers
+//   LMODE_GEMM    M, N >= 32: 16 x 16 threads, 4 x 4 register tile per thread per 64 x 64 block
+//   LMODE_REDUCE  few outputs, long K: S threads per output split K, FP64 partial sums, shuffle /
+//                 shared-memory reduction; the job's root (the amplitude) always takes this mode
+template <typename T, int NT>
+__device__ __forceinline__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx) {
+    using C = cx_t<T>;
+    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
+    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
+    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t N = s.N, K = s.K;
+    for (int32_t m = threadIdx.x; m < s.M; m += blockDim.x) {
+        const int32_t offA = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, s.pow2, m);
+        C acc[NT];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n] = cmake((T)0, (T)0);
+        for (int32_t k = 0; k < K; ++k) {
+            int32_t ka, kb;
+            lgroup_off2(s, k, ka, kb);
+            const C a = cscale(A[offA + ka], sA);
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+                if (n < N)
+                    cfma(acc[n], a, cscale(B[kb + lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n)], sB));
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+            if (n < N) {
+                const C v = acc[n];
+                Cp[m * N + n] = v;
+                mx = fmaxf(mx, absmax2(v));
+            }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx) {
+    using C = cx_t<T>;
+    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
+    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
+    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t M = s.M, N = s.N, K = s.K;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int32_t m0 = 0; m0 < M; m0 += 64)
+        for (int32_t n0 = 0; n0 < N; n0 += 64) {
+            int32_t ra[4], cb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int32_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * i;
+                ra[i] = m < M ? lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, s.pow2, m) : -1;
+                cb[i] = n < N ? lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n) : -1;
+            }
+            C acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cmake((T)0, (T)0);
+            for (int32_t k = 0; k < K; ++k) {
+                int32_t ka, kb;
+                lgroup_off2(s, k, ka, kb);
+                C a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    a[i] = ra[i] >= 0 ? cscale(A[ra[i] + ka], sA) : cmake((T)0, (T)0);
+                    b[i] = cb[i] >= 0 ? cscale(B[kb + cb[i]], sB) : cmake((T)0, (T)0);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) cfma(acc[i][jj], a[i], b[jj]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int32_t m = m0 + ty + 16 * i;
+                if (m >= M) continue;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int32_t n = n0 + tx + 16 * jj;
+                    if (n < N) {
+                        const C v = acc[i][jj];
+                        Cp[m * N + n] = v;
+                        mx = fmaxf(mx, absmax2(v));
+                    }
+                }
+            }
+        }
+}
+
+// REDUCE: threads are grouped S per output (S a power of two, S <= blockDim); each group splits K
+// and sums in FP64; groups of up to 32 lanes reduce with shuffles, larger ones through `red64`.
+template <typename T>
+__device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
+                                             double2 *red64, const JobPtrs &j, int32_t e_out) {
+    using C = cx_t<T>;
+    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
+    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
+    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t O = s.M * s.N, K = s.K, N = s.N;
+    int32_t S = 1;
+    while (S * 2 * O <= (int32_t)blockDim.x && S < K) S *= 2;
+    const int32_t groups = blockDim.x / S;
+    for (int32_t o0 = 0; o0 < O; o0 += groups) {
+        const int32_t o = o0 + threadIdx.x / S, sub = threadIdx.x % S;
+        double2 acc = make_double2(0, 0);
+        if (o < O) {
+            const int32_t m = o / N, n = o - m * N;
+            const int32_t offA = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, s.pow2, m);
+            const int32_t offB = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n);
+            C run = cmake((T)0, (T)0);
+            int cnt = 0;
+            for (int32_t k = sub; k < K; k += S) {
+                int32_t ka, kb;
+                lgroup_off2(s, k, ka, kb);
+                cfma(run, cscale(A[offA + ka], sA), cscale(B[kb + offB], sB));
+                if (++cnt == 32) {
+                    acc.x += (double)run.x;
+                    acc.y += (double)run.y;
+                    run = cmake((T)0, (T)0);
+                    cnt = 0;
+                }
+            }
+            acc.x += (double)run.x;
+            acc.y += (double)run.y;
+        }
+        // reduce the S partials of each output
+        const int32_t w = S < 32 ? S : 32;
+        for (int off = w / 2; off > 0; off >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, off, w);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, off, w);
+        }
+        if (S > 32) {
+            // one partial per warp, then the first lane of each group sums its warps
+            if ((threadIdx.x & 31) == 0) red64[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (sub == 0) {
+                acc = make_double2(0, 0);
+                for (int32_t q = 0; q < S / 32; ++q) {
+                    const double2 p = red64[(threadIdx.x >> 5) + q];
+                    acc.x += p.x;
+                    acc.y += p.y;
+                }
+            }
+            __syncthreads();
+        }
+        if (sub == 0 && o < O) {
+            if (s.flags & LFLAG_JOB_ROOT) {
+                DeviceResult *r = static_cast<DeviceResult *>(j.result);
+                r->re = acc.x;
+                r->im = acc.y;
+                r->exp2 = e_out;
+            } else {
+                const C v = cmake((T)acc.x, (T)acc.y);
+                Cp[o] = v;
+                mx = fmaxf(mx, absmax2(v));
+            }
+        }
+    }
+}
+
+// Runs local program `prog` of job `j` in the calling block.  `dyn` is the block's dynamic shared
+// memory, laid out by local_layout().
+template <typename T>
+__device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *red64) {
+    using C = cx_t<T>;
+    const LocalProg P = j.progs[prog];
+    const LocalSmem L = local_layout(dyn, P.n_slots);
+    C *data = reinterpret_cast<C *>(L.data);
+    // zero the slots, stage the leaves (one warp per leaf) and the first descriptor
+    for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step);
+        int4 *dst = reinterpret_cast<int4 *>(L.desc);
+        for (int i = threadIdx.x; i < (int)(sizeof(LocalStep) / 16); i += blockDim.x) dst[i] = __ldcg(src + i);
+    }
+    __syncthreads();
+    const C *leaf = static_cast<const C *>(j.leaf);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int32_t l = warp; l < P.n_leaves; l += nw) {
+        const LeafRef r = j.leafrefs[P.first_leaf + l];
+        for (int32_t i = lane; i < r.count; i += 32) data[r.smem_off + i] = __ldcg(leaf + r.global_off + i);
+        if (lane == 0) {
+            L.smax[r.slot] = __ldcg(j.maxbits + r.node);
+            L.sexp[r.slot] = __ldcg(j.exp2 + r.node);
+        }
+    }
+    __syncthreads();
+    for (int32_t st = 0; st < P.n_steps; ++st) {
+        const LocalStep &s = L.desc[st & 1];
+        if (st + 1 < P.n_steps && threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
+            const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step + st + 1);
+            reinterpret_cast<int4 *>(L.desc + ((st + 1) & 1))[threadIdx.x] = __ldcg(src + threadIdx.x);
+        }
+        const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
+        const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+        const int32_t e_out = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
+        float mx = 0.f;
+        switch (s.mode) {
+            case LMODE_ROWS:
+                if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx);
+                else if (s.N <= 2) local_rows<T, 2>(s, L, sA, sB, mx);
+                else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx);
+                else if (s.N <= 8) local_rows<T, 8>(s, L, sA, sB, mx);
+                else local_rows<T, 16>(s, L, sA, sB, mx);
+                break;
+            case LMODE_GEMM: local_gemm<T>(s, L, sA, sB, mx); break;
+            default: local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out); break;
+        }
+        mx = warp_max(mx);
+        if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));
+        if (threadIdx.x == 0) L.sexp[s.sc] = e_out;
+        __syncthreads();
+    }
+    // publish the program's result (unless it was the job's amplitude, already written)
+    if (!(P.flags & LFLAG_JOB_ROOT)) {
+        C *out = reinterpret_cast<C *>(j.arena) + P.root_c_off;
+        for (int32_t i = threadIdx.x; i < P.root_size; i += blockDim.x) out[i] = data[P.root_smem_off + i];
+        if (threadIdx.x == 0) {
+            j.maxbits[P.root_node] = L.smax[P.root_slot];
+            j.exp2[P.root_node] = L.sexp[P.root_slot];
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace tn

@@ -56,7 +56,8 @@ class tn_run_info(ctypes.Structure):
     _fields_ = [("device_ms", ctypes.c_double), ("launches", ctypes.c_int32), ("n_gather", ctypes.c_int32),
                 ("n_tile", ctypes.c_int32), ("n_dot", ctypes.c_int32), ("n_tc", ctypes.c_int32),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
-                ("h2d_bytes", ctypes.c_double)]
+                ("h2d_bytes", ctypes.c_double), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
+                ("dyn_smem", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: (getattr(self, f)) for f, _ in self._fields_}
@@ -80,6 +81,7 @@ _SIGS = {
     "tn_ctx_free": (None, [_P]),
     "tn_ctx_synchronize": (_I32, [_P]),
     "tn_ctx_set_exec_mode": (_I32, [_P, _I32]),
+    "tn_ctx_set_local_budget": (_I32, [_P, _I32]),
     "tn_batch_create": (_I32, [_P, _I32, _P, _P, _I32, ctypes.POINTER(_P)]),
     "tn_batch_run": (_I32, [_P, _P]),
     "tn_batch_results": (_I32, [_P, _P, _P, _P]),
@@ -264,6 +266,10 @@ def tn_ctx_synchronize(ctx: Ctx) -> None:
 
 def tn_ctx_set_exec_mode(ctx: Ctx, mode="persistent") -> None:
     _check(lib.tn_ctx_set_exec_mode(ctx, EXEC_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+
+def tn_ctx_set_local_budget(ctx: Ctx, nbytes: int = -1) -> None:
+    _check(lib.tn_ctx_set_local_budget(ctx, int(nbytes)))
 
 
 def _handle_array(hs):

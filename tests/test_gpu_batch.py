@@ -128,3 +128,25 @@ def test_batch_kernel_timing(tnsa):
     assert 0 < ms < 1000
     info = tnsa.tn_batch_last_info(b)
     assert info["launches"] == 2 and info["flops"] > 0 and info["bytes"] > 0
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_subtree_programs_match_global_path(tnsa, prec):
+    """CTA-resident subtree programs (shared memory) and the all-global step path agree."""
+    circ, x = tni.cfg2()
+    net = tni.amplitude_tn(circ, x)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=4, iterations=300, seed=7,
+                               initial_part=tni.qubit_block_partition(net, 24, 4))
+    res = {}
+    for budget in (-1, 0, 16384):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_local_budget(ctx, budget)
+        m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
+        res[budget] = (complex(m) * 2.0 ** e, info)
+    assert res[-1][1]["n_local"] >= 1 and res[0][1]["n_local"] == 0
+    assert res[16384][1]["n_local"] >= 1
+    tol = 1e-12 if prec == "c128" else 1e-5
+    base = res[0][0]
+    for budget in (-1, 16384):
+        assert abs(res[budget][0] - base) <= tol * abs(base) * 10
