@@ -121,6 +121,22 @@ tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **
 tn_status tn_plan_import(const tn_net *net, int32_t k, const int32_t *part, int32_t n_steps,
                          const int32_t *steps, tn_plan **out);
 
+/* What the program compiler makes of (net, plan, precision) with a given shared-memory budget for
+ * subtree programs (see tn_ctx_set_local_budget; here 0 = none and > 0 = that many bytes), without
+ * touching a device.  Errors: TN_EINVAL, TN_EUNSUPPORTED (open network). */
+typedef struct {
+    int32_t global_steps;      /* entries of the global dataflow step list */
+    int32_t n_rows, n_tile, n_dot, n_local;   /* global steps per kernel class; subtree programs */
+    int32_t n_local_steps;     /* pairwise steps executed inside subtree programs */
+    int32_t max_local_smem;    /* largest shared-memory need of a subtree program (bytes) */
+    int32_t levels;            /* dependency levels of the global step list */
+    int64_t total_tiles;       /* work tiles of one contraction */
+    size_t arena_bytes;        /* device memory for intermediates of one contraction */
+    double flops, bytes;       /* algorithmic flops (8 * con_serial) and bytes of one contraction */
+} tn_compile_stats;
+tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_precision prec,
+                                int32_t local_budget, tn_compile_stats *out);
+
 /* Exact counts of the plan's tree B (Section 3):
  *   total_ops = con_serial(B) (Eq. 3.2), crit_ops = con_dist(B, K) (Eq. 3.5, con = con_serial,
  *   comm = 0), mem_elems = mem(B) (Eq. 3.1).  Any pointer may be NULL. */
@@ -245,6 +261,14 @@ tn_status tn_batch_last_info(const tn_batch *b, tn_run_info *info);
  * Errors: TN_EINVAL, TN_EUNSUPPORTED (graph mode), TN_ECUDA. */
 tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms);
 void tn_batch_free(tn_batch *b);
+
+/* Diagnostics: cycle accounting of the persistent kernel (costs a few atomics per work item; off
+ * by default).  tn_batch_profile waits for the stream and returns 16 accumulated SM-cycle sums and
+ * item counts since profiling was switched on: [0..5] work items by kernel class (ROWS, TILE,
+ * DOTP, DOTF, -, subtree program), [8..10] steps inside subtree programs by mode (rows, gemm,
+ * reduce), [12] dependency waits.  Errors: TN_EINVAL, TN_ECUDA. */
+tn_status tn_batch_set_profiling(tn_batch *b, int32_t on);
+tn_status tn_batch_profile(tn_batch *b, int64_t *cycles, int64_t *items);
 
 /* One-shot: create a batch, run it once, return the results on the host, free it. */
 tn_status tn_batch_contract(tn_ctx *ctx, int32_t n, const tn_net *const *nets,

@@ -38,7 +38,7 @@ struct Compiled {
     int64_t total_tiles = 0;
     int32_t dyn_smem = 0;            // largest shared-memory need of a local program
     double flops = 0, bytes = 0;
-    int32_t counts[6] = {0, 0, 0, 0, 0, 0};
+    int32_t counts[7] = {0, 0, 0, 0, 0, 0, 0};   // by StepKind; [6] = steps inside programs
     uint64_t plan_uid = 0, shape_hash = 0;
     // device copies (inside the batch's allocation)
     StepDesc *d_steps = nullptr;
@@ -90,6 +90,7 @@ struct tn_batch {
     size_t footprint = 0, arena_total = 0;
     int32_t grid = 0;
     int32_t dyn_smem = 0;             // dynamic shared memory of the contraction kernels
+    long long *d_prof = nullptr;      // optional per-kind cycle counters (tn_batch_set_profiling)
     // host
     double *h_pinned = nullptr;
     DeviceResult *h_res = nullptr;
@@ -567,7 +568,7 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
         c.dyn_smem = std::max(c.dyn_smem, P.smem_bytes);
         c.progs.push_back(P);
     }
-    c.counts[5] = (int32_t)c.lsteps.size();
+    c.counts[6] = (int32_t)c.lsteps.size();
     c.total_tiles = 0;
     for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
@@ -599,7 +600,8 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         }
         e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess)
-            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->dyn_smem, st);
+            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->dyn_smem,
+                              b->d_prof, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
     } else {
@@ -644,6 +646,7 @@ void batch_destroy(tn_batch *b) {
     if (b->h_res) cudaFreeHost(b->h_res);
     if (b->h_upd) cudaFreeHost(b->h_upd);
     if (b->d_upd) cudaFree(b->d_upd);
+    if (b->d_prof) cudaFree(b->d_prof);
     delete b;
 }
 
@@ -846,7 +849,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->info.n_dot += c.counts[STEP_DOTP];
         b->info.n_tc += c.counts[STEP_TC];
         b->info.n_local += c.counts[STEP_LOCAL];
-        b->info.n_local_steps += c.counts[5];
+        b->info.n_local_steps += c.counts[6];
     }
     b->info.dyn_smem = b->dyn_smem;
     b->info.arena_bytes = b->arena_total;
@@ -990,6 +993,35 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
     return TN_OK;
 }
 
+tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_precision prec,
+                                int32_t local_budget, tn_compile_stats *out) {
+    if (!net || !plan || !out) return fail(TN_EINVAL, "NULL argument");
+    if (prec < TN_C128 || prec > TN_BF16_SPLIT) return fail(TN_EINVAL, "unknown precision");
+    if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
+    if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+    Compiled c;
+    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget);
+    if (s != TN_OK) return s;
+    tn_compile_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.global_steps = (int32_t)c.steps.size();
+    st.n_rows = c.counts[STEP_ROWS];
+    st.n_tile = c.counts[STEP_TILE];
+    st.n_dot = c.counts[STEP_DOTP];
+    st.n_local = c.counts[STEP_LOCAL];
+    st.n_local_steps = c.counts[6];
+    st.max_local_smem = c.dyn_smem;
+    st.total_tiles = c.total_tiles;
+    st.arena_bytes = c.arena_bytes;
+    st.flops = c.flops;
+    st.bytes = c.bytes;
+    int32_t lv = 0;
+    for (const StepDesc &d : c.steps) lv = std::max(lv, d.level);
+    st.levels = lv;
+    *out = st;
+    return TN_OK;
+}
+
 tn_status tn_ctx_set_local_budget(tn_ctx *c, int32_t bytes) {
     if (!c) return fail(TN_EINVAL, "NULL ctx");
     if (bytes < -1) return fail(TN_EINVAL, "bytes must be -1 (automatic), 0 (off) or positive");
@@ -1080,6 +1112,31 @@ tn_status tn_batch_run(tn_batch *b, void *d_results) {
 tn_status tn_batch_results(tn_batch *b, double *amps, int32_t *exp2, int32_t *status) {
     if (!b) return fail(TN_EINVAL, "NULL batch");
     return batch_results(b, amps, exp2, status);
+}
+
+tn_status tn_batch_set_profiling(tn_batch *b, int32_t on) {
+    if (!b) return fail(TN_EINVAL, "NULL batch");
+    CK(cudaSetDevice(b->ctx->device));
+    CK(cudaStreamSynchronize(b->ctx->stream));
+    if (on && !b->d_prof) {
+        CK(cudaMalloc(&b->d_prof, sizeof(long long) * 2 * kProfSlots));
+        CK(cudaMemset(b->d_prof, 0, sizeof(long long) * 2 * kProfSlots));
+    } else if (!on && b->d_prof) {
+        cudaFree(b->d_prof);
+        b->d_prof = nullptr;
+    }
+    return TN_OK;
+}
+
+tn_status tn_batch_profile(tn_batch *b, int64_t *cycles, int64_t *items) {
+    if (!b || !cycles || !items) return fail(TN_EINVAL, "NULL argument");
+    if (!b->d_prof) return fail(TN_EINVAL, "profiling is off (tn_batch_set_profiling)");
+    CK(cudaSetDevice(b->ctx->device));
+    CK(cudaStreamSynchronize(b->ctx->stream));
+    long long h[2 * kProfSlots];
+    CK(cudaMemcpy(h, b->d_prof, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kProfSlots; ++i) { cycles[i] = h[i]; items[i] = h[kProfSlots + i]; }
+    return TN_OK;
 }
 
 tn_status tn_batch_set_tensors(tn_batch *b, int32_t count, const int32_t *job, const int32_t *tensor,

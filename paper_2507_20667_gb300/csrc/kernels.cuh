@@ -130,10 +130,16 @@ cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jo
 cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const JobPtrs &job,
                         int32_t dyn_smem, cudaStream_t stream);
 cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);
+// Optional cycle accounting of the persistent kernel: prof[slot] sums SM cycles (block 0's view
+// of each work item, thread 0), prof[kProfSlots + slot] counts items.  Slots 0..5: work items by
+// StepKind (dependency wait excluded); 8..10: steps inside subtree programs by LocalMode;
+// 11: leaf staging of subtree programs; 12: dependency waits.
+constexpr int kProfSlots = 16;
+
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
                               int64_t n_work, uint32_t *counter, int32_t grid, int32_t dyn_smem,
-                              cudaStream_t stream);
+                              long long *prof, cudaStream_t stream);
 // Co-resident grid of the persistent kernel with `dyn_smem` bytes of dynamic shared memory.
 int32_t persistent_grid(bool c128, int32_t dyn_smem);
 // Dynamic shared memory a local program may use so that `blocks_per_sm` persistent blocks fit.

@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(128) k_leaf_convert(const JobPtrs *__restrict_
 
 template <typename T>
 __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
-                                         float *red, char *dyn) {
-    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, reinterpret_cast<double2 *>(smem));
+                                         float *red, char *dyn, long long *prof) {
+    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, reinterpret_cast<double2 *>(smem), prof);
     else run_tile<T>(d, tile, j, smem, red);
 }
 
@@ -87,13 +87,13 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ 
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
     load_desc(d, steps + step);
-    run_item<T>(d, blockIdx.x, job, smem, red, dyn);
+    run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict__ jobs,
                                                       const WorkItem *__restrict__ work,
-                                                      int64_t n_work, uint32_t *counter) {
+                                                      int64_t n_work, uint32_t *counter, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
     extern __shared__ __align__(16) char dyn[];
     __shared__ StepDesc d;
@@ -108,19 +108,33 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         if ((int64_t)w >= n_work) break;
         const WorkItem it = work[w];
         const JobPtrs &j = jobs[it.job];
+        long long t0 = 0;
         if (threadIdx.x == 0) {
+            if (prof) t0 = clock64();
             const StepDesc *sd = j.steps + it.step;
             bool ok = wait_step(j, __ldcg(&sd->dep0), abort_flag);
             ok = wait_step(j, __ldcg(&sd->dep1), abort_flag) && ok;
             if (!ok) atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
             s_ok = ok;
+            if (prof) {
+                const long long t1 = clock64();
+                atomicAdd((unsigned long long *)(prof + 12), (unsigned long long)(t1 - t0));
+                atomicAdd((unsigned long long *)(prof + kProfSlots + 12), 1ull);
+                t0 = t1;
+            }
         }
         __syncthreads();
         load_desc(d, j.steps + it.step);
-        if (s_ok) run_item<T>(d, it.tile, j, smem, red, dyn);
+        if (s_ok) run_item<T>(d, it.tile, j, smem, red, dyn, prof);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(j.done + it.step, 1);
+        if (threadIdx.x == 0) {
+            atomicAdd(j.done + it.step, 1);
+            if (prof) {
+                atomicAdd((unsigned long long *)(prof + d.kind), (unsigned long long)(clock64() - t0));
+                atomicAdd((unsigned long long *)(prof + kProfSlots + d.kind), 1ull);
+            }
+        }
     }
 }
 
@@ -214,10 +228,11 @@ int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
 }
 
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work, int64_t n_work,
-                              uint32_t *counter, int32_t grid, int32_t dyn_smem, cudaStream_t stream) {
+                              uint32_t *counter, int32_t grid, int32_t dyn_smem, long long *prof,
+                              cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
-    void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter};
+    void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter, (void *)&prof};
     const void *fn = c128 ? (const void *)k_persist<double> : (const void *)k_persist<float>;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, (size_t)dyn_smem, stream);
 }

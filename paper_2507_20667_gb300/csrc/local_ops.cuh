@@ -226,7 +226,7 @@ __device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem
 // Runs local program `prog` of job `j` in the calling block.  `dyn` is the block's dynamic shared
 // memory, laid out by local_layout().
 template <typename T>
-__device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *red64) {
+__device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *red64, long long *prof) {
     using C = cx_t<T>;
     const LocalProg P = j.progs[prog];
     const LocalSmem L = local_layout(dyn, P.n_slots);
@@ -250,6 +250,8 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *re
         }
     }
     __syncthreads();
+    long long tp = 0;
+    if (prof && threadIdx.x == 0) tp = clock64();
     for (int32_t st = 0; st < P.n_steps; ++st) {
         const LocalStep &s = L.desc[st & 1];
         if (st + 1 < P.n_steps && threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
@@ -274,7 +276,14 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *re
         mx = warp_max(mx);
         if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));
         if (threadIdx.x == 0) L.sexp[s.sc] = e_out;
+        const int mode = s.mode;
         __syncthreads();
+        if (prof && threadIdx.x == 0) {
+            const long long t1 = clock64();
+            atomicAdd((unsigned long long *)(prof + 8 + mode), (unsigned long long)(t1 - tp));
+            atomicAdd((unsigned long long *)(prof + kProfSlots + 8 + mode), 1ull);
+            tp = t1;
+        }
     }
     // publish the program's result (unless it was the job's amplitude, already written)
     if (!(P.flags & LFLAG_JOB_ROOT)) {

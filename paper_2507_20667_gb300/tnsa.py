@@ -63,6 +63,13 @@ class tn_run_info(ctypes.Structure):
         return {f: (getattr(self, f)) for f, _ in self._fields_}
 
 
+class tn_compile_stats(ctypes.Structure):
+    _fields_ = [("global_steps", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("n_tile", ctypes.c_int32),
+                ("n_dot", ctypes.c_int32), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
+                ("max_local_smem", ctypes.c_int32), ("levels", ctypes.c_int32), ("total_tiles", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_size_t), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _SIGS = {
@@ -77,6 +84,7 @@ _SIGS = {
     "tn_plan_get_info": (_I32, [_P, ctypes.POINTER(tn_plan_info)]),
     "tn_plan_export": (_I32, [_P, _P, _P, _P, _P]),
     "tn_plan_free": (None, [_P]),
+    "tn_plan_compile_stats": (_I32, [_P, _P, _I32, _I32, ctypes.POINTER(tn_compile_stats)]),
     "tn_ctx_create": (_I32, [_I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "tn_ctx_free": (None, [_P]),
     "tn_ctx_synchronize": (_I32, [_P]),
@@ -89,6 +97,8 @@ _SIGS = {
     "tn_batch_last_info": (_I32, [_P, ctypes.POINTER(tn_run_info)]),
     "tn_batch_kernel_ms": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "tn_batch_set_tensors": (_I32, [_P, _I32, _P, _P, _P]),
+    "tn_batch_set_profiling": (_I32, [_P, _I32]),
+    "tn_batch_profile": (_I32, [_P, _P, _P]),
     "tn_batch_free": (None, [_P]),
     "tn_batch_contract": (_I32, [_P, _I32, _P, _P, _I32, _P, _P]),
     "tn_program_create": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
@@ -253,6 +263,12 @@ def tn_plan_export(plan: Plan, n_tensors: int):
     return part, steps[: ns.value], sp[: ns.value]
 
 
+def tn_plan_compile_stats(net: Net, plan: Plan, precision="c64", local_budget=0) -> dict:
+    st = tn_compile_stats()
+    _check(lib.tn_plan_compile_stats(net, plan, PRECISIONS[precision], int(local_budget), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in tn_compile_stats._fields_}
+
+
 def tn_ctx_create(device=0, stream=None, hbm_budget_bytes=0) -> Ctx:
     out = ctypes.c_void_p()
     _check(lib.tn_ctx_create(int(device), ctypes.c_void_p(stream) if stream else None,
@@ -306,6 +322,18 @@ def tn_batch_set_tensors(batch: Batch, jobs, tensors, data) -> None:
     t = np.ascontiguousarray(tensors, dtype=np.int32)
     d = np.ascontiguousarray(np.asarray(data, dtype=np.complex128).ravel()).view(np.float64)
     _check(lib.tn_batch_set_tensors(batch, len(j), _ptr(j), _ptr(t), _ptr(d)))
+
+
+def tn_batch_set_profiling(batch: Batch, on: bool = True) -> None:
+    _check(lib.tn_batch_set_profiling(batch, 1 if on else 0))
+
+
+def tn_batch_profile(batch: Batch):
+    """(cycles int64 [16], items int64 [16]) accumulated by the persistent kernel."""
+    c = np.zeros(16, np.int64)
+    i = np.zeros(16, np.int64)
+    _check(lib.tn_batch_profile(batch, _ptr(c), _ptr(i)))
+    return c, i
 
 
 def tn_batch_footprint(batch: Batch) -> int:
