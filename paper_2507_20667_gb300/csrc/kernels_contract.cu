@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_leaf_convert(const JobPtrs *__restrict_
 template <typename T>
 __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
                                          float *red, char *dyn, long long *prof) {
-    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, reinterpret_cast<double2 *>(smem), prof);
+    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, smem, prof);
     else run_tile<T>(d, tile, j, smem, red);
 }
 

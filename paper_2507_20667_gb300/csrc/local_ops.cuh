@@ -47,6 +47,34 @@ __device__ __forceinline__ void lgroup_off2(const LocalStep &s, int32_t idx, int
     }
 }
 
+// A power-of-two group list held in registers: offset(idx) = sum ((idx >> lsb) & mask) * stride.
+struct RegGroups {
+    int32_t n;
+    int32_t lsb[kLG], mask[kLG], str[kLG];
+};
+
+__device__ __forceinline__ RegGroups reg_groups(int32_t n, const int32_t *dim, const int32_t *str,
+                                                const uint8_t *lsb) {
+    RegGroups g;
+    g.n = n;
+#pragma unroll
+    for (int i = 0; i < kLG; ++i) {
+        g.lsb[i] = i < n ? lsb[i] : 0;
+        g.mask[i] = i < n ? dim[i] - 1 : 0;
+        g.str[i] = i < n ? str[i] : 0;
+    }
+    return g;
+}
+
+__device__ __forceinline__ int32_t reg_off(const RegGroups &g, int32_t idx) {
+    int32_t off = 0;
+#pragma unroll
+    for (int i = 0; i < kLG; ++i) off += ((idx >> g.lsb[i]) & g.mask[i]) * g.str[i];
+    return off;
+}
+
+constexpr int kKTab = 1024;   // shared indices whose offsets are tabulated per step
+
 struct LocalSmem {
     LocalStep *desc;     // two buffers (double-buffered descriptors)
     uint32_t *smax;      // [n_slots] max-abs bit pattern of each node of the program
@@ -69,38 +97,67 @@ __device__ __forceinline__ LocalSmem local_layout(char *dyn, int32_t n_slots) {
 //   LMODE_REDUCE  few outputs, long K: S threads per output split K, FP64 partial sums, shuffle /
 //                 shared-memory reduction; the job's root (the amplitude) always takes this mode
 template <typename T, int NT>
-__device__ __forceinline__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx) {
+__device__ __forceinline__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
+                                           char *scratch) {
     using C = cx_t<T>;
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
     C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
-    const int32_t N = s.N, K = s.K;
-    for (int32_t m = threadIdx.x; m < s.M; m += blockDim.x) {
-        const int32_t offA = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, s.pow2, m);
+    C *Bd = reinterpret_cast<C *>(scratch);                                   // [K][N], scaled
+    int32_t *kat = reinterpret_cast<int32_t *>(scratch + kRowsMaxKN * sizeof(C));   // [K]
+    const int32_t N = s.N, K = s.K, M = s.M;
+    for (int32_t i = threadIdx.x; i < K * N; i += blockDim.x) {
+        const int32_t k = i / N, n = i - k * N;
+        int32_t ka, kb;
+        lgroup_off2(s, k, ka, kb);
+        kb += lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n);
+        Bd[i] = cscale(B[kb], sB);
+        if (n == 0) kat[k] = ka;
+    }
+    const bool p2 = s.pow2;
+    const RegGroups gm = reg_groups(s.nm, s.m_dim, s.m_str, s.m_lsb);
+    __syncthreads();
+    for (int32_t m = threadIdx.x; m < M; m += blockDim.x) {
+        const int32_t offA = p2 ? reg_off(gm, m) : lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, false, m);
         C acc[NT];
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n] = cmake((T)0, (T)0);
         for (int32_t k = 0; k < K; ++k) {
-            int32_t ka, kb;
-            lgroup_off2(s, k, ka, kb);
-            const C a = cscale(A[offA + ka], sA);
+            const C a = cscale(A[offA + kat[k]], sA);
 #pragma unroll
             for (int n = 0; n < NT; ++n)
-                if (n < N)
-                    cfma(acc[n], a, cscale(B[kb + lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n)], sB));
+                if (n < N) cfma(acc[n], a, Bd[k * N + n]);
         }
+        C *out = Cp + m * N;
 #pragma unroll
         for (int n = 0; n < NT; ++n)
             if (n < N) {
-                const C v = acc[n];
-                Cp[m * N + n] = v;
-                mx = fmaxf(mx, absmax2(v));
+                out[n] = acc[n];
+                mx = fmaxf(mx, absmax2(acc[n]));
             }
     }
 }
 
+// Shared-index offsets of a step, tabulated in shared memory when K <= kKTab.
+__device__ __forceinline__ void build_ktab(const LocalStep &s, int2 *kt) {
+    if (s.K > kKTab) return;
+    for (int32_t k = threadIdx.x; k < s.K; k += blockDim.x) {
+        int32_t ka, kb;
+        lgroup_off2(s, k, ka, kb);
+        kt[k] = make_int2(ka, kb);
+    }
+}
+
+__device__ __forceinline__ int2 kofs(const LocalStep &s, const int2 *kt, int32_t k) {
+    if (s.K <= kKTab) return kt[k];
+    int32_t ka, kb;
+    lgroup_off2(s, k, ka, kb);
+    return make_int2(ka, kb);
+}
+
 template <typename T>
-__device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx) {
+__device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
+                                           const int2 *kt) {
     using C = cx_t<T>;
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
@@ -122,8 +179,8 @@ __device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cmake((T)0, (T)0);
             for (int32_t k = 0; k < K; ++k) {
-                int32_t ka, kb;
-                lgroup_off2(s, k, ka, kb);
+                const int2 ko = kofs(s, kt, k);
+                const int32_t ka = ko.x, kb = ko.y;
                 C a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -156,7 +213,7 @@ __device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &
 // and sums in FP64; groups of up to 32 lanes reduce with shuffles, larger ones through `red64`.
 template <typename T>
 __device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
-                                             double2 *red64, const JobPtrs &j, int32_t e_out) {
+                                             double2 *red64, const JobPtrs &j, int32_t e_out, const int2 *kt) {
     using C = cx_t<T>;
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
@@ -175,9 +232,8 @@ __device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem
             C run = cmake((T)0, (T)0);
             int cnt = 0;
             for (int32_t k = sub; k < K; k += S) {
-                int32_t ka, kb;
-                lgroup_off2(s, k, ka, kb);
-                cfma(run, cscale(A[offA + ka], sA), cscale(B[kb + offB], sB));
+                const int2 ko = kofs(s, kt, k);
+                cfma(run, cscale(A[offA + ko.x], sA), cscale(B[ko.y + offB], sB));
                 if (++cnt == 32) {
                     acc.x += (double)run.x;
                     acc.y += (double)run.y;
@@ -226,7 +282,9 @@ __device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem
 // Runs local program `prog` of job `j` in the calling block.  `dyn` is the block's dynamic shared
 // memory, laid out by local_layout().
 template <typename T>
-__device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *red64, long long *prof) {
+__device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scratch, long long *prof) {
+    // scratch: the block's static tile scratch -- dense B / offset tables, then FP64 partials
+    double2 *red64 = reinterpret_cast<double2 *>(scratch + kKTab * sizeof(int2));
     using C = cx_t<T>;
     const LocalProg P = j.progs[prog];
     const LocalSmem L = local_layout(dyn, P.n_slots);
@@ -262,16 +320,16 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, double2 *re
         const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
         const int32_t e_out = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
         float mx = 0.f;
-        switch (s.mode) {
-            case LMODE_ROWS:
-                if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx);
-                else if (s.N <= 2) local_rows<T, 2>(s, L, sA, sB, mx);
-                else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx);
-                else if (s.N <= 8) local_rows<T, 8>(s, L, sA, sB, mx);
-                else local_rows<T, 16>(s, L, sA, sB, mx);
-                break;
-            case LMODE_GEMM: local_gemm<T>(s, L, sA, sB, mx); break;
-            default: local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out); break;
+        const int2 *kt = reinterpret_cast<const int2 *>(scratch);
+        if (s.mode == LMODE_ROWS) {
+            if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx, scratch);
+            else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
+            else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
+        } else {
+            build_ktab(s, reinterpret_cast<int2 *>(scratch));
+            __syncthreads();
+            if (s.mode == LMODE_GEMM) local_gemm<T>(s, L, sA, sB, mx, kt);
+            else local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out, kt);
         }
         mx = warp_max(mx);
         if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));

@@ -40,7 +40,17 @@ __device__ __forceinline__ int32_t scale_exponent(uint32_t bits) {
     return e == 0 ? -126 : e - 126;
 }
 
-template <typename T> __device__ __forceinline__ T pow2(int32_t e) { return (T)ldexp(1.0, e); }
+// Exact 2^e built from the IEEE-754 exponent field (e within the normal range of T; the scale
+// exponents used here stay in [-128, 128]).
+template <typename T> __device__ __forceinline__ T pow2(int32_t e);
+template <> __device__ __forceinline__ float pow2<float>(int32_t e) {
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    return __int_as_float((e + 127) << 23);
+}
+template <> __device__ __forceinline__ double pow2<double>(int32_t e) {
+    e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
 
 __device__ __forceinline__ float absmax2(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
 __device__ __forceinline__ float absmax2(double2 v) { return (float)fmax(fabs(v.x), fabs(v.y)); }
@@ -132,7 +142,10 @@ template <typename T> struct Scratch {
     static constexpr int rows = kRowsMaxKN * sizeof(C) + kRowsMaxK * sizeof(int64_t);
     static constexpr int tile = 2 * kTileK * kTileM * sizeof(C) + (kTileM + kTileN + 2 * kTileK) * sizeof(int64_t);
     static constexpr int dot = (kThreads / 32) * kDotMaxOut * sizeof(double2) + 2 * kDotMaxOut * sizeof(int64_t);
-    static constexpr int bytes = (rows > tile ? (rows > dot ? rows : dot) : (tile > dot ? tile : dot));
+    static constexpr int local = 1024 * 8 + (kThreads / 32) * 16;   // offset table + FP64 partials
+    static constexpr int m1 = rows > tile ? rows : tile;
+    static constexpr int m2 = dot > local ? dot : local;
+    static constexpr int bytes = m1 > m2 ? m1 : m2;
 };
 
 // ------------------------------------------------------------------------------ ROWS
