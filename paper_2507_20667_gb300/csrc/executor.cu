@@ -246,9 +246,10 @@ size_t plan_memory(const Plan &plan, int32_t n, const std::vector<size_t> &bytes
     return top;
 }
 
+// Rows per work tile of a global ROWS step: large enough to amortise the tile's fixed cost
+// (descriptor, scales, B staging, completion fence), 16 rows per thread at most.
 int32_t rows_per_tile(int64_t M) {
-    if (M <= (1 << 14)) return 256;
-    if (M <= (1 << 20)) return 1024;
+    if (M <= 4096) return (int32_t)std::max<int64_t>(M, 1);
     return 4096;
 }
 
@@ -305,7 +306,7 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     std::sort(lp.leaves.begin(), lp.leaves.end());
     const int64_t slots = (int64_t)lp.nodes.size() + (int64_t)lp.leaves.size();
     if (slots > 32000) return false;
-    const int64_t fixed = 2 * (int64_t)sizeof(LocalStep) + (8 * slots + 15) / 16 * 16;
+    const int64_t fixed = 8 * (int64_t)sizeof(LocalStep) + (8 * slots + 15) / 16 * 16;   // descriptor ring
     for (int32_t x : lp.nodes) {
         const Geom &g = geo[x - n];
         if (g.M > (1 << 30) || g.N > (1 << 30) || g.K > (1 << 30)) return false;

@@ -154,6 +154,6 @@ constexpr int kThreads = 256;
 constexpr int kTileM = 64, kTileN = 64, kTileK = 16;   // CUDA-core GEMM tile
 constexpr int kRowsMaxKN = 1024, kRowsMaxK = 64, kRowsMaxN = 16;
 constexpr int kDotMaxOut = 16;
-constexpr int kDotChunk = 8192;                         // shared indices per DOTP tile
+constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
 
 }  // namespace tn

@@ -75,8 +75,10 @@ __device__ __forceinline__ int32_t reg_off(const RegGroups &g, int32_t idx) {
 
 constexpr int kKTab = 1024;   // shared indices whose offsets are tabulated per step
 
+constexpr int kDescRing = 8;   // step descriptors prefetched ahead of use
+
 struct LocalSmem {
-    LocalStep *desc;     // two buffers (double-buffered descriptors)
+    LocalStep *desc;     // ring of kDescRing descriptors
     uint32_t *smax;      // [n_slots] max-abs bit pattern of each node of the program
     int32_t *sexp;       // [n_slots] power-of-two exponent of each node
     char *data;          // leaves, then the arena of intermediates
@@ -85,9 +87,9 @@ struct LocalSmem {
 __device__ __forceinline__ LocalSmem local_layout(char *dyn, int32_t n_slots) {
     LocalSmem L;
     L.desc = reinterpret_cast<LocalStep *>(dyn);
-    L.smax = reinterpret_cast<uint32_t *>(dyn + 2 * sizeof(LocalStep));
+    L.smax = reinterpret_cast<uint32_t *>(dyn + kDescRing * sizeof(LocalStep));
     L.sexp = reinterpret_cast<int32_t *>(L.smax + n_slots);
-    L.data = dyn + 2 * sizeof(LocalStep) + ((8 * (size_t)n_slots + 15) / 16) * 16;
+    L.data = dyn + kDescRing * sizeof(LocalStep) + ((8 * (size_t)n_slots + 15) / 16) * 16;
     return L;
 }
 
@@ -292,9 +294,12 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     // zero the slots, stage the leaves (one warp per leaf) and the first descriptor
     for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
     {
+        // the first kDescRing - 1 descriptors; step st then prefetches st + kDescRing - 1
+        constexpr int kWords = (int)(sizeof(LocalStep) / 16);
+        const int first = P.n_steps < kDescRing - 1 ? P.n_steps : kDescRing - 1;
         const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step);
         int4 *dst = reinterpret_cast<int4 *>(L.desc);
-        for (int i = threadIdx.x; i < (int)(sizeof(LocalStep) / 16); i += blockDim.x) dst[i] = __ldcg(src + i);
+        for (int i = threadIdx.x; i < first * kWords; i += blockDim.x) dst[i] = __ldcg(src + i);
     }
     __syncthreads();
     const C *leaf = static_cast<const C *>(j.leaf);
@@ -311,10 +316,14 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     long long tp = 0;
     if (prof && threadIdx.x == 0) tp = clock64();
     for (int32_t st = 0; st < P.n_steps; ++st) {
-        const LocalStep &s = L.desc[st & 1];
-        if (st + 1 < P.n_steps && threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
-            const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step + st + 1);
-            reinterpret_cast<int4 *>(L.desc + ((st + 1) & 1))[threadIdx.x] = __ldcg(src + threadIdx.x);
+        const LocalStep &s = L.desc[st % kDescRing];
+        {
+            // refill the slot of step st - 1 (finished at the last barrier) with step st + R - 1
+            const int32_t ahead = st + kDescRing - 1;
+            if (ahead < P.n_steps && threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
+                const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step + ahead);
+                reinterpret_cast<int4 *>(L.desc + (ahead % kDescRing))[threadIdx.x] = __ldcg(src + threadIdx.x);
+            }
         }
         const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
         const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);

@@ -176,6 +176,7 @@ __device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     const int64_t m_begin = tile * (int64_t)d.tile_rows;
     const int64_t m_end = min(d.M, m_begin + (int64_t)d.tile_rows);
     float mx = 0.f;
+#pragma unroll 4
     for (int64_t m = m_begin + threadIdx.x; m < m_end; m += blockDim.x) {
         const int64_t offA = group_off(d.m, m);
         C acc[NT];
