@@ -77,6 +77,16 @@ constexpr int kKTab = 1024;   // shared indices whose offsets are tabulated per 
 
 constexpr int kDescRing = 8;   // step descriptors prefetched ahead of use
 
+// Asynchronous 16-byte global -> shared copies (cp.async): the issuing thread does not wait for
+// the data; it waits for a commit group only when that descriptor is due.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 struct LocalSmem {
     LocalStep *desc;     // ring of kDescRing descriptors
     uint32_t *smax;      // [n_slots] max-abs bit pattern of each node of the program
@@ -317,13 +327,14 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     if (prof && threadIdx.x == 0) tp = clock64();
     for (int32_t st = 0; st < P.n_steps; ++st) {
         const LocalStep &s = L.desc[st % kDescRing];
-        {
-            // refill the slot of step st - 1 (finished at the last barrier) with step st + R - 1
+        if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
+            // refill the slot of step st - 1 (finished at the last barrier) with step st + R - 1;
+            // every step commits one group (possibly empty) so the group count stays in step
             const int32_t ahead = st + kDescRing - 1;
-            if (ahead < P.n_steps && threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
-                const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step + ahead);
-                reinterpret_cast<int4 *>(L.desc + (ahead % kDescRing))[threadIdx.x] = __ldcg(src + threadIdx.x);
-            }
+            if (ahead < P.n_steps)
+                cp_async16(reinterpret_cast<int4 *>(L.desc + (ahead % kDescRing)) + threadIdx.x,
+                           reinterpret_cast<const int4 *>(j.lsteps + P.first_step + ahead) + threadIdx.x);
+            cp_async_commit();
         }
         const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
         const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
@@ -344,6 +355,8 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
         if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));
         if (threadIdx.x == 0) L.sexp[s.sc] = e_out;
         const int mode = s.mode;
+        // the descriptor of step st + 1 was committed R - 2 groups ago
+        if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) cp_async_wait<kDescRing - 2>();
         __syncthreads();
         if (prof && threadIdx.x == 0) {
             const long long t1 = clock64();
@@ -352,6 +365,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
             tp = t1;
         }
     }
+    if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) cp_async_wait<0>();
     // publish the program's result (unless it was the job's amplitude, already written)
     if (!(P.flags & LFLAG_JOB_ROOT)) {
         C *out = reinterpret_cast<C *>(j.arena) + P.root_c_off;
