@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "local_ops.cuh"
 #include "tn_internal.hpp"
 
 using namespace tn;
@@ -31,6 +32,7 @@ struct Compiled {
     std::vector<LocalProg> progs;
     std::vector<LocalStep> lsteps;
     std::vector<LeafRef> leafrefs;
+    std::vector<LocalWave> lwaves;
     std::vector<int64_t> leaf_off;   // [n + 1] element offsets of the leaves
     int32_t n = 0, n_nodes = 0;
     size_t arena_bytes = 0;
@@ -46,6 +48,7 @@ struct Compiled {
     LocalProg *d_progs = nullptr;
     LocalStep *d_lsteps = nullptr;
     LeafRef *d_leafrefs = nullptr;
+    LocalWave *d_lwaves = nullptr;
 };
 
 }  // namespace
@@ -280,7 +283,9 @@ bool make_lgroups(const std::vector<int64_t> &dim, const std::vector<int64_t> &s
 }
 
 struct LocalPlan {
-    std::vector<int32_t> nodes;      // internal nodes, plan order
+    std::vector<int32_t> nodes;      // internal nodes in execution order (wave by wave)
+    std::vector<char> small;         // per entry of `nodes`: one warp runs it
+    std::vector<LocalWave> waves;
     std::vector<int32_t> leaves;     // leaves, increasing
     std::vector<int64_t> loc;        // per node of the subtree: shared-memory element offset
     std::unordered_map<int32_t, int32_t> idx;   // node -> position in loc / slot
@@ -288,29 +293,62 @@ struct LocalPlan {
     int32_t smem_bytes = 0;
 };
 
+// A step one warp runs on its own (no block barrier): few outputs and a short shared index.
+bool small_step(const Geom &g, bool job_root) {
+    return !job_root && g.M * g.N <= 256 && g.K <= 256 && g.M * g.N * g.K <= 4096;
+}
+
 // Can the subtree rooted at v run in one block within `budget` bytes of dynamic shared memory?
-// Simulates its sequential execution (plan order) with a best-fit allocator.
+// Steps are grouped into waves of mutually independent steps (wave = 1 + the latest wave among
+// the step's children inside the subtree); a wave runs its small steps one per warp and its big
+// steps with the whole block.  The memory plan is simulated in that order: all outputs of a wave
+// are placed (best fit) before the inputs it consumed are released.
 bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &geo,
                const std::vector<int64_t> &size, int32_t elem, int32_t budget, LocalPlan &lp) {
     lp = LocalPlan();
-    std::vector<int32_t> stack{v};
+    std::vector<int32_t> nodes, stack{v};
     while (!stack.empty()) {
         int32_t x = stack.back();
         stack.pop_back();
         if (x < n) { lp.leaves.push_back(x); continue; }
-        lp.nodes.push_back(x);
+        nodes.push_back(x);
         stack.push_back(plan.steps[x - n][0]);
         stack.push_back(plan.steps[x - n][1]);
     }
-    std::sort(lp.nodes.begin(), lp.nodes.end());
+    std::sort(nodes.begin(), nodes.end());
     std::sort(lp.leaves.begin(), lp.leaves.end());
-    const int64_t slots = (int64_t)lp.nodes.size() + (int64_t)lp.leaves.size();
+    const int64_t slots = (int64_t)nodes.size() + (int64_t)lp.leaves.size();
     if (slots > 32000) return false;
-    const int64_t fixed = 8 * (int64_t)sizeof(LocalStep) + (8 * slots + 15) / 16 * 16;   // descriptor ring
-    for (int32_t x : lp.nodes) {
+    for (int32_t x : nodes) {
         const Geom &g = geo[x - n];
         if (g.M > (1 << 30) || g.N > (1 << 30) || g.K > (1 << 30)) return false;
     }
+    // waves and execution order
+    std::unordered_map<int32_t, int32_t> wave;
+    int32_t n_waves = 0;
+    for (int32_t x : nodes) {
+        int32_t w = 0;
+        for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
+            if (c >= n) w = std::max(w, wave[c]);
+        wave[x] = w + 1;
+        n_waves = std::max(n_waves, w + 1);
+    }
+    const int32_t root_id = 2 * n - 2;
+    std::vector<std::vector<int32_t>> by_wave(n_waves + 1);
+    for (int32_t x : nodes) by_wave[wave[x]].push_back(x);
+    for (int32_t w = 1; w <= n_waves; ++w) {
+        LocalWave W{(int32_t)lp.nodes.size(), 0, 0, 0};
+        for (int pass = 0; pass < 2; ++pass)
+            for (int32_t x : by_wave[w]) {
+                const bool sm = small_step(geo[x - n], x == root_id);
+                if (sm != (pass == 0)) continue;
+                lp.nodes.push_back(x);
+                lp.small.push_back(sm ? 1 : 0);
+                if (sm) W.n_small++; else W.n_big++;
+            }
+        lp.waves.push_back(W);
+    }
+    const int64_t fixed = (int64_t)local_fixed_bytes((int32_t)lp.nodes.size(), (int32_t)lp.waves.size(), (int32_t)slots);
     int64_t pos = 0;
     for (int32_t t : lp.leaves) {
         lp.idx[t] = (int32_t)lp.loc.size();
@@ -322,23 +360,30 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     Pool pool;
     int64_t top = 0;
     std::unordered_map<int32_t, int64_t> asz;
-    for (int32_t x : lp.nodes) {
-        const int64_t sz = (size[x] + 1) / 2 * 2;
-        size_t at;
-        if (!pool.take((size_t)sz, at)) {
-            at = (size_t)top;
-            top += sz;
+    for (const LocalWave &W : lp.waves) {
+        const int32_t end = W.first + W.n_small + W.n_big;
+        for (int32_t i = W.first; i < end; ++i) {
+            const int32_t x = lp.nodes[i];
+            const int64_t sz = (size[x] + 1) / 2 * 2;
+            size_t at;
+            if (!pool.take((size_t)sz, at)) {
+                at = (size_t)top;
+                top += sz;
+            }
+            lp.idx[x] = (int32_t)lp.loc.size();
+            lp.loc.push_back(lp.leaf_elems + (int64_t)at);
+            asz[x] = sz;
         }
-        lp.idx[x] = (int32_t)lp.loc.size();
-        lp.loc.push_back(lp.leaf_elems + (int64_t)at);
-        asz[x] = sz;
-        for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
-            if (c >= n) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
         if (fixed + (lp.leaf_elems + top) * elem > budget) return false;
+        for (int32_t i = W.first; i < end; ++i) {
+            const int32_t x = lp.nodes[i];
+            for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
+                if (c >= n) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
+        }
     }
     lp.arena_elems = top;
     lp.smem_bytes = (int32_t)(fixed + (lp.leaf_elems + top) * elem);
-    if (lp.loc.back() + size[v] > (1LL << 30)) return false;
+    if (lp.leaf_elems + top > (1LL << 30)) return false;
     // every step must fit the compact descriptor
     for (int32_t x : lp.nodes) {
         const Geom &g = geo[x - n];
@@ -511,6 +556,7 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
     c.progs.clear();
     c.lsteps.clear();
     c.leafrefs.clear();
+    c.lwaves.clear();
     c.dyn_smem = 0;
     for (size_t pi = 0; pi < proot.size(); ++pi) {
         const LocalPlan &lp = lplans[pi];
@@ -529,6 +575,10 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
         P.root_size = (int32_t)size[v];
         P.root_c_off = (int64_t)(arena_off[v] / esz);
         P.flags = (v == nn - 1) ? LFLAG_JOB_ROOT : 0;
+        P.first_wave = (int32_t)c.lwaves.size();
+        P.n_waves = (int32_t)lp.waves.size();
+        // wave step indices are relative to the program (its descriptors are staged per program)
+        for (const LocalWave &W : lp.waves) c.lwaves.push_back(W);
         for (int32_t t : lp.leaves) {
             LeafRef r;
             r.global_off = (int32_t)c.leaf_off[t];
@@ -538,7 +588,8 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
             r.node = t;
             c.leafrefs.push_back(r);
         }
-        for (int32_t x : lp.nodes) {
+        for (size_t si = 0; si < lp.nodes.size(); ++si) {
+            const int32_t x = lp.nodes[si];
             const Geom &g = geo[x - n];
             LocalStep ls;
             std::memset(&ls, 0, sizeof(ls));
@@ -564,6 +615,7 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
             } else {
                 ls.mode = LMODE_REDUCE;
             }
+            if (lp.small[si]) ls.flags |= LFLAG_SMALL;
             c.lsteps.push_back(ls);
         }
         c.dyn_smem = std::max(c.dyn_smem, P.smem_bytes);
@@ -694,13 +746,15 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max(bytes, (size_t)16), 256); return o; };
     std::vector<size_t> o_steps(b->comp.size()), o_loff(b->comp.size());
-    std::vector<size_t> o_progs(b->comp.size()), o_lsteps(b->comp.size()), o_lrefs(b->comp.size());
+    std::vector<size_t> o_progs(b->comp.size()), o_lsteps(b->comp.size()), o_lrefs(b->comp.size()),
+        o_lwaves(b->comp.size());
     for (size_t ci = 0; ci < b->comp.size(); ++ci) {
         o_steps[ci] = carve(sizeof(StepDesc) * b->comp[ci].steps.size());
         o_loff[ci] = carve(sizeof(int64_t) * b->comp[ci].leaf_off.size());
         o_progs[ci] = carve(sizeof(LocalProg) * b->comp[ci].progs.size());
         o_lsteps[ci] = carve(sizeof(LocalStep) * b->comp[ci].lsteps.size());
         o_lrefs[ci] = carve(sizeof(LeafRef) * b->comp[ci].leafrefs.size());
+        o_lwaves[ci] = carve(sizeof(LocalWave) * b->comp[ci].lwaves.size());
         b->dyn_smem = std::max(b->dyn_smem, b->comp[ci].dyn_smem);
     }
     b->leaf64_off.assign(n, 0);
@@ -770,6 +824,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->comp[ci].d_progs = reinterpret_cast<LocalProg *>(base + o_progs[ci]);
         b->comp[ci].d_lsteps = reinterpret_cast<LocalStep *>(base + o_lsteps[ci]);
         b->comp[ci].d_leafrefs = reinterpret_cast<LeafRef *>(base + o_lrefs[ci]);
+        b->comp[ci].d_lwaves = reinterpret_cast<LocalWave *>(base + o_lwaves[ci]);
     }
     b->d_leaf64 = reinterpret_cast<double2 *>(base + o_leaf64);
     char *d_leaf = base + o_leaf;
@@ -795,6 +850,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         j.progs = c.d_progs;
         j.lsteps = c.d_lsteps;
         j.leafrefs = c.d_leafrefs;
+        j.lwaves = c.d_lwaves;
         j.n_steps = (int32_t)c.steps.size();
         j.n_leaves = c.n;
     }
@@ -820,6 +876,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
                                 cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && !c.leafrefs.empty())
             e = cudaMemcpyAsync(c.d_leafrefs, c.leafrefs.data(), sizeof(LeafRef) * c.leafrefs.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !c.lwaves.empty())
+            e = cudaMemcpyAsync(c.d_lwaves, c.lwaves.data(), sizeof(LocalWave) * c.lwaves.size(),
                                 cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess)

@@ -59,7 +59,16 @@ struct StepDesc {
 // element offsets) and at most kLG fused groups per index class.
 constexpr int kLG = 6;
 enum LocalMode : uint8_t { LMODE_ROWS = 0, LMODE_GEMM = 1, LMODE_REDUCE = 2 };
-enum LocalFlags : int32_t { LFLAG_JOB_ROOT = 1 };
+enum LocalFlags : int32_t {
+    LFLAG_JOB_ROOT = 1,     // (program, step) produces the job's amplitude
+    LFLAG_SMALL = 2         // (step) small enough for one warp
+};
+
+// A wave of a program: steps [first, first + n_small) run one per warp, then n_big steps use the
+// whole block; the steps of a wave are independent of each other.
+struct LocalWave {
+    int32_t first, n_small, n_big, pad;
+};
 
 struct LocalStep {
     int32_t M, N, K;
@@ -83,6 +92,7 @@ struct LocalProg {
     int32_t root_smem_off, root_size;   // where the subtree's value sits in shared memory
     int64_t root_c_off;                 // and where it goes in the job's arena
     int32_t flags;                      // LFLAG_JOB_ROOT: the subtree is the whole network
+    int32_t first_wave, n_waves;        // into the job's LocalWave array
     int32_t pad;
 };
 
@@ -107,6 +117,7 @@ struct JobPtrs {
     const LocalProg *progs;  // CTA-resident subtree programs
     const LocalStep *lsteps;
     const LeafRef *leafrefs;
+    const LocalWave *lwaves;
     int32_t n_steps;
     int32_t n_leaves;
 };

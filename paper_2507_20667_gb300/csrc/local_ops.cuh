@@ -75,32 +75,77 @@ __device__ __forceinline__ int32_t reg_off(const RegGroups &g, int32_t idx) {
 
 constexpr int kKTab = 1024;   // shared indices whose offsets are tabulated per step
 
-constexpr int kDescRing = 8;   // step descriptors prefetched ahead of use
-
-// Asynchronous 16-byte global -> shared copies (cp.async): the issuing thread does not wait for
-// the data; it waits for a commit group only when that descriptor is due.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 struct LocalSmem {
-    LocalStep *desc;     // ring of kDescRing descriptors
+    LocalStep *desc;     // all step descriptors of the program, in execution order
+    LocalWave *waves;
     uint32_t *smax;      // [n_slots] max-abs bit pattern of each node of the program
     int32_t *sexp;       // [n_slots] power-of-two exponent of each node
     char *data;          // leaves, then the arena of intermediates
 };
 
-__device__ __forceinline__ LocalSmem local_layout(char *dyn, int32_t n_slots) {
+// Shared-memory layout of a program (the host computes the same sizes in local_fit).
+__device__ __host__ __forceinline__ size_t local_fixed_bytes(int32_t n_steps, int32_t n_waves, int32_t n_slots) {
+    return (size_t)n_steps * sizeof(LocalStep) + (size_t)n_waves * sizeof(LocalWave) +
+           ((8 * (size_t)n_slots + 15) / 16) * 16;
+}
+
+__device__ __forceinline__ LocalSmem local_layout(char *dyn, const LocalProg &P) {
     LocalSmem L;
     L.desc = reinterpret_cast<LocalStep *>(dyn);
-    L.smax = reinterpret_cast<uint32_t *>(dyn + kDescRing * sizeof(LocalStep));
-    L.sexp = reinterpret_cast<int32_t *>(L.smax + n_slots);
-    L.data = dyn + kDescRing * sizeof(LocalStep) + ((8 * (size_t)n_slots + 15) / 16) * 16;
+    L.waves = reinterpret_cast<LocalWave *>(dyn + (size_t)P.n_steps * sizeof(LocalStep));
+    L.smax = reinterpret_cast<uint32_t *>(L.waves + P.n_waves);
+    L.sexp = reinterpret_cast<int32_t *>(L.smax + P.n_slots);
+    L.data = dyn + local_fixed_bytes(P.n_steps, P.n_waves, P.n_slots);
     return L;
+}
+
+// A small step computed by one warp: lane per output, K in registers-resident index maps when all
+// dimensions are powers of two; the warp publishes the output's max-abs and exponent itself.
+template <typename T>
+__device__ __forceinline__ void local_small(const LocalStep &s, const LocalSmem &L) {
+    using C = cx_t<T>;
+    const int lane = threadIdx.x & 31;
+    const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
+    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
+    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
+    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t N = s.N, K = s.K, O = s.M * s.N;
+    float mx = 0.f;
+    if (s.pow2) {
+        const RegGroups gm = reg_groups(s.nm, s.m_dim, s.m_str, s.m_lsb);
+        const RegGroups gn = reg_groups(s.nn, s.n_dim, s.n_str, s.n_lsb);
+        const RegGroups gka = reg_groups(s.nk, s.k_dim, s.k_sa, s.k_lsb);
+        const RegGroups gkb = reg_groups(s.nk, s.k_dim, s.k_sb, s.k_lsb);
+        for (int32_t o = lane; o < O; o += 32) {
+            const int32_t m = o / N, n = o - m * N;
+            const int32_t oa = reg_off(gm, m), ob = reg_off(gn, n);
+            C acc = cmake((T)0, (T)0);
+            for (int32_t k = 0; k < K; ++k)
+                cfma(acc, cscale(A[oa + reg_off(gka, k)], sA), cscale(B[ob + reg_off(gkb, k)], sB));
+            Cp[o] = acc;
+            mx = fmaxf(mx, absmax2(acc));
+        }
+    } else {
+        for (int32_t o = lane; o < O; o += 32) {
+            const int32_t m = o / N, n = o - m * N;
+            const int32_t oa = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, false, m);
+            const int32_t ob = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, false, n);
+            C acc = cmake((T)0, (T)0);
+            for (int32_t k = 0; k < K; ++k) {
+                int32_t ka, kb;
+                lgroup_off2(s, k, ka, kb);
+                cfma(acc, cscale(A[oa + ka], sA), cscale(B[ob + kb], sB));
+            }
+            Cp[o] = acc;
+            mx = fmaxf(mx, absmax2(acc));
+        }
+    }
+    mx = warp_max(mx);
+    if (lane == 0) {
+        L.smax[s.sc] = __float_as_uint(mx);
+        L.sexp[s.sc] = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
+    }
 }
 
 // One step, all operands in shared memory.  Modes:
@@ -299,18 +344,19 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     double2 *red64 = reinterpret_cast<double2 *>(scratch + kKTab * sizeof(int2));
     using C = cx_t<T>;
     const LocalProg P = j.progs[prog];
-    const LocalSmem L = local_layout(dyn, P.n_slots);
+    const LocalSmem L = local_layout(dyn, P);
     C *data = reinterpret_cast<C *>(L.data);
-    // zero the slots, stage the leaves (one warp per leaf) and the first descriptor
-    for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
+    // stage the descriptors and waves, zero the slots, then stage the leaves (one warp per leaf)
     {
-        // the first kDescRing - 1 descriptors; step st then prefetches st + kDescRing - 1
-        constexpr int kWords = (int)(sizeof(LocalStep) / 16);
-        const int first = P.n_steps < kDescRing - 1 ? P.n_steps : kDescRing - 1;
+        const int nd = P.n_steps * (int)(sizeof(LocalStep) / 16);
         const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step);
         int4 *dst = reinterpret_cast<int4 *>(L.desc);
-        for (int i = threadIdx.x; i < first * kWords; i += blockDim.x) dst[i] = __ldcg(src + i);
+        for (int i = threadIdx.x; i < nd; i += blockDim.x) dst[i] = __ldcg(src + i);
+        const int4 *wsrc = reinterpret_cast<const int4 *>(j.lwaves + P.first_wave);
+        int4 *wdst = reinterpret_cast<int4 *>(L.waves);
+        for (int i = threadIdx.x; i < P.n_waves; i += blockDim.x) wdst[i] = __ldcg(wsrc + i);
     }
+    for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
     __syncthreads();
     const C *leaf = static_cast<const C *>(j.leaf);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -325,47 +371,42 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     __syncthreads();
     long long tp = 0;
     if (prof && threadIdx.x == 0) tp = clock64();
-    for (int32_t st = 0; st < P.n_steps; ++st) {
-        const LocalStep &s = L.desc[st % kDescRing];
-        if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) {
-            // refill the slot of step st - 1 (finished at the last barrier) with step st + R - 1;
-            // every step commits one group (possibly empty) so the group count stays in step
-            const int32_t ahead = st + kDescRing - 1;
-            if (ahead < P.n_steps)
-                cp_async16(reinterpret_cast<int4 *>(L.desc + (ahead % kDescRing)) + threadIdx.x,
-                           reinterpret_cast<const int4 *>(j.lsteps + P.first_step + ahead) + threadIdx.x);
-            cp_async_commit();
+    for (int32_t w = 0; w < P.n_waves; ++w) {
+        const LocalWave W = L.waves[w];
+        // independent small steps: one warp each
+        for (int32_t i = warp; i < W.n_small; i += nw) local_small<T>(L.desc[W.first + i], L);
+        // big steps: the whole block, one after the other
+        for (int32_t i = 0; i < W.n_big; ++i) {
+            const LocalStep &s = L.desc[W.first + W.n_small + i];
+            const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
+            const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
+            const int32_t e_out = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
+            float mx = 0.f;
+            const int2 *kt = reinterpret_cast<const int2 *>(scratch);
+            if (s.mode == LMODE_ROWS) {
+                if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx, scratch);
+                else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
+                else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
+            } else {
+                build_ktab(s, reinterpret_cast<int2 *>(scratch));
+                __syncthreads();
+                if (s.mode == LMODE_GEMM) local_gemm<T>(s, L, sA, sB, mx, kt);
+                else local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out, kt);
+            }
+            mx = warp_max(mx);
+            if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));
+            if (threadIdx.x == 0) L.sexp[s.sc] = e_out;
+            __syncthreads();   // scratch (dense B / offset table) is reused by the next big step
         }
-        const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
-        const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
-        const int32_t e_out = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
-        float mx = 0.f;
-        const int2 *kt = reinterpret_cast<const int2 *>(scratch);
-        if (s.mode == LMODE_ROWS) {
-            if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx, scratch);
-            else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
-            else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
-        } else {
-            build_ktab(s, reinterpret_cast<int2 *>(scratch));
-            __syncthreads();
-            if (s.mode == LMODE_GEMM) local_gemm<T>(s, L, sA, sB, mx, kt);
-            else local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out, kt);
-        }
-        mx = warp_max(mx);
-        if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));
-        if (threadIdx.x == 0) L.sexp[s.sc] = e_out;
-        const int mode = s.mode;
-        // the descriptor of step st + 1 was committed R - 2 groups ago
-        if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) cp_async_wait<kDescRing - 2>();
         __syncthreads();
         if (prof && threadIdx.x == 0) {
             const long long t1 = clock64();
-            atomicAdd((unsigned long long *)(prof + 8 + mode), (unsigned long long)(t1 - tp));
-            atomicAdd((unsigned long long *)(prof + kProfSlots + 8 + mode), 1ull);
+            const int slot = W.n_big ? 9 : 8;   // 8: waves of small steps only, 9: waves with big steps
+            atomicAdd((unsigned long long *)(prof + slot), (unsigned long long)(t1 - tp));
+            atomicAdd((unsigned long long *)(prof + kProfSlots + slot), 1ull);
             tp = t1;
         }
     }
-    if (threadIdx.x < (int)(sizeof(LocalStep) / 16)) cp_async_wait<0>();
     // publish the program's result (unless it was the job's amplitude, already written)
     if (!(P.flags & LFLAG_JOB_ROOT)) {
         C *out = reinterpret_cast<C *>(j.arena) + P.root_c_off;
