@@ -137,6 +137,13 @@ typedef struct {
 tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_precision prec,
                                 int32_t local_budget, tn_compile_stats *out);
 
+/* The global step list the compiler produces (same inputs as tn_plan_compile_stats): for each
+ * entry 8 int64 {kernel class (0 ROWS, 1 TILE, 2 DOTP, 3 DOTF, 5 subtree program), M, N, K,
+ * work tiles, dependency level, program steps, program shared-memory bytes}.  At most cap entries
+ * are written to out (may be NULL); *n_out receives the full count.  Errors: as compile_stats. */
+tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_precision prec,
+                                int32_t local_budget, int64_t *out, int32_t cap, int32_t *n_out);
+
 /* Exact counts of the plan's tree B (Section 3):
  *   total_ops = con_serial(B) (Eq. 3.2), crit_ops = con_dist(B, K) (Eq. 3.5, con = con_serial,
  *   comm = 0), mem_elems = mem(B) (Eq. 3.1).  Any pointer may be NULL. */

@@ -86,6 +86,8 @@ struct tn_batch {
     JobPtrs *d_jobs = nullptr;
     WorkItem *d_work = nullptr;
     int64_t n_work = 0;
+    WorkItem *d_local = nullptr;      // (job, pseudo-step) of every subtree program
+    int32_t n_local_items = 0;
     uint32_t *d_counter = nullptr;
     DeviceResult *d_res = nullptr;
     char *d_reset = nullptr;          // results, maxbits, done, counter: zeroed before every run
@@ -653,6 +655,8 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         }
         e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess)
+            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_local_items, b->dyn_smem, b->d_prof, st);
+        if (e == cudaSuccess)
             e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->dyn_smem,
                               b->d_prof, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
@@ -777,7 +781,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     }
     const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
     // work list: (job, step, tile) in (level, job, step, tile) order
-    std::vector<WorkItem> work;
+    std::vector<WorkItem> work, local_items;
     if (b->mode == TN_EXEC_PERSISTENT) {
         int64_t total = 0;
         for (int32_t i = 0; i < n; ++i) total += b->comp[b->job_comp[i]].total_tiles;
@@ -791,11 +795,17 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         work.reserve((size_t)total);
         for (auto &o : order) {
             const StepDesc &d = b->comp[b->job_comp[o[1]]].steps[o[2]];
+            if (d.kind == STEP_LOCAL) {
+                local_items.push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
+                continue;
+            }
             for (int32_t t = 0; t < d.ntiles; ++t) work.push_back({(uint32_t)o[1], (uint32_t)o[2], (uint32_t)t});
         }
     }
     b->n_work = (int64_t)work.size();
+    b->n_local_items = (int32_t)local_items.size();
     const size_t o_work = carve(sizeof(WorkItem) * work.size());
+    const size_t o_litems = carve(sizeof(WorkItem) * local_items.size());
     // reset region: results, maxbits, done, counter
     const size_t o_reset = off;
     const size_t o_res = carve(sizeof(DeviceResult) * (size_t)n);
@@ -830,6 +840,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     char *d_leaf = base + o_leaf;
     b->d_jobs = reinterpret_cast<JobPtrs *>(base + o_jobs);
     b->d_work = reinterpret_cast<WorkItem *>(base + o_work);
+    b->d_local = reinterpret_cast<WorkItem *>(base + o_litems);
     b->d_reset = base + o_reset;
     b->d_res = reinterpret_cast<DeviceResult *>(base + o_res);
     b->d_counter = reinterpret_cast<uint32_t *>(base + o_counter);
@@ -885,6 +896,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         e = cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(JobPtrs) * (size_t)n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !work.empty())
         e = cudaMemcpyAsync(b->d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !local_items.empty())
+        e = cudaMemcpyAsync(b->d_local, local_items.data(), sizeof(WorkItem) * local_items.size(),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
@@ -914,7 +928,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->info.dyn_smem = b->dyn_smem;
     b->info.arena_bytes = b->arena_total;
     if (b->mode == TN_EXEC_PERSISTENT) {
-        b->info.launches = 2;   // leaf conversion + the persistent kernel
+        b->info.launches = 2 + (b->n_local_items > 0 ? 1 : 0);   // leaf conversion, programs, dataflow
     } else {
         int32_t l = 1;
         for (int32_t i = 0; i < n; ++i) l += (int32_t)b->comp[b->job_comp[i]].steps.size();
@@ -1079,6 +1093,27 @@ tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_preci
     for (const StepDesc &d : c.steps) lv = std::max(lv, d.level);
     st.levels = lv;
     *out = st;
+    return TN_OK;
+}
+
+tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_precision prec,
+                                int32_t local_budget, int64_t *out, int32_t cap, int32_t *n_out) {
+    if (!net || !plan || !n_out) return fail(TN_EINVAL, "NULL argument");
+    if (prec < TN_C128 || prec > TN_BF16_SPLIT) return fail(TN_EINVAL, "unknown precision");
+    if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
+    if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
+    Compiled c;
+    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget);
+    if (s != TN_OK) return s;
+    const int32_t n = (int32_t)c.steps.size();
+    for (int32_t i = 0; i < n && i < cap && out; ++i) {
+        const StepDesc &d = c.steps[i];
+        int64_t *r = out + 8 * (int64_t)i;
+        r[0] = d.kind; r[1] = d.M; r[2] = d.N; r[3] = d.K; r[4] = d.ntiles; r[5] = d.level;
+        r[6] = d.kind == STEP_LOCAL ? c.progs[d.tile_rows].n_steps : 0;
+        r[7] = d.kind == STEP_LOCAL ? c.progs[d.tile_rows].smem_bytes : 0;
+    }
+    *n_out = n;
     return TN_OK;
 }
 

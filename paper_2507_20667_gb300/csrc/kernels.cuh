@@ -151,8 +151,11 @@ constexpr int kProfSlots = 16;
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
                               int64_t n_work, uint32_t *counter, int32_t grid, int32_t dyn_smem,
                               long long *prof, cudaStream_t stream);
-// Co-resident grid of the persistent kernel with `dyn_smem` bytes of dynamic shared memory.
+// Co-resident grid of the persistent kernel (second argument unused).
 int32_t persistent_grid(bool c128, int32_t dyn_smem);
+// One block per subtree program; items: (job, pseudo-step, 0).
+cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_items,
+                         int32_t dyn_smem, long long *prof, cudaStream_t stream);
 // Dynamic shared memory a local program may use so that `blocks_per_sm` persistent blocks fit.
 int32_t local_smem_budget(bool c128, int32_t blocks_per_sm);
 cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int64_t n_upd,
@@ -164,7 +167,7 @@ cudaError_t launch_permute(const void *src, void *dst, int32_t elem_bytes, int32
 constexpr int kThreads = 256;
 constexpr int kTileM = 64, kTileN = 64, kTileK = 16;   // CUDA-core GEMM tile
 constexpr int kRowsMaxKN = 1024, kRowsMaxK = 64, kRowsMaxN = 16;
-constexpr int kDotMaxOut = 16;
+constexpr int kDotMaxOut = 4;
 constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
 
 }  // namespace tn

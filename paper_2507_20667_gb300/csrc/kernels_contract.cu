@@ -79,6 +79,30 @@ __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const 
     else run_tile<T>(d, tile, j, smem, red);
 }
 
+// All subtree programs of a batch: one block per program (they depend on leaves only).  Each
+// publishes its pseudo-step as complete, so the dataflow kernel that runs next never waits on it.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_local(const JobPtrs *__restrict__ jobs,
+                                                    const WorkItem *__restrict__ items, long long *prof) {
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ __align__(16) char smem[Scratch<T>::local];
+    const WorkItem it = items[blockIdx.x];
+    const JobPtrs &j = jobs[it.job];
+    const int32_t prog = __ldcg(&j.steps[it.step].tile_rows);
+    long long t0 = 0;
+    if (prof && threadIdx.x == 0) t0 = clock64();
+    run_local<T>(prog, j, dyn, smem, prof);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(j.done + it.step, 1);
+        if (prof) {
+            atomicAdd((unsigned long long *)(prof + STEP_LOCAL), (unsigned long long)(clock64() - t0));
+            atomicAdd((unsigned long long *)(prof + kProfSlots + STEP_LOCAL), 1ull);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ steps, int32_t step,
                                                    JobPtrs job) {
@@ -95,7 +119,6 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
                                                       const WorkItem *__restrict__ work,
                                                       int64_t n_work, uint32_t *counter, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
-    extern __shared__ __align__(16) char dyn[];
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -125,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         }
         __syncthreads();
         load_desc(d, j.steps + it.step);
-        if (s_ok) run_item<T>(d, it.tile, j, smem, red, dyn, prof);
+        if (s_ok) run_tile<T>(d, it.tile, j, smem, red);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -201,16 +224,24 @@ cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int6
     return cudaGetLastError();
 }
 
-int32_t persistent_grid(bool c128, int32_t dyn_smem) {
+int32_t persistent_grid(bool c128, int32_t) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaError_t e = c128 ? allow_dyn_smem(k_persist<double>, dyn_smem) : allow_dyn_smem(k_persist<float>, dyn_smem);
-    if (e != cudaSuccess) return 0;
-    e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, dyn_smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, dyn_smem);
+    cudaError_t e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, 0);
     if (e != cudaSuccess) return 0;
     return sms * per_sm;
+}
+
+cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_items,
+                         int32_t dyn_smem, long long *prof, cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    cudaError_t e = c128 ? allow_dyn_smem(k_local<double>, dyn_smem) : allow_dyn_smem(k_local<float>, dyn_smem);
+    if (e != cudaSuccess) return e;
+    if (c128) k_local<double><<<n_items, kThreads, dyn_smem, stream>>>(jobs_dev, items, prof);
+    else k_local<float><<<n_items, kThreads, dyn_smem, stream>>>(jobs_dev, items, prof);
+    return cudaGetLastError();
 }
 
 int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
@@ -220,7 +251,7 @@ int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
     if (cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) return 0;
     cudaFuncAttributes fa;
-    cudaError_t e = c128 ? cudaFuncGetAttributes(&fa, k_persist<double>) : cudaFuncGetAttributes(&fa, k_persist<float>);
+    cudaError_t e = c128 ? cudaFuncGetAttributes(&fa, k_local<double>) : cudaFuncGetAttributes(&fa, k_local<float>);
     if (e != cudaSuccess) return 0;
     int32_t b = per_sm / blocks_per_sm - reserved - (int32_t)fa.sharedSizeBytes;
     if (b > per_block - (int32_t)fa.sharedSizeBytes) b = per_block - (int32_t)fa.sharedSizeBytes;
@@ -234,7 +265,8 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
     if (grid > n_work) grid = (int32_t)n_work;
     void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter, (void *)&prof};
     const void *fn = c128 ? (const void *)k_persist<double> : (const void *)k_persist<float>;
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, (size_t)dyn_smem, stream);
+    (void)dyn_smem;
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, 0, stream);
 }
 
 }  // namespace tn

@@ -142,7 +142,9 @@ template <typename T> struct Scratch {
     static constexpr int rows = kRowsMaxKN * sizeof(C) + kRowsMaxK * sizeof(int64_t);
     static constexpr int tile = 2 * kTileK * kTileM * sizeof(C) + (kTileM + kTileN + 2 * kTileK) * sizeof(int64_t);
     static constexpr int dot = (kThreads / 32) * kDotMaxOut * sizeof(double2) + 2 * kDotMaxOut * sizeof(int64_t);
-    static constexpr int local = 1024 * 8 + (kThreads / 32) * 16;   // offset table + FP64 partials
+    // subtree programs: the offset table (or dense B) + FP64 partials
+    static constexpr int local = (1024 * 8 > kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4 ? 1024 * 8
+                                  : kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4) + (kThreads / 32) * 16;
     static constexpr int m1 = rows > tile ? rows : tile;
     static constexpr int m2 = dot > local ? dot : local;
     static constexpr int bytes = m1 > m2 ? m1 : m2;

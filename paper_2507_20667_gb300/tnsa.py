@@ -85,6 +85,7 @@ _SIGS = {
     "tn_plan_export": (_I32, [_P, _P, _P, _P, _P]),
     "tn_plan_free": (None, [_P]),
     "tn_plan_compile_stats": (_I32, [_P, _P, _I32, _I32, ctypes.POINTER(tn_compile_stats)]),
+    "tn_plan_compile_steps": (_I32, [_P, _P, _I32, _I32, _P, _I32, _P]),
     "tn_ctx_create": (_I32, [_I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "tn_ctx_free": (None, [_P]),
     "tn_ctx_synchronize": (_I32, [_P]),
@@ -267,6 +268,16 @@ def tn_plan_compile_stats(net: Net, plan: Plan, precision="c64", local_budget=0)
     st = tn_compile_stats()
     _check(lib.tn_plan_compile_stats(net, plan, PRECISIONS[precision], int(local_budget), ctypes.byref(st)))
     return {f: getattr(st, f) for f, _ in tn_compile_stats._fields_}
+
+
+def tn_plan_compile_steps(net: Net, plan: Plan, precision="c64", local_budget=0) -> np.ndarray:
+    """[n, 8] int64: kind, M, N, K, tiles, level, program steps, program shared-memory bytes."""
+    n = ctypes.c_int32()
+    _check(lib.tn_plan_compile_steps(net, plan, PRECISIONS[precision], int(local_budget), None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 8), np.int64)
+    _check(lib.tn_plan_compile_steps(net, plan, PRECISIONS[precision], int(local_budget), _ptr(out), n.value,
+                                     ctypes.byref(n)))
+    return out
 
 
 def tn_ctx_create(device=0, stream=None, hbm_budget_bytes=0) -> Ctx:
