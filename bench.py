@@ -287,9 +287,13 @@ def run_ours(args):
                     "amps_per_s": ws * e2e_steps * B / dt, "steps": e2e_steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_persist<float> (persistent dataflow contraction)",
+                         "kernel": "contraction kernels of one run (k_local<float> subtree programs + "
+                                   "k_persist<float> dataflow steps), events around both",
                          "kernel_ms": kernel_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": info["launches"] * args.steps,
+            "exec": {"subtree_programs": info["n_local"], "steps_in_programs": info["n_local_steps"],
+                     "dyn_smem": info["dyn_smem"], "global_rows": info["n_gather"], "global_tile": info["n_tile"],
+                     "global_dot": info["n_dot"]},
             "clocks": clocks.summary(),
             "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem},
             "cpu_baseline": cpu}
