@@ -94,7 +94,8 @@ struct tn_batch {
     size_t reset_bytes = 0;
     size_t footprint = 0, arena_total = 0;
     int32_t grid = 0;
-    int32_t dyn_smem = 0;             // dynamic shared memory of the contraction kernels
+    int32_t dyn_smem = 0;             // dynamic shared memory of the subtree-program kernel
+    int32_t use_tc = 0;               // the dataflow kernel runs tensor-core tiles
     long long *d_prof = nullptr;      // optional per-kind cycle counters (tn_batch_set_profiling)
     // host
     double *h_pinned = nullptr;
@@ -399,7 +400,8 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     return true;
 }
 
-tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget) {
+tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget,
+                  bool use_tc) {
     const int32_t n = net.n, nn = 2 * n - 1;
     c.n = n;
     c.n_nodes = nn;
@@ -543,6 +545,14 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
             d.ntiles = (int32_t)((M + d.tile_rows - 1) / d.tile_rows);
             c.steps.push_back(d);
             c.counts[STEP_ROWS]++;
+        } else if (use_tc && M >= 64 && N >= 32 && K >= 16) {
+            // dense step on the tensor cores: 128 x 64 complex output tiles, BF16 split
+            d.kind = STEP_TC;
+            const int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
+            if (tiles > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "step too large");
+            d.ntiles = (int32_t)tiles;
+            c.steps.push_back(d);
+            c.counts[STEP_TC]++;
         } else {
             d.kind = STEP_TILE;
             const int64_t tiles = ((M + kTileM - 1) / kTileM) * ((N + kTileN - 1) / kTileN);
@@ -657,7 +667,7 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         if (e == cudaSuccess)
             e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_local_items, b->dyn_smem, b->d_prof, st);
         if (e == cudaSuccess)
-            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->dyn_smem,
+            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->use_tc,
                               b->d_prof, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
@@ -738,7 +748,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         auto it = seen.find(key);
         if (it != seen.end()) { b->job_comp[i] = it->second; continue; }
         Compiled c;
-        tn_status s = compile(c, net, plans[i]->impl, b->elem, budget);
+        tn_status s = compile(c, net, plans[i]->impl, b->elem, budget, prec == TN_BF16_SPLIT);
         if (s != TN_OK) { batch_destroy(b); return s; }
         c.plan_uid = plans[i]->impl.uid;
         c.shape_hash = h;
@@ -902,7 +912,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
-    b->grid = persistent_grid(b->c128, b->dyn_smem);
+    for (const Compiled &c : b->comp)
+        if (c.counts[STEP_TC] > 0) b->use_tc = 1;
+    b->grid = persistent_grid(b->c128, b->use_tc);
     if (b->grid <= 0) { batch_destroy(b); return fail(TN_ECUDA, "occupancy query failed"); }
     tn_status s = TN_OK;
     for (int32_t i = 0; i < n && s == TN_OK; ++i) s = upload_leaves(b, i);
@@ -1074,7 +1086,7 @@ tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_preci
     if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
     if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
     Compiled c;
-    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget);
+    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget, prec == TN_BF16_SPLIT);
     if (s != TN_OK) return s;
     tn_compile_stats st;
     std::memset(&st, 0, sizeof(st));
@@ -1103,7 +1115,7 @@ tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_preci
     if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
     if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
     Compiled c;
-    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget);
+    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget, prec == TN_BF16_SPLIT);
     if (s != TN_OK) return s;
     const int32_t n = (int32_t)c.steps.size();
     for (int32_t i = 0; i < n && i < cap && out; ++i) {

@@ -148,11 +148,12 @@ cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t strea
 constexpr int kProfSlots = 16;
 
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
+// use_tc: the work list holds tensor-core tiles (each block then holds 128 TMEM columns).
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
-                              int64_t n_work, uint32_t *counter, int32_t grid, int32_t dyn_smem,
+                              int64_t n_work, uint32_t *counter, int32_t grid, int32_t use_tc,
                               long long *prof, cudaStream_t stream);
-// Co-resident grid of the persistent kernel (second argument unused).
-int32_t persistent_grid(bool c128, int32_t dyn_smem);
+// Co-resident grid of the persistent kernel, with tensor-core tiles (use_tc) or without.
+int32_t persistent_grid(bool c128, int32_t use_tc);
 // One block per subtree program; items: (job, pseudo-step, 0).
 cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_items,
                          int32_t dyn_smem, long long *prof, cudaStream_t stream);

@@ -12,6 +12,7 @@
 
 #include "kernels.cuh"
 #include "local_ops.cuh"
+#include "tc_ops.cuh"
 #include "tile_ops.cuh"
 
 namespace tn {
@@ -103,6 +104,30 @@ __global__ void __launch_bounds__(kThreads) k_local(const JobPtrs *__restrict__ 
     }
 }
 
+// Tensor-memory accumulator and mbarrier of one block (tensor-core tiles only).
+__device__ __forceinline__ void tc_setup(TcState &tc, uint32_t *tmem_slot, uint64_t *bar, int32_t *abort_flag) {
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, kTcCols);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tc.tmem = *tmem_slot;
+    tc.bar = bar;
+    tc.phase = 0;
+    tc.abort_flag = abort_flag;
+    tc.pending = false;
+}
+
+// Frees the block's tensor memory; after a wait that gave up, first waits (bounded) once more for
+// the MMAs that may still be in flight.
+__device__ __forceinline__ void tc_teardown(TcState &tc) {
+    if (tc.pending) mbar_wait(tc.bar, tc.phase, kTcWaitLimit);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, kTcCols);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ steps, int32_t step,
                                                    JobPtrs job) {
@@ -110,15 +135,35 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ 
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
+    __shared__ uint64_t tc_bar;
+    __shared__ uint32_t tc_tmem;
+    __shared__ int32_t tc_abort;
     load_desc(d, steps + step);
+    if (d.kind == STEP_TC) {
+        if constexpr (sizeof(T) == 4) {
+            if (threadIdx.x == 0) tc_abort = 0;
+            TcState tc;
+            tc_setup(tc, &tc_tmem, &tc_bar, &tc_abort);
+            const bool ok = tile_tc(d, blockIdx.x, job, dyn, smem, red, tc);
+            if (!ok && threadIdx.x == 0) atomicExch(&static_cast<DeviceResult *>(job.result)->status, kStatusTimeout);
+            tc_teardown(tc);
+        }
+        return;
+    }
     run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict__ jobs,
                                                       const WorkItem *__restrict__ work,
-                                                      int64_t n_work, uint32_t *counter, long long *prof) {
+                                                      int64_t n_work, uint32_t *counter, long long *prof,
+                                                      int32_t use_tc) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ uint64_t tc_bar;
+    __shared__ uint32_t tc_tmem;
+    TcState tc;
+    if (use_tc) tc_setup(tc, &tc_tmem, &tc_bar, abort_flag);
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -148,7 +193,16 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         }
         __syncthreads();
         load_desc(d, j.steps + it.step);
-        if (s_ok) run_tile<T>(d, it.tile, j, smem, red);
+        if (s_ok) {
+            if (d.kind == STEP_TC) {
+                if constexpr (sizeof(T) == 4) {
+                            if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
+                        atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
+                }
+            } else {
+                run_tile<T>(d, it.tile, j, smem, red);
+            }
+        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -159,6 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
             }
         }
     }
+    if (use_tc) tc_teardown(tc);
 }
 
 // Scatter staged tensor updates {dst offset, count, src offset} into the complex128 leaves.
@@ -201,7 +256,7 @@ cudaError_t allow_dyn_smem(K kernel, int32_t bytes) {
 cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtrs &job, int32_t dyn_smem,
                         cudaStream_t stream) {
     if (h.ntiles <= 0) return cudaErrorInvalidValue;
-    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : 0;
+    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : (h.kind == STEP_TC ? kTcSmem : 0);
     cudaError_t e = c128 ? allow_dyn_smem(k_step<double>, dyn) : allow_dyn_smem(k_step<float>, dyn);
     if (e != cudaSuccess) return e;
     if (c128) k_step<double><<<(unsigned)h.ntiles, kThreads, dyn, stream>>>(job.steps, step, job);
@@ -224,13 +279,17 @@ cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int6
     return cudaGetLastError();
 }
 
-int32_t persistent_grid(bool c128, int32_t) {
+int32_t persistent_grid(bool c128, int32_t use_tc) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaError_t e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, 0);
+    const int32_t dyn = use_tc ? kTcSmem : 0;
+    cudaError_t e = c128 ? allow_dyn_smem(k_persist<double>, dyn) : allow_dyn_smem(k_persist<float>, dyn);
     if (e != cudaSuccess) return 0;
+    e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, dyn)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, dyn);
+    if (e != cudaSuccess) return 0;
+    if (use_tc && per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
     return sms * per_sm;
 }
 
@@ -259,14 +318,15 @@ int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
 }
 
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work, int64_t n_work,
-                              uint32_t *counter, int32_t grid, int32_t dyn_smem, long long *prof,
+                              uint32_t *counter, int32_t grid, int32_t use_tc, long long *prof,
                               cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
-    void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter, (void *)&prof};
+    int32_t tc = (use_tc && !c128) ? 1 : 0;
+    void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter, (void *)&prof,
+                    (void *)&tc};
     const void *fn = c128 ? (const void *)k_persist<double> : (const void *)k_persist<float>;
-    (void)dyn_smem;
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, 0, stream);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, tc ? kTcSmem : 0, stream);
 }
 
 }  // namespace tn

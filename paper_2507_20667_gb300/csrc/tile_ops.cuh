@@ -145,7 +145,9 @@ template <typename T> struct Scratch {
     // subtree programs: the offset table (or dense B) + FP64 partials
     static constexpr int local = (1024 * 8 > kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4 ? 1024 * 8
                                   : kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4) + (kThreads / 32) * 16;
-    static constexpr int m1 = rows > tile ? rows : tile;
+    static constexpr int tc = (128 + 64 + 32 + 32) * (int)sizeof(int64_t);   // tensor-core tile offsets
+    static constexpr int m0 = rows > tc ? rows : tc;
+    static constexpr int m1 = m0 > tile ? m0 : tile;
     static constexpr int m2 = dot > local ? dot : local;
     static constexpr int bytes = m1 > m2 ? m1 : m2;
 };
