@@ -6,8 +6,10 @@ shared library is missing the import fails loudly; there is no fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -139,21 +141,40 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+_LIVE = {name: weakref.WeakSet() for name in ("tn_batch_free", "tn_program_free", "tn_ctx_free",
+                                               "tn_plan_free", "tn_net_free")}
+
+
 class _Handle:
     _free = None
 
     def __init__(self, ptr, keep=()):
         self.ptr = ptr
         self._keep = keep
+        if self._free:
+            _LIVE[self._free].add(self)
+
+    def close(self):
+        if getattr(self, "ptr", None) and self._free is not None and lib is not None:
+            getattr(lib, self._free)(self.ptr)
+        self.ptr = None
 
     def __del__(self):
-        if getattr(self, "ptr", None) and self._free is not None:
-            getattr(lib, self._free)(self.ptr)
-            self.ptr = None
+        self.close()
 
     @property
     def _as_parameter_(self):
         return self.ptr
+
+
+@atexit.register
+def _free_all():
+    """Release every live handle, dependents first, while the CUDA runtime is still up (at process
+    exit the interpreter would otherwise free them in arbitrary order, possibly after the runtime's
+    own teardown)."""
+    for name in ("tn_batch_free", "tn_program_free", "tn_ctx_free", "tn_plan_free", "tn_net_free"):
+        for h in list(_LIVE[name]):
+            h.close()
 
 
 class Net(_Handle):
