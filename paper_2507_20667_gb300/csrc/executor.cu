@@ -727,6 +727,21 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         if (!nets[i]->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
     }
     CK(cudaSetDevice(ctx->device));
+    // admission: mem(B) of Eq. 3.1 (elements of the largest step's operands and result) is a lower
+    // bound of a job's device footprint; refuse before compiling if it cannot fit
+    {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const double elem = prec == TN_C128 ? 16.0 : 8.0;
+        double need = 0;
+        for (int32_t i = 0; i < n; ++i) need += (double)plans[i]->impl.mem * elem;
+        if (ctx->budget && need > (double)ctx->budget)
+            return fail(TN_EBUDGET, "the plans need at least " + std::to_string(need) +
+                                        " bytes (Eq. 3.1), above the context's budget");
+        if (need > (double)free_b)
+            return fail(TN_EBUDGET, "the plans need at least " + std::to_string(need) +
+                                        " bytes (Eq. 3.1), above the free device memory");
+    }
     tn_batch *b = new (std::nothrow) tn_batch;
     if (!b) return fail(TN_ENOMEM, "allocating the batch");
     b->ctx = ctx;
