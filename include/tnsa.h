@@ -178,6 +178,9 @@ void tn_ctx_free(tn_ctx *ctx);
 /* Block until all work enqueued on the context's stream has finished.  Errors: TN_ECUDA. */
 tn_status tn_ctx_synchronize(tn_ctx *ctx);
 
+/* The CUDA device of the context.  Errors: TN_EINVAL. */
+tn_status tn_ctx_device(const tn_ctx *ctx, int32_t *device);
+
 /* How programs and batches made from the context execute their steps.
  *   TN_EXEC_PERSISTENT (default)  one persistent dataflow kernel per run: every step is cut into
  *       work tiles; resident blocks claim tiles in dependency-level order across all jobs, wait
@@ -310,6 +313,48 @@ tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_by
  * is called.  Errors: TN_EINVAL, TN_ECUDA. */
 tn_status tn_dot_noalloc(int32_t device, void *cuda_stream, const void *d_a, const void *d_b,
                          int64_t n, tn_precision prec, double *d_out);
+
+/* ------------------------------------------------------------------ serving */
+
+/* A request loop with continuous batching (the serving pattern of the engine).  Models -- a
+ * registered (net, plan) -- stay compiled and resident; a request names a model and replaces some
+ * of its tensors (for instance the bra tensors of a bitstring, or the single-qubit slots of an
+ * expectation value).  A worker thread admits queued requests into launches as device memory
+ * allows -- each request needs its model's per-job bytes from a pool of hbm_budget_bytes
+ * allocated at creation -- and keeps up to two launches in flight on two streams, so requests
+ * that arrive while one launch runs start in the next one and overlap with it.  A request's
+ * result depends only on its own data: it is the same alone and in any mix.
+ * The context's device is used; the server owns its streams. */
+typedef struct tn_server tn_server;
+
+typedef struct {
+    int64_t submitted, completed, rejected;   /* rejected: larger than the whole pool (TN_EBUDGET) */
+    int64_t launches, launched_requests;       /* batches launched and the requests they carried */
+    int32_t max_in_flight, pad;                /* most launches on the device at once (<= 2) */
+    size_t pool_used;                          /* pool bytes held by launches in flight */
+} tn_serve_stats;
+
+/* max_batch: most requests per launch.  Errors: TN_EINVAL, TN_ENOMEM (pool), TN_ECUDA. */
+tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_bytes, int32_t max_batch,
+                          tn_server **out);
+/* Compile and keep resident a closed network with its plan (copied; the net's current tensor
+ * values are the model's defaults).  Thread-safe.  Errors: TN_EINVAL, TN_EUNSUPPORTED, TN_ECUDA. */
+tn_status tn_serve_register(tn_server *s, const tn_net *net, const tn_plan *plan, int32_t *model);
+/* Device bytes one request of `model` holds while in flight, and its algorithmic flops. */
+tn_status tn_serve_model_info(tn_server *s, int32_t model, size_t *job_bytes, double *flops);
+/* Queue a request: `count` tensors of the model replaced by `data` (their entries back to back,
+ * complex128 interleaved; copied).  Thread-safe, returns at once with a ticket.  Errors: TN_EINVAL. */
+tn_status tn_serve_submit(tn_server *s, int32_t model, int32_t count, const int32_t *tensors,
+                          const double *data, uint64_t *ticket);
+/* Wait up to timeout_s (0 = do not wait) for a ticket.  *done = 0 if not finished yet; otherwise
+ * the result (value = (re + i im) * 2^exp2) and its latency from submission to completion, and the
+ * ticket is released.  Returns TN_EBUDGET for a request that can never fit the pool, TN_ETIMEOUT or
+ * TN_ECUDA if its launch failed. */
+tn_status tn_serve_poll(tn_server *s, uint64_t ticket, double timeout_s, double out_amp[2],
+                        int32_t *out_exp2, double *latency_s, int32_t *done);
+tn_status tn_serve_get_stats(tn_server *s, tn_serve_stats *stats);
+/* Stops the worker after the launches in flight finish; queued requests are dropped. */
+void tn_serve_free(tn_server *s);
 
 /* ------------------------------------------------------------------ diagnostics */
 

@@ -5,9 +5,10 @@
 // every intermediate (offsets into one arena).  Nets with the same structure that use the same
 // plan share one compiled list and differ only in their leaves.
 //
-// A batch is a set of jobs (independent contractions).  It is executed either by the persistent
-// dataflow kernel (one cooperative launch for all jobs; the default) or, as a reference mode, by
-// one launch per step and job recorded into a CUDA graph.  A program is a batch of one job.
+// A batch is a set of jobs (independent contractions).  It is executed either by the subtree-
+// program kernel plus the persistent dataflow kernel (two launches for all jobs; the default) or,
+// as a reference mode, by one launch per step and job recorded into a CUDA graph.  A program is a
+// batch of one job.
 #include <algorithm>
 #include <array>
 #include <cstring>
@@ -25,33 +26,7 @@
 
 using namespace tn;
 
-namespace {
-
-struct Compiled {
-    std::vector<StepDesc> steps;
-    std::vector<LocalProg> progs;
-    std::vector<LocalStep> lsteps;
-    std::vector<LeafRef> leafrefs;
-    std::vector<LocalWave> lwaves;
-    std::vector<int64_t> leaf_off;   // [n + 1] element offsets of the leaves
-    int32_t n = 0, n_nodes = 0;
-    size_t arena_bytes = 0;
-    int64_t n_partials = 0;          // double2 entries
-    int64_t total_tiles = 0;
-    int32_t dyn_smem = 0;            // largest shared-memory need of a local program
-    double flops = 0, bytes = 0;
-    int32_t counts[7] = {0, 0, 0, 0, 0, 0, 0};   // by StepKind; [6] = steps inside programs
-    uint64_t plan_uid = 0, shape_hash = 0;
-    // device copies (inside the batch's allocation)
-    StepDesc *d_steps = nullptr;
-    int64_t *d_leaf_off = nullptr;
-    LocalProg *d_progs = nullptr;
-    LocalStep *d_lsteps = nullptr;
-    LeafRef *d_leafrefs = nullptr;
-    LocalWave *d_lwaves = nullptr;
-};
-
-}  // namespace
+#include "compile.cuh"
 
 struct tn_ctx {
     int32_t device = 0;
@@ -400,8 +375,10 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     return true;
 }
 
-tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget,
-                  bool use_tc) {
+}  // namespace
+
+tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget,
+                      bool use_tc) {
     const int32_t n = net.n, nn = 2 * n - 1;
     c.n = n;
     c.n_nodes = nn;
@@ -638,6 +615,22 @@ tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, i
     for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
 }
+
+void tn::work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level) {
+    std::vector<std::array<int32_t, 2>> order;   // level, step
+    for (size_t s = 0; s < c.steps.size(); ++s)
+        if (c.steps[s].kind != STEP_LOCAL) order.push_back({c.steps[s].level, (int32_t)s});
+    std::sort(order.begin(), order.end());
+    items.clear();
+    item_level.clear();
+    for (auto &o : order)
+        for (int32_t t = 0; t < c.steps[o[1]].ntiles; ++t) {
+            items.push_back({0u, (uint32_t)o[1], (uint32_t)t});
+            item_level.push_back(o[0]);
+        }
+}
+
+namespace {
 
 tn_status upload_leaves(tn_batch *b, int32_t job) {
     const Net &net = b->nets[job]->impl;
@@ -1074,9 +1067,6 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
     if (prop.major != 10 || prop.minor != 3)
         return fail(TN_ECUDA, "this build targets sm_103a (GB300); device is sm_" +
                                   std::to_string(prop.major) + std::to_string(prop.minor));
-    int coop = 0;
-    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
-    if (!coop) return fail(TN_ECUDA, "device does not support cooperative launches");
     CK(cudaSetDevice(device));
     tn_ctx *c = new (std::nothrow) tn_ctx;
     if (!c) return fail(TN_ENOMEM, "allocating the context");
@@ -1177,6 +1167,12 @@ void tn_ctx_free(tn_ctx *c) {
     batch_destroy(c->cached);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+tn_status tn_ctx_device(const tn_ctx *c, int32_t *device) {
+    if (!c || !device) return fail(TN_EINVAL, "NULL argument");
+    *device = c->device;
+    return TN_OK;
 }
 
 tn_status tn_ctx_synchronize(tn_ctx *c) {

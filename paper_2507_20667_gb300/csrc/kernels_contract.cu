@@ -2,12 +2,15 @@
 //
 //  * k_leaf_convert  complex128 leaves -> storage type, with each leaf's max-abs (one warp/leaf)
 //  * k_step          one step of one job, one block per work tile (graph execution mode)
+//  * k_local         one block per CTA-resident subtree program (all operands in shared memory)
 //  * k_persist       persistent dataflow kernel: every block claims work tiles (job, step, tile)
 //                    from a global list in dependency-level order, waits -- with a bounded spin --
 //                    until the steps producing its operands have completed all their tiles, runs
 //                    the tile and publishes its completion.  Many independent contractions run in
-//                    one launch; the grid is sized to be fully co-resident (cooperative launch),
-//                    which makes the in-order claiming deadlock-free.
+//                    one launch.  Claiming in list order is deadlock-free: a tile is claimed only
+//                    by a running block and waits only on tiles earlier in the list, which were
+//                    claimed by blocks that are running, so the earliest unfinished tile always
+//                    progresses (co-residency of the grid is not needed).
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -322,11 +325,13 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
                               cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
-    int32_t tc = (use_tc && !c128) ? 1 : 0;
-    void *args[] = {(void *)&jobs_dev, (void *)&work, (void *)&n_work, (void *)&counter, (void *)&prof,
-                    (void *)&tc};
-    const void *fn = c128 ? (const void *)k_persist<double> : (const void *)k_persist<float>;
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, tc ? kTcSmem : 0, stream);
+    const int32_t tc = (use_tc && !c128) ? 1 : 0;
+    if (c128)
+        k_persist<double><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof, 0);
+    else
+        k_persist<float><<<(unsigned)grid, kThreads, tc ? kTcSmem : 0, stream>>>(jobs_dev, work, n_work, counter,
+                                                                                prof, tc);
+    return cudaGetLastError();
 }
 
 }  // namespace tn

@@ -238,6 +238,21 @@ def zz_tn(circ: Circuit, i: int, j: int) -> Network:
     return sandwich_tn(circ, [Gate("Z", (i,), Z_MAT), Gate("Z", (j,), Z_MAT)])
 
 
+def zz_slots_tn(circ: Circuit):
+    """<0^n| C^dagger D C |0^n> with D a layer of single-qubit identity slots, one per qubit.
+    Replacing slots i and j by Z gives <psi| Z_i Z_j |psi>, so one network (and one plan) serves
+    every pair.  Returns (network, slot tensor ids by qubit)."""
+    n = circ.n_qubits
+    net = sandwich_tn(circ, [Gate("slot", (q,), np.eye(2)) for q in range(n)])
+    first = n + len(circ.gates)
+    return net, [first + q for q in range(n)]
+
+
+def bra_ids(net: Network, n_qubits: int):
+    """Tensor ids of the bra leaves of an amplitude network, by qubit."""
+    return [net.n_tensors - n_qubits + q for q in range(n_qubits)]
+
+
 def norm_tn(circ: Circuit) -> Network:
     """<psi|psi>: C and its elementwise conjugate joined output wire to output wire (no bras)."""
     n = circ.n_qubits

@@ -72,6 +72,12 @@ class tn_compile_stats(ctypes.Structure):
                 ("arena_bytes", ctypes.c_size_t), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class tn_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("launched_requests", ctypes.c_int64),
+                ("max_in_flight", ctypes.c_int32), ("pad", ctypes.c_int32), ("pool_used", ctypes.c_size_t)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _SIGS = {
@@ -91,6 +97,15 @@ _SIGS = {
     "tn_ctx_create": (_I32, [_I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "tn_ctx_free": (None, [_P]),
     "tn_ctx_synchronize": (_I32, [_P]),
+    "tn_ctx_device": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "tn_serve_create": (_I32, [_P, _I32, ctypes.c_size_t, _I32, ctypes.POINTER(_P)]),
+    "tn_serve_register": (_I32, [_P, _P, _P, ctypes.POINTER(_I32)]),
+    "tn_serve_model_info": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_double)]),
+    "tn_serve_submit": (_I32, [_P, _I32, _I32, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "tn_serve_poll": (_I32, [_P, ctypes.c_uint64, ctypes.c_double, _P, ctypes.POINTER(_I32),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
+    "tn_serve_get_stats": (_I32, [_P, ctypes.POINTER(tn_serve_stats)]),
+    "tn_serve_free": (None, [_P]),
     "tn_ctx_set_exec_mode": (_I32, [_P, _I32]),
     "tn_ctx_set_local_budget": (_I32, [_P, _I32]),
     "tn_batch_create": (_I32, [_P, _I32, _P, _P, _I32, ctypes.POINTER(_P)]),
@@ -141,7 +156,7 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-_LIVE = {name: weakref.WeakSet() for name in ("tn_batch_free", "tn_program_free", "tn_ctx_free",
+_LIVE = {name: weakref.WeakSet() for name in ("tn_serve_free", "tn_batch_free", "tn_program_free", "tn_ctx_free",
                                                "tn_plan_free", "tn_net_free")}
 
 
@@ -172,7 +187,7 @@ def _free_all():
     """Release every live handle, dependents first, while the CUDA runtime is still up (at process
     exit the interpreter would otherwise free them in arbitrary order, possibly after the runtime's
     own teardown)."""
-    for name in ("tn_batch_free", "tn_program_free", "tn_ctx_free", "tn_plan_free", "tn_net_free"):
+    for name in ("tn_serve_free", "tn_batch_free", "tn_program_free", "tn_ctx_free", "tn_plan_free", "tn_net_free"):
         for h in list(_LIVE[name]):
             h.close()
 
@@ -195,6 +210,10 @@ class Program(_Handle):
 
 class Batch(_Handle):
     _free = "tn_batch_free"
+
+
+class Server(_Handle):
+    _free = "tn_serve_free"
 
 
 def tn_build(network) -> Net:
@@ -440,6 +459,59 @@ def tn_dot_noalloc(device: int, stream: int, d_a: int, d_b: int, n: int, precisi
     """Inner product of two device vectors into d_out (device double[2]) without allocating."""
     _check(lib.tn_dot_noalloc(int(device), ctypes.c_void_p(stream) if stream else None, ctypes.c_void_p(d_a),
                               ctypes.c_void_p(d_b), int(n), PRECISIONS[precision], ctypes.c_void_p(d_out)))
+
+
+def tn_ctx_device(ctx: Ctx) -> int:
+    d = ctypes.c_int32()
+    _check(lib.tn_ctx_device(ctx, ctypes.byref(d)))
+    return d.value
+
+
+def tn_serve_create(ctx: Ctx, precision="c64", hbm_budget_bytes=1 << 30, max_batch=64) -> Server:
+    out = ctypes.c_void_p()
+    _check(lib.tn_serve_create(ctx, PRECISIONS[precision], int(hbm_budget_bytes), int(max_batch), ctypes.byref(out)))
+    return Server(out.value, keep=(ctx,))
+
+
+def tn_serve_register(server: Server, net: Net, plan: Plan) -> int:
+    m = ctypes.c_int32()
+    _check(lib.tn_serve_register(server, net, plan, ctypes.byref(m)))
+    return m.value
+
+
+def tn_serve_model_info(server: Server, model: int):
+    b = ctypes.c_size_t()
+    f = ctypes.c_double()
+    _check(lib.tn_serve_model_info(server, int(model), ctypes.byref(b), ctypes.byref(f)))
+    return b.value, f.value
+
+
+def tn_serve_submit(server: Server, model: int, tensors=(), data=()) -> int:
+    t = np.ascontiguousarray(tensors, dtype=np.int32)
+    d = np.ascontiguousarray(np.asarray(data, dtype=np.complex128).ravel()).view(np.float64)
+    tk = ctypes.c_uint64()
+    _check(lib.tn_serve_submit(server, int(model), len(t), _ptr(t), _ptr(d), ctypes.byref(tk)))
+    return tk.value
+
+
+def tn_serve_poll(server: Server, ticket: int, timeout_s: float = 0.0):
+    """None if not finished; else (mantissa complex, exp2, latency_s).  Raises TnError for a
+    request that failed (TN_EBUDGET: larger than the pool)."""
+    amp = np.zeros(2, np.float64)
+    e = ctypes.c_int32()
+    lat = ctypes.c_double()
+    done = ctypes.c_int32()
+    _check(lib.tn_serve_poll(server, ctypes.c_uint64(ticket), float(timeout_s), _ptr(amp), ctypes.byref(e),
+                             ctypes.byref(lat), ctypes.byref(done)))
+    if not done.value:
+        return None
+    return complex(amp[0], amp[1]), e.value, lat.value
+
+
+def tn_serve_get_stats(server: Server) -> dict:
+    st = tn_serve_stats()
+    _check(lib.tn_serve_get_stats(server, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in tn_serve_stats._fields_ if f != "pad"}
 
 
 def tn_version() -> str:

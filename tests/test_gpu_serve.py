@@ -1,0 +1,128 @@
+"""Serving loop with continuous batching (GPU).
+
+Requests for several resident models (amplitudes with different bitstrings, <Z_i Z_j> with
+different pairs) arrive from a client thread at random short intervals while earlier launches
+run.  Every result must equal the same request computed alone through tn_contract bit for bit
+(a request's tiles never depend on other jobs), and match the state vector; a request larger than
+the server's whole memory pool is refused with TN_EBUDGET.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from paper_2507_20667_gb300 import inputs as tni
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tnsa():
+    from paper_2507_20667_gb300 import tnsa as mod
+    return mod
+
+
+def build_models(tnsa):
+    models = []
+    c1 = tni.brickwork_1d(12, 8, seed=51)
+    net = tni.amplitude_tn(c1, [0] * 12)
+    h = tnsa.tn_build(net)
+    models.append(dict(kind="amp", circ=c1, net=net, h=h, ids=tni.bra_ids(net, 12),
+                       plan=tnsa.tn_plan_create(h, k=2, iterations=50, seed=1,
+                                                initial_part=tni.qubit_block_partition(net, 12, 2))))
+    c2 = tni.grid_2d(4, 4, 6, seed=52)
+    net = tni.amplitude_tn(c2, [0] * 16)
+    h = tnsa.tn_build(net)
+    models.append(dict(kind="amp", circ=c2, net=net, h=h, ids=tni.bra_ids(net, 16),
+                       plan=tnsa.tn_plan_create(h, k=4, iterations=50, seed=2,
+                                                initial_part=tni.qubit_block_partition(net, 16, 4))))
+    c3 = tni.brickwork_1d(10, 6, seed=53)
+    net, slots = tni.zz_slots_tn(c3)
+    h = tnsa.tn_build(net)
+    models.append(dict(kind="zz", circ=c3, net=net, h=h, ids=slots,
+                       plan=tnsa.tn_plan_create(h, k=2, iterations=50, seed=3,
+                                                initial_part=tni.qubit_block_partition(net, 10, 2))))
+    return models
+
+
+def request_for(m, rng):
+    n = m["circ"].n_qubits
+    if m["kind"] == "amp":
+        bits = rng.integers(0, 2, n)
+        return m["ids"], np.eye(2, dtype=np.complex128)[bits], ("amp", tuple(int(b) for b in bits))
+    i, j = sorted(rng.choice(n, 2, replace=False))
+    data = [tni.Z_MAT if q in (i, j) else np.eye(2) for q in range(n)]
+    return m["ids"], np.array(data, dtype=np.complex128), ("zz", (int(i), int(j)))
+
+
+def alone(tnsa, ctx, m, tensors, data):
+    h = tnsa.tn_build(m["net"])
+    for t, v in zip(tensors, data):
+        tnsa.tn_net_set_tensor(h, t, v)
+    mant, e, _ = tnsa.tn_contract(ctx, h, m["plan"], "c64")
+    return complex(mant) * 2.0 ** e
+
+
+def test_continuous_batching_mix_equals_alone(tnsa):
+    ctx = tnsa.tn_ctx_create(0)
+    models = build_models(tnsa)
+    server = tnsa.tn_serve_create(ctx, "c64", hbm_budget_bytes=1 << 30, max_batch=16)
+    for m in models:
+        m["id"] = tnsa.tn_serve_register(server, m["h"], m["plan"])
+    rng = np.random.default_rng(9)
+    reqs = []
+    for r in range(90):
+        m = models[r % len(models)]
+        tensors, data, what = request_for(m, rng)
+        reqs.append((m, tensors, data, what))
+    tickets = [None] * len(reqs)
+
+    def client():
+        crng = np.random.default_rng(3)
+        for i, (m, tensors, data, what) in enumerate(reqs):
+            tickets[i] = tnsa.tn_serve_submit(server, m["id"], tensors, data)
+            if crng.random() < 0.3:
+                time.sleep(crng.random() * 0.002)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    results = []
+    for tk in tickets:
+        r = tnsa.tn_serve_poll(server, tk, timeout_s=30.0)
+        assert r is not None
+        results.append(r)
+    stats = tnsa.tn_serve_get_stats(server)
+    assert stats["completed"] == len(reqs) and stats["rejected"] == 0
+    assert stats["launches"] >= 2
+    psi = {id(m["circ"]): sv.simulate(m["circ"]).reshape((2,) * m["circ"].n_qubits) for m in models}
+    for (m, tensors, data, what), (mant, e, lat) in zip(reqs, results):
+        got = complex(mant) * 2.0 ** e
+        assert got == alone(tnsa, ctx, m, tensors, data)        # bit for bit
+        n = m["circ"].n_qubits
+        if what[0] == "amp":
+            ref = psi[id(m["circ"])][what[1]]
+            assert abs(got - ref) <= 1e-5 * max(abs(ref), 2.0 ** (-n / 2))
+        else:
+            ref = sv.zz_expectation(m["circ"], *what[1])
+            assert abs(got - ref) <= 1e-5
+        assert lat > 0
+
+
+def test_request_larger_than_pool_is_refused(tnsa):
+    ctx = tnsa.tn_ctx_create(0)
+    circ = tni.brickwork_1d(20, 10, seed=5)
+    net = tni.amplitude_tn(circ, [0] * 20)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=1)
+    server = tnsa.tn_serve_create(ctx, "c64", hbm_budget_bytes=1 << 20, max_batch=4)
+    mid = tnsa.tn_serve_register(server, h, plan)
+    job_bytes, flops = tnsa.tn_serve_model_info(server, mid)
+    assert job_bytes > (1 << 20)
+    tk = tnsa.tn_serve_submit(server, mid)
+    with pytest.raises(tnsa.TnError) as ei:
+        tnsa.tn_serve_poll(server, tk, timeout_s=10.0)
+    assert ei.value.status == tnsa.TN_EBUDGET
+    assert tnsa.tn_serve_get_stats(server)["rejected"] == 1
