@@ -111,12 +111,21 @@ def test_continuous_batching_mix_equals_alone(tnsa):
         assert lat > 0
 
 
+class _Trace:
+    """trace(A B C) of three 512 x 512 complex matrices: 6 MB of leaves in complex64."""
+    def __init__(self, d=512, seed=1):
+        rng = np.random.default_rng(seed)
+        self.tensors = [rng.standard_normal((d, d)) + 0j for _ in range(3)]
+        self.degrees = np.array([2, 2, 2], np.int32)
+        self.dims = np.array([d] * 6, np.int64)
+        self.data = np.concatenate([t.ravel() for t in self.tensors]).astype(np.complex128).view(np.float64)
+        self.edges = np.array([[0, 1, 1, 0], [1, 1, 2, 0], [2, 1, 0, 0]], np.int32)
+
+
 def test_request_larger_than_pool_is_refused(tnsa):
     ctx = tnsa.tn_ctx_create(0)
-    circ = tni.brickwork_1d(20, 10, seed=5)
-    net = tni.amplitude_tn(circ, [0] * 20)
-    h = tnsa.tn_build(net)
-    plan = tnsa.tn_plan_create(h, k=1)
+    h = tnsa.tn_build(_Trace())
+    plan = tnsa.tn_plan_import(h, [(0, 1), (2, 3)])
     server = tnsa.tn_serve_create(ctx, "c64", hbm_budget_bytes=1 << 20, max_batch=4)
     mid = tnsa.tn_serve_register(server, h, plan)
     job_bytes, flops = tnsa.tn_serve_model_info(server, mid)
