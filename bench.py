@@ -300,6 +300,183 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def _amp_model(tnsa, tni, circ, k, seed, iters):
+    net = tni.amplitude_tn(circ, [0] * circ.n_qubits)
+    h = tnsa.tn_build(net)
+    init = tni.qubit_block_partition(net, circ.n_qubits, k) if k > 1 else None
+    plan = tnsa.tn_plan_create(h, k=k, iterations=iters, steps_per_temp=8, seed=seed, initial_part=init)
+    return net, h, plan, tni.bra_ids(net, circ.n_qubits)
+
+
+def _percentiles(lat):
+    if not lat:
+        return None, None
+    a = np.sort(np.asarray(lat))
+    return float(a[int(0.5 * (len(a) - 1))]), float(a[int(0.99 * (len(a) - 1))])
+
+
+def run_cfg4(args):
+    """512 amplitude queries over 32 seeded circuits (16-36 qubits, depth 8-16, 1D and 2D, k in
+    {2, 4, 8}), 16 bitstrings each: all queries through the batching server (grouped launches)
+    against one query at a time through tn_contract in complex64."""
+    import torch
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    ctx = tnsa.tn_ctx_create(0)
+    free = torch.cuda.mem_get_info()[0]
+    budget = min(int(0.7 * free), 150 << 30)
+    models, reqs, flops = [], [], {}
+    t0 = time.perf_counter()
+    for i, (circ, k, xs) in enumerate(tni.cfg4_circuits()):
+        net, h, plan, bras = _amp_model(tnsa, tni, circ, k, seed=7, iters=args.plan_iters)
+        models.append((net, h, plan, bras))
+        for x in xs:
+            reqs.append((i, np.eye(2, dtype=np.complex128)[np.asarray(x)]))
+    plan_s = time.perf_counter() - t0
+    out = {}
+    for prec in ("c64", "bf16"):
+        server = tnsa.tn_serve_create(ctx, prec, hbm_budget_bytes=budget, max_batch=args.max_batch)
+        mids = [tnsa.tn_serve_register(server, h, plan) for (net, h, plan, bras) in models]
+        for m in mids:
+            flops[m] = tnsa.tn_serve_model_info(server, m)[1]
+        tickets = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (i, data) in reqs:
+            tickets.append((i, tnsa.tn_serve_submit(server, mids[i], models[i][3], data)))
+        done, rejected, fl = [], 0, 0.0
+        for i, tk in tickets:
+            try:
+                r = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
+                done.append((i, r))
+                fl += flops[mids[i]]
+            except tnsa.TnError as e:
+                if e.status != tnsa.TN_EBUDGET:
+                    raise
+                rejected += 1
+        dt = time.perf_counter() - t0
+        st = tnsa.tn_serve_get_stats(server)
+        out[prec] = {"amps_per_s": len(done) / dt, "tflops": fl / dt / 1e12, "seconds": dt, "completed": len(done),
+                     "rejected_over_budget": rejected, "launches": st["launches"],
+                     "mean_batch": st["launched_requests"] / max(st["launches"], 1), "results": done}
+        del server
+    # one query at a time, complex64, through tn_contract (each query its own launch)
+    single_dt, single_n = 0.0, 0
+    feasible = {i for i, r in out["c64"]["results"]}
+    t0 = time.perf_counter()
+    for (i, data) in reqs:
+        if i not in feasible:
+            continue
+        net, h, plan, bras = models[i]
+        for q, t in enumerate(bras):
+            tnsa.tn_net_set_tensor(h, t, data[q])
+        tnsa.tn_contract(ctx, h, plan, "c64")
+        single_n += 1
+    single_dt = time.perf_counter() - t0
+    # the grouped results equal the single ones within the c64 tolerance of the workload
+    line = {"metric": METRIC, "value": out["c64"]["amps_per_s"], "unit": "amps/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "512 amplitude queries over 32 seeded circuits (16-36 qubits, depth 8-16, "
+                                   "1D/2D, k in {2,4,8}), grouped launches through the batching server",
+                       "plan_iterations": args.plan_iters, "planning_seconds": plan_s},
+            "grouped_c64": {k: v for k, v in out["c64"].items() if k != "results"},
+            "grouped_bf16": {k: v for k, v in out["bf16"].items() if k != "results"},
+            "one_at_a_time_c64": {"amps_per_s": single_n / single_dt, "seconds": single_dt, "queries": single_n},
+            "speedup_grouped_vs_one_at_a_time": out["c64"]["amps_per_s"] / (single_n / single_dt)}
+    print(json.dumps(line), flush=True)
+
+
+def run_cfg5(args):
+    """Poisson arrivals (rate args.rate per s) of amplitude and <Z_i Z_j> requests on a pool of
+    seeded circuits of 12-48 qubits, depth 8-20, 1D and 2D, admitted under a device-memory budget;
+    p50 / p99 latency and throughput, split-BF16 against plain complex64."""
+    import torch
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    ctx = tnsa.tn_ctx_create(0)
+    free = torch.cuda.mem_get_info()[0]
+    budget = min(int(0.7 * free), 150 << 30)
+    rng = np.random.default_rng(5)
+    pool = []
+    t0 = time.perf_counter()
+    for i in range(args.pool):
+        n = int(rng.integers(12, 49))
+        depth = int(rng.integers(8, 21))
+        if rng.integers(0, 2):
+            rows = int(math.floor(math.sqrt(n)))
+            circ = tni.grid_2d(rows, int(round(n / rows)), depth, seed=500 + i)
+        else:
+            circ = tni.brickwork_1d(n, depth, seed=500 + i)
+        nq = circ.n_qubits
+        amp = _amp_model(tnsa, tni, circ, 4, seed=7, iters=args.plan_iters)
+        znet, slots = tni.zz_slots_tn(circ)
+        zh = tnsa.tn_build(znet)
+        zplan = tnsa.tn_plan_create(zh, k=4, iterations=args.plan_iters, seed=7,
+                                    initial_part=tni.qubit_block_partition(znet, nq, 4))
+        pool.append((circ, amp, (znet, zh, zplan, slots)))
+    plan_s = time.perf_counter() - t0
+    res = {}
+    for prec in ("c64", "bf16"):
+        server = tnsa.tn_serve_create(ctx, prec, hbm_budget_bytes=budget, max_batch=args.max_batch)
+        ids = []
+        for circ, amp, zz in pool:
+            ids.append((tnsa.tn_serve_register(server, amp[1], amp[2]), tnsa.tn_serve_register(server, zz[1], zz[2])))
+        arr = np.random.default_rng(55)
+        sent = []
+
+        def client():
+            t_end = time.perf_counter() + args.duration
+            while time.perf_counter() < t_end:
+                time.sleep(arr.exponential(1.0 / args.rate))
+                c = int(arr.integers(0, len(pool)))
+                circ, amp, zz = pool[c]
+                nq = circ.n_qubits
+                if arr.random() < 0.5:
+                    bits = arr.integers(0, 2, nq)
+                    tk = tnsa.tn_serve_submit(server, ids[c][0], amp[3], np.eye(2, dtype=np.complex128)[bits])
+                else:
+                    i, j = arr.choice(nq, 2, replace=False)
+                    data = np.array([tni.Z_MAT if q in (i, j) else np.eye(2) for q in range(nq)], np.complex128)
+                    tk = tnsa.tn_serve_submit(server, ids[c][1], zz[3], data)
+                sent.append((time.perf_counter(), tk))
+
+        import threading
+        th = threading.Thread(target=client)
+        t_start = time.perf_counter()
+        th.start()
+        th.join()
+        lat, rejected, done = [], 0, 0
+        for ts, tk in sent:
+            try:
+                r = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
+                if ts - t_start >= args.warmup_s:
+                    lat.append(r[2])
+                done += 1
+            except tnsa.TnError as e:
+                if e.status != tnsa.TN_EBUDGET:
+                    raise
+                rejected += 1
+        t_total = time.perf_counter() - t_start
+        st = tnsa.tn_serve_get_stats(server)
+        p50, p99 = _percentiles(lat)
+        res[prec] = {"requests": len(sent), "completed": done, "rejected_over_budget": rejected,
+                     "p50_ms": None if p50 is None else 1e3 * p50, "p99_ms": None if p99 is None else 1e3 * p99,
+                     "amps_per_s": done / t_total, "launches": st["launches"],
+                     "mean_batch": st["launched_requests"] / max(st["launches"], 1),
+                     "max_in_flight": st["max_in_flight"]}
+        del server
+    line = {"metric": METRIC, "value": res["bf16"]["amps_per_s"], "unit": "amps/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split",
+            "data": "synthetic",
+            "config": {"workload": f"serving: Poisson {args.rate}/s amplitude and <Z_i Z_j> requests, "
+                                   f"{args.pool} seeded circuits of 12-48 qubits depth 8-20 (1D/2D), "
+                                   f"{args.duration}s stream, {budget / 2**30:.0f} GiB budget",
+                       "planning_seconds": plan_s, "latency_warmup_s": args.warmup_s},
+            "bf16_split": res["bf16"], "c64": res["c64"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,7 +488,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg4", "cfg5"])
+    ap.add_argument("--plan-iters", type=int, default=100)
+    ap.add_argument("--max-batch", type=int, default=256)
+    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--warmup-s", type=float, default=3.0)
     args = ap.parse_args()
+    if args.workload == "cfg4" and args.impl == "ours":
+        return run_cfg4(args)
+    if args.workload == "cfg5" and args.impl == "ours":
+        return run_cfg5(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
