@@ -330,7 +330,7 @@ def run_cfg4(args):
     for i, (circ, k, xs) in enumerate(tni.cfg4_circuits()):
         net, h, plan, bras = _amp_model(tnsa, tni, circ, k, seed=7, iters=args.plan_iters)
         models.append((net, h, plan, bras))
-        for x in xs:
+        for x in xs[:args.queries_per_circuit]:
             reqs.append((i, np.eye(2, dtype=np.complex128)[np.asarray(x)]))
     plan_s = time.perf_counter() - t0
     out = {}
@@ -409,21 +409,30 @@ def run_cfg5(args):
         else:
             circ = tni.brickwork_1d(n, depth, seed=500 + i)
         nq = circ.n_qubits
-        amp = _amp_model(tnsa, tni, circ, 4, seed=7, iters=args.plan_iters)
+        try:   # a plan above 2^120 operations is infeasible: its requests count as refused
+            amp = _amp_model(tnsa, tni, circ, 4, seed=7, iters=args.plan_iters)
+        except tnsa.TnError:
+            amp = None
         znet, slots = tni.zz_slots_tn(circ)
         zh = tnsa.tn_build(znet)
-        zplan = tnsa.tn_plan_create(zh, k=4, iterations=args.plan_iters, seed=7,
-                                    initial_part=tni.qubit_block_partition(znet, nq, 4))
-        pool.append((circ, amp, (znet, zh, zplan, slots)))
+        try:
+            zplan = tnsa.tn_plan_create(zh, k=4, iterations=args.plan_iters, seed=7,
+                                        initial_part=tni.qubit_block_partition(znet, nq, 4))
+            zz = (znet, zh, zplan, slots)
+        except tnsa.TnError:
+            zz = None
+        pool.append((circ, amp, zz))
     plan_s = time.perf_counter() - t0
     res = {}
     for prec in ("c64", "bf16"):
         server = tnsa.tn_serve_create(ctx, prec, hbm_budget_bytes=budget, max_batch=args.max_batch)
         ids = []
         for circ, amp, zz in pool:
-            ids.append((tnsa.tn_serve_register(server, amp[1], amp[2]), tnsa.tn_serve_register(server, zz[1], zz[2])))
+            ids.append((tnsa.tn_serve_register(server, amp[1], amp[2]) if amp else None,
+                        tnsa.tn_serve_register(server, zz[1], zz[2]) if zz else None))
         arr = np.random.default_rng(55)
         sent = []
+        unplannable = [0]
 
         def client():
             t_end = time.perf_counter() + args.duration
@@ -434,9 +443,15 @@ def run_cfg5(args):
                 nq = circ.n_qubits
                 if arr.random() < 0.5:
                     bits = arr.integers(0, 2, nq)
+                    if ids[c][0] is None:
+                        unplannable[0] += 1
+                        continue
                     tk = tnsa.tn_serve_submit(server, ids[c][0], amp[3], np.eye(2, dtype=np.complex128)[bits])
                 else:
                     i, j = arr.choice(nq, 2, replace=False)
+                    if ids[c][1] is None:
+                        unplannable[0] += 1
+                        continue
                     data = np.array([tni.Z_MAT if q in (i, j) else np.eye(2) for q in range(nq)], np.complex128)
                     tk = tnsa.tn_serve_submit(server, ids[c][1], zz[3], data)
                 sent.append((time.perf_counter(), tk))
@@ -460,7 +475,8 @@ def run_cfg5(args):
         t_total = time.perf_counter() - t_start
         st = tnsa.tn_serve_get_stats(server)
         p50, p99 = _percentiles(lat)
-        res[prec] = {"requests": len(sent), "completed": done, "rejected_over_budget": rejected,
+        res[prec] = {"requests": len(sent) + unplannable[0], "completed": done,
+                     "rejected_over_budget": rejected, "refused_plan_above_2e120": unplannable[0],
                      "p50_ms": None if p50 is None else 1e3 * p50, "p99_ms": None if p99 is None else 1e3 * p99,
                      "amps_per_s": done / t_total, "launches": st["launches"],
                      "mean_batch": st["launched_requests"] / max(st["launches"], 1),
@@ -489,6 +505,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg4", "cfg5"])
+    ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--pool", type=int, default=32)

@@ -408,9 +408,9 @@ tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_byte
     S->elem = S->c128 ? 16 : 8;
     S->max_batch = max_batch;
     S->local_budget = local_smem_budget(S->c128, 2);
-    // two launches may run at once: each persistent grid takes half of the co-resident capacity
-    S->grid = std::max(1, persistent_grid(S->c128, 0) / 2);
-    S->grid_tc = std::max(1, persistent_grid(S->c128, 1) / 2);
+    // full co-resident grids: a second launch's blocks start as the first one's retire
+    S->grid = std::max(1, persistent_grid(S->c128, 0));
+    S->grid_tc = std::max(1, persistent_grid(S->c128, 1));
     cudaError_t e = cudaMalloc(&S->pool, hbm_budget_bytes);
     if (e != cudaSuccess) {
         delete S;
