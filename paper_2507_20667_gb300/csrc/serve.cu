@@ -314,7 +314,7 @@ void worker_loop(tn_server *S) {
             while (!S->queue.empty() && (int32_t)take.size() < S->max_batch) {
                 Request &r = S->queue.front();
                 const Model &m = *S->models[r.model];
-                if (m.job_bytes + meta_bytes(S, {r}) > S->pool_bytes) {   // can never fit
+                if (m.job_bytes >= S->pool_bytes || m.job_bytes + meta_bytes(S, {r}) > S->pool_bytes) {
                     Result res;
                     res.status = TN_EBUDGET;
                     res.latency = now_s() - r.t_submit;
@@ -439,6 +439,18 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     if (cudaSetDevice(S->device) != cudaSuccess) return fail(TN_ECUDA, "cudaSetDevice");
     std::unique_ptr<Model> m(new (std::nothrow) Model);
     if (!m) return fail(TN_ENOMEM, "allocating the model");
+    // a model whose exact memory count (Eq. 3.1) exceeds the pool can never run: keep it as a
+    // placeholder whose requests are refused with TN_EBUDGET
+    if ((double)plan->impl.mem * (double)S->elem > (double)S->pool_bytes) {
+        m->job_bytes = SIZE_MAX / 4;
+        m->c.n = net->impl.n;
+        m->leaf_off = net->impl.data_off;
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (S->models.size() >= kMaxModels) return fail(TN_EINVAL, "too many models");
+        *model = (int32_t)S->models.size();
+        S->models.push_back(std::move(m));
+        return TN_OK;
+    }
     tn_status s = compile(m->c, net->impl, plan->impl, S->elem, S->local_budget, S->prec == TN_BF16_SPLIT);
     if (s != TN_OK) return s;
     m->leaves = net->impl.data;
