@@ -152,14 +152,22 @@ def dist_env():
     return ws, rank, local
 
 
-def reduce_max(value, ws):
+def reduce_max(value, ws, device="cuda"):
+    """Maximum of `value` over the ranks (the slowest rank's time); no-op for one rank."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank, local_seconds, ws, device="cuda"):
+    """Whole-job throughput of N independent replicas: all ranks' units over the slowest rank's
+    time (max over ranks).  Returns (value, max_seconds)."""
+    t = reduce_max(local_seconds, ws, device)
+    return ws * units_per_rank / t, t
 
 
 def barrier(ws):
@@ -247,9 +255,8 @@ def run_ours(args):
     barrier(ws)
     ms = ev0.elapsed_time(ev1)
     kernel_ms = tnsa.tn_batch_kernel_ms(batch, min(args.steps, 256))
-    ms = reduce_max(ms, ws)
-    ms_per_step = ms / args.steps
-    value = ws * flops_per_step / (ms_per_step * 1e-3) / 1e12
+    value, sec = replica_throughput(args.steps * flops_per_step / 1e12, ms * 1e-3, ws)
+    ms_per_step = 1e3 * sec / args.steps
 
     # end to end through the C ABI with host buffers: every step B new bitstrings are written into
     # pinned host memory, copied to the device with the step, and the B results are read back
