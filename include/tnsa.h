@@ -275,8 +275,8 @@ void tn_batch_free(tn_batch *b);
 /* Diagnostics: cycle accounting of the persistent kernel (costs a few atomics per work item; off
  * by default).  tn_batch_profile waits for the stream and returns 16 accumulated SM-cycle sums and
  * item counts since profiling was switched on: [0..5] work items by kernel class (ROWS, TILE,
- * DOTP, DOTF, -, subtree program), [8..10] steps inside subtree programs by mode (rows, gemm,
- * reduce), [12] dependency waits.  Errors: TN_EINVAL, TN_ECUDA. */
+ * DOTP, DOTF, -, subtree program, TC), [8] waves of subtree programs made of small steps only,
+ * [9] waves that hold block-wide steps, [12] dependency waits.  Errors: TN_EINVAL, TN_ECUDA. */
 tn_status tn_batch_set_profiling(tn_batch *b, int32_t on);
 tn_status tn_batch_profile(tn_batch *b, int64_t *cycles, int64_t *items);
 
