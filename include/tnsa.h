@@ -133,6 +133,8 @@ typedef struct {
     int64_t total_tiles;       /* work tiles of one contraction */
     size_t arena_bytes;        /* device memory for intermediates of one contraction */
     double flops, bytes;       /* algorithmic flops (8 * con_serial) and bytes of one contraction */
+    int32_t n_warp_progs;      /* warp programs: subtrees of small steps run by one warp each */
+    int32_t n_warp_steps;      /* pairwise steps executed inside warp programs */
 } tn_compile_stats;
 tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_precision prec,
                                 int32_t local_budget, tn_compile_stats *out);
@@ -206,9 +208,10 @@ typedef struct {
     double bytes;              /* algorithmic bytes: sum over steps of (|A|+|B|+|C|) * element size */
     size_t arena_bytes;        /* device memory held for intermediates */
     double h2d_bytes;          /* host-to-device bytes copied by the last run (leaf uploads) */
-    int32_t n_local;           /* CTA-resident subtree programs */
-    int32_t n_local_steps;     /* steps executed inside them */
+    int32_t n_local;           /* CTA-resident subtree programs (one block each) */
+    int32_t n_local_steps;     /* steps executed inside subtree and warp programs */
     int32_t dyn_smem;          /* dynamic shared memory per block of the contraction kernels */
+    int32_t n_warp_progs;      /* warp programs (one warp each) */
 } tn_run_info;
 
 /* Compile (net, plan, precision) into a device program: per-step layouts, index maps, kernel

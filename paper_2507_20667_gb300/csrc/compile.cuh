@@ -22,7 +22,9 @@ struct Compiled {
     int64_t total_tiles = 0;
     int32_t dyn_smem = 0;            // largest shared-memory need of a local program
     double flops = 0, bytes = 0;
-    int32_t counts[7] = {0, 0, 0, 0, 0, 0, 0};   // by StepKind; [6] = steps inside programs
+    // by StepKind ([5] = block programs); [6] = steps inside block programs; [7] = warp programs,
+    // [8] = steps inside warp programs
+    int32_t counts[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t plan_uid = 0, shape_hash = 0;
     // device copies (inside the batch's allocation)
     StepDesc *d_steps = nullptr;

@@ -16,6 +16,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -62,7 +63,8 @@ struct tn_batch {
     WorkItem *d_work = nullptr;
     int64_t n_work = 0;
     WorkItem *d_local = nullptr;      // (job, pseudo-step) of every subtree program
-    int32_t n_local_items = 0;
+    int32_t n_warp_items = 0;         // warp programs (first in d_local), then block programs
+    int32_t n_block_items = 0;
     uint32_t *d_counter = nullptr;
     DeviceResult *d_res = nullptr;
     char *d_reset = nullptr;          // results, maxbits, done, counter: zeroed before every run
@@ -282,32 +284,36 @@ bool small_step(const Geom &g, bool job_root) {
 // steps with the whole block.  The memory plan is simulated in that order: all outputs of a wave
 // are placed (best fit) before the inputs it consumed are released.
 bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &geo,
-               const std::vector<int64_t> &size, int32_t elem, int32_t budget, LocalPlan &lp) {
+               const std::vector<int64_t> &size, int32_t elem, int32_t budget,
+               const std::vector<int32_t> &input_prog, LocalPlan &lp) {
     lp = LocalPlan();
     std::vector<int32_t> nodes, stack{v};
     while (!stack.empty()) {
         int32_t x = stack.back();
         stack.pop_back();
-        if (x < n) { lp.leaves.push_back(x); continue; }
+        // inputs: network leaves and the results of warp programs (already in device memory)
+        if (x < n || (x != v && input_prog[x] >= 0)) { lp.leaves.push_back(x); continue; }
         nodes.push_back(x);
         stack.push_back(plan.steps[x - n][0]);
         stack.push_back(plan.steps[x - n][1]);
     }
+    std::unordered_set<int32_t> inner(nodes.begin(), nodes.end());
     std::sort(nodes.begin(), nodes.end());
     std::sort(lp.leaves.begin(), lp.leaves.end());
     const int64_t slots = (int64_t)nodes.size() + (int64_t)lp.leaves.size();
     if (slots > 32000) return false;
-    for (int32_t x : nodes) {
-        const Geom &g = geo[x - n];
-        if (g.M > (1 << 30) || g.N > (1 << 30) || g.K > (1 << 30)) return false;
-    }
+    // element offsets inside one operand are packed in 16 bits by the small-step path
+    for (int32_t x : nodes)
+        if (size[x] > 0xffff) return false;
+    for (int32_t t : lp.leaves)
+        if (size[t] > 0xffff) return false;
     // waves and execution order
     std::unordered_map<int32_t, int32_t> wave;
     int32_t n_waves = 0;
     for (int32_t x : nodes) {
         int32_t w = 0;
         for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
-            if (c >= n) w = std::max(w, wave[c]);
+            if (inner.count(c)) w = std::max(w, wave[c]);
         wave[x] = w + 1;
         n_waves = std::max(n_waves, w + 1);
     }
@@ -356,7 +362,7 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
         for (int32_t i = W.first; i < end; ++i) {
             const int32_t x = lp.nodes[i];
             for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
-                if (c >= n) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
+                if (inner.count(c)) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
         }
     }
     lp.arena_elems = top;
@@ -364,6 +370,68 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     if (lp.leaf_elems + top > (1LL << 30)) return false;
     // every step must fit the compact descriptor
     for (int32_t x : lp.nodes) {
+        const Geom &g = geo[x - n];
+        LocalStep ls;
+        bool p2 = true;
+        if (!make_lgroups(g.md, g.ms, g.ms, false, ls.m_dim, ls.m_str, nullptr, ls.m_lsb, ls.nm, p2) ||
+            !make_lgroups(g.nd, g.ns, g.ns, false, ls.n_dim, ls.n_str, nullptr, ls.n_lsb, ls.nn, p2) ||
+            !make_lgroups(g.kd, g.ksa, g.ksb, true, ls.k_dim, ls.k_sa, ls.k_sb, ls.k_lsb, ls.nk, p2))
+            return false;
+    }
+    return true;
+}
+
+// A warp program: a subtree whose steps are all small, run by one warp in plan order with its
+// intermediates in a kWarpSlice-byte shared-memory slice; leaves are read from device memory and
+// the root's value is written there.
+struct WarpPlan {
+    std::vector<int32_t> nodes;                 // internal nodes, plan order
+    std::unordered_map<int32_t, int32_t> slot;  // internal node -> scale slot
+    std::unordered_map<int32_t, int64_t> loc;   // internal node (not the root) -> element offset
+    int32_t smem_bytes = 0;
+};
+
+bool warp_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &geo,
+              const std::vector<int64_t> &size, int32_t elem, WarpPlan &wp) {
+    wp = WarpPlan();
+    const int32_t root_id = 2 * n - 2;
+    std::vector<int32_t> stack{v};
+    while (!stack.empty()) {
+        const int32_t x = stack.back();
+        stack.pop_back();
+        if (x < n) {
+            if (size[x] > 0xffff) return false;
+            continue;
+        }
+        if (!small_step(geo[x - n], x == root_id) || size[x] > 0xffff) return false;
+        wp.nodes.push_back(x);
+        if (wp.nodes.size() > 4096) return false;
+        stack.push_back(plan.steps[x - n][0]);
+        stack.push_back(plan.steps[x - n][1]);
+    }
+    std::sort(wp.nodes.begin(), wp.nodes.end());
+    for (size_t i = 0; i < wp.nodes.size(); ++i) wp.slot[wp.nodes[i]] = (int32_t)i;
+    const int64_t fixed = (int64_t)warp_fixed_bytes((int32_t)wp.nodes.size());
+    Pool pool;
+    int64_t top = 0;
+    std::unordered_map<int32_t, int64_t> asz;
+    for (int32_t x : wp.nodes) {
+        if (x != v) {
+            const int64_t sz = (size[x] + 1) / 2 * 2;   // 16-byte granules
+            size_t at;
+            if (!pool.take((size_t)sz, at)) {
+                at = (size_t)top;
+                top += sz;
+            }
+            wp.loc[x] = (int64_t)at;
+            asz[x] = sz;
+            if (fixed + top * elem > kWarpSlice) return false;
+        }
+        for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
+            if (c >= n) pool.release((size_t)wp.loc[c], (size_t)asz[c]);
+    }
+    wp.smem_bytes = (int32_t)(fixed + top * elem);
+    for (int32_t x : wp.nodes) {
         const Geom &g = geo[x - n];
         LocalStep ls;
         bool p2 = true;
@@ -428,17 +496,36 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         c.bytes += (double)(size[g.a] + size[g.b] + size[o]) * (double)esz;
     }
     // pass 2: CTA-resident subtree programs -- the maximal subtrees that fit the budget
+    // Warp programs first (maximal subtrees of small steps), then block programs (maximal subtrees
+    // that fit the budget, whose inputs are leaves and warp-program results).
     std::vector<int32_t> prog_of(nn, -1);     // program index for every internal node inside one
+    std::vector<int32_t> wprog_of(nn, -1);    // the same, warp programs only
     std::vector<LocalPlan> lplans;
-    std::vector<int32_t> proot;
+    std::vector<WarpPlan> wplans;
+    std::vector<int32_t> proot, wroot;
     if (local_budget > 0 && n > 1) {
         std::vector<int32_t> stack{nn - 1};
         while (!stack.empty()) {
             const int32_t v = stack.back();
             stack.pop_back();
             if (v < n) continue;
+            WarpPlan wp;
+            if (warp_fit(v, n, plan, geo, size, elem, wp)) {
+                for (int32_t x : wp.nodes) wprog_of[x] = (int32_t)wroot.size();
+                wroot.push_back(v);
+                wplans.push_back(std::move(wp));
+            } else {
+                stack.push_back(plan.steps[v - n][0]);
+                stack.push_back(plan.steps[v - n][1]);
+            }
+        }
+        stack.assign(1, nn - 1);
+        while (!stack.empty()) {
+            const int32_t v = stack.back();
+            stack.pop_back();
+            if (v < n || wprog_of[v] >= 0) continue;
             LocalPlan lp;
-            if (local_fit(v, n, plan, geo, size, elem, local_budget, lp)) {
+            if (local_fit(v, n, plan, geo, size, elem, local_budget, wprog_of, lp)) {
                 for (int32_t x : lp.nodes) prog_of[x] = (int32_t)proot.size();
                 proot.push_back(v);
                 lplans.push_back(std::move(lp));
@@ -447,9 +534,13 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
                 stack.push_back(plan.steps[v - n][1]);
             }
         }
+        // warp programs are numbered after the block programs
+        for (int32_t v = n; v < nn; ++v)
+            if (wprog_of[v] >= 0) prog_of[v] = (int32_t)proot.size() + wprog_of[v];
     }
     std::vector<char> is_proot(nn, 0);
     for (int32_t v : proot) is_proot[v] = 1;
+    for (int32_t v : wroot) is_proot[v] = 1;
     // global memory: outputs of global steps and of programs (not the intermediates of programs)
     std::vector<size_t> bytes(nn, 0), arena_off;
     for (int32_t v = n; v < nn; ++v)
@@ -532,7 +623,11 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             c.counts[STEP_TC]++;
         } else {
             d.kind = STEP_TILE;
-            const int64_t tiles = ((M + kTileM - 1) / kTileM) * ((N + kTileN - 1) / kTileN);
+            // narrow complex64 outputs (N <= 32) use 128 x 32 tiles so no thread computes padding
+            const bool narrow = N <= kTileN / 2 && elem == 8;
+            d.tile_rows = narrow ? kTileNarrow : 0;
+            const int64_t tm = narrow ? 2 * kTileM : kTileM, tn = narrow ? kTileN / 2 : kTileN;
+            const int64_t tiles = ((M + tm - 1) / tm) * ((N + tn - 1) / tn);
             if (tiles > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "step too large");
             d.ntiles = (int32_t)tiles;
             c.steps.push_back(d);
@@ -570,11 +665,14 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         for (const LocalWave &W : lp.waves) c.lwaves.push_back(W);
         for (int32_t t : lp.leaves) {
             LeafRef r;
-            r.global_off = (int32_t)c.leaf_off[t];
+            int64_t goff = t < n ? c.leaf_off[t] : (int64_t)(arena_off[t] / esz);
+            if (goff > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "program input offset above 2^31 elements");
+            r.global_off = (int32_t)goff;
             r.count = (int32_t)size[t];
             r.smem_off = (int32_t)lp.loc[lp.idx.at(t)];
             r.slot = lp.idx.at(t);
             r.node = t;
+            r.src = t < n ? 0 : 1;
             c.leafrefs.push_back(r);
         }
         for (size_t si = 0; si < lp.nodes.size(); ++si) {
@@ -611,6 +709,47 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         c.progs.push_back(P);
     }
     c.counts[6] = (int32_t)c.lsteps.size();
+    // warp programs
+    for (size_t wi = 0; wi < wroot.size(); ++wi) {
+        const WarpPlan &wp = wplans[wi];
+        const int32_t v = wroot[wi];
+        LocalProg P;
+        std::memset(&P, 0, sizeof(P));
+        P.first_step = (int32_t)c.lsteps.size();
+        P.n_steps = (int32_t)wp.nodes.size();
+        P.n_slots = (int32_t)wp.nodes.size();
+        P.smem_bytes = wp.smem_bytes;
+        P.root_node = v;
+        P.root_slot = wp.slot.at(v);
+        P.root_size = (int32_t)size[v];
+        P.root_c_off = (int64_t)(arena_off[v] / esz);
+        P.warp = 1;
+        for (int32_t x : wp.nodes) {
+            const Geom &g = geo[x - n];
+            LocalStep ls;
+            std::memset(&ls, 0, sizeof(ls));
+            ls.M = (int32_t)g.M; ls.N = (int32_t)g.N; ls.K = (int32_t)g.K;
+            ls.flags = LFLAG_SMALL;
+            if (g.a < n) { ls.a_off = g.a; ls.flags |= LFLAG_A_LEAF; }
+            else { ls.a_off = (int32_t)wp.loc.at(g.a); ls.sa = (int16_t)wp.slot.at(g.a); }
+            if (g.b < n) { ls.b_off = g.b; ls.flags |= LFLAG_B_LEAF; }
+            else { ls.b_off = (int32_t)wp.loc.at(g.b); ls.sb = (int16_t)wp.slot.at(g.b); }
+            if (x == v) ls.flags |= LFLAG_C_OUT;
+            else ls.c_off = (int32_t)wp.loc.at(x);
+            ls.sc = (int16_t)wp.slot.at(x);
+            bool p2 = true;
+            make_lgroups(g.md, g.ms, g.ms, false, ls.m_dim, ls.m_str, nullptr, ls.m_lsb, ls.nm, p2);
+            make_lgroups(g.nd, g.ns, g.ns, false, ls.n_dim, ls.n_str, nullptr, ls.n_lsb, ls.nn, p2);
+            make_lgroups(g.kd, g.ksa, g.ksb, true, ls.k_dim, ls.k_sa, ls.k_sb, ls.k_lsb, ls.nk, p2);
+            ls.pow2 = p2 ? 1 : 0;
+            ls.mode = LMODE_ROWS;
+            c.lsteps.push_back(ls);
+        }
+        c.dyn_smem = std::max(c.dyn_smem, (int32_t)kWarpSlice);
+        c.progs.push_back(P);
+        c.counts[7]++;
+        c.counts[8] += P.n_steps;
+    }
     c.total_tiles = 0;
     for (const StepDesc &d : c.steps) c.total_tiles += d.ntiles;
     return TN_OK;
@@ -658,7 +797,8 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         }
         e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess)
-            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_local_items, b->dyn_smem, b->d_prof, st);
+            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, b->n_block_items, b->dyn_smem,
+                             b->d_prof, st);
         if (e == cudaSuccess)
             e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->use_tc,
                               b->d_prof, st);
@@ -799,7 +939,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     }
     const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
     // work list: (job, step, tile) in (level, job, step, tile) order
-    std::vector<WorkItem> work, local_items;
+    std::vector<WorkItem> work, local_items, warp_items;
     if (b->mode == TN_EXEC_PERSISTENT) {
         int64_t total = 0;
         for (int32_t i = 0; i < n; ++i) total += b->comp[b->job_comp[i]].total_tiles;
@@ -814,14 +954,24 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         for (auto &o : order) {
             const StepDesc &d = b->comp[b->job_comp[o[1]]].steps[o[2]];
             if (d.kind == STEP_LOCAL) {
-                local_items.push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
+                const Compiled &c = b->comp[b->job_comp[o[1]]];
+                const LocalProg &P = c.progs[d.tile_rows];
+                (P.warp ? warp_items : local_items).push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
                 continue;
             }
             for (int32_t t = 0; t < d.ntiles; ++t) work.push_back({(uint32_t)o[1], (uint32_t)o[2], (uint32_t)t});
         }
     }
     b->n_work = (int64_t)work.size();
-    b->n_local_items = (int32_t)local_items.size();
+    // warp programs first, longest first (a block of four warps lasts as long as its longest
+    // program), then the block programs
+    std::stable_sort(warp_items.begin(), warp_items.end(), [&](const WorkItem &x, const WorkItem &y) {
+        const Compiled &cx = b->comp[b->job_comp[x.job]], &cy = b->comp[b->job_comp[y.job]];
+        return cx.progs[cx.steps[x.step].tile_rows].n_steps > cy.progs[cy.steps[y.step].tile_rows].n_steps;
+    });
+    b->n_warp_items = (int32_t)warp_items.size();
+    b->n_block_items = (int32_t)local_items.size();
+    local_items.insert(local_items.begin(), warp_items.begin(), warp_items.end());
     const size_t o_work = carve(sizeof(WorkItem) * work.size());
     const size_t o_litems = carve(sizeof(WorkItem) * local_items.size());
     // reset region: results, maxbits, done, counter
@@ -942,13 +1092,15 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->info.n_tile += c.counts[STEP_TILE];
         b->info.n_dot += c.counts[STEP_DOTP];
         b->info.n_tc += c.counts[STEP_TC];
-        b->info.n_local += c.counts[STEP_LOCAL];
-        b->info.n_local_steps += c.counts[6];
+        b->info.n_local += c.counts[STEP_LOCAL] - c.counts[7];
+        b->info.n_local_steps += c.counts[6] + c.counts[8];
+        b->info.n_warp_progs += c.counts[7];
     }
     b->info.dyn_smem = b->dyn_smem;
     b->info.arena_bytes = b->arena_total;
     if (b->mode == TN_EXEC_PERSISTENT) {
-        b->info.launches = 2 + (b->n_local_items > 0 ? 1 : 0);   // leaf conversion, programs, dataflow
+        // leaf conversion, warp programs, block programs, dataflow
+        b->info.launches = 2 + (b->n_warp_items > 0 ? 1 : 0) + (b->n_block_items > 0 ? 1 : 0);
     } else {
         int32_t l = 1;
         for (int32_t i = 0; i < n; ++i) l += (int32_t)b->comp[b->job_comp[i]].steps.size();
@@ -1099,8 +1251,10 @@ tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_preci
     st.n_rows = c.counts[STEP_ROWS];
     st.n_tile = c.counts[STEP_TILE];
     st.n_dot = c.counts[STEP_DOTP];
-    st.n_local = c.counts[STEP_LOCAL];
+    st.n_local = c.counts[STEP_LOCAL] - c.counts[7];
     st.n_local_steps = c.counts[6];
+    st.n_warp_progs = c.counts[7];
+    st.n_warp_steps = c.counts[8];
     st.max_local_smem = c.dyn_smem;
     st.total_tiles = c.total_tiles;
     st.arena_bytes = c.arena_bytes;

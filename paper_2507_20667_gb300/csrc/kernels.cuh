@@ -47,7 +47,8 @@ struct StepDesc {
     int32_t flags;
     int32_t ntiles;                // work tiles of this step
     int32_t dep0, dep1;            // steps producing A and B (-1: a leaf); DOTF: dep0 = its DOTP
-    int32_t tile_rows;             // ROWS: output rows per tile; DOTP: shared indices per tile
+    int32_t tile_rows;             // ROWS: output rows per tile; DOTP: shared indices per tile;
+                                   // TILE: tile shape (0: 64 x 64, kTileNarrow: 128 x 32)
     int32_t part_off;              // DOTP / DOTF: offset of the step's partials (in double2)
     int32_t level;                 // longest path from the leaves (scheduling order)
     int32_t pad[3];
@@ -61,7 +62,11 @@ constexpr int kLG = 6;
 enum LocalMode : uint8_t { LMODE_ROWS = 0, LMODE_GEMM = 1, LMODE_REDUCE = 2 };
 enum LocalFlags : int32_t {
     LFLAG_JOB_ROOT = 1,     // (program, step) produces the job's amplitude
-    LFLAG_SMALL = 2         // (step) small enough for one warp
+    LFLAG_SMALL = 2,        // (step) small enough for one warp
+    // warp programs only: operands read straight from global memory and the program's result
+    LFLAG_A_LEAF = 4,       // A is network leaf number a_off (leaf buffer, maxbits / exp2 of that node)
+    LFLAG_B_LEAF = 8,       // B is network leaf number b_off
+    LFLAG_C_OUT = 16        // C is the program's result: written to the job's arena at root_c_off
 };
 
 // A wave of a program: steps [first, first + n_small) run one per warp, then n_big steps use the
@@ -93,12 +98,13 @@ struct LocalProg {
     int64_t root_c_off;                 // and where it goes in the job's arena
     int32_t flags;                      // LFLAG_JOB_ROOT: the subtree is the whole network
     int32_t first_wave, n_waves;        // into the job's LocalWave array
-    int32_t pad;
+    int32_t warp;                       // 1: a warp program (one warp runs it, steps in order)
 };
 
 struct LeafRef {
-    int32_t global_off, count;          // element offset and size in the job's leaf buffer
-    int32_t smem_off, slot, node;
+    int32_t global_off, count;          // element offset and size in the job's leaf buffer (src 0)
+                                        // or in its arena (src 1: the result of a warp program)
+    int32_t smem_off, slot, node, src;
 };
 
 // Everything one contraction (a "job") owns on the device.  Several jobs may share one compiled
@@ -154,9 +160,10 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
                               long long *prof, cudaStream_t stream);
 // Co-resident grid of the persistent kernel, with tensor-core tiles (use_tc) or without.
 int32_t persistent_grid(bool c128, int32_t use_tc);
-// One block per subtree program; items: (job, pseudo-step, 0).
-cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_items,
-                         int32_t dyn_smem, long long *prof, cudaStream_t stream);
+// Subtree programs; items: (job, pseudo-step, 0), the n_warp warp programs first (four per
+// block of kWarpThreads), then the n_block block programs (one per block, `dyn_smem` bytes).
+cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_warp,
+                         int32_t n_block, int32_t dyn_smem, long long *prof, cudaStream_t stream);
 // Dynamic shared memory a local program may use so that `blocks_per_sm` persistent blocks fit.
 int32_t local_smem_budget(bool c128, int32_t blocks_per_sm);
 cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int64_t n_upd,
@@ -167,8 +174,13 @@ cudaError_t launch_permute(const void *src, void *dst, int32_t elem_bytes, int32
 // Tiling constants shared by the compiler and the kernels.
 constexpr int kThreads = 256;
 constexpr int kTileM = 64, kTileN = 64, kTileK = 16;   // CUDA-core GEMM tile
+constexpr int kTileNarrow = 1;                          // TILE: tile_rows = 1 selects 128 x 32 tiles
 constexpr int kRowsMaxKN = 1024, kRowsMaxK = 64, kRowsMaxN = 16;
 constexpr int kDotMaxOut = 4;
 constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
+// Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
+// slice (step descriptor, scale slots, intermediates).
+constexpr int kWarpThreads = 128;
+constexpr int kWarpSlice = 8192;
 
 }  // namespace tn

@@ -2,6 +2,7 @@
 //
 //  * k_leaf_convert  complex128 leaves -> storage type, with each leaf's max-abs (one warp/leaf)
 //  * k_step          one step of one job, one block per work tile (graph execution mode)
+//  * k_warp          warp programs: subtrees of small steps, one warp each, four per block
 //  * k_local         one block per CTA-resident subtree program (all operands in shared memory)
 //  * k_persist       persistent dataflow kernel: every block claims work tiles (job, step, tile)
 //                    from a global list in dependency-level order, waits -- with a bounded spin --
@@ -79,8 +80,43 @@ __global__ void __launch_bounds__(128) k_leaf_convert(const JobPtrs *__restrict_
 template <typename T>
 __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
                                          float *red, char *dyn, long long *prof) {
-    if (d.kind == STEP_LOCAL) run_local<T>(d.tile_rows, j, dyn, smem, prof);
-    else run_tile<T>(d, tile, j, smem, red);
+    if (d.kind == STEP_LOCAL) {
+        if (__ldcg(&j.progs[d.tile_rows].warp)) {
+            if (threadIdx.x < 32) run_warp_prog<T>(d.tile_rows, j, dyn);   // graph mode: warp 0
+            __syncthreads();
+        } else {
+            run_local<T>(d.tile_rows, j, dyn, smem, prof);
+        }
+    } else {
+        run_tile<T>(d, tile, j, smem, red);
+    }
+}
+
+// Warp programs: every warp of the block runs its own program (no block barrier), in its own
+// kWarpSlice-byte slice of shared memory, and publishes its pseudo-step as complete.
+template <typename T>
+__global__ void __launch_bounds__(kWarpThreads, 6) k_warp(const JobPtrs *__restrict__ jobs,
+                                                          const WorkItem *__restrict__ items, int32_t n_items,
+                                                          long long *prof) {
+    extern __shared__ __align__(16) char dyn[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t g = blockIdx.x * (kWarpThreads / 32) + warp;
+    if (g >= n_items) return;   // warp-uniform; the kernel has no block barrier
+    const WorkItem it = items[g];
+    const JobPtrs &j = jobs[it.job];
+    const int32_t prog = __ldcg(&j.steps[it.step].tile_rows);
+    long long t0 = 0;
+    if (prof && lane == 0) t0 = clock64();
+    run_warp_prog<T>(prog, j, dyn + warp * kWarpSlice);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        atomicAdd(j.done + it.step, 1);
+        if (prof) {
+            atomicAdd((unsigned long long *)(prof + 10), (unsigned long long)(clock64() - t0));
+            atomicAdd((unsigned long long *)(prof + kProfSlots + 10), 1ull);
+        }
+    }
 }
 
 // All subtree programs of a batch: one block per program (they depend on leaves only).  Each
@@ -138,35 +174,42 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ 
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
+    load_desc(d, steps + step);
+    run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
+}
+
+// One tensor-core step (graph execution mode): one block per 128 x 64 output tile.
+__global__ void __launch_bounds__(kThreads) k_step_tc(const StepDesc *__restrict__ steps, int32_t step,
+                                                      JobPtrs job) {
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ StepDesc d;
+    __shared__ __align__(16) char smem[Scratch<float>::bytes];
+    __shared__ float red[32];
     __shared__ uint64_t tc_bar;
     __shared__ uint32_t tc_tmem;
     __shared__ int32_t tc_abort;
     load_desc(d, steps + step);
-    if (d.kind == STEP_TC) {
-        if constexpr (sizeof(T) == 4) {
-            if (threadIdx.x == 0) tc_abort = 0;
-            TcState tc;
-            tc_setup(tc, &tc_tmem, &tc_bar, &tc_abort);
-            const bool ok = tile_tc(d, blockIdx.x, job, dyn, smem, red, tc);
-            if (!ok && threadIdx.x == 0) atomicExch(&static_cast<DeviceResult *>(job.result)->status, kStatusTimeout);
-            tc_teardown(tc);
-        }
-        return;
-    }
-    run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
+    if (threadIdx.x == 0) tc_abort = 0;
+    TcState tc;
+    tc_setup(tc, &tc_tmem, &tc_bar, &tc_abort);
+    const bool ok = tile_tc(d, blockIdx.x, job, dyn, smem, red, tc);
+    if (!ok && threadIdx.x == 0) atomicExch(&static_cast<DeviceResult *>(job.result)->status, kStatusTimeout);
+    tc_teardown(tc);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict__ jobs,
-                                                      const WorkItem *__restrict__ work,
-                                                      int64_t n_work, uint32_t *counter, long long *prof,
-                                                      int32_t use_tc) {
+// Persistent dataflow kernel.  TC: the work list holds tensor-core tiles (complex64 storage
+// only); it is a separate instantiation so that the CUDA-core variant carries no tensor-memory
+// code and keeps two blocks per SM.
+template <typename T, bool TC>
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !TC) ? 2 : 1)
+    k_persist(const JobPtrs *__restrict__ jobs, const WorkItem *__restrict__ work, int64_t n_work,
+              uint32_t *counter, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
     extern __shared__ __align__(16) char dyn[];
     __shared__ uint64_t tc_bar;
     __shared__ uint32_t tc_tmem;
     TcState tc;
-    if (use_tc) tc_setup(tc, &tc_tmem, &tc_bar, abort_flag);
+    if constexpr (TC) tc_setup(tc, &tc_tmem, &tc_bar, abort_flag);
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -179,6 +222,9 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
         if ((int64_t)w >= n_work) break;
         const WorkItem it = work[w];
         const JobPtrs &j = jobs[it.job];
+        // the descriptor's loads are in flight while thread 0 waits for the operands
+        int4 dr[kDescRounds];
+        desc_fetch(dr, j.steps + it.step);
         long long t0 = 0;
         if (threadIdx.x == 0) {
             if (prof) t0 = clock64();
@@ -194,13 +240,15 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
                 t0 = t1;
             }
         }
+        desc_store(dr, d);
         __syncthreads();
-        load_desc(d, j.steps + it.step);
         if (s_ok) {
-            if (d.kind == STEP_TC) {
-                if constexpr (sizeof(T) == 4) {
-                            if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
+            if constexpr (TC) {
+                if (d.kind == STEP_TC) {
+                    if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
                         atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
+                } else {
+                    run_tile<T>(d, it.tile, j, smem, red);
                 }
             } else {
                 run_tile<T>(d, it.tile, j, smem, red);
@@ -216,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_persist(const JobPtrs *__restrict_
             }
         }
     }
-    if (use_tc) tc_teardown(tc);
+    if constexpr (TC) tc_teardown(tc);
 }
 
 // Scatter staged tensor updates {dst offset, count, src offset} into the complex128 leaves.
@@ -259,7 +307,14 @@ cudaError_t allow_dyn_smem(K kernel, int32_t bytes) {
 cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtrs &job, int32_t dyn_smem,
                         cudaStream_t stream) {
     if (h.ntiles <= 0) return cudaErrorInvalidValue;
-    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : (h.kind == STEP_TC ? kTcSmem : 0);
+    if (h.kind == STEP_TC) {
+        if (c128) return cudaErrorInvalidValue;
+        cudaError_t e = allow_dyn_smem(k_step_tc, kTcSmem);
+        if (e != cudaSuccess) return e;
+        k_step_tc<<<(unsigned)h.ntiles, kThreads, kTcSmem, stream>>>(job.steps, step, job);
+        return cudaGetLastError();
+    }
+    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : 0;
     cudaError_t e = c128 ? allow_dyn_smem(k_step<double>, dyn) : allow_dyn_smem(k_step<float>, dyn);
     if (e != cudaSuccess) return e;
     if (c128) k_step<double><<<(unsigned)h.ntiles, kThreads, dyn, stream>>>(job.steps, step, job);
@@ -286,23 +341,39 @@ int32_t persistent_grid(bool c128, int32_t use_tc) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const int32_t dyn = use_tc ? kTcSmem : 0;
-    cudaError_t e = c128 ? allow_dyn_smem(k_persist<double>, dyn) : allow_dyn_smem(k_persist<float>, dyn);
+    cudaError_t e;
+    if (c128) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double, false>, kThreads, 0);
+    } else if (use_tc) {
+        e = allow_dyn_smem(k_persist<float, true>, kTcSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, true>, kThreads, kTcSmem);
+        if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads, 0);
+    }
     if (e != cudaSuccess) return 0;
-    e = c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, dyn)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, dyn);
-    if (e != cudaSuccess) return 0;
-    if (use_tc && per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
     return sms * per_sm;
 }
 
-cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_items,
-                         int32_t dyn_smem, long long *prof, cudaStream_t stream) {
-    if (n_items <= 0) return cudaSuccess;
+cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_warp,
+                         int32_t n_block, int32_t dyn_smem, long long *prof, cudaStream_t stream) {
+    if (n_warp > 0) {
+        constexpr int per_block = kWarpThreads / 32;
+        const int32_t smem = per_block * kWarpSlice;
+        cudaError_t e = c128 ? allow_dyn_smem(k_warp<double>, smem) : allow_dyn_smem(k_warp<float>, smem);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = (unsigned)((n_warp + per_block - 1) / per_block);
+        if (c128) k_warp<double><<<grid, kWarpThreads, smem, stream>>>(jobs_dev, items, n_warp, prof);
+        else k_warp<float><<<grid, kWarpThreads, smem, stream>>>(jobs_dev, items, n_warp, prof);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_block <= 0) return cudaSuccess;
     cudaError_t e = c128 ? allow_dyn_smem(k_local<double>, dyn_smem) : allow_dyn_smem(k_local<float>, dyn_smem);
     if (e != cudaSuccess) return e;
-    if (c128) k_local<double><<<n_items, kThreads, dyn_smem, stream>>>(jobs_dev, items, prof);
-    else k_local<float><<<n_items, kThreads, dyn_smem, stream>>>(jobs_dev, items, prof);
+    if (c128) k_local<double><<<n_block, kThreads, dyn_smem, stream>>>(jobs_dev, items + n_warp, prof);
+    else k_local<float><<<n_block, kThreads, dyn_smem, stream>>>(jobs_dev, items + n_warp, prof);
     return cudaGetLastError();
 }
 
@@ -325,12 +396,12 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
                               cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
-    const int32_t tc = (use_tc && !c128) ? 1 : 0;
     if (c128)
-        k_persist<double><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof, 0);
+        k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
+    else if (use_tc)
+        k_persist<float, true><<<(unsigned)grid, kThreads, kTcSmem, stream>>>(jobs_dev, work, n_work, counter, prof);
     else
-        k_persist<float><<<(unsigned)grid, kThreads, tc ? kTcSmem : 0, stream>>>(jobs_dev, work, n_work, counter,
-                                                                                prof, tc);
+        k_persist<float, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
     return cudaGetLastError();
 }
 

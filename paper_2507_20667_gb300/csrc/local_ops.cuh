@@ -99,52 +99,152 @@ __device__ __forceinline__ LocalSmem local_layout(char *dyn, const LocalProg &P)
     return L;
 }
 
-// A small step computed by one warp: lane per output, K in registers-resident index maps when all
-// dimensions are powers of two; the warp publishes the output's max-abs and exponent itself.
+// A small step computed by one warp: C = A * B with A, B and C at any address (shared memory, or
+// global memory in warp programs).  S lanes share an output (S a power of two, S <= 32 / outputs,
+// S <= K) and split its shared index; their partial sums are combined with xor shuffles.  The
+// shared-index offsets are computed once per 32 indices -- lane l holds (kA, kB) of index k0 + l,
+// packed in 16 bits each (program operands have fewer than 2^16 elements) -- and are broadcast
+// with a shuffle.  The operand scales 2^-eA and 2^-eB are applied together on the B side when
+// their product is a normal number (products then round exactly as with separate scaling), else
+// separately.  Returns the warp-wide max-abs of C (every lane).
 template <typename T>
-__device__ __forceinline__ void local_small(const LocalStep &s, const LocalSmem &L) {
+__device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A, const cx_t<T> *B, cx_t<T> *Cp,
+                                            int32_t eA, int32_t eB) {
     using C = cx_t<T>;
     const int lane = threadIdx.x & 31;
-    const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
-    const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
-    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
-    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
-    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t es = eA + eB;
+    const bool fold = es > -120 && es < 120;
+    const T sA = fold ? (T)1 : pow2<T>(-eA);
+    const T sB = fold ? pow2<T>(-es) : pow2<T>(-eB);
     const int32_t N = s.N, K = s.K, O = s.M * s.N;
+    int32_t S = 1;
+    while (S * 2 * O <= 32 && S < K) S *= 2;
+    const int32_t sub = lane & (S - 1), per_pass = 32 / S;
+    const bool p2 = s.pow2;
     float mx = 0.f;
-    if (s.pow2) {
-        const RegGroups gm = reg_groups(s.nm, s.m_dim, s.m_str, s.m_lsb);
-        const RegGroups gn = reg_groups(s.nn, s.n_dim, s.n_str, s.n_lsb);
-        const RegGroups gka = reg_groups(s.nk, s.k_dim, s.k_sa, s.k_lsb);
-        const RegGroups gkb = reg_groups(s.nk, s.k_dim, s.k_sb, s.k_lsb);
-        for (int32_t o = lane; o < O; o += 32) {
+    for (int32_t o0 = 0; o0 < O; o0 += per_pass) {
+        const int32_t o = o0 + lane / S;
+        const bool act = o < O;
+        int32_t oa = 0, ob = 0;
+        if (act) {
             const int32_t m = o / N, n = o - m * N;
-            const int32_t oa = reg_off(gm, m), ob = reg_off(gn, n);
-            C acc = cmake((T)0, (T)0);
-            for (int32_t k = 0; k < K; ++k)
-                cfma(acc, cscale(A[oa + reg_off(gka, k)], sA), cscale(B[ob + reg_off(gkb, k)], sB));
-            Cp[o] = acc;
-            mx = fmaxf(mx, absmax2(acc));
+            oa = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, p2, m);
+            ob = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, p2, n);
         }
-    } else {
-        for (int32_t o = lane; o < O; o += 32) {
-            const int32_t m = o / N, n = o - m * N;
-            const int32_t oa = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, false, m);
-            const int32_t ob = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, false, n);
-            C acc = cmake((T)0, (T)0);
-            for (int32_t k = 0; k < K; ++k) {
+        C acc = cmake((T)0, (T)0);
+        for (int32_t k0 = 0; k0 < K; k0 += 32) {
+            uint32_t packed = 0;
+            if (k0 + lane < K) {
                 int32_t ka, kb;
-                lgroup_off2(s, k, ka, kb);
-                cfma(acc, cscale(A[oa + ka], sA), cscale(B[ob + kb], sB));
+                lgroup_off2(s, k0 + lane, ka, kb);
+                packed = (uint32_t)ka | ((uint32_t)kb << 16);
             }
+            const int32_t kn = min(32, K - k0);
+            for (int32_t kk = 0; kk < kn; kk += S) {
+                const int32_t k = kk + sub;
+                const uint32_t p = __shfl_sync(0xffffffffu, packed, k & 31);
+                if (act && k < kn) {
+                    const C a = A[oa + (int32_t)(p & 0xffffu)];
+                    const C b = B[ob + (int32_t)(p >> 16)];
+                    cfma(acc, fold ? a : cscale(a, sA), cscale(b, sB));
+                }
+            }
+        }
+        for (int32_t off = S >> 1; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (act && sub == 0) {
             Cp[o] = acc;
             mx = fmaxf(mx, absmax2(acc));
         }
     }
-    mx = warp_max(mx);
-    if (lane == 0) {
+    // non-negative floats order like their bit patterns
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+}
+
+// A small step of a block program, run by one warp; the warp publishes the output's max-abs and
+// exponent itself.
+template <typename T>
+__device__ __forceinline__ void local_small(const LocalStep &s, const LocalSmem &L) {
+    using C = cx_t<T>;
+    const int32_t eA = scale_exponent(L.smax[s.sa]), eB = scale_exponent(L.smax[s.sb]);
+    const float mx = small_core<T>(s, reinterpret_cast<const C *>(L.data) + s.a_off,
+                                   reinterpret_cast<const C *>(L.data) + s.b_off,
+                                   reinterpret_cast<C *>(L.data) + s.c_off, eA, eB);
+    if ((threadIdx.x & 31) == 0) {
         L.smax[s.sc] = __float_as_uint(mx);
         L.sexp[s.sc] = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
+    }
+}
+
+// Shared-memory slice of a warp program: the current step's descriptor, the scale slots of its
+// intermediates, then the intermediates (the host computes the same sizes).
+__device__ __host__ __forceinline__ size_t warp_fixed_bytes(int32_t n_slots) {
+    return sizeof(LocalStep) + ((8 * (size_t)n_slots + 15) / 16) * 16;
+}
+
+// Runs warp program `prog` of job `j` in the calling warp, `slice` being its kWarpSlice bytes of
+// shared memory.  Steps run in plan order; leaf operands are read from the job's leaf buffer, the
+// last step writes the program's result (and its max-abs and exponent) to global memory.  Each
+// step's descriptor is prefetched while the previous step runs.
+template <typename T>
+__device__ void run_warp_prog(int32_t prog, const JobPtrs &j, char *slice) {
+    using C = cx_t<T>;
+    const int lane = threadIdx.x & 31;
+    const LocalProg &P = j.progs[prog];
+    const int32_t n_steps = P.n_steps, first = P.first_step, n_slots = P.n_slots;
+    const int64_t root_c_off = P.root_c_off;
+    const int32_t root_node = P.root_node;
+    LocalStep *desc = reinterpret_cast<LocalStep *>(slice);
+    uint32_t *smax = reinterpret_cast<uint32_t *>(slice + sizeof(LocalStep));
+    int32_t *sexp = reinterpret_cast<int32_t *>(smax + n_slots);
+    C *data = reinterpret_cast<C *>(slice + warp_fixed_bytes(n_slots));
+    const C *leaf = static_cast<const C *>(j.leaf);
+    constexpr int kPieces = (int)(sizeof(LocalStep) / sizeof(int4));
+    static_assert(kPieces <= 32, "one descriptor piece per lane");
+    const int4 *dsrc = reinterpret_cast<const int4 *>(j.lsteps + first);
+    int4 nxt = make_int4(0, 0, 0, 0);
+    if (lane < kPieces) nxt = __ldg(dsrc + lane);
+    for (int32_t si = 0; si < n_steps; ++si) {
+        __syncwarp();   // the previous step is done with the descriptor
+        if (lane < kPieces) reinterpret_cast<int4 *>(desc)[lane] = nxt;
+        __syncwarp();
+        if (si + 1 < n_steps && lane < kPieces) nxt = __ldg(dsrc + (int64_t)(si + 1) * kPieces + lane);
+        const LocalStep &s = *desc;
+        const C *A, *B;
+        int32_t eA, eB, xA, xB;
+        if (s.flags & LFLAG_A_LEAF) {
+            A = leaf + __ldg(j.leaf_off + s.a_off);
+            eA = scale_exponent(__ldcg(j.maxbits + s.a_off));
+            xA = __ldcg(j.exp2 + s.a_off);
+        } else {
+            A = data + s.a_off;
+            eA = scale_exponent(smax[s.sa]);
+            xA = sexp[s.sa];
+        }
+        if (s.flags & LFLAG_B_LEAF) {
+            B = leaf + __ldg(j.leaf_off + s.b_off);
+            eB = scale_exponent(__ldcg(j.maxbits + s.b_off));
+            xB = __ldcg(j.exp2 + s.b_off);
+        } else {
+            B = data + s.b_off;
+            eB = scale_exponent(smax[s.sb]);
+            xB = sexp[s.sb];
+        }
+        const bool out = s.flags & LFLAG_C_OUT;
+        C *Cp = out ? reinterpret_cast<C *>(j.arena) + root_c_off : data + s.c_off;
+        const float mx = small_core<T>(s, A, B, Cp, eA, eB);
+        if (lane == 0) {
+            const int32_t e = xA + eA + xB + eB;
+            if (out) {
+                j.maxbits[root_node] = __float_as_uint(mx);
+                j.exp2[root_node] = e;
+            } else {
+                smax[s.sc] = __float_as_uint(mx);
+                sexp[s.sc] = e;
+            }
+        }
     }
 }
 
@@ -351,6 +451,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
         const int nd = P.n_steps * (int)(sizeof(LocalStep) / 16);
         const int4 *src = reinterpret_cast<const int4 *>(j.lsteps + P.first_step);
         int4 *dst = reinterpret_cast<int4 *>(L.desc);
+#pragma unroll 4
         for (int i = threadIdx.x; i < nd; i += blockDim.x) dst[i] = __ldcg(src + i);
         const int4 *wsrc = reinterpret_cast<const int4 *>(j.lwaves + P.first_wave);
         int4 *wdst = reinterpret_cast<int4 *>(L.waves);
@@ -358,16 +459,26 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     }
     for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
     __syncthreads();
+    // one leaf per thread, its elements in bursts of LB independent loads (gate tensors have at
+    // most 16 elements, so a leaf usually costs one memory latency)
     const C *leaf = static_cast<const C *>(j.leaf);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int32_t l = warp; l < P.n_leaves; l += nw) {
+    constexpr int LB = sizeof(T) == 4 ? 16 : 8;
+    for (int32_t l = threadIdx.x; l < P.n_leaves; l += blockDim.x) {
         const LeafRef r = j.leafrefs[P.first_leaf + l];
-        for (int32_t i = lane; i < r.count; i += 32) data[r.smem_off + i] = __ldcg(leaf + r.global_off + i);
-        if (lane == 0) {
-            L.smax[r.slot] = __ldcg(j.maxbits + r.node);
-            L.sexp[r.slot] = __ldcg(j.exp2 + r.node);
+        L.smax[r.slot] = __ldcg(j.maxbits + r.node);
+        L.sexp[r.slot] = __ldcg(j.exp2 + r.node);
+        const C *src = (r.src ? reinterpret_cast<const C *>(j.arena) : leaf) + r.global_off;
+        for (int32_t i0 = 0; i0 < r.count; i0 += LB) {
+            C v[LB];
+#pragma unroll
+            for (int u = 0; u < LB; ++u)
+                if (i0 + u < r.count) v[u] = __ldcg(src + i0 + u);
+#pragma unroll
+            for (int u = 0; u < LB; ++u)
+                if (i0 + u < r.count) data[r.smem_off + i0 + u] = v[u];
         }
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     long long tp = 0;
     if (prof && threadIdx.x == 0) tp = clock64();

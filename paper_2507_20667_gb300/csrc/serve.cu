@@ -85,7 +85,8 @@ struct Model {
     std::vector<int64_t> leaf_off;
     std::vector<WorkItem> tmpl;       // global work items (job field unused)
     std::vector<int32_t> tmpl_level;
-    std::vector<int32_t> local_steps; // pseudo-steps of subtree programs
+    std::vector<int32_t> local_steps; // pseudo-steps of block programs
+    std::vector<int32_t> warp_steps;  // pseudo-steps of warp programs
     size_t o_leaf = 0, o_arena = 0, o_part = 0, o_exp = 0, job_bytes = 0;
     int32_t max_level = 0;
 };
@@ -192,6 +193,10 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
                 work.push_back(w);
             }
         }
+    // warp programs first, then block programs (launch_local's item order)
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t s : S->models[f.reqs[i].model]->warp_steps) local.push_back({(uint32_t)i, (uint32_t)s, 0u});
+    const int32_t n_warp = (int32_t)local.size();
     for (int32_t i = 0; i < n; ++i)
         for (int32_t s : S->models[f.reqs[i].model]->local_steps) local.push_back({(uint32_t)i, (uint32_t)s, 0u});
     size_t off = 0;
@@ -273,8 +278,8 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     if (e == cudaSuccess) e = cudaMemsetAsync(meta + o_reset, 0, reset_bytes, f.st);
     if (e == cudaSuccess) e = launch_leaf_convert(S->c128, d_jobs, n, max_leaves, f.st);
     if (e == cudaSuccess)
-        e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), (int32_t)local.size(),
-                         S->dyn_smem, nullptr, f.st);
+        e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), n_warp,
+                         (int32_t)local.size() - n_warp, S->dyn_smem, nullptr, f.st);
     if (e == cudaSuccess && !work.empty())
         e = launch_persistent(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_work),
                               (int64_t)work.size(), reinterpret_cast<uint32_t *>(meta + o_counter),
@@ -291,7 +296,7 @@ size_t meta_bytes(tn_server *S, const std::vector<Request> &reqs) {
     for (const Request &r : reqs) {
         const Model &m = *S->models[r.model];
         b += sizeof(double2) * (size_t)m.leaf_off.back() + sizeof(JobPtrs) +
-             sizeof(WorkItem) * (m.tmpl.size() + m.local_steps.size()) + sizeof(DeviceResult) +
+             sizeof(WorkItem) * (m.tmpl.size() + m.local_steps.size() + m.warp_steps.size()) + sizeof(DeviceResult) +
              sizeof(uint32_t) * (size_t)m.c.n_nodes + sizeof(int32_t) * m.c.steps.size() + 5 * 256;
     }
     return b + 16 * 256;
@@ -457,7 +462,8 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     m->leaf_off = net->impl.data_off;
     work_template(m->c, m->tmpl, m->tmpl_level);
     for (size_t st = 0; st < m->c.steps.size(); ++st)
-        if (m->c.steps[st].kind == STEP_LOCAL) m->local_steps.push_back((int32_t)st);
+        if (m->c.steps[st].kind == STEP_LOCAL)
+            (m->c.progs[m->c.steps[st].tile_rows].warp ? m->warp_steps : m->local_steps).push_back((int32_t)st);
     for (int32_t lv : m->tmpl_level) m->max_level = std::max(m->max_level, lv);
     // per-request device bytes: storage leaves, arena, partials, exponents
     size_t off = 0;

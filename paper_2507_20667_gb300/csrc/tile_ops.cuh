@@ -100,6 +100,28 @@ __device__ __forceinline__ void load_desc(StepDesc &dst, const StepDesc *src) {
 }
 static_assert(sizeof(StepDesc) % sizeof(int4) == 0, "descriptor must be a multiple of 16 bytes");
 
+// The same copy in two halves, so that the loads can be in flight while thread 0 waits on the
+// step's dependencies: desc_fetch issues them (one 16-byte piece per thread and round), desc_store
+// writes the pieces to shared memory (the caller then synchronises).
+constexpr int kDescPieces = (int)(sizeof(StepDesc) / sizeof(int4));
+constexpr int kDescRounds = (kDescPieces + kThreads - 1) / kThreads;
+__device__ __forceinline__ void desc_fetch(int4 (&r)[kDescRounds], const StepDesc *src) {
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+#pragma unroll
+    for (int q = 0; q < kDescRounds; ++q) {
+        const int i = threadIdx.x + q * kThreads;
+        if (i < kDescPieces) r[q] = __ldcg(s + i);
+    }
+}
+__device__ __forceinline__ void desc_store(const int4 (&r)[kDescRounds], StepDesc &dst) {
+    int4 *d = reinterpret_cast<int4 *>(&dst);
+#pragma unroll
+    for (int q = 0; q < kDescRounds; ++q) {
+        const int i = threadIdx.x + q * kThreads;
+        if (i < kDescPieces) d[i] = r[q];
+    }
+}
+
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -140,7 +162,9 @@ __device__ __forceinline__ void write_exponent(const StepDesc &d, const JobPtrs 
 template <typename T> struct Scratch {
     using C = cx_t<T>;
     static constexpr int rows = kRowsMaxKN * sizeof(C) + kRowsMaxK * sizeof(int64_t);
-    static constexpr int tile = 2 * kTileK * kTileM * sizeof(C) + (kTileM + kTileN + 2 * kTileK) * sizeof(int64_t);
+    // GEMM operand tiles and index arrays: 64 x 64, and for complex64 also 128 x 32 (the larger)
+    static constexpr int tile_cols = sizeof(T) == 4 ? 2 * kTileM + kTileN / 2 : kTileM + kTileN;
+    static constexpr int tile = kTileK * tile_cols * sizeof(C) + (tile_cols + 4 * kTileK) * sizeof(int64_t);
     static constexpr int dot = (kThreads / 32) * kDotMaxOut * sizeof(double2) + 2 * kDotMaxOut * sizeof(int64_t);
     // subtree programs: the offset table (or dense B) + FP64 partials
     static constexpr int local = (1024 * 8 > kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4 ? 1024 * 8
@@ -155,10 +179,13 @@ template <typename T> struct Scratch {
 // ------------------------------------------------------------------------------ ROWS
 // Tiny-bond contraction (N <= NT <= 16, K <= 64): B (K x N) is staged in shared memory, each
 // thread owns output rows m, reads their K entries of A through the index map and writes N
-// consecutive outputs.  HBM traffic: one read of A, one write of C.
+// consecutive outputs.  The K entries of a row are loaded in bursts of KC independent loads, so
+// a row pays one memory latency per burst instead of one per entry.  HBM traffic: one read of A,
+// one write of C.
 template <typename T, int NT>
 __device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem, float *red) {
     using C = cx_t<T>;
+    constexpr int KC = 8;
     C *Bs = reinterpret_cast<C *>(smem);
     int64_t *kA = reinterpret_cast<int64_t *>(smem + kRowsMaxKN * sizeof(C));
     const int32_t N = (int32_t)d.N, K = (int32_t)d.K;
@@ -180,25 +207,32 @@ __device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     const int64_t m_begin = tile * (int64_t)d.tile_rows;
     const int64_t m_end = min(d.M, m_begin + (int64_t)d.tile_rows);
     float mx = 0.f;
-#pragma unroll 4
     for (int64_t m = m_begin + threadIdx.x; m < m_end; m += blockDim.x) {
-        const int64_t offA = group_off(d.m, m);
+        const C *Arow = A + group_off(d.m, m);
         C acc[NT];
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n] = cmake((T)0, (T)0);
-        for (int32_t k = 0; k < K; ++k) {
-            const C a = ldc(A + offA + kA[k]);
+        for (int32_t k0 = 0; k0 < K; k0 += KC) {
+            C a[KC];
 #pragma unroll
-            for (int n = 0; n < NT; ++n)
-                if (n < N) cfma(acc[n], a, Bs[k * N + n]);
+            for (int kk = 0; kk < KC; ++kk)
+                a[kk] = (k0 + kk < K) ? ldc(Arow + kA[k0 + kk]) : cmake((T)0, (T)0);
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                if (k0 + kk >= K) break;
+                const C av = cscale(a[kk], sA);
+                const C *Bk = Bs + (k0 + kk) * N;
+#pragma unroll
+                for (int n = 0; n < NT; ++n)
+                    if (n < N) cfma(acc[n], av, Bk[n]);
+            }
         }
         C *out = Cp + m * N;
 #pragma unroll
         for (int n = 0; n < NT; ++n)
             if (n < N) {
-                C v = cscale(acc[n], sA);
-                out[n] = v;
-                mx = fmaxf(mx, absmax2(v));
+                out[n] = acc[n];
+                mx = fmaxf(mx, absmax2(acc[n]));
             }
     }
     publish_max(mx, j.maxbits + d.node_c, red);
@@ -216,20 +250,26 @@ __device__ __forceinline__ void tile_rows_dispatch(const StepDesc &d, int64_t ti
 }
 
 // ------------------------------------------------------------------------------ TILE (GEMM)
-// General contraction on CUDA cores: a 64 x 64 output tile, K in chunks of 16, operand tiles
-// gathered through the index maps into shared memory, 4 x 4 outputs per thread.
-template <typename T>
+// General contraction on CUDA cores: a TM x TN output tile (64 x 64, or 128 x 32 for narrow N),
+// K in chunks of kTileK, operand tiles gathered through the index maps into shared memory, 4 x 4
+// outputs per thread.  The gathers of chunk c + 1 are issued into registers before chunk c is
+// computed, so their latency overlaps the arithmetic.
+template <typename T, int TM, int TN>
 __device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem, float *red) {
     using C = cx_t<T>;
-    C(*As)[kTileM] = reinterpret_cast<C(*)[kTileM]>(smem);
-    C(*Bs)[kTileN] = reinterpret_cast<C(*)[kTileN]>(smem + kTileK * kTileM * sizeof(C));
-    int64_t *rowA = reinterpret_cast<int64_t *>(smem + 2 * kTileK * kTileM * sizeof(C));
-    int64_t *colB = rowA + kTileM;
-    int64_t *kAo = colB + kTileN;
-    int64_t *kBo = kAo + kTileK;
+    constexpr int TX = TN / 4, TY = TM / 4;
+    static_assert(TX * TY == kThreads, "one 4 x 4 register tile per thread");
+    constexpr int RA = TM * kTileK / kThreads, RB = TN * kTileK / kThreads;
+    static_assert(RA * kThreads == TM * kTileK && RB * kThreads == TN * kTileK, "operand tile split");
+    C(*As)[TM] = reinterpret_cast<C(*)[TM]>(smem);
+    C(*Bs)[TN] = reinterpret_cast<C(*)[TN]>(smem + kTileK * TM * sizeof(C));
+    int64_t *rowA = reinterpret_cast<int64_t *>(smem + kTileK * (TM + TN) * sizeof(C));
+    int64_t *colB = rowA + TM;
+    int64_t(*kAo)[kTileK] = reinterpret_cast<int64_t(*)[kTileK]>(colB + TN);   // [2][kTileK]
+    int64_t(*kBo)[kTileK] = kAo + 2;
     const int64_t M = d.M, N = d.N, K = d.K;
-    const int64_t tiles_n = (N + kTileN - 1) / kTileN;
-    const int64_t m0 = (tile / tiles_n) * kTileM, n0 = (tile % tiles_n) * kTileN;
+    const int64_t tiles_n = (N + TN - 1) / TN;
+    const int64_t m0 = (tile / tiles_n) * TM, n0 = (tile % tiles_n) * TN;
     int32_t eA, eB;
     step_scales(d, j, eA, eB);
     const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
@@ -237,50 +277,65 @@ __device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     const C *__restrict__ B = operand<C>(d, j, false);
     C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
     const int tid = threadIdx.x;
-    if (tid < kTileM) rowA[tid] = (m0 + tid < M) ? group_off(d.m, m0 + tid) : -1;
-    else if (tid < kTileM + kTileN) {
-        int c = tid - kTileM;
-        colB[c] = (n0 + c < N) ? group_off(d.n, n0 + c) : -1;
+    for (int i = tid; i < TM + TN; i += kThreads) {
+        if (i < TM) rowA[i] = (m0 + i < M) ? group_off(d.m, m0 + i) : -1;
+        else colB[i - TM] = (n0 + i - TM < N) ? group_off(d.n, n0 + i - TM) : -1;
     }
-    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t nch = (K + kTileK - 1) / kTileK;
+    auto koffs = [&](int64_t c) {
+        if (tid < kTileK) {
+            const int64_t k = c * kTileK + tid;
+            int64_t oa = -1, ob = -1;
+            if (k < K) group_off2(d.k, k, oa, ob);
+            kAo[c & 1][tid] = oa;
+            kBo[c & 1][tid] = ob;
+        }
+    };
+    C ra[RA], rb[RB];
+    auto gather = [&](int64_t c) {
+        const int64_t *ka = kAo[c & 1], *kb = kBo[c & 1];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) {
+            const int i = tid + r * kThreads, row = i % TM, kk = i / TM;
+            ra[r] = (rowA[row] >= 0 && ka[kk] >= 0) ? ldc(A + rowA[row] + ka[kk]) : cmake((T)0, (T)0);
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int i = tid + r * kThreads, col = i % TN, kk = i / TN;
+            rb[r] = (colB[col] >= 0 && kb[kk] >= 0) ? ldc(B + kb[kk] + colB[col]) : cmake((T)0, (T)0);
+        }
+    };
+    koffs(0);
+    __syncthreads();
+    gather(0);
+    const int tx = tid % TX, ty = tid / TX;
     C acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cmake((T)0, (T)0);
-    for (int64_t k0 = 0; k0 < K; k0 += kTileK) {
-        __syncthreads();
-        if (tid < kTileK) {
-            int64_t oa = -1, ob = -1;
-            if (k0 + tid < K) group_off2(d.k, k0 + tid, oa, ob);
-            kAo[tid] = oa;
-            kBo[tid] = ob;
-        }
-        __syncthreads();
+    for (int64_t c = 0; c < nch; ++c) {
+        __syncthreads();   // the previous chunk's arithmetic is done with As / Bs
 #pragma unroll
-        for (int r = 0; r < (kTileM * kTileK) / kThreads; ++r) {
-            int i = tid + r * kThreads;
-            int row = i % kTileM, kk = i / kTileM;
-            C v = cmake((T)0, (T)0);
-            if (rowA[row] >= 0 && kAo[kk] >= 0) v = cscale(ldc(A + rowA[row] + kAo[kk]), sA);
-            As[kk][row] = v;
+        for (int r = 0; r < RA; ++r) {
+            const int i = tid + r * kThreads;
+            As[i / TM][i % TM] = cscale(ra[r], sA);
         }
 #pragma unroll
-        for (int r = 0; r < (kTileN * kTileK) / kThreads; ++r) {
-            int i = tid + r * kThreads;
-            int col = i % kTileN, kk = i / kTileN;
-            C v = cmake((T)0, (T)0);
-            if (colB[col] >= 0 && kBo[kk] >= 0) v = cscale(ldc(B + kBo[kk] + colB[col]), sB);
-            Bs[kk][col] = v;
+        for (int r = 0; r < RB; ++r) {
+            const int i = tid + r * kThreads;
+            Bs[i / TN][i % TN] = cscale(rb[r], sB);
         }
+        if (c + 1 < nch) koffs(c + 1);
         __syncthreads();
+        if (c + 1 < nch) gather(c + 1);
 #pragma unroll
         for (int kk = 0; kk < kTileK; ++kk) {
             C a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) b[jj] = Bs[kk][tx + 16 * jj];
+            for (int jj = 0; jj < 4; ++jj) b[jj] = Bs[kk][tx + TX * jj];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -290,11 +345,11 @@ __device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     float mx = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int64_t m = m0 + ty + 16 * i;
+        int64_t m = m0 + ty + TY * i;
         if (m >= M) continue;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            int64_t n = n0 + tx + 16 * jj;
+            int64_t n = n0 + tx + TX * jj;
             if (n < N) {
                 Cp[m * N + n] = acc[i][jj];
                 mx = fmaxf(mx, absmax2(acc[i][jj]));
@@ -306,9 +361,9 @@ __device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
 }
 
 // ------------------------------------------------------------------------------ DOT
-// Small outputs (M * N <= 16) with a long shared index.  DOTP: each tile reduces kDotChunk shared
-// indices; products are formed in the storage precision, summed in runs of 32 in that precision
-// and then in FP64.  DOTF: one tile sums the partials in a fixed order, so results are
+// Small outputs (M * N <= kDotMaxOut) with a long shared index.  DOTP: each tile reduces
+// kDotChunk shared indices; products are formed in the storage precision, summed per thread in
+// bursts of 8 in that precision and then in FP64.  DOTF: one tile sums the partials in a fixed order, so results are
 // reproducible.  The root step of a closed network (M = N = 1) always takes this path: the final
 // reduction of the amplitude is FP64.
 template <typename T>
@@ -328,38 +383,48 @@ __device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     const C *__restrict__ A = operand<C>(d, j, true);
     const C *__restrict__ B = operand<C>(d, j, false);
     double2 acc[kDotMaxOut];
-    C run[kDotMaxOut];
 #pragma unroll
-    for (int i = 0; i < kDotMaxOut; ++i) { acc[i] = make_double2(0, 0); run[i] = cmake((T)0, (T)0); }
+    for (int i = 0; i < kDotMaxOut; ++i) acc[i] = make_double2(0, 0);
     const int64_t k_begin = tile * (int64_t)d.tile_rows;
     const int64_t k_end = min(d.K, k_begin + (int64_t)d.tile_rows);
-    int cnt = 0;
-    for (int64_t k = k_begin + threadIdx.x; k < k_end; k += blockDim.x) {
-        int64_t oa, ob;
-        group_off2(d.k, k, oa, ob);
+    // bursts of U shared indices per thread: offsets first, then U independent load pairs; each
+    // burst is summed in the storage precision and then added in FP64
+    constexpr int U = 8;
+    for (int64_t kb = k_begin; kb < k_end; kb += (int64_t)U * blockDim.x) {
+        int64_t oa[U], ob[U];
 #pragma unroll
-        for (int i = 0; i < kDotMaxOut; ++i) {
-            if (i < MN) {
-                int m = i / N, n = i - m * N;
-                C a = cscale(ldc(A + oa + rowA[m]), sA), b = cscale(ldc(B + ob + colB[n]), sB);
-                cfma(run[i], a, b);
-            }
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = kb + (int64_t)u * blockDim.x + threadIdx.x;
+            oa[u] = -1;
+            ob[u] = 0;
+            if (k < k_end) group_off2(d.k, k, oa[u], ob[u]);
         }
-        if (++cnt == 32) {
+        C run[kDotMaxOut];
+#pragma unroll
+        for (int i = 0; i < kDotMaxOut; ++i) run[i] = cmake((T)0, (T)0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (oa[u] < 0) continue;
 #pragma unroll
             for (int i = 0; i < kDotMaxOut; ++i) {
-                acc[i].x += (double)run[i].x;
-                acc[i].y += (double)run[i].y;
-                run[i] = cmake((T)0, (T)0);
+                if (i < MN) {
+                    const int m = i / N, n = i - m * N;
+                    const C a = cscale(ldc(A + oa[u] + rowA[m]), sA), b = cscale(ldc(B + ob[u] + colB[n]), sB);
+                    cfma(run[i], a, b);
+                }
             }
-            cnt = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kDotMaxOut; ++i) {
+            acc[i].x += (double)run[i].x;
+            acc[i].y += (double)run[i].y;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < kDotMaxOut; ++i) {
         if (i >= MN) break;
-        double x = acc[i].x + (double)run[i].x, y = acc[i].y + (double)run[i].y;
+        double x = acc[i].x, y = acc[i].y;
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_down_sync(0xffffffffu, x, o);
             y += __shfl_down_sync(0xffffffffu, y, o);
@@ -423,7 +488,15 @@ __device__ __forceinline__ void run_tile(const StepDesc &d, int64_t tile, const 
                                          float *red) {
     switch (d.kind) {
         case STEP_ROWS: tile_rows_dispatch<T>(d, tile, j, smem, red); break;
-        case STEP_TILE: tile_gemm<T>(d, tile, j, smem, red); break;
+        case STEP_TILE:
+            if constexpr (sizeof(T) == 4) {
+                if (d.tile_rows == kTileNarrow) {
+                    tile_gemm<T, 2 * kTileM, kTileN / 2>(d, tile, j, smem, red);
+                    break;
+                }
+            }
+            tile_gemm<T, kTileM, kTileN>(d, tile, j, smem, red);
+            break;
         case STEP_DOTP: tile_dotp<T>(d, tile, j, smem); break;
         case STEP_DOTF: tile_dotf<T>(d, j, smem); break;
         default: break;

@@ -59,7 +59,7 @@ class tn_run_info(ctypes.Structure):
                 ("n_tile", ctypes.c_int32), ("n_dot", ctypes.c_int32), ("n_tc", ctypes.c_int32),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
                 ("h2d_bytes", ctypes.c_double), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
-                ("dyn_smem", ctypes.c_int32)]
+                ("dyn_smem", ctypes.c_int32), ("n_warp_progs", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: (getattr(self, f)) for f, _ in self._fields_}
@@ -69,7 +69,8 @@ class tn_compile_stats(ctypes.Structure):
     _fields_ = [("global_steps", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("n_tile", ctypes.c_int32),
                 ("n_dot", ctypes.c_int32), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
                 ("max_local_smem", ctypes.c_int32), ("levels", ctypes.c_int32), ("total_tiles", ctypes.c_int64),
-                ("arena_bytes", ctypes.c_size_t), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("arena_bytes", ctypes.c_size_t), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("n_warp_progs", ctypes.c_int32), ("n_warp_steps", ctypes.c_int32)]
 
 
 class tn_serve_stats(ctypes.Structure):

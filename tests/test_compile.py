@@ -1,0 +1,53 @@
+"""Program compiler (host only, no GPU): how the pairwise steps of a plan are split between warp
+programs (subtrees of small steps, one warp each), block programs (subtrees that fit a block's
+shared memory) and global dataflow steps.
+
+Every pairwise step of the tree (n - 1 of them, Section 2.2) must be executed exactly once: the
+steps inside warp programs, inside block programs, and the global steps (a DOTP + DOTF pair is one
+pairwise step; a program's pseudo-step is not a pairwise step) add up to n - 1, at every budget.
+The algorithmic flop count is the plan's con_serial times 8 (Eq. 3.2), whatever the split.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_20667_gb300 import inputs as tni
+from paper_2507_20667_gb300 import tnsa
+
+KIND_LOCAL, KIND_DOTF = 5, 3
+
+
+def _cfg2_like(n_qubits=16, depth=10, k=4):
+    circ = tni.brickwork_1d(n_qubits, depth, seed=2)
+    net = tni.amplitude_tn(circ, tni.random_bitstring(n_qubits, 1002))
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_create(h, k=k, iterations=200, seed=7,
+                               initial_part=tni.qubit_block_partition(net, n_qubits, k))
+    return net, h, plan
+
+
+@pytest.mark.parametrize("budget", [0, 4096, 32768, 100000])
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_every_step_runs_once(budget, precision):
+    net, h, plan = _cfg2_like()
+    n = len(net.degrees)
+    st = tnsa.tn_plan_compile_stats(h, plan, precision, budget)
+    steps = tnsa.tn_plan_compile_steps(h, plan, precision, budget)
+    kinds = steps[:, 0]
+    global_pairwise = int(np.sum((kinds != KIND_LOCAL) & (kinds != KIND_DOTF)))
+    assert global_pairwise + st["n_local_steps"] + st["n_warp_steps"] == n - 1
+    assert int(np.sum(kinds == KIND_LOCAL)) == st["n_local"] + st["n_warp_progs"]
+    total, _, _ = tnsa.tn_plan_counts(plan)
+    assert st["flops"] == pytest.approx(8.0 * total, rel=1e-12)
+    if budget == 0:
+        assert st["n_local"] == 0 and st["n_warp_progs"] == 0
+
+
+def test_small_step_subtrees_become_warp_programs():
+    """With a budget, gate absorption (tiny steps near the leaves) runs in warp programs and the
+    programs' shared-memory needs respect their limits."""
+    net, h, plan = _cfg2_like()
+    st = tnsa.tn_plan_compile_stats(h, plan, "c64", 100000)
+    assert st["n_warp_progs"] > 0 and st["n_warp_steps"] > 0
+    steps = tnsa.tn_plan_compile_steps(h, plan, "c64", 100000)
+    progs = steps[steps[:, 0] == KIND_LOCAL]
+    assert (progs[:, 7] <= 100000).all() and (progs[:, 6] >= 1).all()
