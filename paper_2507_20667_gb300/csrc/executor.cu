@@ -386,8 +386,9 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
 // the root's value is written there.
 struct WarpPlan {
     std::vector<int32_t> nodes;                 // internal nodes, plan order
-    std::unordered_map<int32_t, int32_t> slot;  // internal node -> scale slot
-    std::unordered_map<int32_t, int64_t> loc;   // internal node (not the root) -> element offset
+    std::vector<int32_t> leaves;                // leaves, increasing
+    std::unordered_map<int32_t, int32_t> slot;  // node (leaf or internal) -> scale slot
+    std::unordered_map<int32_t, int64_t> loc;   // node (not the root) -> element offset in the slice
     int32_t smem_bytes = 0;
 };
 
@@ -401,6 +402,7 @@ bool warp_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &g
         stack.pop_back();
         if (x < n) {
             if (size[x] > 0xffff) return false;
+            wp.leaves.push_back(x);
             continue;
         }
         if (!small_step(geo[x - n], x == root_id) || size[x] > 0xffff) return false;
@@ -410,27 +412,37 @@ bool warp_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &g
         stack.push_back(plan.steps[x - n][1]);
     }
     std::sort(wp.nodes.begin(), wp.nodes.end());
-    for (size_t i = 0; i < wp.nodes.size(); ++i) wp.slot[wp.nodes[i]] = (int32_t)i;
-    const int64_t fixed = (int64_t)warp_fixed_bytes((int32_t)wp.nodes.size());
+    std::sort(wp.leaves.begin(), wp.leaves.end());
+    int32_t ns = 0;
+    for (int32_t t : wp.leaves) wp.slot[t] = ns++;
+    for (int32_t x : wp.nodes) wp.slot[x] = ns++;
+    const int64_t fixed = (int64_t)warp_fixed_bytes(ns);
+    // leaves at the bottom of the slice (staged once), intermediates above them
+    int64_t lpos = 0;
+    for (int32_t t : wp.leaves) {
+        wp.loc[t] = lpos;
+        lpos += (size[t] + 1) / 2 * 2;   // 16-byte granules
+    }
+    if (fixed + lpos * elem > kWarpSlice) return false;
     Pool pool;
     int64_t top = 0;
     std::unordered_map<int32_t, int64_t> asz;
     for (int32_t x : wp.nodes) {
         if (x != v) {
-            const int64_t sz = (size[x] + 1) / 2 * 2;   // 16-byte granules
+            const int64_t sz = (size[x] + 1) / 2 * 2;
             size_t at;
             if (!pool.take((size_t)sz, at)) {
                 at = (size_t)top;
                 top += sz;
             }
-            wp.loc[x] = (int64_t)at;
+            wp.loc[x] = lpos + (int64_t)at;
             asz[x] = sz;
-            if (fixed + top * elem > kWarpSlice) return false;
+            if (fixed + (lpos + top) * elem > kWarpSlice) return false;
         }
         for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
-            if (c >= n) pool.release((size_t)wp.loc[c], (size_t)asz[c]);
+            if (c >= n) pool.release((size_t)(wp.loc[c] - lpos), (size_t)asz[c]);
     }
-    wp.smem_bytes = (int32_t)(fixed + top * elem);
+    wp.smem_bytes = (int32_t)(fixed + (lpos + top) * elem);
     for (int32_t x : wp.nodes) {
         const Geom &g = geo[x - n];
         LocalStep ls;
@@ -441,6 +453,26 @@ bool warp_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &g
             return false;
     }
     return true;
+}
+
+// Staging records of one program input (a leaf, or a warp program's result): pieces of at most
+// kStagePiece elements, so that each thread of the staging loop copies one piece with one burst of
+// loads; the first piece carries the input's scale slot and node.
+constexpr int32_t kStagePiece = 16;
+tn_status push_input(std::vector<LeafRef> &out, int64_t goff, int64_t count, int64_t smem_off, int32_t slot,
+                     int32_t node, int32_t src) {
+    for (int64_t p = 0; p < std::max<int64_t>(count, 1); p += kStagePiece) {
+        if (goff + p > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "program input offset above 2^31 elements");
+        LeafRef r;
+        r.global_off = (int32_t)(goff + p);
+        r.count = (int32_t)std::min<int64_t>(kStagePiece, count - p);
+        r.smem_off = (int32_t)(smem_off + p);
+        r.slot = p == 0 ? slot : -1;
+        r.node = node;
+        r.src = src;
+        out.push_back(r);
+    }
+    return TN_OK;
 }
 
 }  // namespace
@@ -664,17 +696,11 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         // wave step indices are relative to the program (its descriptors are staged per program)
         for (const LocalWave &W : lp.waves) c.lwaves.push_back(W);
         for (int32_t t : lp.leaves) {
-            LeafRef r;
-            int64_t goff = t < n ? c.leaf_off[t] : (int64_t)(arena_off[t] / esz);
-            if (goff > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "program input offset above 2^31 elements");
-            r.global_off = (int32_t)goff;
-            r.count = (int32_t)size[t];
-            r.smem_off = (int32_t)lp.loc[lp.idx.at(t)];
-            r.slot = lp.idx.at(t);
-            r.node = t;
-            r.src = t < n ? 0 : 1;
-            c.leafrefs.push_back(r);
+            const int64_t goff = t < n ? c.leaf_off[t] : (int64_t)(arena_off[t] / esz);
+            tn_status st = push_input(c.leafrefs, goff, size[t], lp.loc[lp.idx.at(t)], lp.idx.at(t), t, t < n ? 0 : 1);
+            if (st != TN_OK) return st;
         }
+        P.n_leaves = (int32_t)c.leafrefs.size() - P.first_leaf;
         for (size_t si = 0; si < lp.nodes.size(); ++si) {
             const int32_t x = lp.nodes[si];
             const Geom &g = geo[x - n];
@@ -717,7 +743,13 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         std::memset(&P, 0, sizeof(P));
         P.first_step = (int32_t)c.lsteps.size();
         P.n_steps = (int32_t)wp.nodes.size();
-        P.n_slots = (int32_t)wp.nodes.size();
+        P.n_slots = (int32_t)(wp.leaves.size() + wp.nodes.size());
+        P.first_leaf = (int32_t)c.leafrefs.size();
+        for (int32_t t : wp.leaves) {
+            tn_status st = push_input(c.leafrefs, c.leaf_off[t], size[t], wp.loc.at(t), wp.slot.at(t), t, 0);
+            if (st != TN_OK) return st;
+        }
+        P.n_leaves = (int32_t)c.leafrefs.size() - P.first_leaf;
         P.smem_bytes = wp.smem_bytes;
         P.root_node = v;
         P.root_slot = wp.slot.at(v);
@@ -730,10 +762,10 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             std::memset(&ls, 0, sizeof(ls));
             ls.M = (int32_t)g.M; ls.N = (int32_t)g.N; ls.K = (int32_t)g.K;
             ls.flags = LFLAG_SMALL;
-            if (g.a < n) { ls.a_off = g.a; ls.flags |= LFLAG_A_LEAF; }
-            else { ls.a_off = (int32_t)wp.loc.at(g.a); ls.sa = (int16_t)wp.slot.at(g.a); }
-            if (g.b < n) { ls.b_off = g.b; ls.flags |= LFLAG_B_LEAF; }
-            else { ls.b_off = (int32_t)wp.loc.at(g.b); ls.sb = (int16_t)wp.slot.at(g.b); }
+            ls.a_off = (int32_t)wp.loc.at(g.a);
+            ls.sa = (int16_t)wp.slot.at(g.a);
+            ls.b_off = (int32_t)wp.loc.at(g.b);
+            ls.sb = (int16_t)wp.slot.at(g.b);
             if (x == v) ls.flags |= LFLAG_C_OUT;
             else ls.c_off = (int32_t)wp.loc.at(x);
             ls.sc = (int16_t)wp.slot.at(x);
@@ -784,9 +816,16 @@ tn_status upload_leaves(tn_batch *b, int32_t job) {
     return TN_OK;
 }
 
+// The stage of the last enqueue_run that failed (for the error message).
+thread_local const char *t_enqueue_stage = "";
+
 cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
+    t_enqueue_stage = "reset";
     cudaError_t e = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
-    if (e == cudaSuccess) e = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+    if (e == cudaSuccess) {
+        t_enqueue_stage = "leaf conversion";
+        e = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+    }
     if (e != cudaSuccess) return e;
     if (b->mode == TN_EXEC_PERSISTENT) {
         cudaEvent_t *ev = b->kev[b->runs % tn_batch::kRing];
@@ -796,12 +835,16 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
             if (e != cudaSuccess) return e;
         }
         e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess) {
+            t_enqueue_stage = "subtree programs";
             e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, b->n_block_items, b->dyn_smem,
                              b->d_prof, st);
-        if (e == cudaSuccess)
+        }
+        if (e == cudaSuccess) {
+            t_enqueue_stage = "dataflow kernel";
             e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->use_tc,
-                              b->d_prof, st);
+                                  b->d_prof, st);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
     } else {
@@ -1165,7 +1208,11 @@ tn_status batch_run(tn_batch *b, void *d_results) {
     }
     CK(cudaEventRecord(b->ev0, st));
     if (b->mode == TN_EXEC_GRAPH) CK(cudaGraphLaunch(b->gexec, st));
-    else CK(enqueue_run(b, st));
+    else {
+        const cudaError_t e = enqueue_run(b, st);
+        if (e != cudaSuccess)
+            return fail(TN_ECUDA, std::string("run (") + t_enqueue_stage + "): " + cudaGetErrorString(e));
+    }
     CK(cudaEventRecord(b->ev1, st));
     if (d_results && d_results != (void *)b->d_res)
         CK(cudaMemcpyAsync(d_results, b->d_res, sizeof(DeviceResult) * (size_t)b->n_jobs,

@@ -63,10 +63,8 @@ enum LocalMode : uint8_t { LMODE_ROWS = 0, LMODE_GEMM = 1, LMODE_REDUCE = 2 };
 enum LocalFlags : int32_t {
     LFLAG_JOB_ROOT = 1,     // (program, step) produces the job's amplitude
     LFLAG_SMALL = 2,        // (step) small enough for one warp
-    // warp programs only: operands read straight from global memory and the program's result
-    LFLAG_A_LEAF = 4,       // A is network leaf number a_off (leaf buffer, maxbits / exp2 of that node)
-    LFLAG_B_LEAF = 8,       // B is network leaf number b_off
-    LFLAG_C_OUT = 16        // C is the program's result: written to the job's arena at root_c_off
+    LFLAG_C_OUT = 16        // (warp programs) C is the program's result: written to the job's
+                            // arena at root_c_off
 };
 
 // A wave of a program: steps [first, first + n_small) run one per warp, then n_big steps use the
@@ -101,9 +99,12 @@ struct LocalProg {
     int32_t warp;                       // 1: a warp program (one warp runs it, steps in order)
 };
 
+// A staging piece of a program input: `count` (at most 16) elements at element offset global_off
+// of the job's leaf buffer (src 0) or of its arena (src 1: a warp program's result), copied to
+// shared-memory element offset smem_off.  The first piece of an input has slot >= 0 and also
+// copies the max-abs and exponent of node `node` into that scale slot.
 struct LeafRef {
-    int32_t global_off, count;          // element offset and size in the job's leaf buffer (src 0)
-                                        // or in its arena (src 1: the result of a warp program)
+    int32_t global_off, count;
     int32_t smem_off, slot, node, src;
 };
 

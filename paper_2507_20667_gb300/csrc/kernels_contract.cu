@@ -297,10 +297,11 @@ cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jo
     return cudaGetLastError();
 }
 
-// Kernels that take more than 48 KB of dynamic shared memory must opt in once per size.
+// Static plus dynamic shared memory above 48 KB per block needs an opt-in for the dynamic part;
+// it is set whenever a kernel takes dynamic shared memory (a cheap host call).
 template <typename K>
 cudaError_t allow_dyn_smem(K kernel, int32_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 0) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -398,8 +399,11 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
     if (grid > n_work) grid = (int32_t)n_work;
     if (c128)
         k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
-    else if (use_tc)
+    else if (use_tc) {
+        const cudaError_t e = allow_dyn_smem(k_persist<float, true>, kTcSmem);
+        if (e != cudaSuccess) return e;
         k_persist<float, true><<<(unsigned)grid, kThreads, kTcSmem, stream>>>(jobs_dev, work, n_work, counter, prof);
+    }
     else
         k_persist<float, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
     return cudaGetLastError();

@@ -99,6 +99,33 @@ __device__ __forceinline__ LocalSmem local_layout(char *dyn, const LocalProg &P)
     return L;
 }
 
+// Copies a program's inputs into shared memory: one staging piece (at most 16 elements of a leaf
+// or of a warp program's result) per thread, its elements loaded in one burst of independent
+// loads; the first piece of each input also copies the input's max-abs and exponent.
+template <typename T>
+__device__ __forceinline__ void stage_inputs(const JobPtrs &j, const LeafRef *refs, int32_t n_refs, int32_t t0,
+                                             int32_t stride, cx_t<T> *data, uint32_t *smax, int32_t *sexp) {
+    using C = cx_t<T>;
+    constexpr int LB = 16;
+    for (int32_t l = t0; l < n_refs; l += stride) {
+        const LeafRef r = refs[l];
+        if (r.slot >= 0) {
+            smax[r.slot] = __ldcg(j.maxbits + r.node);
+            sexp[r.slot] = __ldcg(j.exp2 + r.node);
+        }
+        const C *src = (r.src ? reinterpret_cast<const C *>(j.arena) : static_cast<const C *>(j.leaf)) + r.global_off;
+        for (int32_t i0 = 0; i0 < r.count; i0 += LB) {
+            C v[LB];
+#pragma unroll
+            for (int u = 0; u < LB; ++u)
+                if (i0 + u < r.count) v[u] = __ldcg(src + i0 + u);
+#pragma unroll
+            for (int u = 0; u < LB; ++u)
+                if (i0 + u < r.count) data[r.smem_off + i0 + u] = v[u];
+        }
+    }
+}
+
 // A small step computed by one warp: C = A * B with A, B and C at any address (shared memory, or
 // global memory in warp programs).  S lanes share an output (S a power of two, S <= 32 / outputs,
 // S <= K) and split its shared index; their partial sums are combined with xor shuffles.  The
@@ -185,9 +212,10 @@ __device__ __host__ __forceinline__ size_t warp_fixed_bytes(int32_t n_slots) {
 }
 
 // Runs warp program `prog` of job `j` in the calling warp, `slice` being its kWarpSlice bytes of
-// shared memory.  Steps run in plan order; leaf operands are read from the job's leaf buffer, the
-// last step writes the program's result (and its max-abs and exponent) to global memory.  Each
-// step's descriptor is prefetched while the previous step runs.
+// shared memory.  The warp stages the program's leaves into the slice, then runs the steps in
+// plan order with every operand in shared memory; the last step writes the program's result (and
+// its max-abs and exponent) to global memory.  Each step's descriptor is prefetched while the
+// previous step runs.
 template <typename T>
 __device__ void run_warp_prog(int32_t prog, const JobPtrs &j, char *slice) {
     using C = cx_t<T>;
@@ -200,43 +228,24 @@ __device__ void run_warp_prog(int32_t prog, const JobPtrs &j, char *slice) {
     uint32_t *smax = reinterpret_cast<uint32_t *>(slice + sizeof(LocalStep));
     int32_t *sexp = reinterpret_cast<int32_t *>(smax + n_slots);
     C *data = reinterpret_cast<C *>(slice + warp_fixed_bytes(n_slots));
-    const C *leaf = static_cast<const C *>(j.leaf);
     constexpr int kPieces = (int)(sizeof(LocalStep) / sizeof(int4));
     static_assert(kPieces <= 32, "one descriptor piece per lane");
     const int4 *dsrc = reinterpret_cast<const int4 *>(j.lsteps + first);
     int4 nxt = make_int4(0, 0, 0, 0);
     if (lane < kPieces) nxt = __ldg(dsrc + lane);
+    stage_inputs<T>(j, j.leafrefs + P.first_leaf, P.n_leaves, lane, 32, data, smax, sexp);
     for (int32_t si = 0; si < n_steps; ++si) {
-        __syncwarp();   // the previous step is done with the descriptor
+        __syncwarp();   // staging / the previous step are done with the slice and the descriptor
         if (lane < kPieces) reinterpret_cast<int4 *>(desc)[lane] = nxt;
         __syncwarp();
         if (si + 1 < n_steps && lane < kPieces) nxt = __ldg(dsrc + (int64_t)(si + 1) * kPieces + lane);
         const LocalStep &s = *desc;
-        const C *A, *B;
-        int32_t eA, eB, xA, xB;
-        if (s.flags & LFLAG_A_LEAF) {
-            A = leaf + __ldg(j.leaf_off + s.a_off);
-            eA = scale_exponent(__ldcg(j.maxbits + s.a_off));
-            xA = __ldcg(j.exp2 + s.a_off);
-        } else {
-            A = data + s.a_off;
-            eA = scale_exponent(smax[s.sa]);
-            xA = sexp[s.sa];
-        }
-        if (s.flags & LFLAG_B_LEAF) {
-            B = leaf + __ldg(j.leaf_off + s.b_off);
-            eB = scale_exponent(__ldcg(j.maxbits + s.b_off));
-            xB = __ldcg(j.exp2 + s.b_off);
-        } else {
-            B = data + s.b_off;
-            eB = scale_exponent(smax[s.sb]);
-            xB = sexp[s.sb];
-        }
+        const int32_t eA = scale_exponent(smax[s.sa]), eB = scale_exponent(smax[s.sb]);
+        const int32_t e = sexp[s.sa] + eA + sexp[s.sb] + eB;
         const bool out = s.flags & LFLAG_C_OUT;
         C *Cp = out ? reinterpret_cast<C *>(j.arena) + root_c_off : data + s.c_off;
-        const float mx = small_core<T>(s, A, B, Cp, eA, eB);
+        const float mx = small_core<T>(s, data + s.a_off, data + s.b_off, Cp, eA, eB);
         if (lane == 0) {
-            const int32_t e = xA + eA + xB + eB;
             if (out) {
                 j.maxbits[root_node] = __float_as_uint(mx);
                 j.exp2[root_node] = e;
@@ -248,53 +257,11 @@ __device__ void run_warp_prog(int32_t prog, const JobPtrs &j, char *slice) {
     }
 }
 
-// One step, all operands in shared memory.  Modes:
-//   LMODE_ROWS    N <= 16, K <= 64: a thread owns output rows and keeps the N outputs in registers
-//   LMODE_GEMM    M, N >= 32: 16 x 16 threads, 4 x 4 register tile per thread per 64 x 64 block
-//   LMODE_REDUCE  few outputs, long K: S threads per output split K, FP64 partial sums, shuffle /
-//                 shared-memory reduction; the job's root (the amplitude) always takes this mode
-template <typename T, int NT>
-__device__ __forceinline__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
-                                           char *scratch) {
-    using C = cx_t<T>;
-    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
-    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
-    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
-    C *Bd = reinterpret_cast<C *>(scratch);                                   // [K][N], scaled
-    int32_t *kat = reinterpret_cast<int32_t *>(scratch + kRowsMaxKN * sizeof(C));   // [K]
-    const int32_t N = s.N, K = s.K, M = s.M;
-    for (int32_t i = threadIdx.x; i < K * N; i += blockDim.x) {
-        const int32_t k = i / N, n = i - k * N;
-        int32_t ka, kb;
-        lgroup_off2(s, k, ka, kb);
-        kb += lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n);
-        Bd[i] = cscale(B[kb], sB);
-        if (n == 0) kat[k] = ka;
-    }
-    const bool p2 = s.pow2;
-    const RegGroups gm = reg_groups(s.nm, s.m_dim, s.m_str, s.m_lsb);
-    __syncthreads();
-    for (int32_t m = threadIdx.x; m < M; m += blockDim.x) {
-        const int32_t offA = p2 ? reg_off(gm, m) : lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, false, m);
-        C acc[NT];
-#pragma unroll
-        for (int n = 0; n < NT; ++n) acc[n] = cmake((T)0, (T)0);
-        for (int32_t k = 0; k < K; ++k) {
-            const C a = cscale(A[offA + kat[k]], sA);
-#pragma unroll
-            for (int n = 0; n < NT; ++n)
-                if (n < N) cfma(acc[n], a, Bd[k * N + n]);
-        }
-        C *out = Cp + m * N;
-#pragma unroll
-        for (int n = 0; n < NT; ++n)
-            if (n < N) {
-                out[n] = acc[n];
-                mx = fmaxf(mx, absmax2(acc[n]));
-            }
-    }
-}
-
+// Block-wide steps of block programs (all operands in shared memory).  Modes:
+//   LMODE_ROWS / LMODE_GEMM   register-tiled GEMM (local_mm), tile shape chosen by N
+//   LMODE_REDUCE              few outputs, long K: S threads per output split K, FP64 partial sums,
+//                             shuffle / shared-memory reduction; the job's root (the amplitude)
+//                             always takes this mode
 // Shared-index offsets of a step, tabulated in shared memory when K <= kKTab.
 __device__ __forceinline__ void build_ktab(const LocalStep &s, int2 *kt) {
     if (s.K > kKTab) return;
@@ -312,58 +279,106 @@ __device__ __forceinline__ int2 kofs(const LocalStep &s, const int2 *kt, int32_t
     return make_int2(ka, kb);
 }
 
-template <typename T>
-__device__ __forceinline__ void local_gemm(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
-                                           const int2 *kt) {
+// Block-wide contraction with every operand in shared memory, register-tiled: the block's 256
+// threads form TX x TY with RM x RN outputs each, covering a (TY*RM) x (TX*RN) output tile.  The
+// shared index runs in chunks of TK: the chunk's A and B entries are gathered through the index
+// maps (scaled exactly) into padded, transposed tiles of the scratch area -- so that the
+// arithmetic loop reads them without bank conflicts -- and each thread accumulates its outputs in
+// registers.  The gather maps consecutive threads along whichever index is contiguous in the
+// operand (k or m for A, k or n for B).
+template <typename T, int TX, int TY, int RM, int RN, int TK>
+__device__ void local_mm(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx, char *scratch) {
     using C = cx_t<T>;
+    static_assert(TX * TY == kThreads, "256 threads");
+    constexpr int TM = TY * RM, TN = TX * RN, PA = TM + 1, PB = TN + 1;
+    C *As = reinterpret_cast<C *>(scratch);              // [TK][PA]
+    C *Bs = As + TK * PA;                                // [TK][PB]
+    int32_t *ra = reinterpret_cast<int32_t *>(Bs + TK * PB);   // [TM] row offsets in A
+    int32_t *cb = ra + TM;                                      // [TN] column offsets in B
+    int2 *kt = reinterpret_cast<int2 *>(cb + TN);               // [TK] shared-index offsets
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
     C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
     const int32_t M = s.M, N = s.N, K = s.K;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int32_t m0 = 0; m0 < M; m0 += 64)
-        for (int32_t n0 = 0; n0 < N; n0 += 64) {
-            int32_t ra[4], cb[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int32_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * i;
-                ra[i] = m < M ? lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, s.pow2, m) : -1;
-                cb[i] = n < N ? lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, s.pow2, n) : -1;
+    const bool p2 = s.pow2;
+    const bool a_k_inner = s.nk > 0 && s.k_sa[0] == 1;   // k contiguous in A
+    const bool b_k_inner = s.nk > 0 && s.k_sb[0] == 1;   // k contiguous in B
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    for (int32_t m0 = 0; m0 < M; m0 += TM)
+        for (int32_t n0 = 0; n0 < N; n0 += TN) {
+            __syncthreads();   // the previous tile is done with the scratch
+            for (int i = tid; i < TM + TN; i += kThreads) {
+                if (i < TM) ra[i] = m0 + i < M ? lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, p2, m0 + i) : -1;
+                else cb[i - TM] = n0 + i - TM < N ? lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, p2, n0 + i - TM) : -1;
             }
-            C acc[4][4];
+            C acc[RM][RN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = cmake((T)0, (T)0);
-            for (int32_t k = 0; k < K; ++k) {
-                const int2 ko = kofs(s, kt, k);
-                const int32_t ka = ko.x, kb = ko.y;
-                C a[4], b[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    a[i] = ra[i] >= 0 ? cscale(A[ra[i] + ka], sA) : cmake((T)0, (T)0);
-                    b[i] = cb[i] >= 0 ? cscale(B[kb + cb[i]], sB) : cmake((T)0, (T)0);
+                for (int jj = 0; jj < RN; ++jj) acc[i][jj] = cmake((T)0, (T)0);
+            for (int32_t k0 = 0; k0 < K; k0 += TK) {
+                if (tid < TK) {
+                    int2 o = make_int2(-1, -1);
+                    if (k0 + tid < K) lgroup_off2(s, k0 + tid, o.x, o.y);
+                    kt[tid] = o;
                 }
+                __syncthreads();
+                for (int e = tid; e < TM * TK; e += kThreads) {
+                    const int row = a_k_inner ? e / TK : e % TM, kk = a_k_inner ? e % TK : e / TM;
+                    const int2 o = kt[kk];
+                    As[kk * PA + row] = (ra[row] >= 0 && o.x >= 0) ? cscale(A[ra[row] + o.x], sA) : cmake((T)0, (T)0);
+                }
+                for (int e = tid; e < TN * TK; e += kThreads) {
+                    const int col = b_k_inner ? e / TK : e % TN, kk = b_k_inner ? e % TK : e / TN;
+                    const int2 o = kt[kk];
+                    Bs[kk * PB + col] = (cb[col] >= 0 && o.x >= 0) ? cscale(B[o.y + cb[col]], sB) : cmake((T)0, (T)0);
+                }
+                __syncthreads();
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int kk = 0; kk < TK; ++kk) {
+                    C a[RM], b[RN];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) cfma(acc[i][jj], a[i], b[jj]);
+                    for (int i = 0; i < RM; ++i) a[i] = As[kk * PA + ty + TY * i];
+#pragma unroll
+                    for (int jj = 0; jj < RN; ++jj) b[jj] = Bs[kk * PB + tx + TX * jj];
+#pragma unroll
+                    for (int i = 0; i < RM; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < RN; ++jj) cfma(acc[i][jj], a[i], b[jj]);
+                }
+                __syncthreads();   // the chunk's tiles and offsets are rewritten next
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int32_t m = m0 + ty + 16 * i;
+            for (int i = 0; i < RM; ++i) {
+                const int32_t m = m0 + ty + TY * i;
                 if (m >= M) continue;
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int32_t n = n0 + tx + 16 * jj;
+                for (int jj = 0; jj < RN; ++jj) {
+                    const int32_t n = n0 + tx + TX * jj;
                     if (n < N) {
-                        const C v = acc[i][jj];
-                        Cp[m * N + n] = v;
-                        mx = fmaxf(mx, absmax2(v));
+                        Cp[m * N + n] = acc[i][jj];
+                        mx = fmaxf(mx, absmax2(acc[i][jj]));
                     }
                 }
             }
         }
+}
+
+// Scratch bytes of local_mm: the largest tile set (TK = 8 for complex64, 4 for complex128).
+template <typename T> struct LocalMmScratch {
+    static constexpr int TK = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int bytes = TK * (257 + 65) * (int)sizeof(cx_t<T>) + (256 + 64) * 4 + TK * 8;
+};
+
+template <typename T>
+__device__ __forceinline__ void local_mm_dispatch(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
+                                                  char *scratch) {
+    constexpr int TK = LocalMmScratch<T>::TK;
+    if (s.N <= 4) local_mm<T, 1, 256, 1, 4, TK>(s, L, sA, sB, mx, scratch);
+    else if (s.N <= 8) local_mm<T, 2, 128, 2, 4, TK>(s, L, sA, sB, mx, scratch);
+    else if (s.N <= 16) local_mm<T, 4, 64, 4, 4, TK>(s, L, sA, sB, mx, scratch);
+    else if (s.N <= 32) local_mm<T, 8, 32, 4, 4, TK>(s, L, sA, sB, mx, scratch);
+    else local_mm<T, 16, 16, 4, 4, TK>(s, L, sA, sB, mx, scratch);
 }
 
 // REDUCE: threads are grouped S per output (S a power of two, S <= blockDim); each group splits K
@@ -459,25 +474,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     }
     for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
     __syncthreads();
-    // one leaf per thread, its elements in bursts of LB independent loads (gate tensors have at
-    // most 16 elements, so a leaf usually costs one memory latency)
-    const C *leaf = static_cast<const C *>(j.leaf);
-    constexpr int LB = sizeof(T) == 4 ? 16 : 8;
-    for (int32_t l = threadIdx.x; l < P.n_leaves; l += blockDim.x) {
-        const LeafRef r = j.leafrefs[P.first_leaf + l];
-        L.smax[r.slot] = __ldcg(j.maxbits + r.node);
-        L.sexp[r.slot] = __ldcg(j.exp2 + r.node);
-        const C *src = (r.src ? reinterpret_cast<const C *>(j.arena) : leaf) + r.global_off;
-        for (int32_t i0 = 0; i0 < r.count; i0 += LB) {
-            C v[LB];
-#pragma unroll
-            for (int u = 0; u < LB; ++u)
-                if (i0 + u < r.count) v[u] = __ldcg(src + i0 + u);
-#pragma unroll
-            for (int u = 0; u < LB; ++u)
-                if (i0 + u < r.count) data[r.smem_off + i0 + u] = v[u];
-        }
-    }
+    stage_inputs<T>(j, j.leafrefs + P.first_leaf, P.n_leaves, threadIdx.x, blockDim.x, data, L.smax, L.sexp);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     long long tp = 0;
@@ -494,15 +491,12 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
             const int32_t e_out = L.sexp[s.sa] + eA + L.sexp[s.sb] + eB;
             float mx = 0.f;
             const int2 *kt = reinterpret_cast<const int2 *>(scratch);
-            if (s.mode == LMODE_ROWS) {
-                if (s.N <= 1) local_rows<T, 1>(s, L, sA, sB, mx, scratch);
-                else if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
-                else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
+            if (s.mode != LMODE_REDUCE) {
+                local_mm_dispatch<T>(s, L, sA, sB, mx, scratch);
             } else {
                 build_ktab(s, reinterpret_cast<int2 *>(scratch));
                 __syncthreads();
-                if (s.mode == LMODE_GEMM) local_gemm<T>(s, L, sA, sB, mx, kt);
-                else local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out, kt);
+                local_reduce<T>(s, L, sA, sB, mx, red64, j, e_out, kt);
             }
             mx = warp_max(mx);
             if (lane == 0 && mx > 0.f) atomicMax(L.smax + s.sc, __float_as_uint(mx));

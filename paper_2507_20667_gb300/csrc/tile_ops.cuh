@@ -161,14 +161,16 @@ __device__ __forceinline__ void write_exponent(const StepDesc &d, const JobPtrs 
 // Shared-memory scratch needed by any tile function, per element type.
 template <typename T> struct Scratch {
     using C = cx_t<T>;
+    static constexpr int TK_MM = sizeof(T) == 4 ? 8 : 4;   // shared-index chunk of local_mm
     static constexpr int rows = kRowsMaxKN * sizeof(C) + kRowsMaxK * sizeof(int64_t);
     // GEMM operand tiles and index arrays: 64 x 64, and for complex64 also 128 x 32 (the larger)
     static constexpr int tile_cols = sizeof(T) == 4 ? 2 * kTileM + kTileN / 2 : kTileM + kTileN;
     static constexpr int tile = kTileK * tile_cols * sizeof(C) + (tile_cols + 4 * kTileK) * sizeof(int64_t);
     static constexpr int dot = (kThreads / 32) * kDotMaxOut * sizeof(double2) + 2 * kDotMaxOut * sizeof(int64_t);
-    // subtree programs: the offset table (or dense B) + FP64 partials
-    static constexpr int local = (1024 * 8 > kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4 ? 1024 * 8
-                                  : kRowsMaxKN * (int)sizeof(C) + kRowsMaxK * 4) + (kThreads / 32) * 16;
+    // subtree programs: the register-tiled GEMM's operand tiles and offsets, or the REDUCE mode's
+    // offset table and FP64 partials
+    static constexpr int mm = (TK_MM * (257 + 65) * (int)sizeof(C) + (256 + 64) * 4 + TK_MM * 8 + 15) / 16 * 16;
+    static constexpr int local = mm > 1024 * 8 + (kThreads / 32) * 16 ? mm : 1024 * 8 + (kThreads / 32) * 16;
     static constexpr int tc = (128 + 64 + 32 + 32) * (int)sizeof(int64_t);   // tensor-core tile offsets
     static constexpr int m0 = rows > tc ? rows : tc;
     static constexpr int m1 = m0 > tile ? m0 : tile;
