@@ -220,6 +220,11 @@ def run_ours(args):
     con_serial, con_dist, mem = tnsa.tn_plan_counts(plan)
     stream = torch.cuda.Stream()
     ctx = tnsa.tn_ctx_create(local, stream=stream.cuda_stream)
+    tuning = None
+    if not args.no_autotune:
+        # untimed setup: the library's autotuner times its candidate configurations on this batch
+        best, best_ms, cand = tnsa.tn_ctx_autotune(ctx, handles, [plan] * B, args.precision, runs=5)
+        tuning = {"config": best, "ms_per_run": best_ms, "candidates_ms": cand}
     batch = tnsa.tn_batch_create(ctx, handles, [plan] * B, args.precision)
     info = tnsa.tn_batch_last_info(batch)
     flops_per_step = B * 8.0 * con_serial
@@ -294,15 +299,17 @@ def run_ours(args):
                     "amps_per_s": ws * e2e_steps * B / dt, "steps": e2e_steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "contraction kernels of one run (k_local<float> subtree programs + "
-                                   "k_persist<float> dataflow steps), events around both",
+                         "kernel": "contraction kernels of one run (k_warp warp programs, k_local block "
+                                   "programs, k_persist dataflow steps), events around all of them",
                          "kernel_ms": kernel_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
             "gpu_launches": info["launches"] * args.steps,
-            "exec": {"subtree_programs": info["n_local"], "steps_in_programs": info["n_local_steps"],
+            "exec": {"warp_programs": info["n_warp_progs"], "block_programs": info["n_local"],
+                     "steps_in_programs": info["n_local_steps"],
                      "dyn_smem": info["dyn_smem"], "global_rows": info["n_gather"], "global_tile": info["n_tile"],
                      "global_dot": info["n_dot"]},
             "clocks": clocks.summary(),
             "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem},
+            "tuning": tuning,
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
@@ -511,6 +518,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg4", "cfg5"])
     ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)

@@ -200,6 +200,38 @@ tn_status tn_ctx_set_exec_mode(tn_ctx *ctx, int32_t mode);
  * Takes effect for programs and batches created afterwards.  Errors: TN_EINVAL. */
 tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
 
+/* Execution configuration of a context (applies to programs, batches and servers created
+ * afterwards; the autotuner below picks one by measurement).
+ *   local_budget     as tn_ctx_set_local_budget: shared memory per block program, -1 automatic
+ *                    (two blocks per SM), 0 no subtree programs of any kind
+ *   big_programs     1: large programs -- maximal subtrees that fit the shared memory of one block
+ *                    per SM, each input staged when it is consumed (fan-in chains); 0: none
+ *   warp_programs    1: warp programs -- subtrees of small steps run by one warp each; 0: none
+ *   tc_min_m/n/k     in the split precisions, a dense step runs on the tensor cores when
+ *                    M >= tc_min_m, N >= tc_min_n and K >= tc_min_k
+ * Defaults: {-1, 0, 1, 64, 32, 16} (large programs off: on the 24-qubit brickwork benchmark they
+ * measured slower than running fan-in chains as dataflow steps).  Errors: TN_EINVAL. */
+typedef struct {
+    int32_t local_budget;
+    int32_t big_programs;
+    int32_t warp_programs;
+    int32_t tc_min_m, tc_min_n, tc_min_k;
+} tn_exec_config;
+tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
+tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);
+
+/* Autotuner: for the batch (n, nets, plans, prec) -- the same arguments as tn_batch_create --
+ * build a batch under each candidate configuration (program kinds on and off, block-program
+ * budgets for two and three blocks per SM, no programs; in the split precisions also tensor-core
+ * thresholds), time `runs` runs of each with CUDA events after warm-up, keep the fastest
+ * configuration in the context and return it.  out_ms (may be NULL) receives its mean device time
+ * per run; cand_ms (may be NULL, cap entries) the mean time of every candidate in the order tried,
+ * with *n_cand the number of candidates (failed ones: a negative time).  Errors: TN_EINVAL, those
+ * of tn_batch_create when no candidate builds. */
+tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
+                          tn_precision prec, int32_t runs, tn_exec_config *out_best, double *out_ms,
+                          double *cand_ms, int32_t cap, int32_t *n_cand);
+
 typedef struct {
     double device_ms;          /* device time of the contraction (CUDA events) */
     int32_t launches;          /* kernels launched */
@@ -277,9 +309,11 @@ void tn_batch_free(tn_batch *b);
 
 /* Diagnostics: cycle accounting of the persistent kernel (costs a few atomics per work item; off
  * by default).  tn_batch_profile waits for the stream and returns 16 accumulated SM-cycle sums and
- * item counts since profiling was switched on: [0..5] work items by kernel class (ROWS, TILE,
- * DOTP, DOTF, -, subtree program, TC), [8] waves of subtree programs made of small steps only,
- * [9] waves that hold block-wide steps, [12] dependency waits.  Errors: TN_EINVAL, TN_ECUDA. */
+ * item counts since profiling was switched on: [0..4] work items of the dataflow kernel by class
+ * (ROWS, TILE, DOTP, DOTF, TC), [5] block programs, [6] large programs, [8] program waves made of
+ * small steps only, [9] waves that hold block-wide steps (block programs), [10] warp programs,
+ * [12] dependency waits, [13] waves with block-wide steps (large programs).
+ * Errors: TN_EINVAL, TN_ECUDA. */
 tn_status tn_batch_set_profiling(tn_batch *b, int32_t on);
 tn_status tn_batch_profile(tn_batch *b, int64_t *cycles, int64_t *items);
 

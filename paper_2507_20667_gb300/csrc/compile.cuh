@@ -20,11 +20,12 @@ struct Compiled {
     size_t arena_bytes = 0;
     int64_t n_partials = 0;          // double2 entries
     int64_t total_tiles = 0;
-    int32_t dyn_smem = 0;            // largest shared-memory need of a local program
+    int32_t dyn_smem = 0;            // largest shared-memory need of a block (or warp) program
+    int32_t dyn_big = 0;             // largest shared-memory need of a large program
     double flops = 0, bytes = 0;
-    // by StepKind ([5] = block programs); [6] = steps inside block programs; [7] = warp programs,
-    // [8] = steps inside warp programs
-    int32_t counts[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // by StepKind ([5] = all programs); [6] = steps inside block and large programs; [7] = warp
+    // programs, [8] = steps inside warp programs; [9] = large programs
+    int32_t counts[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t plan_uid = 0, shape_hash = 0;
     // device copies (inside the batch's allocation)
     StepDesc *d_steps = nullptr;
@@ -36,12 +37,29 @@ struct Compiled {
 };
 
 
-// Compile (network structure, plan) for complex elements of `elem` bytes: the global dataflow
-// step list, the CTA-resident subtree programs (maximal subtrees whose working set fits
-// `local_budget` bytes of shared memory; 0 = none) and the arena plan of one contraction.
-// use_tc: dense steps go to the tensor cores (BF16 split).
-tn_status compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget,
-                  bool use_tc);
+// What the compiler may use.  Programs: warp programs (maximal subtrees of small steps), block
+// programs (maximal subtrees whose working set fits local_budget bytes of shared memory; 0 = no
+// programs at all) and large programs (maximal subtrees within big_budget bytes, inputs staged
+// when consumed; none if big_budget <= local_budget).  tc_mode: dense steps (M >= tc_min_m,
+// N >= tc_min_n, K >= tc_min_k) go to the tensor cores, 1 = BF16 split, 2 = TF32 split.
+struct CompileOpts {
+    int32_t elem = 8;                 // bytes per complex element (8: complex64, 16: complex128)
+    int32_t local_budget = 0;
+    int32_t big_budget = 0;
+    bool warp_programs = true;
+    int32_t tc_mode = 0;
+    int32_t tc_min_m = 64, tc_min_n = 32, tc_min_k = 16;
+};
+
+// Compile (network structure, plan): the global dataflow step list, the subtree programs and the
+// arena plan of one contraction.
+tn_status compile(Compiled &c, const Net &net, const Plan &plan, const CompileOpts &o);
+
+// Tensor-core mode of a precision (0: CUDA cores only).
+int32_t tc_mode_of(int32_t prec);
+
+// Compiler options of an execution configuration on the current device.
+CompileOpts compile_opts(const tn_exec_config &cfg, int32_t prec, bool c128);
 
 // Sorted work items (level, step, tile) of one compiled structure, subtree programs excluded.
 void work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level);

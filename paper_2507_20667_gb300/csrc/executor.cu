@@ -35,7 +35,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    int32_t local_budget = -1;        // shared memory per subtree program: -1 auto, 0 none
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16};   // programs and tensor-core thresholds
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -65,6 +65,8 @@ struct tn_batch {
     WorkItem *d_local = nullptr;      // (job, pseudo-step) of every subtree program
     int32_t n_warp_items = 0;         // warp programs (first in d_local), then block programs
     int32_t n_block_items = 0;
+    int32_t n_big_items = 0;          // large programs (last in d_local)
+    int32_t dyn_big = 0;              // dynamic shared memory of the large-program launch
     uint32_t *d_counter = nullptr;
     DeviceResult *d_res = nullptr;
     char *d_reset = nullptr;          // results, maxbits, done, counter: zeroed before every run
@@ -269,6 +271,7 @@ struct LocalPlan {
     std::vector<int32_t> leaves;     // leaves, increasing
     std::vector<int64_t> loc;        // per node of the subtree: shared-memory element offset
     std::unordered_map<int32_t, int32_t> idx;   // node -> position in loc / slot
+    std::vector<std::vector<int32_t>> wave_inputs;  // lazy programs: inputs staged before each wave
     int64_t leaf_elems = 0, arena_elems = 0;
     int32_t smem_bytes = 0;
 };
@@ -283,15 +286,17 @@ bool small_step(const Geom &g, bool job_root) {
 // the step's children inside the subtree); a wave runs its small steps one per warp and its big
 // steps with the whole block.  The memory plan is simulated in that order: all outputs of a wave
 // are placed (best fit) before the inputs it consumed are released.
+// lazy: each input is staged into the pool right before the wave that consumes it and released
+// after it (large programs), instead of all inputs up front below the pool.
 bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &geo,
                const std::vector<int64_t> &size, int32_t elem, int32_t budget,
-               const std::vector<int32_t> &input_prog, LocalPlan &lp) {
+               const std::vector<int32_t> &input_prog, bool lazy, LocalPlan &lp) {
     lp = LocalPlan();
     std::vector<int32_t> nodes, stack{v};
     while (!stack.empty()) {
         int32_t x = stack.back();
         stack.pop_back();
-        // inputs: network leaves and the results of warp programs (already in device memory)
+        // inputs: network leaves and the results of earlier programs (already in device memory)
         if (x < n || (x != v && input_prog[x] >= 0)) { lp.leaves.push_back(x); continue; }
         nodes.push_back(x);
         stack.push_back(plan.steps[x - n][0]);
@@ -321,7 +326,7 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     std::vector<std::vector<int32_t>> by_wave(n_waves + 1);
     for (int32_t x : nodes) by_wave[wave[x]].push_back(x);
     for (int32_t w = 1; w <= n_waves; ++w) {
-        LocalWave W{(int32_t)lp.nodes.size(), 0, 0, 0};
+        LocalWave W{(int32_t)lp.nodes.size(), 0, 0, 0, 0, {0, 0, 0}};
         for (int pass = 0; pass < 2; ++pass)
             for (int32_t x : by_wave[w]) {
                 const bool sm = small_step(geo[x - n], x == root_id);
@@ -336,15 +341,41 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
     int64_t pos = 0;
     for (int32_t t : lp.leaves) {
         lp.idx[t] = (int32_t)lp.loc.size();
-        lp.loc.push_back(pos);
-        pos += size[t];
+        lp.loc.push_back(pos);   // lazy: set when the input is staged
+        if (!lazy) pos += size[t];
     }
     lp.leaf_elems = (pos + 1) / 2 * 2;   // keep the arena 16-byte aligned
     if (fixed + lp.leaf_elems * elem > budget) return false;
     Pool pool;
     int64_t top = 0;
     std::unordered_map<int32_t, int64_t> asz;
-    for (const LocalWave &W : lp.waves) {
+    // lazy: the inputs of wave w are copied while wave w - 1 runs, so they are placed when wave
+    // w - 1's results are, clear of everything wave w - 1 touches (each input has one consumer)
+    auto place_inputs = [&](size_t wi) {
+        const LocalWave &W = lp.waves[wi];
+        const int32_t end = W.first + W.n_small + W.n_big;
+        for (int32_t i = W.first; i < end; ++i) {
+            const int32_t x = lp.nodes[i];
+            for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]}) {
+                if (inner.count(c)) continue;
+                const int64_t sz = (size[c] + 1) / 2 * 2;
+                size_t at;
+                if (!pool.take((size_t)sz, at)) {
+                    at = (size_t)top;
+                    top += sz;
+                }
+                lp.loc[lp.idx[c]] = (int64_t)at;
+                asz[c] = sz;
+                lp.wave_inputs[wi].push_back(c);
+            }
+        }
+    };
+    if (lazy) {
+        lp.wave_inputs.assign(lp.waves.size(), {});
+        if (!lp.waves.empty()) place_inputs(0);
+    }
+    for (size_t wi = 0; wi < lp.waves.size(); ++wi) {
+        const LocalWave &W = lp.waves[wi];
         const int32_t end = W.first + W.n_small + W.n_big;
         for (int32_t i = W.first; i < end; ++i) {
             const int32_t x = lp.nodes[i];
@@ -358,11 +389,12 @@ bool local_fit(int32_t v, int32_t n, const Plan &plan, const std::vector<Geom> &
             lp.loc.push_back(lp.leaf_elems + (int64_t)at);
             asz[x] = sz;
         }
+        if (lazy && wi + 1 < lp.waves.size()) place_inputs(wi + 1);
         if (fixed + (lp.leaf_elems + top) * elem > budget) return false;
         for (int32_t i = W.first; i < end; ++i) {
             const int32_t x = lp.nodes[i];
             for (int32_t c : {plan.steps[x - n][0], plan.steps[x - n][1]})
-                if (inner.count(c)) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
+                if (inner.count(c) || lazy) pool.release((size_t)(lp.loc[lp.idx[c]] - lp.leaf_elems), (size_t)asz[c]);
         }
     }
     lp.arena_elems = top;
@@ -477,8 +509,39 @@ tn_status push_input(std::vector<LeafRef> &out, int64_t goff, int64_t count, int
 
 }  // namespace
 
-tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t elem, int32_t local_budget,
-                      bool use_tc) {
+int32_t tn::tc_mode_of(int32_t prec) { return prec == TN_BF16_SPLIT ? 1 : prec == TN_TF32_SPLIT ? 2 : 0; }
+
+tn::CompileOpts tn::compile_opts(const tn_exec_config &cfg, int32_t prec, bool c128) {
+    CompileOpts o;
+    o.elem = c128 ? 16 : 8;
+    o.local_budget = cfg.local_budget >= 0 ? cfg.local_budget : local_smem_budget(c128, 2);
+    o.big_budget = (o.local_budget > 0 && cfg.big_programs) ? local_smem_budget(c128, 1) : 0;
+    o.warp_programs = cfg.warp_programs != 0;
+    o.tc_mode = tc_mode_of(prec);
+    o.tc_min_m = cfg.tc_min_m;
+    o.tc_min_n = cfg.tc_min_n;
+    o.tc_min_k = cfg.tc_min_k;
+    return o;
+}
+
+namespace {
+// Options of the device-free compile statistics: the given block budget, and for large programs
+// twice that (a device gives one block per SM about twice what two blocks per SM get), at most
+// 200 KB.
+CompileOpts stats_opts(int32_t prec, int32_t local_budget) {
+    CompileOpts o;
+    o.elem = prec == TN_C128 ? 16 : 8;
+    o.local_budget = local_budget;
+    o.big_budget = local_budget > 0 ? std::min(2 * local_budget, 200 * 1024) : 0;
+    o.tc_mode = tc_mode_of(prec);
+    return o;
+}
+}  // namespace
+
+tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const CompileOpts &opt) {
+    const int32_t elem = opt.elem, local_budget = opt.local_budget, big_budget = opt.big_budget,
+                  tc_mode = opt.tc_mode;
+    const bool use_tc = tc_mode != 0;
     const int32_t n = net.n, nn = 2 * n - 1;
     c.n = n;
     c.n_nodes = nn;
@@ -535,6 +598,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
     std::vector<LocalPlan> lplans;
     std::vector<WarpPlan> wplans;
     std::vector<int32_t> proot, wroot;
+    std::vector<int32_t> pkind;                // ProgKind of each entry of proot
     if (local_budget > 0 && n > 1) {
         std::vector<int32_t> stack{nn - 1};
         while (!stack.empty()) {
@@ -542,7 +606,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             stack.pop_back();
             if (v < n) continue;
             WarpPlan wp;
-            if (warp_fit(v, n, plan, geo, size, elem, wp)) {
+            if (opt.warp_programs && warp_fit(v, n, plan, geo, size, elem, wp)) {
                 for (int32_t x : wp.nodes) wprog_of[x] = (int32_t)wroot.size();
                 wroot.push_back(v);
                 wplans.push_back(std::move(wp));
@@ -557,16 +621,40 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             stack.pop_back();
             if (v < n || wprog_of[v] >= 0) continue;
             LocalPlan lp;
-            if (local_fit(v, n, plan, geo, size, elem, local_budget, wprog_of, lp)) {
+            if (local_fit(v, n, plan, geo, size, elem, local_budget, wprog_of, false, lp)) {
                 for (int32_t x : lp.nodes) prog_of[x] = (int32_t)proot.size();
                 proot.push_back(v);
+                pkind.push_back(PROG_BLOCK);
                 lplans.push_back(std::move(lp));
             } else {
                 stack.push_back(plan.steps[v - n][0]);
                 stack.push_back(plan.steps[v - n][1]);
             }
         }
-        // warp programs are numbered after the block programs
+        // large programs: maximal subtrees within the one-block-per-SM budget whose inputs are
+        // leaves and the results of the programs above, each input staged when it is consumed
+        if (big_budget > local_budget) {
+            std::vector<int32_t> covered(nn, -1);
+            for (int32_t v = n; v < nn; ++v)
+                if (wprog_of[v] >= 0 || prog_of[v] >= 0) covered[v] = 1;
+            stack.assign(1, nn - 1);
+            while (!stack.empty()) {
+                const int32_t v = stack.back();
+                stack.pop_back();
+                if (v < n || covered[v] >= 0) continue;
+                LocalPlan lp;
+                if (local_fit(v, n, plan, geo, size, elem, big_budget, covered, true, lp) && lp.nodes.size() > 1) {
+                    for (int32_t x : lp.nodes) prog_of[x] = (int32_t)proot.size();
+                    proot.push_back(v);
+                    pkind.push_back(PROG_BIG);
+                    lplans.push_back(std::move(lp));
+                } else {
+                    stack.push_back(plan.steps[v - n][0]);
+                    stack.push_back(plan.steps[v - n][1]);
+                }
+            }
+        }
+        // warp programs are numbered after the block and large programs
         for (int32_t v = n; v < nn; ++v)
             if (wprog_of[v] >= 0) prog_of[v] = (int32_t)proot.size() + wprog_of[v];
     }
@@ -645,9 +733,10 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             d.ntiles = (int32_t)((M + d.tile_rows - 1) / d.tile_rows);
             c.steps.push_back(d);
             c.counts[STEP_ROWS]++;
-        } else if (use_tc && M >= 64 && N >= 32 && K >= 16) {
-            // dense step on the tensor cores: 128 x 64 complex output tiles, BF16 split
+        } else if (use_tc && M >= opt.tc_min_m && N >= opt.tc_min_n && K >= opt.tc_min_k) {
+            // dense step on the tensor cores: 128 x 64 complex output tiles, BF16 or TF32 split
             d.kind = STEP_TC;
+            if (tc_mode == 2) d.flags |= FLAG_TF32;
             const int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
             if (tiles > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "step too large");
             d.ntiles = (int32_t)tiles;
@@ -693,13 +782,30 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         P.flags = (v == nn - 1) ? LFLAG_JOB_ROOT : 0;
         P.first_wave = (int32_t)c.lwaves.size();
         P.n_waves = (int32_t)lp.waves.size();
-        // wave step indices are relative to the program (its descriptors are staged per program)
-        for (const LocalWave &W : lp.waves) c.lwaves.push_back(W);
-        for (int32_t t : lp.leaves) {
+        P.kind = pkind[pi];
+        auto stage = [&](int32_t t) -> tn_status {
             const int64_t goff = t < n ? c.leaf_off[t] : (int64_t)(arena_off[t] / esz);
-            tn_status st = push_input(c.leafrefs, goff, size[t], lp.loc[lp.idx.at(t)], lp.idx.at(t), t, t < n ? 0 : 1);
-            if (st != TN_OK) return st;
+            return push_input(c.leafrefs, goff, size[t], lp.loc[lp.idx.at(t)], lp.idx.at(t), t, t < n ? 0 : 1);
+        };
+        // wave step indices are relative to the program (its descriptors are staged per program)
+        for (size_t wi = 0; wi < lp.waves.size(); ++wi) {
+            LocalWave W = lp.waves[wi];
+            if (P.kind == PROG_BIG) {
+                W.first_in = (int32_t)c.leafrefs.size();
+                for (int32_t t : lp.wave_inputs[wi]) {
+                    tn_status st = stage(t);
+                    if (st != TN_OK) return st;
+                }
+                W.n_in = (int32_t)c.leafrefs.size() - W.first_in;
+            }
+            c.lwaves.push_back(W);
         }
+        P.first_leaf = (int32_t)c.leafrefs.size();
+        if (P.kind != PROG_BIG)
+            for (int32_t t : lp.leaves) {
+                tn_status st = stage(t);
+                if (st != TN_OK) return st;
+            }
         P.n_leaves = (int32_t)c.leafrefs.size() - P.first_leaf;
         for (size_t si = 0; si < lp.nodes.size(); ++si) {
             const int32_t x = lp.nodes[si];
@@ -731,7 +837,12 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
             if (lp.small[si]) ls.flags |= LFLAG_SMALL;
             c.lsteps.push_back(ls);
         }
-        c.dyn_smem = std::max(c.dyn_smem, P.smem_bytes);
+        if (P.kind == PROG_BIG) {
+            c.dyn_big = std::max(c.dyn_big, P.smem_bytes);
+            c.counts[9]++;
+        } else {
+            c.dyn_smem = std::max(c.dyn_smem, P.smem_bytes);
+        }
         c.progs.push_back(P);
     }
     c.counts[6] = (int32_t)c.lsteps.size();
@@ -755,7 +866,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, int32_t ele
         P.root_slot = wp.slot.at(v);
         P.root_size = (int32_t)size[v];
         P.root_c_off = (int64_t)(arena_off[v] / esz);
-        P.warp = 1;
+        P.kind = PROG_WARP;
         for (int32_t x : wp.nodes) {
             const Geom &g = geo[x - n];
             LocalStep ls;
@@ -837,8 +948,8 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess) {
             t_enqueue_stage = "subtree programs";
-            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, b->n_block_items, b->dyn_smem,
-                             b->d_prof, st);
+            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, b->n_block_items, b->n_big_items,
+                             b->dyn_smem, b->dyn_big, b->d_prof, st);
         }
         if (e == cudaSuccess) {
             t_enqueue_stage = "dataflow kernel";
@@ -851,7 +962,7 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb) {
             const Compiled &c = b->comp[b->job_comp[jb]];
             for (size_t s = 0; e == cudaSuccess && s < c.steps.size(); ++s)
-                e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], b->dyn_smem, st);
+                e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], std::max(b->dyn_smem, b->dyn_big), st);
         }
     }
     for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb)
@@ -930,7 +1041,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->uploaded.assign(n, ~0ull);
     b->job_comp.assign(n, -1);
     // compile every distinct (structure, plan) once
-    const int32_t budget = ctx->local_budget >= 0 ? ctx->local_budget : local_smem_budget(b->c128, 2);
+    CompileOpts copt = compile_opts(ctx->cfg, prec, b->c128);
     std::unordered_map<std::string, int32_t> seen;
     for (int32_t i = 0; i < n; ++i) {
         const Net &net = nets[i]->impl;
@@ -939,7 +1050,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         auto it = seen.find(key);
         if (it != seen.end()) { b->job_comp[i] = it->second; continue; }
         Compiled c;
-        tn_status s = compile(c, net, plans[i]->impl, b->elem, budget, prec == TN_BF16_SPLIT);
+        tn_status s = compile(c, net, plans[i]->impl, copt);
         if (s != TN_OK) { batch_destroy(b); return s; }
         c.plan_uid = plans[i]->impl.uid;
         c.shape_hash = h;
@@ -961,6 +1072,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         o_lrefs[ci] = carve(sizeof(LeafRef) * b->comp[ci].leafrefs.size());
         o_lwaves[ci] = carve(sizeof(LocalWave) * b->comp[ci].lwaves.size());
         b->dyn_smem = std::max(b->dyn_smem, b->comp[ci].dyn_smem);
+        b->dyn_big = std::max(b->dyn_big, b->comp[ci].dyn_big);
     }
     b->leaf64_off.assign(n, 0);
     int64_t leaf_total = 0;
@@ -982,7 +1094,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     }
     const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
     // work list: (job, step, tile) in (level, job, step, tile) order
-    std::vector<WorkItem> work, local_items, warp_items;
+    std::vector<WorkItem> work, local_items, warp_items, big_items;
     if (b->mode == TN_EXEC_PERSISTENT) {
         int64_t total = 0;
         for (int32_t i = 0; i < n; ++i) total += b->comp[b->job_comp[i]].total_tiles;
@@ -999,7 +1111,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
             if (d.kind == STEP_LOCAL) {
                 const Compiled &c = b->comp[b->job_comp[o[1]]];
                 const LocalProg &P = c.progs[d.tile_rows];
-                (P.warp ? warp_items : local_items).push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
+                (P.kind == PROG_WARP ? warp_items : P.kind == PROG_BIG ? big_items : local_items)
+                    .push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
                 continue;
             }
             for (int32_t t = 0; t < d.ntiles; ++t) work.push_back({(uint32_t)o[1], (uint32_t)o[2], (uint32_t)t});
@@ -1014,7 +1127,9 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     });
     b->n_warp_items = (int32_t)warp_items.size();
     b->n_block_items = (int32_t)local_items.size();
+    b->n_big_items = (int32_t)big_items.size();
     local_items.insert(local_items.begin(), warp_items.begin(), warp_items.end());
+    local_items.insert(local_items.end(), big_items.begin(), big_items.end());
     const size_t o_work = carve(sizeof(WorkItem) * work.size());
     const size_t o_litems = carve(sizeof(WorkItem) * local_items.size());
     // reset region: results, maxbits, done, counter
@@ -1143,7 +1258,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->info.arena_bytes = b->arena_total;
     if (b->mode == TN_EXEC_PERSISTENT) {
         // leaf conversion, warp programs, block programs, dataflow
-        b->info.launches = 2 + (b->n_warp_items > 0 ? 1 : 0) + (b->n_block_items > 0 ? 1 : 0);
+        b->info.launches = 2 + (b->n_warp_items > 0 ? 1 : 0) + (b->n_block_items > 0 ? 1 : 0) +
+                           (b->n_big_items > 0 ? 1 : 0);
     } else {
         int32_t l = 1;
         for (int32_t i = 0; i < n; ++i) l += (int32_t)b->comp[b->job_comp[i]].steps.size();
@@ -1290,7 +1406,7 @@ tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_preci
     if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
     if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
     Compiled c;
-    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget, prec == TN_BF16_SPLIT);
+    tn_status s = compile(c, net->impl, plan->impl, stats_opts(prec, local_budget));
     if (s != TN_OK) return s;
     tn_compile_stats st;
     std::memset(&st, 0, sizeof(st));
@@ -1321,7 +1437,7 @@ tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_preci
     if (plan->impl.n != net->impl.n) return fail(TN_EINVAL, "plan and network do not match");
     if (!net->impl.closed) return fail(TN_EUNSUPPORTED, "open networks are not supported by tn_contract");
     Compiled c;
-    tn_status s = compile(c, net->impl, plan->impl, prec == TN_C128 ? 16 : 8, local_budget, prec == TN_BF16_SPLIT);
+    tn_status s = compile(c, net->impl, plan->impl, stats_opts(prec, local_budget));
     if (s != TN_OK) return s;
     const int32_t n = (int32_t)c.steps.size();
     for (int32_t i = 0; i < n && i < cap && out; ++i) {
@@ -1335,16 +1451,39 @@ tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_preci
     return TN_OK;
 }
 
-tn_status tn_ctx_set_local_budget(tn_ctx *c, int32_t bytes) {
-    if (!c) return fail(TN_EINVAL, "NULL ctx");
-    if (bytes < -1) return fail(TN_EINVAL, "bytes must be -1 (automatic), 0 (off) or positive");
+namespace {
+void drop_cached(tn_ctx *c) {
     if (c->cached) {
         cudaSetDevice(c->device);
         cudaStreamSynchronize(c->stream);
         batch_destroy(c->cached);
         c->cached = nullptr;
     }
-    c->local_budget = bytes;
+}
+}  // namespace
+
+tn_status tn_ctx_set_local_budget(tn_ctx *c, int32_t bytes) {
+    if (!c) return fail(TN_EINVAL, "NULL ctx");
+    if (bytes < -1) return fail(TN_EINVAL, "bytes must be -1 (automatic), 0 (off) or positive");
+    drop_cached(c);
+    c->cfg.local_budget = bytes;
+    return TN_OK;
+}
+
+tn_status tn_ctx_get_config(const tn_ctx *c, tn_exec_config *cfg) {
+    if (!c || !cfg) return fail(TN_EINVAL, "NULL argument");
+    *cfg = c->cfg;
+    return TN_OK;
+}
+
+tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
+    if (!c || !cfg) return fail(TN_EINVAL, "NULL argument");
+    if (cfg->local_budget < -1 || cfg->tc_min_m < 1 || cfg->tc_min_n < 1 || cfg->tc_min_k < 1)
+        return fail(TN_EINVAL, "invalid configuration");
+    drop_cached(c);
+    c->cfg = *cfg;
+    c->cfg.big_programs = cfg->big_programs ? 1 : 0;
+    c->cfg.warp_programs = cfg->warp_programs ? 1 : 0;
     return TN_OK;
 }
 
@@ -1587,3 +1726,75 @@ tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_by
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------ autotuner
+
+tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
+                          tn_precision prec, int32_t runs, tn_exec_config *out_best, double *out_ms,
+                          double *cand_ms, int32_t cap, int32_t *n_cand) {
+    if (!ctx || n < 1 || !nets || !plans || runs < 1 || cap < 0) return fail(TN_EINVAL, "invalid argument");
+    if (prec < TN_C128 || prec > TN_BF16_SPLIT) return fail(TN_EINVAL, "unknown precision");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(TN_ECUDA, "cudaSetDevice");
+    const bool c128 = prec == TN_C128;
+    // candidates: program kinds on and off, block budgets for two and three blocks per SM, no
+    // programs; in the split precisions the tensor-core thresholds too
+    const int32_t b3 = local_smem_budget(c128, 3);
+    std::vector<tn_exec_config> cands = {
+        {-1, 1, 1, 64, 32, 16}, {-1, 0, 1, 64, 32, 16}, {-1, 1, 0, 64, 32, 16},
+        {b3, 1, 1, 64, 32, 16}, {b3, 0, 1, 64, 32, 16}, {0, 0, 0, 64, 32, 16}};
+    if (tc_mode_of(prec)) {
+        const int32_t off = 1 << 30;
+        cands.push_back({-1, 1, 1, off, off, off});
+        cands.push_back({-1, 0, 1, off, off, off});
+        cands.push_back({-1, 1, 1, 32, 32, 16});
+        cands.push_back({-1, 0, 1, 32, 32, 16});
+    }
+    const tn_exec_config saved = ctx->cfg;
+    drop_cached(ctx);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(TN_ECUDA, "cudaEventCreate");
+    }
+    double best_ms = -1;
+    int32_t best = -1;
+    tn_status first_err = TN_OK;
+    std::string first_msg;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        ctx->cfg = cands[i];
+        tn_batch *b = nullptr;
+        double ms = -1;
+        tn_status s = batch_create(ctx, n, nets, plans, prec, &b);
+        if (s == TN_OK) {
+            for (int w = 0; w < 2 && s == TN_OK; ++w) s = batch_run(b, nullptr);
+            if (s == TN_OK && cudaEventRecord(e0, ctx->stream) == cudaSuccess) {
+                for (int32_t r = 0; r < runs && s == TN_OK; ++r) s = batch_run(b, nullptr);
+                float t = 0.f;
+                if (s == TN_OK && cudaEventRecord(e1, ctx->stream) == cudaSuccess &&
+                    cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+                    ms = (double)t / runs;
+            }
+            batch_destroy(b);
+        }
+        if (s != TN_OK && first_err == TN_OK) {
+            first_err = s;
+            first_msg = tn_last_error();
+        }
+        if (cand_ms && (int32_t)i < cap) cand_ms[i] = ms;
+        if (ms > 0 && (best < 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = (int32_t)i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_cand) *n_cand = (int32_t)cands.size();
+    if (best < 0) {
+        ctx->cfg = saved;
+        return fail(first_err == TN_OK ? TN_ECUDA : first_err, "autotune: no candidate ran: " + first_msg);
+    }
+    ctx->cfg = cands[best];
+    if (out_best) *out_best = cands[best];
+    if (out_ms) *out_ms = best_ms;
+    return TN_OK;
+}

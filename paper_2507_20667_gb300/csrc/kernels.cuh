@@ -36,7 +36,8 @@ enum StepFlags : int32_t {
     FLAG_A_LEAF = 1,    // A lives in the job's leaf buffer (else in its arena)
     FLAG_B_LEAF = 2,
     FLAG_ROOT = 4,      // the step produces the network's value: write the job's result record
-    FLAG_NO_C = 8       // no tensor output (DOTP, or the root's DOTF)
+    FLAG_NO_C = 8,      // no tensor output (DOTP, or the root's DOTF)
+    FLAG_TF32 = 16      // TC: TF32 split (else BF16 split)
 };
 
 struct StepDesc {
@@ -70,8 +71,11 @@ enum LocalFlags : int32_t {
 // A wave of a program: steps [first, first + n_small) run one per warp, then n_big steps use the
 // whole block; the steps of a wave are independent of each other.
 struct LocalWave {
-    int32_t first, n_small, n_big, pad;
+    int32_t first, n_small, n_big;
+    int32_t first_in, n_in;             // staging pieces loaded before the wave (lazy programs)
+    int32_t pad[3];
 };
+static_assert(sizeof(LocalWave) % 16 == 0, "waves are staged in 16-byte pieces");
 
 struct LocalStep {
     int32_t M, N, K;
@@ -96,8 +100,12 @@ struct LocalProg {
     int64_t root_c_off;                 // and where it goes in the job's arena
     int32_t flags;                      // LFLAG_JOB_ROOT: the subtree is the whole network
     int32_t first_wave, n_waves;        // into the job's LocalWave array
-    int32_t warp;                       // 1: a warp program (one warp runs it, steps in order)
+    int32_t kind;                       // ProgKind
 };
+// Program kinds: PROG_BLOCK -- one block, inputs staged up front, two blocks per SM;
+// PROG_WARP -- one warp, steps in plan order; PROG_BIG -- one block per SM, each input staged at
+// the wave that consumes it (large subtrees such as fan-in chains).
+enum ProgKind : int32_t { PROG_BLOCK = 0, PROG_WARP = 1, PROG_BIG = 2 };
 
 // A staging piece of a program input: `count` (at most 16) elements at element offset global_off
 // of the job's leaf buffer (src 0) or of its arena (src 1: a warp program's result), copied to
@@ -149,9 +157,10 @@ cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const J
                         int32_t dyn_smem, cudaStream_t stream);
 cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);
 // Optional cycle accounting of the persistent kernel: prof[slot] sums SM cycles (block 0's view
-// of each work item, thread 0), prof[kProfSlots + slot] counts items.  Slots 0..5: work items by
-// StepKind (dependency wait excluded); 8..10: steps inside subtree programs by LocalMode;
-// 11: leaf staging of subtree programs; 12: dependency waits.
+// of each work item, thread 0), prof[kProfSlots + slot] counts items.  Slots 0..4: work items by
+// StepKind (dependency wait excluded); 5: block programs; 6: large programs; 8: waves of small
+// steps; 9: waves with block-wide steps (block programs); 10: warp programs (lane 0's view);
+// 12: dependency waits; 13: waves with block-wide steps (large programs).
 constexpr int kProfSlots = 16;
 
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
@@ -162,9 +171,11 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
 // Co-resident grid of the persistent kernel, with tensor-core tiles (use_tc) or without.
 int32_t persistent_grid(bool c128, int32_t use_tc);
 // Subtree programs; items: (job, pseudo-step, 0), the n_warp warp programs first (four per
-// block of kWarpThreads), then the n_block block programs (one per block, `dyn_smem` bytes).
+// block of kWarpThreads), then the n_block block programs (one per block, `dyn_smem` bytes), then
+// the n_big large programs (one per block, `dyn_big` bytes).
 cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_warp,
-                         int32_t n_block, int32_t dyn_smem, long long *prof, cudaStream_t stream);
+                         int32_t n_block, int32_t n_big, int32_t dyn_smem, int32_t dyn_big, long long *prof,
+                         cudaStream_t stream);
 // Dynamic shared memory a local program may use so that `blocks_per_sm` persistent blocks fit.
 int32_t local_smem_budget(bool c128, int32_t blocks_per_sm);
 cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int64_t n_upd,

@@ -81,7 +81,7 @@ template <typename T>
 __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
                                          float *red, char *dyn, long long *prof) {
     if (d.kind == STEP_LOCAL) {
-        if (__ldcg(&j.progs[d.tile_rows].warp)) {
+        if (__ldcg(&j.progs[d.tile_rows].kind) == PROG_WARP) {
             if (threadIdx.x < 32) run_warp_prog<T>(d.tile_rows, j, dyn);   // graph mode: warp 0
             __syncthreads();
         } else {
@@ -136,9 +136,10 @@ __global__ void __launch_bounds__(kThreads) k_local(const JobPtrs *__restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(j.done + it.step, 1);
-        if (prof) {
-            atomicAdd((unsigned long long *)(prof + STEP_LOCAL), (unsigned long long)(clock64() - t0));
-            atomicAdd((unsigned long long *)(prof + kProfSlots + STEP_LOCAL), 1ull);
+        if (prof) {   // slot 5: block programs, 6: large programs
+            const int slot = __ldcg(&j.progs[prog].kind) == PROG_BIG ? 6 : STEP_LOCAL;
+            atomicAdd((unsigned long long *)(prof + slot), (unsigned long long)(clock64() - t0));
+            atomicAdd((unsigned long long *)(prof + kProfSlots + slot), 1ull);
         }
     }
 }
@@ -358,7 +359,8 @@ int32_t persistent_grid(bool c128, int32_t use_tc) {
 }
 
 cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *items, int32_t n_warp,
-                         int32_t n_block, int32_t dyn_smem, long long *prof, cudaStream_t stream) {
+                         int32_t n_block, int32_t n_big, int32_t dyn_smem, int32_t dyn_big, long long *prof,
+                         cudaStream_t stream) {
     if (n_warp > 0) {
         constexpr int per_block = kWarpThreads / 32;
         const int32_t smem = per_block * kWarpSlice;
@@ -370,12 +372,20 @@ cudaError_t launch_local(bool c128, const JobPtrs *jobs_dev, const WorkItem *ite
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (n_block <= 0) return cudaSuccess;
-    cudaError_t e = c128 ? allow_dyn_smem(k_local<double>, dyn_smem) : allow_dyn_smem(k_local<float>, dyn_smem);
-    if (e != cudaSuccess) return e;
-    if (c128) k_local<double><<<n_block, kThreads, dyn_smem, stream>>>(jobs_dev, items + n_warp, prof);
-    else k_local<float><<<n_block, kThreads, dyn_smem, stream>>>(jobs_dev, items + n_warp, prof);
-    return cudaGetLastError();
+    // block programs, then the large ones (each launch with its own shared-memory size)
+    const int32_t counts[2] = {n_block, n_big}, dyn[2] = {dyn_smem, dyn_big};
+    const WorkItem *it = items + n_warp;
+    for (int q = 0; q < 2; ++q) {
+        if (counts[q] <= 0) continue;
+        cudaError_t e = c128 ? allow_dyn_smem(k_local<double>, dyn[q]) : allow_dyn_smem(k_local<float>, dyn[q]);
+        if (e != cudaSuccess) return e;
+        if (c128) k_local<double><<<counts[q], kThreads, dyn[q], stream>>>(jobs_dev, it, prof);
+        else k_local<float><<<counts[q], kThreads, dyn[q], stream>>>(jobs_dev, it, prof);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        it += counts[q];
+    }
+    return cudaSuccess;
 }
 
 int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {

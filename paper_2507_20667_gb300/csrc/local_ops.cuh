@@ -100,13 +100,12 @@ __device__ __forceinline__ LocalSmem local_layout(char *dyn, const LocalProg &P)
 }
 
 // Copies a program's inputs into shared memory: one staging piece (at most 16 elements of a leaf
-// or of a warp program's result) per thread, its elements loaded in one burst of independent
-// loads; the first piece of each input also copies the input's max-abs and exponent.
-template <typename T>
+// or of a program's result) per thread, its elements loaded in bursts of LB independent loads;
+// the first piece of each input also copies the input's max-abs and exponent.
+template <typename T, int LB = 16>
 __device__ __forceinline__ void stage_inputs(const JobPtrs &j, const LeafRef *refs, int32_t n_refs, int32_t t0,
                                              int32_t stride, cx_t<T> *data, uint32_t *smax, int32_t *sexp) {
     using C = cx_t<T>;
-    constexpr int LB = 16;
     for (int32_t l = t0; l < n_refs; l += stride) {
         const LeafRef r = refs[l];
         if (r.slot >= 0) {
@@ -122,6 +121,42 @@ __device__ __forceinline__ void stage_inputs(const JobPtrs &j, const LeafRef *re
 #pragma unroll
             for (int u = 0; u < LB; ++u)
                 if (i0 + u < r.count) data[r.smem_off + i0 + u] = v[u];
+        }
+    }
+}
+
+// Asynchronous copies (cp.async) of program inputs into shared memory, so that a large program's
+// next wave of inputs is in flight while the current wave computes.
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// stage_inputs with asynchronous copies (the caller commits, waits and synchronises); the scale
+// slots are written at once.
+template <typename T>
+__device__ __forceinline__ void stage_inputs_async(const JobPtrs &j, const LeafRef *refs, int32_t n_refs, int32_t t0,
+                                                   int32_t stride, cx_t<T> *data, uint32_t *smax, int32_t *sexp) {
+    using C = cx_t<T>;
+    for (int32_t l = t0; l < n_refs; l += stride) {
+        const LeafRef r = refs[l];
+        if (r.slot >= 0) {
+            smax[r.slot] = __ldcg(j.maxbits + r.node);
+            sexp[r.slot] = __ldcg(j.exp2 + r.node);
+        }
+        const C *src = (r.src ? reinterpret_cast<const C *>(j.arena) : static_cast<const C *>(j.leaf)) + r.global_off;
+        for (int32_t i = 0; i < r.count; ++i) {
+            if constexpr (sizeof(C) == 8) cp_async8(data + r.smem_off + i, src + i);
+            else cp_async16(data + r.smem_off + i, src + i);
         }
     }
 }
@@ -258,7 +293,8 @@ __device__ void run_warp_prog(int32_t prog, const JobPtrs &j, char *slice) {
 }
 
 // Block-wide steps of block programs (all operands in shared memory).  Modes:
-//   LMODE_ROWS / LMODE_GEMM   register-tiled GEMM (local_mm), tile shape chosen by N
+//   LMODE_ROWS / LMODE_GEMM   row by row (local_rows, N and K <= 16) or register-tiled
+//                             (local_mm, tile shape chosen by N)
 //   LMODE_REDUCE              few outputs, long K: S threads per output split K, FP64 partial sums,
 //                             shuffle / shared-memory reduction; the job's root (the amplitude)
 //                             always takes this mode
@@ -364,17 +400,95 @@ __device__ void local_mm(const LocalStep &s, const LocalSmem &L, T sA, T sB, flo
         }
 }
 
+// Block-wide narrow contraction (N <= NT <= 16, K <= 16) with every operand in shared memory:
+// each thread owns R rows (m, m + blockDim, ...), R = 32 / NT, with their R x N accumulators in
+// registers; per shared index it reads the rows' A entries and one row of B from a dense, scaled,
+// padded copy in the scratch area, and every B entry feeds R complex multiply-adds.  No barrier
+// inside the loop.  When k is the contiguous index of A, a thread starts its k loop at m mod K, so
+// that the threads of a warp read different banks of A (the padded B rows keep their B reads apart
+// too).
+template <typename T, int NT>
+__device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx, char *scratch) {
+    using C = cx_t<T>;
+    constexpr int R = (sizeof(T) == 4 ? 32 : 16) / NT > 0 ? (sizeof(T) == 4 ? 32 : 16) / NT : 1;
+    const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
+    const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
+    C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
+    const int32_t N = s.N, K = s.K, M = s.M, PB = N + 1;
+    C *Bd = reinterpret_cast<C *>(scratch);                                  // [K][N + 1], scaled
+    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 1));          // [K] offsets in A
+    const bool p2 = s.pow2;
+    for (int32_t i = threadIdx.x; i < K * N; i += blockDim.x) {
+        const int32_t k = i / N, n = i - k * N;
+        int32_t ka, kb;
+        lgroup_off2(s, k, ka, kb);
+        kb += lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, p2, n);
+        Bd[k * PB + n] = cscale(B[kb], sB);
+        if (n == 0) kat[k] = ka;
+    }
+    __syncthreads();
+    const bool skew = s.nk > 0 && s.k_sa[0] == 1;
+    const int32_t step = blockDim.x;
+    for (int32_t m0 = threadIdx.x; m0 < M; m0 += step * R) {
+        int32_t offA[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int32_t m = m0 + r * step;
+            offA[r] = m < M ? lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, p2, m) : -1;
+        }
+        const int32_t sh = skew ? m0 % K : 0;   // step is a multiple of K when K divides 256
+        C acc[R][NT];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int n = 0; n < NT; ++n) acc[r][n] = cmake((T)0, (T)0);
+#pragma unroll 1
+        for (int32_t kk = 0; kk < K; ++kk) {
+            int32_t k = kk + sh;
+            if (k >= K) k -= K;
+            const int32_t ko = kat[k];
+            C av[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) av[r] = offA[r] >= 0 ? cscale(A[offA[r] + ko], sA) : cmake((T)0, (T)0);
+            const C *Bk = Bd + k * PB;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                if (n >= N) break;
+                const C b = Bk[n];
+#pragma unroll
+                for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (offA[r] < 0) continue;
+            C *out = Cp + (m0 + r * step) * N;
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+                if (n < N) {
+                    out[n] = acc[r][n];
+                    mx = fmaxf(mx, absmax2(acc[r][n]));
+                }
+        }
+    }
+}
+
 // Scratch bytes of local_mm: the largest tile set (TK = 8 for complex64, 4 for complex128).
 template <typename T> struct LocalMmScratch {
     static constexpr int TK = sizeof(T) == 4 ? 8 : 4;
     static constexpr int bytes = TK * (257 + 65) * (int)sizeof(cx_t<T>) + (256 + 64) * 4 + TK * 8;
 };
 
+// Block-wide steps: narrow ones (N, K <= 16) row by row, the rest register-tiled.
 template <typename T>
 __device__ __forceinline__ void local_mm_dispatch(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
                                                   char *scratch) {
     constexpr int TK = LocalMmScratch<T>::TK;
-    if (s.N <= 4) local_mm<T, 1, 256, 1, 4, TK>(s, L, sA, sB, mx, scratch);
+    if (s.N <= 16 && s.K <= 16) {
+        if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
+        else if (s.N <= 8) local_rows<T, 8>(s, L, sA, sB, mx, scratch);
+        else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
+    } else if (s.N <= 4) local_mm<T, 1, 256, 1, 4, TK>(s, L, sA, sB, mx, scratch);
     else if (s.N <= 8) local_mm<T, 2, 128, 2, 4, TK>(s, L, sA, sB, mx, scratch);
     else if (s.N <= 16) local_mm<T, 4, 64, 4, 4, TK>(s, L, sA, sB, mx, scratch);
     else if (s.N <= 32) local_mm<T, 8, 32, 4, 4, TK>(s, L, sA, sB, mx, scratch);
@@ -470,7 +584,8 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
         for (int i = threadIdx.x; i < nd; i += blockDim.x) dst[i] = __ldcg(src + i);
         const int4 *wsrc = reinterpret_cast<const int4 *>(j.lwaves + P.first_wave);
         int4 *wdst = reinterpret_cast<int4 *>(L.waves);
-        for (int i = threadIdx.x; i < P.n_waves; i += blockDim.x) wdst[i] = __ldcg(wsrc + i);
+        const int nw4 = P.n_waves * (int)(sizeof(LocalWave) / 16);
+        for (int i = threadIdx.x; i < nw4; i += blockDim.x) wdst[i] = __ldcg(wsrc + i);
     }
     for (int32_t i = threadIdx.x; i < P.n_slots; i += blockDim.x) { L.smax[i] = 0u; L.sexp[i] = 0; }
     __syncthreads();
@@ -479,8 +594,31 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     __syncthreads();
     long long tp = 0;
     if (prof && threadIdx.x == 0) tp = clock64();
+    // large programs: each wave's inputs are copied asynchronously one wave ahead (the compiler
+    // places them clear of the previous wave's operands and results)
+    const bool lazy = P.kind == PROG_BIG;
+    if (lazy && P.n_waves > 0) {
+        const LocalWave W0 = L.waves[0];
+        stage_inputs_async<T>(j, j.leafrefs + W0.first_in, W0.n_in, threadIdx.x, blockDim.x, data, L.smax, L.sexp);
+        cp_async_commit();
+    }
     for (int32_t w = 0; w < P.n_waves; ++w) {
         const LocalWave W = L.waves[w];
+        if (lazy) {
+            if (w + 1 < P.n_waves) {
+                const LocalWave W1 = L.waves[w + 1];
+                stage_inputs_async<T>(j, j.leafrefs + W1.first_in, W1.n_in, threadIdx.x, blockDim.x, data, L.smax,
+                                      L.sexp);
+            }
+            cp_async_commit();
+            cp_async_wait_prev();   // this wave's inputs have landed (the next wave's may be in flight)
+            __syncthreads();
+            if (prof && threadIdx.x == 0) {   // slot 14: waiting for the inputs of large programs
+                const long long t1 = clock64();
+                atomicAdd((unsigned long long *)(prof + 14), (unsigned long long)(t1 - tp));
+                atomicAdd((unsigned long long *)(prof + kProfSlots + 14), 1ull);
+            }
+        }
         // independent small steps: one warp each
         for (int32_t i = warp; i < W.n_small; i += nw) local_small<T>(L.desc[W.first + i], L);
         // big steps: the whole block, one after the other
@@ -506,12 +644,14 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
         __syncthreads();
         if (prof && threadIdx.x == 0) {
             const long long t1 = clock64();
-            const int slot = W.n_big ? 9 : 8;   // 8: waves of small steps only, 9: waves with big steps
+            // 8: waves of small steps only, 9: waves with block-wide steps, 13: those of large programs
+            const int slot = W.n_big ? (P.kind == PROG_BIG ? 13 : 9) : 8;
             atomicAdd((unsigned long long *)(prof + slot), (unsigned long long)(t1 - tp));
             atomicAdd((unsigned long long *)(prof + kProfSlots + slot), 1ull);
             tp = t1;
         }
     }
+    if (lazy) cp_async_wait_all();
     // publish the program's result (unless it was the job's amplitude, already written)
     if (!(P.flags & LFLAG_JOB_ROOT)) {
         C *out = reinterpret_cast<C *>(j.arena) + P.root_c_off;

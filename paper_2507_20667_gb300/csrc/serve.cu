@@ -87,6 +87,7 @@ struct Model {
     std::vector<int32_t> tmpl_level;
     std::vector<int32_t> local_steps; // pseudo-steps of block programs
     std::vector<int32_t> warp_steps;  // pseudo-steps of warp programs
+    std::vector<int32_t> big_steps;   // pseudo-steps of large programs
     size_t o_leaf = 0, o_arena = 0, o_part = 0, o_exp = 0, job_bytes = 0;
     int32_t max_level = 0;
 };
@@ -126,7 +127,7 @@ struct tn_server {
     bool c128 = false;
     int32_t elem = 8;
     int32_t max_batch = 64;
-    int32_t local_budget = 0;
+    CompileOpts copt;                 // compiler options (from the context's configuration)
     char *pool = nullptr;
     size_t pool_bytes = 0;
     Arena arena;
@@ -139,7 +140,7 @@ struct tn_server {
     Flight fl[2];
     std::thread worker;
     std::atomic<bool> stop{false};
-    int32_t dyn_smem = 0, grid = 0, grid_tc = 0;
+    int32_t dyn_smem = 0, dyn_big = 0, grid = 0, grid_tc = 0;
     bool any_tc = false;
     std::string worker_error;
     tn_serve_stats stats{};
@@ -199,6 +200,10 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     const int32_t n_warp = (int32_t)local.size();
     for (int32_t i = 0; i < n; ++i)
         for (int32_t s : S->models[f.reqs[i].model]->local_steps) local.push_back({(uint32_t)i, (uint32_t)s, 0u});
+    const int32_t n_block = (int32_t)local.size() - n_warp;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t s : S->models[f.reqs[i].model]->big_steps) local.push_back({(uint32_t)i, (uint32_t)s, 0u});
+    const int32_t n_big = (int32_t)local.size() - n_warp - n_block;
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off = align256(off + std::max<size_t>(bytes, 16)); return o; };
     const size_t o_l64 = carve(sizeof(double2) * (size_t)leaf_total);
@@ -278,8 +283,8 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     if (e == cudaSuccess) e = cudaMemsetAsync(meta + o_reset, 0, reset_bytes, f.st);
     if (e == cudaSuccess) e = launch_leaf_convert(S->c128, d_jobs, n, max_leaves, f.st);
     if (e == cudaSuccess)
-        e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), n_warp,
-                         (int32_t)local.size() - n_warp, S->dyn_smem, nullptr, f.st);
+        e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), n_warp, n_block,
+                         n_big, S->dyn_smem, S->dyn_big, nullptr, f.st);
     if (e == cudaSuccess && !work.empty())
         e = launch_persistent(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_work),
                               (int64_t)work.size(), reinterpret_cast<uint32_t *>(meta + o_counter),
@@ -296,7 +301,8 @@ size_t meta_bytes(tn_server *S, const std::vector<Request> &reqs) {
     for (const Request &r : reqs) {
         const Model &m = *S->models[r.model];
         b += sizeof(double2) * (size_t)m.leaf_off.back() + sizeof(JobPtrs) +
-             sizeof(WorkItem) * (m.tmpl.size() + m.local_steps.size() + m.warp_steps.size()) + sizeof(DeviceResult) +
+             sizeof(WorkItem) * (m.tmpl.size() + m.local_steps.size() + m.warp_steps.size() + m.big_steps.size()) +
+             sizeof(DeviceResult) +
              sizeof(uint32_t) * (size_t)m.c.n_nodes + sizeof(int32_t) * m.c.steps.size() + 5 * 256;
     }
     return b + 16 * 256;
@@ -412,7 +418,13 @@ tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_byte
     S->c128 = prec == TN_C128;
     S->elem = S->c128 ? 16 : 8;
     S->max_batch = max_batch;
-    S->local_budget = local_smem_budget(S->c128, 2);
+    tn_exec_config cfg;
+    s = tn_ctx_get_config(ctx, &cfg);
+    if (s != TN_OK) {
+        delete S;
+        return s;
+    }
+    S->copt = compile_opts(cfg, prec, S->c128);
     // full co-resident grids: a second launch's blocks start as the first one's retire
     S->grid = std::max(1, persistent_grid(S->c128, 0));
     S->grid_tc = std::max(1, persistent_grid(S->c128, 1));
@@ -456,14 +468,18 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
         S->models.push_back(std::move(m));
         return TN_OK;
     }
-    tn_status s = compile(m->c, net->impl, plan->impl, S->elem, S->local_budget, S->prec == TN_BF16_SPLIT);
+    tn_status s = compile(m->c, net->impl, plan->impl, S->copt);
     if (s != TN_OK) return s;
     m->leaves = net->impl.data;
     m->leaf_off = net->impl.data_off;
     work_template(m->c, m->tmpl, m->tmpl_level);
     for (size_t st = 0; st < m->c.steps.size(); ++st)
         if (m->c.steps[st].kind == STEP_LOCAL)
-            (m->c.progs[m->c.steps[st].tile_rows].warp ? m->warp_steps : m->local_steps).push_back((int32_t)st);
+        {
+            const int32_t kind = m->c.progs[m->c.steps[st].tile_rows].kind;
+            (kind == PROG_WARP ? m->warp_steps : kind == PROG_BIG ? m->big_steps : m->local_steps)
+                .push_back((int32_t)st);
+        }
     for (int32_t lv : m->tmpl_level) m->max_level = std::max(m->max_level, lv);
     // per-request device bytes: storage leaves, arena, partials, exponents
     size_t off = 0;
@@ -511,6 +527,7 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     }
     // the subtree-program kernel's shared memory covers every registered model
     S->dyn_smem = std::max(S->dyn_smem, c.dyn_smem);
+    S->dyn_big = std::max(S->dyn_big, c.dyn_big);
     *model = (int32_t)S->models.size();
     S->models.push_back(std::move(m));
     return TN_OK;

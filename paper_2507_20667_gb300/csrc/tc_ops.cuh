@@ -1,18 +1,19 @@
 // Dense complex contraction steps on the 5th-generation tensor cores (tcgen05, sm_103a), in a
-// split precision: every real operand x is written as hi + lo with hi = bf16(x) and
-// lo = bf16(x - hi), and the product is accumulated in FP32 as hi*hi + hi*lo + lo*hi (the lo*lo
-// term is dropped).
+// split precision: every real operand x is written as hi + lo with hi = r(x) and lo = r(x - hi),
+// r rounding to BF16 (kind::f16) or to TF32 (kind::tf32), and the product is accumulated in FP32 as
+// hi*hi + hi*lo + lo*hi (the lo*lo term is dropped).
 //
 // Complex arithmetic uses the real 4M form.  A complex [M, K] is the real [M, 2K] matrix whose row
 // holds (Re, Im) pairs; B'' is the real [2N, 2K] matrix whose rows 2n and 2n+1 hold (Re B, -Im B)
 // and (Im B, Re B) pairs.  Then A_real * B''^T is the complex C [M, N] with (Re, Im) interleaved,
 // i.e. exactly the complex64 storage of C.
 //
-// One work tile = 128 rows of C x 64 complex columns (128 real columns).  Per K-block of 32 complex
-// indices the block gathers A and B through the step's index maps (scaled exactly by the
-// power-of-two operand scales), splits them and stores four 16 KB operand tiles in the canonical
-// K-major, 128-byte-swizzled shared-memory layout; one thread issues 12 tcgen05.mma (3 products x
-// 4 slices of K = 16) into a 128 x 128 FP32 accumulator in tensor memory and commits them to an
+// One work tile = 128 rows of C x 64 complex columns (128 real columns).  Per K-block (32 complex
+// indices for BF16, 16 for TF32: one 128-byte row of the operand tile either way) the block
+// gathers A and B through the step's index maps (scaled exactly by the power-of-two operand
+// scales), splits them and stores four 16 KB operand tiles in the canonical K-major,
+// 128-byte-swizzled shared-memory layout; one thread issues 12 tcgen05.mma (3 products x 4 slices
+// of 32 bytes of K) into a 128 x 128 FP32 accumulator in tensor memory and commits them to an
 // mbarrier; every wait on it is bounded.  The epilogue reads the accumulator with tcgen05.ld.
 #pragma once
 
@@ -27,7 +28,7 @@ namespace tn {
 constexpr int kTcM = 128;          // rows of C per tile (TMEM lanes)
 constexpr int kTcNc = 64;          // complex columns of C per tile
 constexpr int kTcN = 2 * kTcNc;    // real columns (MMA N)
-constexpr int kTcKc = 32;          // complex shared indices per K-block
+constexpr int kTcKc = 32;          // complex shared indices per K-block (BF16; TF32 takes 16)
 constexpr int kTcTileBytes = kTcM * 128;           // one 128-row operand tile: 16 KB
 constexpr int kTcSmem = 4 * kTcTileBytes + 1024;   // A hi, A lo, B hi, B lo (+ alignment slack)
 constexpr uint32_t kTcCols = 128;                  // TMEM columns (FP32 accumulator)
@@ -78,6 +79,15 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t tmem_d, uint64_t da, uint64
         : "memory");
 }
 
+__device__ __forceinline__ void tc_mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -104,14 +114,17 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
            ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+// Instruction descriptors (FP32 accumulator, A and B both K-major, M x N): kind::f16 with BF16
+// operands (format 1), kind::tf32 with TF32 operands (format 2).
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
 
-// Byte offset of bf16 column c (0..63) of row r in a K-major 128-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t c) {
-    const uint32_t b = 2 * c;
+// Byte offset of byte b (0..127) of row r in a K-major 128-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t b) {
     return r * 128u + ((((b >> 4) ^ (r & 7u)) << 4) | (b & 15u));
 }
 
@@ -120,17 +133,32 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Store the complex pair (re, im) as columns 2kk, 2kk+1 of row r, hi part and lo part.
+// Round to TF32 (10 explicit mantissa bits), nearest with ties away from zero.
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Store the complex pair (re, im) as the real columns 2kk, 2kk+1 of row r: hi part and lo part.
+template <bool TF32>
 __device__ __forceinline__ void put_pair(char *hi_tile, char *lo_tile, uint32_t r, uint32_t kk, float re, float im) {
-    __nv_bfloat16 h0, l0, h1, l1;
-    split_bf16(re, h0, l0);
-    split_bf16(im, h1, l1);
-    const uint32_t off = sw128_off(r, 2 * kk);
-    __nv_bfloat162 h, l;
-    h.x = h0; h.y = h1;
-    l.x = l0; l.y = l1;
-    *reinterpret_cast<__nv_bfloat162 *>(hi_tile + off) = h;
-    *reinterpret_cast<__nv_bfloat162 *>(lo_tile + off) = l;
+    if constexpr (TF32) {
+        const float h0 = round_tf32(re), h1 = round_tf32(im);
+        const uint32_t off = sw128_off(r, 8 * kk);
+        *reinterpret_cast<float2 *>(hi_tile + off) = make_float2(h0, h1);
+        *reinterpret_cast<float2 *>(lo_tile + off) = make_float2(round_tf32(re - h0), round_tf32(im - h1));
+    } else {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(re, h0, l0);
+        split_bf16(im, h1, l1);
+        const uint32_t off = sw128_off(r, 4 * kk);
+        __nv_bfloat162 h, l;
+        h.x = h0; h.y = h1;
+        l.x = l0; l.y = l1;
+        *reinterpret_cast<__nv_bfloat162 *>(hi_tile + off) = h;
+        *reinterpret_cast<__nv_bfloat162 *>(lo_tile + off) = l;
+    }
 }
 
 struct TcState {
@@ -143,11 +171,14 @@ struct TcState {
 
 constexpr long long kTcWaitLimit = 8000000000LL;   // cycles (~4 s at 2 GHz)
 
-// One tensor-core work tile of step d (complex64 storage, BF16 split).  Returns false if a wait on
-// the tensor core gave up (the caller reports TN_ETIMEOUT).
-__device__ bool tile_tc(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem_raw, char *scratch,
-                        float *red, TcState &tc) {
+// One tensor-core work tile of step d (complex64 storage; BF16 split, or TF32 split when the step
+// has FLAG_TF32).  Returns false if a wait on the tensor core gave up (the caller reports
+// TN_ETIMEOUT).
+template <bool TF32>
+__device__ bool tile_tc_impl(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem_raw, char *scratch,
+                             float *red, TcState &tc) {
     using C = float2;
+    constexpr int KC = TF32 ? kTcKc / 2 : kTcKc;   // complex indices per 128-byte operand row
     // 1024-byte aligned operand tiles
     char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     char *Ah = base, *Al = base + kTcTileBytes, *Bh = base + 2 * kTcTileBytes, *Bl = base + 3 * kTcTileBytes;
@@ -167,40 +198,40 @@ __device__ bool tile_tc(const StepDesc &d, int64_t tile, const JobPtrs &j, char 
     const int tid = threadIdx.x;
     for (int i = tid; i < kTcM; i += blockDim.x) rowA[i] = (m0 + i < M) ? group_off(d.m, m0 + i) : -1;
     for (int i = tid; i < kTcNc; i += blockDim.x) colB[i] = (n0 + i < N) ? group_off(d.n, n0 + i) : -1;
-    const uint32_t idesc = idesc_bf16(kTcM, kTcN);
+    const uint32_t idesc = TF32 ? idesc_tf32(kTcM, kTcN) : idesc_bf16(kTcM, kTcN);
     bool ok = true;
     uint32_t acc = 0;
-    for (int64_t k0 = 0; k0 < K && ok; k0 += kTcKc) {
+    for (int64_t k0 = 0; k0 < K && ok; k0 += KC) {
         __syncthreads();   // previous K-block's offsets are no longer read
-        for (int i = tid; i < kTcKc; i += blockDim.x) {
+        for (int i = tid; i < KC; i += blockDim.x) {
             int64_t oa = -1, ob = -1;
             if (k0 + i < K) group_off2(d.k, k0 + i, oa, ob);
             kAo[i] = oa;
             kBo[i] = ob;
         }
         __syncthreads();
-        // A: 128 rows x 32 complex k
-        for (int e = tid; e < kTcM * kTcKc; e += blockDim.x) {
-            const int r = e / kTcKc, kk = e - r * kTcKc;
+        // A: 128 rows x KC complex k
+        for (int e = tid; e < kTcM * KC; e += blockDim.x) {
+            const int r = e / KC, kk = e - r * KC;
             float re = 0.f, im = 0.f;
             if (rowA[r] >= 0 && kAo[kk] >= 0) {
                 const C v = ldc(A + rowA[r] + kAo[kk]);
                 re = v.x * sA;
                 im = v.y * sA;
             }
-            put_pair(Ah, Al, r, kk, re, im);
+            put_pair<TF32>(Ah, Al, r, kk, re, im);
         }
-        // B'': rows 2n = (Re B, -Im B), 2n+1 = (Im B, Re B), 64 complex n x 32 complex k
-        for (int e = tid; e < kTcNc * kTcKc; e += blockDim.x) {
-            const int nn = e / kTcKc, kk = e - nn * kTcKc;
+        // B'': rows 2n = (Re B, -Im B), 2n+1 = (Im B, Re B), 64 complex n x KC complex k
+        for (int e = tid; e < kTcNc * KC; e += blockDim.x) {
+            const int nn = e / KC, kk = e - nn * KC;
             float re = 0.f, im = 0.f;
             if (colB[nn] >= 0 && kBo[kk] >= 0) {
                 const C v = ldc(B + kBo[kk] + colB[nn]);
                 re = v.x * sB;
                 im = v.y * sB;
             }
-            put_pair(Bh, Bl, 2 * nn, kk, re, -im);
-            put_pair(Bh, Bl, 2 * nn + 1, kk, im, re);
+            put_pair<TF32>(Bh, Bl, 2 * nn, kk, re, -im);
+            put_pair<TF32>(Bh, Bl, 2 * nn + 1, kk, im, re);
         }
         fence_async_smem();   // make the generic-proxy stores visible to the tensor core
         tc_fence_before();
@@ -210,12 +241,19 @@ __device__ bool tile_tc(const StepDesc &d, int64_t tile, const JobPtrs &j, char 
             const uint64_t ah = smem_desc_sw128(smem_u32(Ah)), al = smem_desc_sw128(smem_u32(Al));
             const uint64_t bh = smem_desc_sw128(smem_u32(Bh)), bl = smem_desc_sw128(smem_u32(Bl));
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {   // K = 16 bf16 per MMA: advance 32 bytes inside the atom
+            for (int s = 0; s < 4; ++s) {   // 32 bytes of K per MMA: advance inside the atom
                 const uint64_t adv = (uint64_t)(s * 32 >> 4);
-                tc_mma_bf16(tc.tmem, ah + adv, bh + adv, idesc, acc);
-                acc = 1;
-                tc_mma_bf16(tc.tmem, ah + adv, bl + adv, idesc, 1);
-                tc_mma_bf16(tc.tmem, al + adv, bh + adv, idesc, 1);
+                if constexpr (TF32) {
+                    tc_mma_tf32(tc.tmem, ah + adv, bh + adv, idesc, acc);
+                    acc = 1;
+                    tc_mma_tf32(tc.tmem, ah + adv, bl + adv, idesc, 1);
+                    tc_mma_tf32(tc.tmem, al + adv, bh + adv, idesc, 1);
+                } else {
+                    tc_mma_bf16(tc.tmem, ah + adv, bh + adv, idesc, acc);
+                    acc = 1;
+                    tc_mma_bf16(tc.tmem, ah + adv, bl + adv, idesc, 1);
+                    tc_mma_bf16(tc.tmem, al + adv, bh + adv, idesc, 1);
+                }
             }
             tc_commit(tc.bar);
         }
@@ -260,6 +298,12 @@ __device__ bool tile_tc(const StepDesc &d, int64_t tile, const JobPtrs &j, char 
     tc_fence_after();
     if (tile == 0 && threadIdx.x == 0) write_exponent(d, j, eA, eB);
     return true;
+}
+
+__device__ __forceinline__ bool tile_tc(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem_raw,
+                                        char *scratch, float *red, TcState &tc) {
+    if (d.flags & FLAG_TF32) return tile_tc_impl<true>(d, tile, j, smem_raw, scratch, red, tc);
+    return tile_tc_impl<false>(d, tile, j, smem_raw, scratch, red, tc);
 }
 
 }  // namespace tn

@@ -73,6 +73,15 @@ class tn_compile_stats(ctypes.Structure):
                 ("n_warp_progs", ctypes.c_int32), ("n_warp_steps", ctypes.c_int32)]
 
 
+class tn_exec_config(ctypes.Structure):
+    _fields_ = [("local_budget", ctypes.c_int32), ("big_programs", ctypes.c_int32),
+                ("warp_programs", ctypes.c_int32), ("tc_min_m", ctypes.c_int32), ("tc_min_n", ctypes.c_int32),
+                ("tc_min_k", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class tn_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("launched_requests", ctypes.c_int64),
@@ -109,6 +118,10 @@ _SIGS = {
     "tn_serve_free": (None, [_P]),
     "tn_ctx_set_exec_mode": (_I32, [_P, _I32]),
     "tn_ctx_set_local_budget": (_I32, [_P, _I32]),
+    "tn_ctx_get_config": (_I32, [_P, ctypes.POINTER(tn_exec_config)]),
+    "tn_ctx_set_config": (_I32, [_P, ctypes.POINTER(tn_exec_config)]),
+    "tn_ctx_autotune": (_I32, [_P, _I32, _P, _P, _I32, _I32, ctypes.POINTER(tn_exec_config),
+                               ctypes.POINTER(ctypes.c_double), _P, _I32, ctypes.POINTER(_I32)]),
     "tn_batch_create": (_I32, [_P, _I32, _P, _P, _I32, ctypes.POINTER(_P)]),
     "tn_batch_run": (_I32, [_P, _P]),
     "tn_batch_results": (_I32, [_P, _P, _P, _P]),
@@ -338,6 +351,40 @@ def tn_ctx_set_exec_mode(ctx: Ctx, mode="persistent") -> None:
 
 def tn_ctx_set_local_budget(ctx: Ctx, nbytes: int = -1) -> None:
     _check(lib.tn_ctx_set_local_budget(ctx, int(nbytes)))
+
+
+def tn_ctx_get_config(ctx: Ctx) -> dict:
+    cfg = tn_exec_config()
+    _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
+    return cfg.as_dict()
+
+
+def tn_ctx_set_config(ctx: Ctx, **fields) -> None:
+    """Change fields of the context's execution configuration (local_budget, big_programs,
+    warp_programs, tc_min_m, tc_min_n, tc_min_k); the others keep their values."""
+    cfg = tn_exec_config()
+    _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
+    for k, v in fields.items():
+        if k not in cfg.as_dict():
+            raise ValueError(f"unknown configuration field {k}")
+        setattr(cfg, k, int(v))
+    _check(lib.tn_ctx_set_config(ctx, ctypes.byref(cfg)))
+
+
+def tn_ctx_autotune(ctx: Ctx, nets, plans, precision="c64", runs=5):
+    """Times the batch under each candidate configuration, keeps the fastest in ctx.
+    Returns (best configuration dict, its ms per run, [ms of every candidate])."""
+    if len(nets) != len(plans):
+        raise ValueError("nets and plans must have the same length")
+    pn, keep_n = _handle_array(nets)
+    pp, keep_p = _handle_array(plans)
+    best = tn_exec_config()
+    ms = ctypes.c_double()
+    cand = np.zeros(32, np.float64)
+    nc = _I32()
+    _check(lib.tn_ctx_autotune(ctx, len(nets), pn, pp, PRECISIONS[precision], int(runs), ctypes.byref(best),
+                               ctypes.byref(ms), _ptr(cand), len(cand), ctypes.byref(nc)))
+    return best.as_dict(), ms.value, cand[:min(nc.value, len(cand))].tolist()
 
 
 def _handle_array(hs):

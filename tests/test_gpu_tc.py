@@ -1,7 +1,8 @@
-"""Dense contraction steps on the tcgen05 tensor cores (BF16 hi/lo split, FP32 accumulation).
+"""Dense contraction steps on the tcgen05 tensor cores (BF16 or TF32 hi/lo split, FP32
+accumulation).
 
 trace(A B C) written as a closed network of three matrices: the first step A*B is a dense GEMM
-(M = rows of A, N = columns of B, K = the shared leg), so in the BF16-split precision it runs as
+(M = rows of A, N = columns of B, K = the shared leg), so in the split precisions it runs as
 tensor-core tiles; the last step is the FP64 inner product with C.  Checked against the same
 network in complex128 (CUDA cores) and against numpy.einsum.
 """
@@ -41,18 +42,21 @@ def test_tc_gemm_matches_c128(tnsa, shape):
     plan = tnsa.tn_plan_import(h, [(0, 1), (2, 3)])
     ref = net.exact()
     res = {}
-    for prec in ("c128", "c64", "bf16"):
+    for prec in ("c128", "c64", "bf16", "tf32"):
         ctx = tnsa.tn_ctx_create(0)
         tnsa.tn_ctx_set_local_budget(ctx, 0)
         m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
         res[prec] = (complex(m) * 2.0 ** e, info)
-    assert res["bf16"][1]["n_tc"] == 1 and res["c64"][1]["n_tc"] == 0
+    assert res["bf16"][1]["n_tc"] == 1 and res["tf32"][1]["n_tc"] == 1 and res["c64"][1]["n_tc"] == 0
     assert abs(res["c128"][0] - ref) <= 1e-12 * abs(ref)
     assert abs(res["c64"][0] - ref) <= 1e-5 * abs(ref)
     assert abs(res["bf16"][0] - ref) <= 1e-4 * abs(ref), (res["bf16"][0], ref)
+    # three TF32 products carry about 21 bits: the complex64 tolerance
+    assert abs(res["tf32"][0] - ref) <= 1e-5 * abs(ref), (res["tf32"][0], ref)
 
 
-def test_tc_persistent_equals_graph(tnsa):
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_persistent_equals_graph(tnsa, prec):
     net = _Trace(256, 96, 192, seed=5)
     h = tnsa.tn_build(net)
     plan = tnsa.tn_plan_import(h, [(0, 1), (2, 3)])
@@ -61,7 +65,7 @@ def test_tc_persistent_equals_graph(tnsa):
         ctx = tnsa.tn_ctx_create(0)
         tnsa.tn_ctx_set_local_budget(ctx, 0)
         tnsa.tn_ctx_set_exec_mode(ctx, mode)
-        m, e, info = tnsa.tn_contract(ctx, h, plan, "bf16")
+        m, e, info = tnsa.tn_contract(ctx, h, plan, prec)
         out[mode] = (m, e)
         assert info["n_tc"] == 1
     assert out["persistent"] == out["graph"]

@@ -1,0 +1,75 @@
+"""Execution configurations and the autotuner.
+
+Every configuration of the program compiler -- warp programs, block programs, large programs on
+or off, no programs at all -- executes the same contraction tree, so the amplitudes agree with the
+state vector within the complex64 tolerance in every one of them; the autotuner times each
+candidate on the batch, keeps the fastest in the context, and that configuration is the one the
+context then reports.
+"""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from paper_2507_20667_gb300 import inputs as tni
+
+pytestmark = pytest.mark.gpu
+
+N_Q = 16
+
+
+@pytest.fixture(scope="module")
+def tnsa():
+    from paper_2507_20667_gb300 import tnsa as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def batch_inputs(tnsa):
+    circ = tni.brickwork_1d(N_Q, 10, seed=11)
+    xs = [tni.random_bitstring(N_Q, 300 + i) for i in range(24)]
+    nets = [tni.amplitude_tn(circ, x) for x in xs]
+    hs = [tnsa.tn_build(n) for n in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=4, iterations=100, seed=3,
+                               initial_part=tni.qubit_block_partition(nets[0], N_Q, 4))
+    psi = sv.simulate(circ).reshape((2,) * N_Q)
+    ref = np.array([psi[tuple(x)] for x in xs])
+    return hs, plan, ref
+
+
+def _err(got, ref):
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 2.0 ** (-N_Q / 2)))
+
+
+def _run(tnsa, ctx, hs, plan):
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), "c64")
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+    assert (st == 0).all()
+    info = tnsa.tn_batch_last_info(b)
+    b.close()
+    return mant * np.ldexp(1.0, e2), info
+
+
+@pytest.mark.parametrize("cfg", [dict(big_programs=0), dict(warp_programs=0), dict(big_programs=0, warp_programs=0),
+                                 dict(local_budget=0), dict(local_budget=24576)])
+def test_configurations_agree_with_state_vector(tnsa, batch_inputs, cfg):
+    hs, plan, ref = batch_inputs
+    ctx = tnsa.tn_ctx_create(0)
+    tnsa.tn_ctx_set_config(ctx, **cfg)
+    got, info = _run(tnsa, ctx, hs, plan)
+    assert _err(got, ref) <= 1e-5
+    if cfg.get("warp_programs") == 0 or cfg.get("local_budget") == 0:
+        assert info["n_warp_progs"] == 0
+    if cfg.get("local_budget") == 0:
+        assert info["n_local"] == 0
+
+
+def test_autotune_keeps_the_fastest(tnsa, batch_inputs):
+    hs, plan, ref = batch_inputs
+    ctx = tnsa.tn_ctx_create(0)
+    best, ms, cands = tnsa.tn_ctx_autotune(ctx, hs, [plan] * len(hs), "c64", runs=3)
+    ok = [c for c in cands if c > 0]
+    assert len(ok) >= 2 and ms == pytest.approx(min(ok))
+    assert tnsa.tn_ctx_get_config(ctx) == best
+    got, _ = _run(tnsa, ctx, hs, plan)
+    assert _err(got, ref) <= 1e-5
