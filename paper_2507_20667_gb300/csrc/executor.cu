@@ -731,6 +731,15 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             d.kind = STEP_ROWS;
             d.tile_rows = rows_per_tile(M);
             d.ntiles = (int32_t)((M + d.tile_rows - 1) / d.tile_rows);
+            // complex64 steps whose A fits shared memory are staged through it (one tile, every
+            // thread owning 32 / NT rows in one pass)
+            const int64_t nt = N <= 4 ? 4 : (N <= 8 ? 8 : 16);
+            if (elem == 8 && K <= 16 && !(d.flags & FLAG_A_LEAF) && M * K <= kRowsSmemElems &&
+                M * (N + 1) <= kRowsSmemElems && M <= (int64_t)kThreads * (32 / nt)) {
+                d.flags |= FLAG_A_SMEM;
+                d.tile_rows = (int32_t)M;
+                d.ntiles = 1;
+            }
             c.steps.push_back(d);
             c.counts[STEP_ROWS]++;
         } else if (use_tc && M >= opt.tc_min_m && N >= opt.tc_min_n && K >= opt.tc_min_k) {

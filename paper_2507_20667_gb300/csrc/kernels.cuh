@@ -37,7 +37,8 @@ enum StepFlags : int32_t {
     FLAG_B_LEAF = 2,
     FLAG_ROOT = 4,      // the step produces the network's value: write the job's result record
     FLAG_NO_C = 8,      // no tensor output (DOTP, or the root's DOTF)
-    FLAG_TF32 = 16      // TC: TF32 split (else BF16 split)
+    FLAG_TF32 = 16,     // TC: TF32 split (else BF16 split)
+    FLAG_A_SMEM = 32    // ROWS: A is copied whole into shared memory and C leaves through it
 };
 
 struct StepDesc {
@@ -189,6 +190,10 @@ constexpr int kTileM = 64, kTileN = 64, kTileK = 16;   // CUDA-core GEMM tile
 constexpr int kTileNarrow = 1;                          // TILE: tile_rows = 1 selects 128 x 32 tiles
 constexpr int kRowsMaxKN = 1024, kRowsMaxK = 64, kRowsMaxN = 16;
 constexpr int kDotMaxOut = 4;
+// ROWS steps staged through shared memory (complex64): A (M K elements) and then the padded C
+// (M (N + 1) elements) share kRowsSmemElems elements of the dataflow kernel's dynamic shared memory.
+constexpr int kRowsSmemElems = 9216;
+constexpr int kPersistDynSmem = kRowsSmemElems * 8;
 constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
 // Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
 // slice (step descriptor, scale slots, intermediates).

@@ -24,6 +24,9 @@ namespace tn {
 namespace {
 
 constexpr int32_t kStatusTimeout = 5;
+// Dynamic shared memory of the complex64 dataflow kernels: staged ROWS steps, and with tensor
+// cores also the operand tiles (used at different times).
+constexpr int32_t kPersistTcDyn = kTcSmem > kPersistDynSmem ? kTcSmem : kPersistDynSmem;
 constexpr long long kSpinLimitNs = 4000000000LL;   // a wait gives up after ~4 s
 
 __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
@@ -88,7 +91,7 @@ __device__ __forceinline__ void run_item(const StepDesc &d, int64_t tile, const 
             run_local<T>(d.tile_rows, j, dyn, smem, prof);
         }
     } else {
-        run_tile<T>(d, tile, j, smem, red);
+        run_tile<T>(d, tile, j, smem, red, dyn);
     }
 }
 
@@ -249,10 +252,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !TC) ? 2 : 1)
                     if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
                         atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
                 } else {
-                    run_tile<T>(d, it.tile, j, smem, red);
+                    run_tile<T>(d, it.tile, j, smem, red, dyn);
                 }
             } else {
-                run_tile<T>(d, it.tile, j, smem, red);
+                run_tile<T>(d, it.tile, j, smem, red, dyn);
             }
         }
         __threadfence();
@@ -316,7 +319,7 @@ cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtr
         k_step_tc<<<(unsigned)h.ntiles, kThreads, kTcSmem, stream>>>(job.steps, step, job);
         return cudaGetLastError();
     }
-    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : 0;
+    const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : ((h.flags & FLAG_A_SMEM) ? kPersistDynSmem : 0);
     cudaError_t e = c128 ? allow_dyn_smem(k_step<double>, dyn) : allow_dyn_smem(k_step<float>, dyn);
     if (e != cudaSuccess) return e;
     if (c128) k_step<double><<<(unsigned)h.ntiles, kThreads, dyn, stream>>>(job.steps, step, job);
@@ -347,12 +350,15 @@ int32_t persistent_grid(bool c128, int32_t use_tc) {
     if (c128) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double, false>, kThreads, 0);
     } else if (use_tc) {
-        e = allow_dyn_smem(k_persist<float, true>, kTcSmem);
+        e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, true>, kThreads, kTcSmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, true>, kThreads, kPersistTcDyn);
         if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads, 0);
+        e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads,
+                                                              kPersistDynSmem);
     }
     if (e != cudaSuccess) return 0;
     return sms * per_sm;
@@ -410,12 +416,16 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
     if (c128)
         k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
     else if (use_tc) {
-        const cudaError_t e = allow_dyn_smem(k_persist<float, true>, kTcSmem);
+        const cudaError_t e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
         if (e != cudaSuccess) return e;
-        k_persist<float, true><<<(unsigned)grid, kThreads, kTcSmem, stream>>>(jobs_dev, work, n_work, counter, prof);
+        k_persist<float, true><<<(unsigned)grid, kThreads, kPersistTcDyn, stream>>>(jobs_dev, work, n_work, counter,
+                                                                                    prof);
+    } else {
+        const cudaError_t e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
+        if (e != cudaSuccess) return e;
+        k_persist<float, false><<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work,
+                                                                                       counter, prof);
     }
-    else
-        k_persist<float, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
     return cudaGetLastError();
 }
 

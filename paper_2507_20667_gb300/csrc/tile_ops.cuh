@@ -241,9 +241,110 @@ __device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     if (tile == 0 && threadIdx.x == 0) write_exponent(d, j, eA, eB);
 }
 
+// ROWS step whose A fits in shared memory (complex64, FLAG_A_SMEM; the tile covers all M rows):
+// A is copied whole with 16-byte cp.async (coalesced), B densely and scaled into the scratch area;
+// each thread owns R = 32 / NT rows with their accumulators in registers, reading A from shared
+// memory (a row starts its shared index at m mod K when k is contiguous in A, which keeps a warp's
+// reads in different banks); C is then written into the same shared memory with padded rows and
+// leaves it in coalesced order.  HBM traffic: one read of A, one write of C, both coalesced.
+template <int NT>
+__device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red) {
+    using C = float2;
+    constexpr int R = 32 / NT;
+    C *As = reinterpret_cast<C *>(dyn);
+    C *Bd = reinterpret_cast<C *>(smem);                              // [K][N + 1], scaled
+    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 1));   // [K] offsets in A
+    const int32_t M = (int32_t)d.M, N = (int32_t)d.N, K = (int32_t)d.K, PB = N + 1, MK = M * K;
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
+    const C *__restrict__ A = operand<C>(d, j, true);
+    const C *__restrict__ B = operand<C>(d, j, false);
+    C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
+    const int tid = threadIdx.x;
+    for (int32_t i = tid; 2 * i + 1 < MK; i += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(As + 2 * i)),
+                     "l"(A + 2 * i)
+                     : "memory");
+    if ((MK & 1) && tid == 0)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(As + MK - 1)),
+                     "l"(A + MK - 1)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int32_t i = tid; i < K * N; i += blockDim.x) {
+        const int32_t k = i / N, n = i - k * N;
+        int64_t oa, ob;
+        group_off2(d.k, k, oa, ob);
+        ob += group_off(d.n, n);
+        Bd[k * PB + n] = cscale(ldc(B + ob), sB);
+        if (n == 0) kat[k] = (int32_t)oa;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const bool skew = d.k.n > 0 && d.k.sa[0] == 1;
+    const int32_t step = blockDim.x;
+    C acc[R][NT];
+    int32_t rows[R];
+    // rows m0 + r * step of this thread (one pass: M <= R * blockDim by construction)
+    const int32_t m0 = tid;
+    const int32_t sh = skew ? m0 % K : 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int32_t m = m0 + r * step;
+        rows[r] = m < M ? (int32_t)group_off(d.m, m) : -1;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[r][n] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int32_t kk = 0; kk < K; ++kk) {
+        int32_t k = kk + sh;
+        if (k >= K) k -= K;
+        const int32_t ko = kat[k];
+        C av[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) av[r] = rows[r] >= 0 ? cscale(As[rows[r] + ko], sA) : make_float2(0.f, 0.f);
+        const C *Bk = Bd + k * PB;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            if (n >= N) break;
+            const C b = Bk[n];
+#pragma unroll
+            for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
+        }
+    }
+    __syncthreads();   // every thread is done reading A
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int32_t m = m0 + r * step;
+        if (m >= M) continue;
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+            if (n < N) {
+                As[m * PB + n] = acc[r][n];
+                mx = fmaxf(mx, absmax2(acc[r][n]));
+            }
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < M * N; i += blockDim.x) {
+        const int32_t m = i / N;
+        Cp[i] = As[m * PB + (i - m * N)];
+    }
+    publish_max(mx, j.maxbits + d.node_c, red);
+    if (threadIdx.x == 0) write_exponent(d, j, eA, eB);
+}
+
 template <typename T>
 __device__ __forceinline__ void tile_rows_dispatch(const StepDesc &d, int64_t tile, const JobPtrs &j,
-                                                   char *smem, float *red) {
+                                                   char *smem, float *red, char *dyn) {
+    if constexpr (sizeof(T) == 4) {
+        if (d.flags & FLAG_A_SMEM) {
+            if (d.N <= 4) tile_rows_smem<4>(d, j, smem, dyn, red);
+            else if (d.N <= 8) tile_rows_smem<8>(d, j, smem, dyn, red);
+            else tile_rows_smem<16>(d, j, smem, dyn, red);
+            return;
+        }
+    }
     if (d.N <= 1) tile_rows<T, 1>(d, tile, j, smem, red);
     else if (d.N <= 2) tile_rows<T, 2>(d, tile, j, smem, red);
     else if (d.N <= 4) tile_rows<T, 4>(d, tile, j, smem, red);
@@ -487,9 +588,9 @@ __device__ void tile_dotf(const StepDesc &d, const JobPtrs &j, char *smem) {
 
 template <typename T>
 __device__ __forceinline__ void run_tile(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem,
-                                         float *red) {
+                                         float *red, char *dyn) {
     switch (d.kind) {
-        case STEP_ROWS: tile_rows_dispatch<T>(d, tile, j, smem, red); break;
+        case STEP_ROWS: tile_rows_dispatch<T>(d, tile, j, smem, red, dyn); break;
         case STEP_TILE:
             if constexpr (sizeof(T) == 4) {
                 if (d.tile_rows == kTileNarrow) {
