@@ -61,6 +61,9 @@ int32_t tc_mode_of(int32_t prec);
 // Compiler options of an execution configuration on the current device.
 CompileOpts compile_opts(const tn_exec_config &cfg, int32_t prec, bool c128);
 
+// The dataflow work item of tile `tile` of step `step` (with the step's dependencies).
+WorkItem dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_t tile);
+
 // Sorted work items (level, step, tile) of one compiled structure, subtree programs excluded.
 void work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level);
 

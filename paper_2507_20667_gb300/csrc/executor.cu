@@ -907,6 +907,19 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
     return TN_OK;
 }
 
+WorkItem tn::dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_t tile) {
+    const StepDesc &d = c.steps[step];
+    WorkItem w;
+    w.job = job;
+    w.step = (uint32_t)step;
+    w.tile = (uint32_t)tile;
+    w.dep0 = d.dep0;
+    w.dep1 = d.dep1;
+    w.need0 = d.dep0 >= 0 ? (uint32_t)c.steps[d.dep0].ntiles : 0u;
+    w.need1 = d.dep1 >= 0 ? (uint32_t)c.steps[d.dep1].ntiles : 0u;
+    return w;
+}
+
 void tn::work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level) {
     std::vector<std::array<int32_t, 2>> order;   // level, step
     for (size_t s = 0; s < c.steps.size(); ++s)
@@ -916,7 +929,7 @@ void tn::work_template(const Compiled &c, std::vector<WorkItem> &items, std::vec
     item_level.clear();
     for (auto &o : order)
         for (int32_t t = 0; t < c.steps[o[1]].ntiles; ++t) {
-            items.push_back({0u, (uint32_t)o[1], (uint32_t)t});
+            items.push_back(dataflow_item(c, 0u, o[1], t));
             item_level.push_back(o[0]);
         }
 }
@@ -1124,7 +1137,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
                     .push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
                 continue;
             }
-            for (int32_t t = 0; t < d.ntiles; ++t) work.push_back({(uint32_t)o[1], (uint32_t)o[2], (uint32_t)t});
+            const Compiled &cj = b->comp[b->job_comp[o[1]]];
+            for (int32_t t = 0; t < d.ntiles; ++t) work.push_back(dataflow_item(cj, (uint32_t)o[1], o[2], t));
         }
     }
     b->n_work = (int64_t)work.size();

@@ -146,10 +146,16 @@ struct DeviceResult {
     int64_t pad;
 };
 
-// A unit of persistent work: tile `tile` of step `step` of job `job`.
+// A unit of persistent work: tile `tile` of step `step` of job `job`.  Dataflow items also carry
+// their dependencies -- the steps producing A and B (-1: none) and how many tiles each has -- so
+// that a block can wait on them without first reading the step descriptors.
 struct WorkItem {
     uint32_t job, step, tile;
+    int32_t dep0 = -1, dep1 = -1;
+    uint32_t need0 = 0, need1 = 0;
+    uint32_t pad = 0;
 };
+static_assert(sizeof(WorkItem) == 32, "work items are 32 bytes");
 
 // Launchers (all enqueue on `stream`, return the launch error).
 cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jobs,

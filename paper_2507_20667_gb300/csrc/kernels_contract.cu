@@ -35,16 +35,20 @@ __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
     return v;
 }
 
-// Wait until step `dep` of job `j` has completed all its tiles; false if the wait gave up.  The
+// Wait until the steps producing a work item's operands have completed all their tiles; false if
+// the wait gave up.  Both counters are read together (one round trip when they are done).  The
 // first wait that gives up raises the launch-wide abort flag, after which every wait returns at
 // once, so a broken dependency costs one time-out, not one per waiting tile.
-__device__ bool wait_step(const JobPtrs &j, int32_t dep, int32_t *abort_flag) {
-    if (dep < 0) return true;
-    const uint32_t need = (uint32_t)__ldcg(&j.steps[dep].ntiles);
-    if (ld_acquire(j.done + dep) >= need) return true;
+__device__ bool wait_deps(const JobPtrs &j, const WorkItem &it, int32_t *abort_flag) {
+    const bool d0 = it.dep0 >= 0, d1 = it.dep1 >= 0;
+    uint32_t c0 = d0 ? ld_acquire(j.done + it.dep0) : 0u, c1 = d1 ? ld_acquire(j.done + it.dep1) : 0u;
+    if ((!d0 || c0 >= it.need0) && (!d1 || c1 >= it.need1)) return true;
     long long t0 = clock64();
     unsigned ns = 32;
-    while (ld_acquire(j.done + dep) < need) {
+    while (true) {
+        if (d0 && c0 < it.need0) c0 = ld_acquire(j.done + it.dep0);
+        if (d1 && c1 < it.need1) c1 = ld_acquire(j.done + it.dep1);
+        if ((!d0 || c0 >= it.need0) && (!d1 || c1 >= it.need1)) return true;
         if (ld_acquire(abort_flag)) return false;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
@@ -54,30 +58,36 @@ __device__ bool wait_step(const JobPtrs &j, int32_t dep, int32_t *abort_flag) {
             return false;
         }
     }
-    return true;
 }
 
+// One thread per leaf: the leaf's complex128 entries are read in bursts of 8 independent loads,
+// converted to the storage type, and reduced to the leaf's max-abs (gate tensors have at most 16
+// entries, so a leaf costs one or two memory latencies).
 template <typename T>
 __global__ void __launch_bounds__(128) k_leaf_convert(const JobPtrs *__restrict__ jobs) {
     using C = cx_t<T>;
     const JobPtrs &j = jobs[blockIdx.y];
-    const int32_t leaf = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int32_t leaf = blockIdx.x * blockDim.x + threadIdx.x;
     if (leaf >= j.n_leaves) return;
-    const int lane = threadIdx.x & 31;
     const int64_t b = j.leaf_off[leaf], e = j.leaf_off[leaf + 1];
     C *dst = static_cast<C *>(const_cast<void *>(j.leaf));
     float mx = 0.f;
-    for (int64_t i = b + lane; i < e; i += 32) {
-        double2 v = j.leaf64[i];
-        C w = cmake((T)v.x, (T)v.y);
-        dst[i] = w;
-        mx = fmaxf(mx, absmax2(w));
+    constexpr int U = 8;
+    for (int64_t i0 = b; i0 < e; i0 += U) {
+        double2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u < e) v[u] = j.leaf64[i0 + u];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u < e) {
+                const C w = cmake((T)v[u].x, (T)v[u].y);
+                dst[i0 + u] = w;
+                mx = fmaxf(mx, absmax2(w));
+            }
     }
-    mx = warp_max(mx);
-    if (lane == 0) {
-        j.maxbits[leaf] = __float_as_uint(mx);
-        j.exp2[leaf] = 0;
-    }
+    j.maxbits[leaf] = __float_as_uint(mx);
+    j.exp2[leaf] = 0;
 }
 
 template <typename T>
@@ -219,8 +229,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !TC) ? 2 : 1)
     __shared__ float red[32];
     __shared__ uint32_t s_item;
     __shared__ int32_t s_ok;
+    // Claim-ahead: thread 0 claims the next item while the current one runs, so the claim's round
+    // trip is off the critical path.  A block claims items in increasing order and runs them in
+    // that order; the earliest unfinished item is therefore always being run (never only held),
+    // which keeps the list order deadlock-free.
+    uint32_t nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(counter, 1u);
     while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) s_item = nxt;
         __syncthreads();
         const uint32_t w = s_item;
         if ((int64_t)w >= n_work) break;
@@ -232,9 +248,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !TC) ? 2 : 1)
         long long t0 = 0;
         if (threadIdx.x == 0) {
             if (prof) t0 = clock64();
-            const StepDesc *sd = j.steps + it.step;
-            bool ok = wait_step(j, __ldcg(&sd->dep0), abort_flag);
-            ok = wait_step(j, __ldcg(&sd->dep1), abort_flag) && ok;
+            nxt = atomicAdd(counter, 1u);
+            const bool ok = wait_deps(j, it, abort_flag);
             if (!ok) atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
             s_ok = ok;
             if (prof) {
@@ -295,7 +310,7 @@ __global__ void k_finish_leaf(JobPtrs j) {
 cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jobs,
                                 int32_t max_leaves, cudaStream_t stream) {
     if (n_jobs <= 0 || max_leaves <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((max_leaves + 3) / 4), (unsigned)n_jobs);
+    dim3 grid((unsigned)((max_leaves + 127) / 128), (unsigned)n_jobs);
     if (c128) k_leaf_convert<double><<<grid, 128, 0, stream>>>(jobs_dev);
     else k_leaf_convert<float><<<grid, 128, 0, stream>>>(jobs_dev);
     return cudaGetLastError();
