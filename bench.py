@@ -507,6 +507,117 @@ def run_cfg5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cfg3(args):
+    """Precision sweep on the 2D grid circuit: complex128, complex64, TF32 split and BF16 split, each
+    timed on a batch of amplitudes (CUDA events, after warm-up) and checked against the oracle on
+    the 4x5 depth-8 instance; the 5x8 depth-12 instance is planned and its exact memory count
+    reported (its contraction is infeasible with Greedy partition trees)."""
+    import torch
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    from oracle import contract as oc
+    torch.cuda.set_device(0)
+    circ, x0 = tni.cfg3(small=True)
+    n = circ.n_qubits
+    B = min(args.batch, 256)
+    xs = [x0] + [tni.random_bitstring(n, 7000 + i) for i in range(B - 1)]
+    nets = [tni.amplitude_tn(circ, x) for x in xs]
+    hs = [tnsa.tn_build(t) for t in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=8, iterations=args.plan_iters, steps_per_temp=8, seed=7,
+                               initial_part=tni.qubit_block_partition(nets[0], n, 8))
+    con_serial, con_dist, mem = tnsa.tn_plan_counts(plan)
+    part, steps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+    tree = [(int(l), int(r)) for l, r, o in steps]
+    check = sorted({0, B // 2, B - 1})
+    refs = {i: oc.contract_scalar(nets[i], tree) for i in check}
+    stream = torch.cuda.Stream()
+    rows = {}
+    for prec in ("c128", "c64", "tf32", "bf16"):
+        ctx = tnsa.tn_ctx_create(0, stream=stream.cuda_stream)
+        b = tnsa.tn_batch_create(ctx, hs, [plan] * B, prec)
+        info = tnsa.tn_batch_last_info(b)
+        for _ in range(max(args.warmup, 3)):
+            tnsa.tn_batch_run(b)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        steps_t = max(1, min(args.steps, 50))
+        for _ in range(steps_t):
+            tnsa.tn_batch_run(b)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps_t
+        mant, e2, st = tnsa.tn_batch_results(b, B)
+        errs = []
+        for i in check:
+            got = complex(mant[i]) * 2.0 ** int(e2[i])
+            errs.append(abs(got - refs[i]) / max(abs(refs[i]), 2.0 ** (-n / 2)))
+        rows[prec] = {"ms_per_step": ms, "amps_per_s": B / (ms * 1e-3), "tflops": B * 8.0 * con_serial / (ms * 1e-3) / 1e12,
+                      "max_err_vs_oracle": max(errs), "status_ok": bool((st == 0).all()),
+                      "tensor_core_steps": info["n_tc"], "launches": info["launches"]}
+        b.close()
+        ctx.close()
+    big, bh = tni.amplitude_tn(tni.cfg3()[0], tni.cfg3()[1]), None
+    bh = tnsa.tn_build(big)
+    bplan = tnsa.tn_plan_create(bh, k=8, iterations=args.plan_iters, steps_per_temp=8, seed=7,
+                                initial_part=tni.qubit_block_partition(big, 40, 8))
+    _, _, bmem = tnsa.tn_plan_counts(bplan)
+    line = {"metric": METRIC, "value": rows["bf16"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-split", "data": "synthetic",
+            "config": {"workload": f"2D grid 4x5 depth 8 (seed 3), k=8 SA partitions, batch of {B} amplitudes; "
+                                   "precision sweep with the error against the complex128 oracle",
+                       "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem}},
+            "precisions": rows,
+            "full_size_5x8_depth12": {"mem_elements": bmem, "fits_hbm": bmem * 8 < 250e9}}
+    print(json.dumps(line), flush=True)
+
+
+def run_permute(args):
+    """TTGT permutation kernels on a 2^26-element complex64 tensor (512 MiB, 26 binary axes) --
+    the largest intermediate size of the 24-qubit workload: achieved HBM bandwidth (read + write
+    bytes over CUDA-event time, after warm-up; the tensor is 4x the L2) against the measured copy
+    peak, for an axis reversal (shared-memory tile path) and a permutation of the outer axes that
+    keeps the innermost 8 (row path)."""
+    import torch
+    from paper_2507_20667_gb300 import tnsa
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = tnsa.tn_ctx_create(0, stream=stream.cuda_stream)
+    n_ax = 26
+    dims = (2,) * n_ax
+    d_in = torch.randn(1 << n_ax, 2, device="cuda")
+    d_out = torch.empty_like(d_in)
+    cases = {"reverse_all_axes": tuple(range(n_ax - 1, -1, -1)),
+             "outer_axes_permuted_inner_8_kept": tuple([17, 3, 12, 0, 9, 5, 14, 1, 16, 7, 10, 2, 15, 4, 11, 6, 13, 8])
+                                                  + tuple(range(18, 26))}
+    peak, peak_kind = measured_peaks()
+    res = {}
+    for name, perm in cases.items():
+        for _ in range(max(args.warmup, 3)):
+            tnsa.tn_permute(ctx, d_in.data_ptr(), d_out.data_ptr(), 8, dims, perm)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 50))
+        ev0.record(stream)
+        for _ in range(reps):
+            tnsa.tn_permute(ctx, d_in.data_ptr(), d_out.data_ptr(), 8, dims, perm)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        gbs = 2 * (8 << n_ax) / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "GB/s": gbs, "frac": gbs / peak}
+    best = max(r["GB/s"] for r in res.values())
+    line = {"metric": "TTGT permutation bandwidth", "value": best, "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "permute a 2^26-element complex64 tensor (26 binary axes), 512 MiB in and out",
+                       "l2": "tensor 4x the L2"},
+            "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} hbm_gbs"},
+            "cases": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,7 +630,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg4", "cfg5"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "permute"])
     ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)
     ap.add_argument("--max-batch", type=int, default=256)
@@ -528,6 +639,10 @@ def main():
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--warmup-s", type=float, default=3.0)
     args = ap.parse_args()
+    if args.workload == "cfg3" and args.impl == "ours":
+        return run_cfg3(args)
+    if args.workload == "permute" and args.impl == "ours":
+        return run_permute(args)
     if args.workload == "cfg4" and args.impl == "ours":
         return run_cfg4(args)
     if args.workload == "cfg5" and args.impl == "ours":

@@ -494,9 +494,9 @@ constexpr int32_t kStagePiece = 16;
 tn_status push_input(std::vector<LeafRef> &out, int64_t goff, int64_t count, int64_t smem_off, int32_t slot,
                      int32_t node, int32_t src) {
     for (int64_t p = 0; p < std::max<int64_t>(count, 1); p += kStagePiece) {
-        if (goff + p > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "program input offset above 2^31 elements");
         LeafRef r;
-        r.global_off = (int32_t)(goff + p);
+        r.global_off = goff + p;
+        r.pad = 0;
         r.count = (int32_t)std::min<int64_t>(kStagePiece, count - p);
         r.smem_off = (int32_t)(smem_off + p);
         r.slot = p == 0 ? slot : -1;

@@ -113,9 +113,10 @@ enum ProgKind : int32_t { PROG_BLOCK = 0, PROG_WARP = 1, PROG_BIG = 2 };
 // shared-memory element offset smem_off.  The first piece of an input has slot >= 0 and also
 // copies the max-abs and exponent of node `node` into that scale slot.
 struct LeafRef {
-    int32_t global_off, count;
-    int32_t smem_off, slot, node, src;
+    int64_t global_off;
+    int32_t count, smem_off, slot, node, src, pad;
 };
+static_assert(sizeof(LeafRef) == 32, "staging pieces are 32 bytes");
 
 // Everything one contraction (a "job") owns on the device.  Several jobs may share one compiled
 // step list (same network structure and plan) and differ only in their leaves.
@@ -200,7 +201,7 @@ constexpr int kDotMaxOut = 4;
 // (M (N + 1) elements) share kRowsSmemElems elements of the dataflow kernel's dynamic shared memory.
 constexpr int kRowsSmemElems = 9216;
 constexpr int kPersistDynSmem = kRowsSmemElems * 8;
-constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
+constexpr int kDotChunk = 8192;                         // shared indices per DOTP tile
 // Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
 // slice (step descriptor, scale slots, intermediates).
 constexpr int kWarpThreads = 128;

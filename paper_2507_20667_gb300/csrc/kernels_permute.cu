@@ -1,9 +1,12 @@
 // Axis permutation of a row-major tensor (the "T" of TTGT, Section 5.1): out axis t = in axis
 // perm[t].  Moves bytes only, so it is exact for any payload.  Axes that stay adjacent and in
-// order are fused first.  When the innermost axis survives the permutation, each thread copies
-// one element along it (coalesced on both sides); otherwise a 32 x 32 tile of (output-innermost,
-// input-innermost) is staged in shared memory so that both the reads and the writes are
-// coalesced.
+// order are fused first.  When the innermost axis survives the permutation, the tensor is a set
+// of contiguous rows moved as wholes: one warp per row, lane 0 computes the row's source offset
+// and broadcasts it with a shuffle, and the lanes copy the row in 16-byte vectors when both ends
+// are 16-byte aligned (element by element otherwise).  Otherwise a 32 x 32 tile of
+// (output-innermost, input-innermost) is staged in shared memory so that both the reads and the
+// writes are coalesced.
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -25,18 +28,57 @@ struct PermPlan {
     int64_t total;
 };
 
+// Row copy: the output is rows of length odim[a] (the fused innermost axis, stride 1 on both
+// sides); warp w of the grid moves rows w, w + warps, ...
 template <typename E>
-__global__ void __launch_bounds__(256) k_perm_gather(const E *__restrict__ in, E *__restrict__ out,
-                                                     PermPlan p) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t rem = i, src = 0;
+__global__ void __launch_bounds__(256) k_perm_rows(const E *__restrict__ in, E *__restrict__ out, PermPlan p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t len = p.odim[p.a], rows = p.total / len;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const bool vec = (len * (int64_t)sizeof(E)) % 16 == 0 && sizeof(E) <= 16 &&
+                     (reinterpret_cast<uintptr_t>(in) % 16) == 0 && (reinterpret_cast<uintptr_t>(out) % 16) == 0;
+    constexpr int per = 16 / sizeof(E) > 0 ? 16 / (int)sizeof(E) : 1;   // elements per 16-byte vector
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        int64_t src = 0;
+        if (lane == 0) {
+            int64_t rem = r;
+            for (int32_t t = p.rank - 1; t >= 0; --t) {
+                if (t == p.a) continue;
+                const int64_t dgt = rem % p.odim[t];
+                rem /= p.odim[t];
+                src += dgt * p.istride[t];
+            }
+        }
+        src = __shfl_sync(0xffffffffu, src, 0);
+        const E *ip = in + src;
+        E *op = out + r * len;
+        if (vec) {
+            const uint4 *iv = reinterpret_cast<const uint4 *>(ip);
+            uint4 *ov = reinterpret_cast<uint4 *>(op);
+            const int64_t nv = len / per;
+            for (int64_t i = lane; i < nv; i += 32) ov[i] = __ldg(iv + i);
+        } else {
+            for (int64_t i = lane; i < len; i += 32) op[i] = __ldg(ip + i);
+        }
+    }
+}
+
+// Short rows (fewer than 64 bytes): one thread per row, copying it element by element; the
+// threads of a warp write consecutive rows, so the writes stay coalesced.
+template <typename E>
+__global__ void __launch_bounds__(256) k_perm_short_rows(const E *__restrict__ in, E *__restrict__ out,
+                                                         PermPlan p) {
+    const int64_t len = p.odim[p.a], rows = p.total / len;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = r, src = 0;
         for (int32_t t = p.rank - 1; t >= 0; --t) {
-            int64_t dgt = rem % p.odim[t];
+            if (t == p.a) continue;
+            const int64_t dgt = rem % p.odim[t];
             rem /= p.odim[t];
             src += dgt * p.istride[t];
         }
-        out[i] = in[src];
+        for (int64_t i = 0; i < len; ++i) out[r * len + i] = __ldg(in + src + i);
     }
 }
 
@@ -73,15 +115,118 @@ __global__ void __launch_bounds__(256) k_perm_tile(const E *__restrict__ in, E *
     }
 }
 
+// Grouped tile, for permutations of many short axes (the bit permutations of qubit tensors): the
+// output's innermost axes whose sizes multiply to at most 32 form group A, the input's innermost
+// axes (outside A) group B.  A block moves one PA x PB tile of (A index, B index) for one index of
+// the remaining axes through shared memory: it reads with consecutive threads along B (contiguous
+// in the input) and writes with consecutive threads along A (contiguous in the output).
+struct GroupTile {
+    int32_t pa, pb;                           // sizes of the two groups (products of their dims)
+    int32_t nrest;
+    int64_t in_a[32], out_a[32];              // offsets of each A index in the input / output
+    int64_t in_b[32], out_b[32];              // same for B
+    int64_t rdim[kMaxRank], rin[kMaxRank], rout[kMaxRank];   // remaining axes, outermost first
+};
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ in, E *__restrict__ out,
+                                                         const GroupTile g) {
+    __shared__ E tile[32][33];
+    int64_t blk = blockIdx.x, ib = 0, ob = 0;
+    for (int32_t t = g.nrest - 1; t >= 0; --t) {
+        const int64_t dgt = blk % g.rdim[t];
+        blk /= g.rdim[t];
+        ib += dgt * g.rin[t];
+        ob += dgt * g.rout[t];
+    }
+    for (int e = threadIdx.x; e < g.pa * g.pb; e += blockDim.x) {
+        const int b = e % g.pb, a = e / g.pb;
+        tile[a][b] = __ldg(in + ib + g.in_a[a] + g.in_b[b]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < g.pa * g.pb; e += blockDim.x) {
+        const int a = e % g.pa, b = e / g.pa;
+        out[ob + g.out_a[a] + g.out_b[b]] = tile[a][b];
+    }
+}
+
+// Builds the grouped tile of plan p; false when it does not apply (a single axis of 32 or more
+// innermost in the output, or groups smaller than 8 elements).
+bool group_tile(const PermPlan &p, GroupTile &g) {
+    std::vector<char> in_a(p.rank, 0), in_b(p.rank, 0);
+    int64_t pa = 1, pb = 1;
+    std::vector<int32_t> ga, gb;   // innermost first
+    for (int32_t t = p.rank - 1; t >= 0 && pa * p.odim[t] <= 32; --t) {
+        pa *= p.odim[t];
+        ga.push_back(t);
+        in_a[t] = 1;
+    }
+    // input order: axes by decreasing input stride; group B takes the innermost ones outside A
+    std::vector<int32_t> by_in(p.rank);
+    for (int32_t t = 0; t < p.rank; ++t) by_in[t] = t;
+    std::sort(by_in.begin(), by_in.end(), [&](int32_t x, int32_t y) { return p.istride[x] < p.istride[y]; });
+    for (int32_t t : by_in) {
+        if (in_a[t]) continue;
+        if (pb * p.odim[t] > 32) break;
+        pb *= p.odim[t];
+        gb.push_back(t);
+        in_b[t] = 1;
+    }
+    if (pa < 8 || pb < 8) return false;
+    g.pa = (int32_t)pa;
+    g.pb = (int32_t)pb;
+    auto offsets = [&](const std::vector<int32_t> &axes, int64_t *oin, int64_t *oout, int64_t n) {
+        for (int64_t idx = 0; idx < n; ++idx) {
+            int64_t rem = idx, si = 0, so = 0;
+            for (int32_t t : axes) {   // innermost first
+                const int64_t d = rem % p.odim[t];
+                rem /= p.odim[t];
+                si += d * p.istride[t];
+                so += d * p.ostride[t];
+            }
+            oin[idx] = si;
+            oout[idx] = so;
+        }
+    };
+    offsets(ga, g.in_a, g.out_a, pa);
+    offsets(gb, g.in_b, g.out_b, pb);
+    g.nrest = 0;
+    for (int32_t t = 0; t < p.rank; ++t) {
+        if (in_a[t] || in_b[t]) continue;
+        g.rdim[g.nrest] = p.odim[t];
+        g.rin[g.nrest] = p.istride[t];
+        g.rout[g.nrest] = p.ostride[t];
+        g.nrest++;
+    }
+    return true;
+}
+
 template <typename E>
 cudaError_t perm_launch(const void *src, void *dst, const PermPlan &p, cudaStream_t st) {
     const E *in = static_cast<const E *>(src);
     E *out = static_cast<E *>(dst);
     if (p.total == 0) return cudaSuccess;
+    if (p.b >= 0 && p.odim[p.a] < 32) {
+        GroupTile g;
+        if (group_tile(p, g)) {
+            const int64_t blocks = p.total / ((int64_t)g.pa * g.pb);
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+            k_perm_group_tile<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, g);
+            return cudaGetLastError();
+        }
+    }
     if (p.b < 0) {
-        int64_t blocks = (p.total + 255) / 256;
-        if (blocks > 152 * 32) blocks = 152 * 32;
-        k_perm_gather<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p);
+        const int64_t rows = p.total / p.odim[p.a];
+        if (p.odim[p.a] * (int64_t)sizeof(E) < 64) {
+            int64_t blocks = (rows + 255) / 256;
+            if (blocks > 152 * 16) blocks = 152 * 16;
+            k_perm_short_rows<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p);
+        } else {
+            // one warp per row, 8 rows per block, at most 152 SMs x 8 blocks
+            int64_t blocks = (rows + 7) / 8;
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            k_perm_rows<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p);
+        }
     } else {
         int64_t da = p.odim[p.a], db = p.odim[p.b];
         int64_t ta = (da + 31) / 32, tb = (db + 31) / 32;

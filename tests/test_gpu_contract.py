@@ -142,6 +142,8 @@ def test_cfg3_oracle_instance(tnsa, ctx, prec):
     got, info = gpu_amp(tnsa, ctx, net, prec=prec, k=8, iterations=200, steps_per_temp=8, seed=7,
                         initial_part=tni.qubit_block_partition(net, 20, 8))
     assert amp_err(got, ref, 20) <= TOL[prec], (got, ref)
+    if prec in ("tf32", "bf16"):   # the dense fan-in steps run on the tensor cores
+        assert info["n_tc"] > 0
 
 
 def test_cfg2_full_size(tnsa, ctx):

@@ -20,6 +20,9 @@ CASES = [
     ((2,) * 10, None), ((2,) * 20, None), ((3, 5, 7, 2), None), ((33, 65, 3), None),
     ((1, 7, 1, 9), None), ((1000, 1000), (1, 0)), ((4, 4, 4, 4, 4, 4), None), ((17,), (0,)),
     ((2,) * 24, None), ((6, 1, 8, 31, 2), None),
+    # the innermost axis survives: rows copied whole (16-byte vectors when aligned, and short rows)
+    ((8, 16, 64), (1, 0, 2)), ((2,) * 12, (3, 1, 0, 2, 4, 5, 6, 7, 8, 9, 10, 11)), ((5, 7, 3), (1, 0, 2)),
+    ((4, 6, 10), (1, 0, 2)), ((3, 3, 5), (0, 1, 2)),
 ]
 
 
