@@ -201,7 +201,7 @@ constexpr int kDotMaxOut = 4;
 // (M (N + 1) elements) share kRowsSmemElems elements of the dataflow kernel's dynamic shared memory.
 constexpr int kRowsSmemElems = 9216;
 constexpr int kPersistDynSmem = kRowsSmemElems * 8;
-constexpr int kDotChunk = 8192;                         // shared indices per DOTP tile
+constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
 // Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
 // slice (step descriptor, scale slots, intermediates).
 constexpr int kWarpThreads = 128;

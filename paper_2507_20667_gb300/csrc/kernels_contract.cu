@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_step_tc(const StepDesc *__restrict
 // only); it is a separate instantiation so that the CUDA-core variant carries no tensor-memory
 // code and keeps two blocks per SM.
 template <typename T, bool TC>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !TC) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_persist(const JobPtrs *__restrict__ jobs, const WorkItem *__restrict__ work, int64_t n_work,
               uint32_t *counter, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
