@@ -210,26 +210,31 @@ __device__ bool tile_tc_impl(const StepDesc &d, int64_t tile, const JobPtrs &j, 
             kBo[i] = ob;
         }
         __syncthreads();
-        // A: 128 rows x KC complex k
-        for (int e = tid; e < kTcM * KC; e += blockDim.x) {
-            const int r = e / KC, kk = e - r * KC;
-            float re = 0.f, im = 0.f;
-            if (rowA[r] >= 0 && kAo[kk] >= 0) {
-                const C v = ldc(A + rowA[r] + kAo[kk]);
-                re = v.x * sA;
-                im = v.y * sA;
-            }
-            put_pair<TF32>(Ah, Al, r, kk, re, im);
+        // The block's kThreads threads gather the K-block: every load is issued first (RA + RB
+        // independent loads in flight per thread), then the values are split and stored.
+        // A: 128 rows x KC complex k;  B'': rows 2n = (Re B, -Im B), 2n+1 = (Im B, Re B)
+        constexpr int RA = kTcM * KC / kThreads, RB = kTcNc * KC / kThreads;
+        static_assert(RA * kThreads == kTcM * KC && RB * kThreads == kTcNc * KC, "gather split");
+        C va[RA], vb[RB];
+#pragma unroll
+        for (int q = 0; q < RA; ++q) {
+            const int e = tid + q * kThreads, r = e / KC, kk = e - r * KC;
+            va[q] = (rowA[r] >= 0 && kAo[kk] >= 0) ? ldc(A + rowA[r] + kAo[kk]) : make_float2(0.f, 0.f);
         }
-        // B'': rows 2n = (Re B, -Im B), 2n+1 = (Im B, Re B), 64 complex n x KC complex k
-        for (int e = tid; e < kTcNc * KC; e += blockDim.x) {
-            const int nn = e / KC, kk = e - nn * KC;
-            float re = 0.f, im = 0.f;
-            if (colB[nn] >= 0 && kBo[kk] >= 0) {
-                const C v = ldc(B + kBo[kk] + colB[nn]);
-                re = v.x * sB;
-                im = v.y * sB;
-            }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const int e = tid + q * kThreads, nn = e / KC, kk = e - nn * KC;
+            vb[q] = (colB[nn] >= 0 && kBo[kk] >= 0) ? ldc(B + kBo[kk] + colB[nn]) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < RA; ++q) {
+            const int e = tid + q * kThreads, r = e / KC, kk = e - r * KC;
+            put_pair<TF32>(Ah, Al, r, kk, va[q].x * sA, va[q].y * sA);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const int e = tid + q * kThreads, nn = e / KC, kk = e - nn * KC;
+            const float re = vb[q].x * sB, im = vb[q].y * sB;
             put_pair<TF32>(Bh, Bl, 2 * nn, kk, re, -im);
             put_pair<TF32>(Bh, Bl, 2 * nn + 1, kk, im, re);
         }
