@@ -618,6 +618,69 @@ def run_permute(args):
     print(json.dumps(line), flush=True)
 
 
+class _TraceNet:
+    """trace(A B C) as a closed network of three complex matrices (A: I x K, B: K x J, C: J x I):
+    the first pairwise step A*B is a dense GEMM (M = I, N = J, K = K)."""
+
+    def __init__(self, I, K, J, seed):
+        rng = np.random.default_rng(seed)
+
+        def rnd(*sh):
+            return (rng.standard_normal(sh) + 1j * rng.standard_normal(sh)) / np.sqrt(2)
+        A, B, C = rnd(I, K), rnd(K, J), rnd(J, I)
+        self.degrees = np.array([2, 2, 2], np.int32)
+        self.dims = np.array([I, K, K, J, J, I], np.int64)
+        self.data = np.concatenate([A.ravel(), B.ravel(), C.ravel()]).view(np.float64)
+        self.edges = np.array([[0, 1, 1, 0], [1, 1, 2, 0], [2, 1, 0, 0]], np.int32)
+
+
+def run_tcgemm(args):
+    """A dense complex GEMM step (trace(A B C), I = J = 4096, K = 1024 by default) in BF16 split,
+    TF32 split (tcgen05 tensor cores) and complex64 (CUDA cores): device time of the contraction
+    kernels per run, algorithmic TFLOP/s (8 M N K) and executed tensor-core TFLOP/s (24 M N K,
+    three products of the 4M real form) against the measured BF16 peak."""
+    from paper_2507_20667_gb300 import tnsa
+    I, K, J = args.gemm
+    net = _TraceNet(I, K, J, seed=1)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_import(h, [(0, 1), (2, 3)])
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peaks = json.load(f)
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    mnk = I * J * K
+    res = {}
+    for prec in ("bf16", "tf32", "c64"):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_local_budget(ctx, 0)
+        b = tnsa.tn_batch_create(ctx, [h], [plan], prec)
+        for _ in range(max(args.warmup, 3)):
+            tnsa.tn_batch_run(b)
+        reps = max(1, min(args.steps, 20))
+        for _ in range(reps):
+            tnsa.tn_batch_run(b)
+        ms = tnsa.tn_batch_kernel_ms(b, reps)
+        info = tnsa.tn_batch_last_info(b)
+        r = {"ms": ms, "algorithmic_tflops": 8 * mnk / ms / 1e9, "tensor_core_steps": info["n_tc"]}
+        if prec != "c64":
+            executed = 24 * mnk / ms / 1e9
+            peak = bf16_peak if prec == "bf16" else bf16_peak / 2   # TF32 dense rate is half of BF16
+            r.update({"executed_tflops": executed, "tensor_frac": executed / peak})
+        res[prec] = r
+        b.close()
+        ctx.close()
+    line = {"metric": "dense complex GEMM step, TFLOP/s", "value": res["bf16"]["algorithmic_tflops"],
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split", "data": "synthetic",
+            "config": {"workload": f"trace(A B C), A {I}x{K}, B {K}x{J}, C {J}x{I} complex; the A*B step"},
+            "roofline": {"bound": "tensor", "peak": bf16_peak, "unit": "TFLOP/s",
+                         "peak_kind": "measured bf16_tflops" if peaks else "fallback"},
+            "precisions": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -630,7 +693,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "permute"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "permute", "tcgemm"])
+    ap.add_argument("--gemm", type=int, nargs=3, default=[4096, 1024, 4096], metavar=("I", "K", "J"))
     ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)
     ap.add_argument("--max-batch", type=int, default=256)
@@ -643,6 +707,8 @@ def main():
         return run_cfg3(args)
     if args.workload == "permute" and args.impl == "ours":
         return run_permute(args)
+    if args.workload == "tcgemm" and args.impl == "ours":
+        return run_tcgemm(args)
     if args.workload == "cfg4" and args.impl == "ours":
         return run_cfg4(args)
     if args.workload == "cfg5" and args.impl == "ours":

@@ -365,9 +365,14 @@ int32_t persistent_grid(bool c128, int32_t use_tc) {
     if (c128) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double, false>, kThreads, 0);
     } else if (use_tc) {
+        // the occupancy query reports one block per SM for a kernel that allocates tensor memory;
+        // registers and shared memory allow two (as for the CUDA-core instantiation, which has the
+        // same footprint), and two blocks use 2 x 128 of the SM's 512 TMEM columns
         e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
+        if (e == cudaSuccess) e = allow_dyn_smem(k_persist<float, false>, kPersistTcDyn);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, true>, kThreads, kPersistTcDyn);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads,
+                                                              kPersistTcDyn);
         if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
     } else {
         e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);

@@ -1,9 +1,9 @@
 // Axis permutation of a row-major tensor (the "T" of TTGT, Section 5.1): out axis t = in axis
 // perm[t].  Moves bytes only, so it is exact for any payload.  Axes that stay adjacent and in
 // order are fused first.  When the innermost axis survives the permutation, the tensor is a set
-// of contiguous rows moved as wholes: one warp per row, lane 0 computes the row's source offset
-// and broadcasts it with a shuffle, and the lanes copy the row in 16-byte vectors when both ends
-// are 16-byte aligned (element by element otherwise).  Otherwise a 32 x 32 tile of
+// of contiguous rows moved as wholes: a group of lanes per row, whose first lane computes the
+// row's source offset and broadcasts it with a shuffle, copies the row in 16-byte vectors when both
+// ends are 16-byte aligned (element by element otherwise).  Otherwise a 32 x 32 tile of
 // (output-innermost, input-innermost) is staged in shared memory so that both the reads and the
 // writes are coalesced.
 #include <algorithm>
@@ -29,18 +29,25 @@ struct PermPlan {
 };
 
 // Row copy: the output is rows of length odim[a] (the fused innermost axis, stride 1 on both
-// sides); warp w of the grid moves rows w, w + warps, ...
+// sides).  A group of G lanes (G = 16-byte vectors per row, at most 32, a power of two) moves one
+// row: its first lane computes the row's source offset and shares it with a shuffle, and the group
+// copies the row in 16-byte vectors (element by element when a row is not 16-byte aligned).
 template <typename E>
-__global__ void __launch_bounds__(256) k_perm_rows(const E *__restrict__ in, E *__restrict__ out, PermPlan p) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_perm_rows(const E *__restrict__ in, E *__restrict__ out, PermPlan p,
+                                                   int32_t G) {
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
     const int64_t len = p.odim[p.a], rows = p.total / len;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 5) * (32 / G);
     const bool vec = (len * (int64_t)sizeof(E)) % 16 == 0 && sizeof(E) <= 16 &&
                      (reinterpret_cast<uintptr_t>(in) % 16) == 0 && (reinterpret_cast<uintptr_t>(out) % 16) == 0;
     constexpr int per = 16 / sizeof(E) > 0 ? 16 / (int)sizeof(E) : 1;   // elements per 16-byte vector
-    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const int64_t first = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + grp;
+    // every lane runs the same number of iterations (the shuffle needs the whole warp)
+    const int64_t iters = (rows + groups - 1) / groups;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t r = first + it * groups;
         int64_t src = 0;
-        if (lane == 0) {
+        if (sub == 0 && r < rows) {
             int64_t rem = r;
             for (int32_t t = p.rank - 1; t >= 0; --t) {
                 if (t == p.a) continue;
@@ -49,16 +56,17 @@ __global__ void __launch_bounds__(256) k_perm_rows(const E *__restrict__ in, E *
                 src += dgt * p.istride[t];
             }
         }
-        src = __shfl_sync(0xffffffffu, src, 0);
+        src = __shfl_sync(0xffffffffu, src, lane - sub);
+        if (r >= rows) continue;
         const E *ip = in + src;
         E *op = out + r * len;
         if (vec) {
             const uint4 *iv = reinterpret_cast<const uint4 *>(ip);
             uint4 *ov = reinterpret_cast<uint4 *>(op);
             const int64_t nv = len / per;
-            for (int64_t i = lane; i < nv; i += 32) ov[i] = __ldg(iv + i);
+            for (int64_t i = sub; i < nv; i += G) ov[i] = __ldg(iv + i);
         } else {
-            for (int64_t i = lane; i < len; i += 32) op[i] = __ldg(ip + i);
+            for (int64_t i = sub; i < len; i += G) op[i] = __ldg(ip + i);
         }
     }
 }
@@ -130,23 +138,43 @@ struct GroupTile {
 
 template <typename E>
 __global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ in, E *__restrict__ out,
-                                                         const GroupTile g) {
+                                                         const GroupTile g, int64_t n_tiles) {
+    constexpr int kTiles = 4;   // tiles per block
     __shared__ E tile[32][33];
-    int64_t blk = blockIdx.x, ib = 0, ob = 0;
-    for (int32_t t = g.nrest - 1; t >= 0; --t) {
-        const int64_t dgt = blk % g.rdim[t];
-        blk /= g.rdim[t];
-        ib += dgt * g.rin[t];
-        ob += dgt * g.rout[t];
-    }
-    for (int e = threadIdx.x; e < g.pa * g.pb; e += blockDim.x) {
-        const int b = e % g.pb, a = e / g.pb;
-        tile[a][b] = __ldg(in + ib + g.in_a[a] + g.in_b[b]);
+    __shared__ int64_t s_in_a[32], s_out_a[32], s_in_b[32], s_out_b[32], s_ib[kTiles], s_ob[kTiles];
+    const int tid = threadIdx.x;
+    // the offset tables move from the parameters to shared memory once (the arithmetic loops index
+    // them per thread), and the first kTiles threads decompose the block's tile indices
+    if (tid < 32) {
+        s_in_a[tid] = tid < g.pa ? g.in_a[tid] : 0;
+        s_out_a[tid] = tid < g.pa ? g.out_a[tid] : 0;
+        s_in_b[tid] = tid < g.pb ? g.in_b[tid] : 0;
+        s_out_b[tid] = tid < g.pb ? g.out_b[tid] : 0;
+    } else if (tid < 32 + kTiles) {
+        int64_t blk = (int64_t)blockIdx.x * kTiles + (tid - 32), ib = 0, ob = 0;
+        for (int32_t t = g.nrest - 1; t >= 0; --t) {
+            const int64_t dgt = blk % g.rdim[t];
+            blk /= g.rdim[t];
+            ib += dgt * g.rin[t];
+            ob += dgt * g.rout[t];
+        }
+        s_ib[tid - 32] = ib;
+        s_ob[tid - 32] = ob;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < g.pa * g.pb; e += blockDim.x) {
-        const int a = e % g.pa, b = e / g.pa;
-        out[ob + g.out_a[a] + g.out_b[b]] = tile[a][b];
+    for (int q = 0; q < kTiles; ++q) {
+        if ((int64_t)blockIdx.x * kTiles + q >= n_tiles) break;   // block-uniform
+        const int64_t ib = s_ib[q], ob = s_ob[q];
+        for (int e = tid; e < g.pa * g.pb; e += blockDim.x) {
+            const int b = e % g.pb, a = e / g.pb;
+            tile[a][b] = __ldg(in + ib + s_in_a[a] + s_in_b[b]);
+        }
+        __syncthreads();
+        for (int e = tid; e < g.pa * g.pb; e += blockDim.x) {
+            const int a = e % g.pa, b = e / g.pa;
+            out[ob + s_out_a[a] + s_out_b[b]] = tile[a][b];
+        }
+        __syncthreads();
     }
 }
 
@@ -209,9 +237,9 @@ cudaError_t perm_launch(const void *src, void *dst, const PermPlan &p, cudaStrea
     if (p.b >= 0 && p.odim[p.a] < 32) {
         GroupTile g;
         if (group_tile(p, g)) {
-            const int64_t blocks = p.total / ((int64_t)g.pa * g.pb);
+            const int64_t tiles = p.total / ((int64_t)g.pa * g.pb), blocks = (tiles + 3) / 4;
             if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-            k_perm_group_tile<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, g);
+            k_perm_group_tile<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, g, tiles);
             return cudaGetLastError();
         }
     }
@@ -222,10 +250,14 @@ cudaError_t perm_launch(const void *src, void *dst, const PermPlan &p, cudaStrea
             if (blocks > 152 * 16) blocks = 152 * 16;
             k_perm_short_rows<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p);
         } else {
-            // one warp per row, 8 rows per block, at most 152 SMs x 8 blocks
-            int64_t blocks = (rows + 7) / 8;
+            // G lanes per row (its 16-byte vectors, rounded up to a power of two, at most 32)
+            const int64_t nvec = (p.odim[p.a] * (int64_t)sizeof(E) + 15) / 16;
+            int32_t G = 1;
+            while (G < 32 && G < nvec) G *= 2;
+            const int64_t per_block = 8 * (32 / G);
+            int64_t blocks = (rows + per_block - 1) / per_block;
             if (blocks > 152 * 8) blocks = 152 * 8;
-            k_perm_rows<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p);
+            k_perm_rows<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, p, G);
         }
     } else {
         int64_t da = p.odim[p.a], db = p.odim[p.b];
