@@ -36,12 +36,22 @@ N_QUBITS, DEPTH, K_PARTS = 24, 14, 4
 PLAN_ITERS, PLAN_SEED = 2000, 7
 
 
-def workload_config(batch):
+PRECISION_NAMES = {"c64": "complex64, FP64 final reduction",
+                   "bf16": "BF16 hi/lo split on tcgen05 for dense steps (FP32 accumulation), complex64 storage, "
+                           "FP64 final reduction",
+                   "tf32": "TF32 hi/lo split on tcgen05 for dense steps (FP32 accumulation), complex64 storage, "
+                           "FP64 final reduction",
+                   "c128": "complex128"}
+# relative error bound asserted against the oracle, per precision
+PRECISION_TOL = {"c64": 1e-5, "tf32": 1e-5, "bf16": 1e-4, "c128": 1e-12}
+
+
+def workload_config(batch, precision="c64"):
     return {"workload": f"24-qubit 1D brickwork depth {DEPTH} (seed 2), single amplitudes, "
                         f"k={K_PARTS} SA partitions (directed, {PLAN_ITERS} iterations, seed {PLAN_SEED}), "
                         f"batch of {batch} bitstrings per step",
             "n_qubits": N_QUBITS, "depth": DEPTH, "k": K_PARTS, "batch": batch,
-            "precision": "complex64, FP64 final reduction",
+            "precision": PRECISION_NAMES.get(precision, precision),
             "l2": "per-step working set larger than the 129 MB L2 (no flush needed)"}
 
 
@@ -242,7 +252,7 @@ def run_ours(args):
             ref = oc.contract_scalar(nets[i], tree)
             got = complex(mant[i]) * 2.0 ** int(e2[i])
             err = abs(got - ref) / abs(ref)
-            assert err <= 1e-5, f"job {i}: relative error {err:.2e}"
+            assert err <= PRECISION_TOL[args.precision], f"job {i}: relative error {err:.2e}"
 
     # device-resident timing: K steps bracketed by barrier + synchronize, CUDA events on the stream
     for _ in range(args.warmup):
@@ -293,7 +303,8 @@ def run_ours(args):
     cpu = oracle_sample(nets, budget_s=args.cpu_seconds) if not args.skip_cpu else None
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": workload_config(B),
+            "vs_baseline": None, "dtype": args.precision if args.precision != "bf16" else "bf16-split",
+            "data": "synthetic", "config": workload_config(B, args.precision),
             "amps_per_s": ws * B / (ms_per_step * 1e-3),
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                     "amps_per_s": ws * e2e_steps * B / dt, "steps": e2e_steps},

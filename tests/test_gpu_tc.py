@@ -13,17 +13,21 @@ pytestmark = pytest.mark.gpu
 
 
 class _Trace:
-    def __init__(self, I, K, J, seed):
+    """transposed_a: A is stored K x I, so the GEMM's row index (I) is A's contiguous one."""
+    def __init__(self, I, K, J, seed, transposed_a=False):
         rng = np.random.default_rng(seed)
         def rnd(*s):
             return (rng.standard_normal(s) + 1j * rng.standard_normal(s)) / np.sqrt(2)
         self.A, self.B, self.C = rnd(I, K), rnd(K, J), rnd(J, I)
-        self.tensors = [self.A, self.B, self.C]
+        a_store = self.A.T.copy() if transposed_a else self.A
+        self.tensors = [a_store, self.B, self.C]
         self.degrees = np.array([2, 2, 2], np.int32)
-        self.dims = np.array([I, K, K, J, J, I], np.int64)
+        self.dims = np.array([K, I, K, J, J, I] if transposed_a else [I, K, K, J, J, I], np.int64)
         self.data = np.concatenate([t.ravel() for t in self.tensors]).view(np.float64)
-        # A axis 1 - B axis 0 (K); B axis 1 - C axis 0 (J); C axis 1 - A axis 0 (I)
-        self.edges = np.array([[0, 1, 1, 0], [1, 1, 2, 0], [2, 1, 0, 0]], np.int32)
+        if transposed_a:   # A axis 0 - B axis 0 (K); B axis 1 - C axis 0 (J); C axis 1 - A axis 1 (I)
+            self.edges = np.array([[0, 0, 1, 0], [1, 1, 2, 0], [2, 1, 0, 1]], np.int32)
+        else:              # A axis 1 - B axis 0 (K); B axis 1 - C axis 0 (J); C axis 1 - A axis 0 (I)
+            self.edges = np.array([[0, 1, 1, 0], [1, 1, 2, 0], [2, 1, 0, 0]], np.int32)
 
     def exact(self):
         return complex(np.einsum("ik,kj,ji->", self.A, self.B, self.C))
@@ -35,9 +39,12 @@ def tnsa():
     return mod
 
 
-@pytest.mark.parametrize("shape", [(256, 64, 256), (200, 40, 100), (128, 512, 96), (64, 16, 32)])
+@pytest.mark.parametrize("shape", [(256, 64, 256), (200, 40, 100), (128, 512, 96), (64, 16, 32),
+                                   (256, 64, 256, True), (136, 48, 72, True)])
 def test_tc_gemm_matches_c128(tnsa, shape):
-    net = _Trace(*shape, seed=sum(shape))
+    """Both gather orders of the operand tiles: k contiguous in A, and (transposed A) the row
+    index contiguous in A; B always has its column index contiguous."""
+    net = _Trace(*shape[:3], seed=sum(shape[:3]), transposed_a=len(shape) > 3)
     h = tnsa.tn_build(net)
     plan = tnsa.tn_plan_import(h, [(0, 1), (2, 3)])
     ref = net.exact()
