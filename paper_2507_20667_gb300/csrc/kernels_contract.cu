@@ -1,9 +1,11 @@
 // Contraction kernels for sm_103a.
 //
-//  * k_leaf_convert  complex128 leaves -> storage type, with each leaf's max-abs (one warp/leaf)
-//  * k_step          one step of one job, one block per work tile (graph execution mode)
+//  * k_leaf_convert  complex128 leaves -> storage type, with each leaf's max-abs (one thread/leaf)
+//  * k_step          one step of one job, one block per work tile (graph execution mode);
+//    k_step_tc       the same for tensor-core steps
 //  * k_warp          warp programs: subtrees of small steps, one warp each, four per block
-//  * k_local         one block per CTA-resident subtree program (all operands in shared memory)
+//  * k_local         one block per CTA-resident subtree program (all operands in shared memory);
+//                    block programs and large programs are two launches of it
 //  * k_persist       persistent dataflow kernel: every block claims work tiles (job, step, tile)
 //                    from a global list in dependency-level order, waits -- with a bounded spin --
 //                    until the steps producing its operands have completed all their tiles, runs
@@ -11,7 +13,9 @@
 //                    one launch.  Claiming in list order is deadlock-free: a tile is claimed only
 //                    by a running block and waits only on tiles earlier in the list, which were
 //                    claimed by blocks that are running, so the earliest unfinished tile always
-//                    progresses (co-residency of the grid is not needed).
+//                    progresses (co-residency of the grid is not needed).  A block claims its
+//                    next tile while the current one runs.  k_persist<float, true> also runs
+//                    tensor-core tiles (each block then holds 128 TMEM columns).
 #include <cstdint>
 
 #include "kernels.cuh"

@@ -26,7 +26,30 @@ struct PermPlan {
     int32_t a;                    // output-innermost axis (index into the arrays above)
     int32_t b;                    // axis that is innermost in the input (-1 if same as a)
     int64_t total;
+    int32_t pow2;                 // every output dim is a power of two: digits by shift and mask
+    int32_t lg[kMaxRank];         // log2 of each output dim (pow2 only)
 };
+
+// Input offset of output row r (all axes but the innermost, p.a); the digits come out by shift
+// and mask when every dim is a power of two.
+__device__ __forceinline__ int64_t row_src(const PermPlan &p, int64_t r) {
+    int64_t src = 0;
+    if (p.pow2) {
+        for (int32_t t = p.rank - 1; t >= 0; --t) {
+            if (t == p.a) continue;
+            src += (r & (p.odim[t] - 1)) * p.istride[t];
+            r >>= p.lg[t];
+        }
+    } else {
+        for (int32_t t = p.rank - 1; t >= 0; --t) {
+            if (t == p.a) continue;
+            const int64_t dgt = r % p.odim[t];
+            r /= p.odim[t];
+            src += dgt * p.istride[t];
+        }
+    }
+    return src;
+}
 
 // Row copy: the output is rows of length odim[a] (the fused innermost axis, stride 1 on both
 // sides).  A group of G lanes (G = 16-byte vectors per row, at most 32, a power of two) moves one
@@ -47,15 +70,7 @@ __global__ void __launch_bounds__(256) k_perm_rows(const E *__restrict__ in, E *
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t r = first + it * groups;
         int64_t src = 0;
-        if (sub == 0 && r < rows) {
-            int64_t rem = r;
-            for (int32_t t = p.rank - 1; t >= 0; --t) {
-                if (t == p.a) continue;
-                const int64_t dgt = rem % p.odim[t];
-                rem /= p.odim[t];
-                src += dgt * p.istride[t];
-            }
-        }
+        if (sub == 0 && r < rows) src = row_src(p, r);
         src = __shfl_sync(0xffffffffu, src, lane - sub);
         if (r >= rows) continue;
         const E *ip = in + src;
@@ -79,13 +94,7 @@ __global__ void __launch_bounds__(256) k_perm_short_rows(const E *__restrict__ i
     const int64_t len = p.odim[p.a], rows = p.total / len;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
          r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t rem = r, src = 0;
-        for (int32_t t = p.rank - 1; t >= 0; --t) {
-            if (t == p.a) continue;
-            const int64_t dgt = rem % p.odim[t];
-            rem /= p.odim[t];
-            src += dgt * p.istride[t];
-        }
+        const int64_t src = row_src(p, r);
         for (int64_t i = 0; i < len; ++i) out[r * len + i] = __ldg(in + src + i);
     }
 }
@@ -310,6 +319,13 @@ cudaError_t launch_permute(const void *src, void *dst, int32_t elem_bytes, int32
             if (p.istride[t] == 1) p.b = t;
     }
     if (p.rank == 0) { p.rank = 1; p.odim[0] = 1; p.istride[0] = 1; p.ostride[0] = 1; p.a = 0; }
+    p.pow2 = 1;
+    for (int32_t t = 0; t < p.rank; ++t) {
+        int32_t l = 0;
+        while ((int64_t(1) << l) < p.odim[t]) ++l;
+        p.lg[t] = l;
+        if ((int64_t(1) << l) != p.odim[t]) p.pow2 = 0;
+    }
     switch (elem_bytes) {
         case 1: return perm_launch<uint8_t>(src, dst, p, stream);
         case 2: return perm_launch<uint16_t>(src, dst, p, stream);
