@@ -692,6 +692,98 @@ def run_tcgemm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_planner(args):
+    """Planner quality on the 24-qubit brickwork circuit (host only): for k in a sweep, the initial
+    qubit-block partition and simulated annealing in both modes (Algorithm 2, naive and directed),
+    each with the exact con_dist (Eq. 3.5, the critical path) and mem (Eq. 3.1) relative to the
+    serial Greedy tree (k = 1, whose con_dist is its con_serial)."""
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    circ = tni.brickwork_1d(N_QUBITS, DEPTH, seed=2)
+    net = tni.amplitude_tn(circ, tni.random_bitstring(N_QUBITS, 1002))
+    h = tnsa.tn_build(net)
+    serial = tnsa.tn_plan_create(h, k=1)
+    s_total, s_crit, s_mem = tnsa.tn_plan_counts(serial)
+    rows = []
+    for k in args.k_sweep:
+        # qubit blocks need at least one qubit per part; beyond that the balanced BFS start is used
+        init = tni.qubit_block_partition(net, N_QUBITS, k) if k <= N_QUBITS else None
+        row = {"k": k, "initial": "qubit_block" if init is not None else "bfs"}
+        for name, kw in (("initial", dict(iterations=1)),
+                         ("sa_naive", dict(mode="naive", iterations=args.plan_iters)),
+                         ("sa_directed", dict(mode="directed", iterations=args.plan_iters))):
+            t0 = time.perf_counter()
+            plan = tnsa.tn_plan_create(h, k=k, steps_per_temp=8, seed=7, initial_part=init, **kw)
+            sec = time.perf_counter() - t0
+            total, crit, mem = tnsa.tn_plan_counts(plan)
+            row[name] = {"con_dist_ratio": crit / s_crit, "con_serial_ratio": total / s_total,
+                         "mem_ratio": mem / s_mem, "seconds": sec}
+        rows.append(row)
+    line = {"metric": "con_dist of the k-partitioned plan relative to serial Greedy (lower is better)",
+            "value": min(r["sa_directed"]["con_dist_ratio"] for r in rows), "unit": "ratio",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"24-qubit brickwork depth {DEPTH}: qubit-block start, SA naive and directed "
+                                   f"({args.plan_iters} iterations, seed 7) for k in {list(args.k_sweep)}",
+                       "serial": {"con_serial": s_total, "mem": s_mem}},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_costmodel(args):
+    """Measured time against the paper's cost model: plans of the 24-qubit brickwork circuit with
+    different k and SA modes, each timed on the GPU (a batch of amplitudes, CUDA events, kernel
+    time per amplitude) beside its exact con_dist and con_serial; reports the Pearson correlation
+    of time with each count (the paper reports 0.998 for its distributed runs)."""
+    import torch
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    torch.cuda.set_device(0)
+    B = min(args.batch, 608)
+    circ, xs, nets = make_workload(B)
+    hs = [tnsa.tn_build(n) for n in nets]
+    ctx = tnsa.tn_ctx_create(0)
+    rows = []
+    settings = [(1, "directed", 1)] + [(k, mode, iters) for k in args.k_sweep if k > 1
+                                       for mode in ("naive", "directed") for iters in (30, 300, 2000)]
+    for k, mode, iters in settings:
+        init = tni.qubit_block_partition(nets[0], N_QUBITS, k) if 1 < k <= N_QUBITS else None
+        plan = tnsa.tn_plan_create(hs[0], k=k, mode=mode, iterations=iters, steps_per_temp=8, seed=7,
+                                   initial_part=init)
+        total, crit, mem = tnsa.tn_plan_counts(plan)
+        row = {"k": k, "mode": mode, "iterations": iters, "con_serial": total, "con_dist": crit, "mem": mem}
+        if mem * 8 * B > 32e9:   # the batch's intermediates would exceed 32 GB: not timed
+            rows.append(dict(row, skipped="intermediates of the batch above 32 GB"))
+            continue
+        try:
+            b = tnsa.tn_batch_create(ctx, hs, [plan] * B, "c64")
+        except tnsa.TnError as e:
+            rows.append(dict(row, error=str(e)))
+            continue
+        for _ in range(max(args.warmup, 3)):
+            tnsa.tn_batch_run(b)
+        reps = max(1, min(args.steps, 20))
+        for _ in range(reps):
+            tnsa.tn_batch_run(b)
+        ms = tnsa.tn_batch_kernel_ms(b, reps)
+        rows.append(dict(row, us_per_amplitude=1e3 * ms / B))
+        b.close()
+    ok = [r for r in rows if "us_per_amplitude" in r]
+    t = np.array([r["us_per_amplitude"] for r in ok])
+
+    def pearson(x):
+        x = np.array(x, dtype=np.float64)
+        return float(np.corrcoef(x, t)[0, 1]) if len(ok) > 2 else None
+    line = {"metric": "Pearson r of measured GPU time per amplitude with the plan's op counts",
+            "value": pearson([r["con_serial"] for r in ok]), "unit": "r", "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"24-qubit brickwork depth {DEPTH}, batch of {B}, complex64; plans for k in "
+                                   f"{list(args.k_sweep)}, SA naive and directed with 30, 300 and 2000 iterations"},
+            "r_con_serial": pearson([r["con_serial"] for r in ok]),
+            "r_con_dist": pearson([r["con_dist"] for r in ok]),
+            "plans": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,7 +796,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "permute", "tcgemm"])
+    ap.add_argument("--workload", default="cfg2",
+                    choices=["cfg2", "cfg3", "cfg4", "cfg5", "permute", "tcgemm", "planner", "costmodel"])
+    ap.add_argument("--k-sweep", type=int, nargs="+", default=[1, 2, 4, 8, 16])
     ap.add_argument("--gemm", type=int, nargs=3, default=[4096, 1024, 4096], metavar=("I", "K", "J"))
     ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)
@@ -720,6 +814,10 @@ def main():
         return run_permute(args)
     if args.workload == "tcgemm" and args.impl == "ours":
         return run_tcgemm(args)
+    if args.workload == "planner":
+        return run_planner(args)
+    if args.workload == "costmodel" and args.impl == "ours":
+        return run_costmodel(args)
     if args.workload == "cfg4" and args.impl == "ours":
         return run_cfg4(args)
     if args.workload == "cfg5" and args.impl == "ours":
