@@ -171,15 +171,33 @@ __global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ i
         s_ob[tid - 32] = ob;
     }
     __syncthreads();
+    // every read of the block's tiles is issued first (up to kTiles x 4 loads in flight per
+    // thread), then each tile goes through shared memory in turn
+    const int n = g.pa * g.pb;                       // at most 1024 = 4 per thread
+    int nq = kTiles;
+    if ((int64_t)blockIdx.x * kTiles + nq > n_tiles) nq = (int)(n_tiles - (int64_t)blockIdx.x * kTiles);
+    E v[kTiles][4];
+#pragma unroll
+    for (int q = 0; q < kTiles; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + u * 256;
+            if (q < nq && e < n) {
+                const int b = e % g.pb, a = e / g.pb;
+                v[q][u] = __ldg(in + s_ib[q] + s_in_a[a] + s_in_b[b]);
+            }
+        }
+#pragma unroll
     for (int q = 0; q < kTiles; ++q) {
-        if ((int64_t)blockIdx.x * kTiles + q >= n_tiles) break;   // block-uniform
-        const int64_t ib = s_ib[q], ob = s_ob[q];
-        for (int e = tid; e < g.pa * g.pb; e += blockDim.x) {
-            const int b = e % g.pb, a = e / g.pb;
-            tile[a][b] = __ldg(in + ib + s_in_a[a] + s_in_b[b]);
+        if (q >= nq) break;   // block-uniform
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + u * 256;
+            if (e < n) tile[e / g.pb][e % g.pb] = v[q][u];
         }
         __syncthreads();
-        for (int e = tid; e < g.pa * g.pb; e += blockDim.x) {
+        const int64_t ob = s_ob[q];
+        for (int e = tid; e < n; e += blockDim.x) {
             const int a = e % g.pa, b = e / g.pa;
             out[ob + s_out_a[a] + s_out_b[b]] = tile[a][b];
         }
