@@ -15,6 +15,7 @@ struct Compiled {
     std::vector<LocalStep> lsteps;
     std::vector<LeafRef> leafrefs;
     std::vector<LocalWave> lwaves;
+    std::vector<int2> ktab;          // shared-index offset tables of DOTP steps
     std::vector<int64_t> leaf_off;   // [n + 1] element offsets of the leaves
     int32_t n = 0, n_nodes = 0;
     size_t arena_bytes = 0;
@@ -34,6 +35,7 @@ struct Compiled {
     LocalStep *d_lsteps = nullptr;
     LeafRef *d_leafrefs = nullptr;
     LocalWave *d_lwaves = nullptr;
+    int2 *d_ktab = nullptr;
 };
 
 

@@ -676,6 +676,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
         const bool root = (s == n - 2);
         StepDesc d;
         std::memset(&d, 0, sizeof(d));
+        d.ktab_off = -1;
         d.M = g.M; d.N = g.N; d.K = g.K;
         d.node_a = g.a; d.node_b = g.b; d.node_c = o;
         d.c_off = (int64_t)(arena_off[o] / esz);
@@ -715,6 +716,26 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             p.ntiles = (int32_t)((K + kDotChunk - 1) / kDotChunk);
             p.part_off = (int32_t)c.n_partials;
             c.n_partials += (int64_t)p.ntiles * kDotMaxOut;
+            // tabulate the shared-index offsets (the tile then reads one int2 per index instead of
+            // decomposing the index over its leg groups) when the table stays small
+            if (K <= (1 << 20)) {
+                bool fits = true;
+                const size_t t0 = c.ktab.size();
+                c.ktab.resize(t0 + (size_t)K);
+                for (int64_t k = 0; k < K && fits; ++k) {
+                    int64_t idx = k, oa = 0, ob = 0;
+                    for (int32_t i = 0; i < p.k.n; ++i) {
+                        const int64_t dg = idx % p.k.dim[i];
+                        idx /= p.k.dim[i];
+                        oa += dg * p.k.sa[i];
+                        ob += dg * p.k.sb[i];
+                    }
+                    if (oa > 0x7fffffffLL || ob > 0x7fffffffLL) fits = false;
+                    c.ktab[t0 + (size_t)k] = make_int2((int32_t)oa, (int32_t)ob);
+                }
+                if (fits && t0 <= 0x7fffffffULL) p.ktab_off = (int32_t)t0;
+                else c.ktab.resize(t0);
+            }
             c.steps.push_back(p);
             StepDesc f = d;
             f.kind = STEP_DOTF;
@@ -1085,7 +1106,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max(bytes, (size_t)16), 256); return o; };
     std::vector<size_t> o_steps(b->comp.size()), o_loff(b->comp.size());
     std::vector<size_t> o_progs(b->comp.size()), o_lsteps(b->comp.size()), o_lrefs(b->comp.size()),
-        o_lwaves(b->comp.size());
+        o_lwaves(b->comp.size()), o_ktab(b->comp.size());
     for (size_t ci = 0; ci < b->comp.size(); ++ci) {
         o_steps[ci] = carve(sizeof(StepDesc) * b->comp[ci].steps.size());
         o_loff[ci] = carve(sizeof(int64_t) * b->comp[ci].leaf_off.size());
@@ -1093,6 +1114,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         o_lsteps[ci] = carve(sizeof(LocalStep) * b->comp[ci].lsteps.size());
         o_lrefs[ci] = carve(sizeof(LeafRef) * b->comp[ci].leafrefs.size());
         o_lwaves[ci] = carve(sizeof(LocalWave) * b->comp[ci].lwaves.size());
+        o_ktab[ci] = carve(sizeof(int2) * b->comp[ci].ktab.size());
         b->dyn_smem = std::max(b->dyn_smem, b->comp[ci].dyn_smem);
         b->dyn_big = std::max(b->dyn_big, b->comp[ci].dyn_big);
     }
@@ -1184,6 +1206,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->comp[ci].d_lsteps = reinterpret_cast<LocalStep *>(base + o_lsteps[ci]);
         b->comp[ci].d_leafrefs = reinterpret_cast<LeafRef *>(base + o_lrefs[ci]);
         b->comp[ci].d_lwaves = reinterpret_cast<LocalWave *>(base + o_lwaves[ci]);
+        b->comp[ci].d_ktab = reinterpret_cast<int2 *>(base + o_ktab[ci]);
     }
     b->d_leaf64 = reinterpret_cast<double2 *>(base + o_leaf64);
     char *d_leaf = base + o_leaf;
@@ -1211,6 +1234,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         j.lsteps = c.d_lsteps;
         j.leafrefs = c.d_leafrefs;
         j.lwaves = c.d_lwaves;
+        j.ktab = c.d_ktab;
         j.n_steps = (int32_t)c.steps.size();
         j.n_leaves = c.n;
     }
@@ -1240,6 +1264,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         if (e == cudaSuccess && !c.lwaves.empty())
             e = cudaMemcpyAsync(c.d_lwaves, c.lwaves.data(), sizeof(LocalWave) * c.lwaves.size(),
                                 cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !c.ktab.empty())
+            e = cudaMemcpyAsync(c.d_ktab, c.ktab.data(), sizeof(int2) * c.ktab.size(), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_jobs, b->jobs.data(), sizeof(JobPtrs) * (size_t)n, cudaMemcpyHostToDevice, st);

@@ -53,7 +53,8 @@ struct StepDesc {
                                    // TILE: tile shape (0: 64 x 64, kTileNarrow: 128 x 32)
     int32_t part_off;              // DOTP / DOTF: offset of the step's partials (in double2)
     int32_t level;                 // longest path from the leaves (scheduling order)
-    int32_t pad[3];
+    int32_t ktab_off;              // DOTP: first entry of its shared-index offset table (-1: none)
+    int32_t pad[2];
     Groups m, n, k;
 };
 
@@ -135,6 +136,7 @@ struct JobPtrs {
     const LocalStep *lsteps;
     const LeafRef *leafrefs;
     const LocalWave *lwaves;
+    const int2 *ktab;        // (offset in A, offset in B) of each shared index of tabulated DOTP steps
     int32_t n_steps;
     int32_t n_leaves;
 };

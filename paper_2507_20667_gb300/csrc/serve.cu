@@ -269,6 +269,7 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
         j.lsteps = m.c.d_lsteps;
         j.leafrefs = m.c.d_leafrefs;
         j.lwaves = m.c.d_lwaves;
+        j.ktab = m.c.d_ktab;
         j.n_steps = (int32_t)m.c.steps.size();
         j.n_leaves = m.c.n;
     }
@@ -496,6 +497,7 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     const size_t a = tcarve(sizeof(StepDesc) * c.steps.size()), b = tcarve(sizeof(int64_t) * c.leaf_off.size());
     const size_t p = tcarve(sizeof(LocalProg) * c.progs.size()), q = tcarve(sizeof(LocalStep) * c.lsteps.size());
     const size_t r = tcarve(sizeof(LeafRef) * c.leafrefs.size()), w = tcarve(sizeof(LocalWave) * c.lwaves.size());
+    const size_t kt = tcarve(sizeof(int2) * c.ktab.size());
     cudaError_t e = cudaMalloc(&m->dev, t);
     if (e != cudaSuccess) return fail(TN_ENOMEM, cudaGetErrorString(e));
     char *d = static_cast<char *>(m->dev);
@@ -505,6 +507,7 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     m->c.d_lsteps = reinterpret_cast<LocalStep *>(d + q);
     m->c.d_leafrefs = reinterpret_cast<LeafRef *>(d + r);
     m->c.d_lwaves = reinterpret_cast<LocalWave *>(d + w);
+    m->c.d_ktab = reinterpret_cast<int2 *>(d + kt);
     e = cudaMemcpy(m->c.d_steps, c.steps.data(), sizeof(StepDesc) * c.steps.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(m->c.d_leaf_off, c.leaf_off.data(), sizeof(int64_t) * c.leaf_off.size(), cudaMemcpyHostToDevice);
@@ -516,6 +519,8 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
         e = cudaMemcpy(m->c.d_leafrefs, c.leafrefs.data(), sizeof(LeafRef) * c.leafrefs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !c.lwaves.empty())
         e = cudaMemcpy(m->c.d_lwaves, c.lwaves.data(), sizeof(LocalWave) * c.lwaves.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !c.ktab.empty())
+        e = cudaMemcpy(m->c.d_ktab, c.ktab.data(), sizeof(int2) * c.ktab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(m->dev);
         return fail(TN_ECUDA, cudaGetErrorString(e));

@@ -495,12 +495,27 @@ __device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     constexpr int U = 8;
     for (int64_t kb = k_begin; kb < k_end; kb += (int64_t)U * blockDim.x) {
         int64_t oa[U], ob[U];
+        if (d.ktab_off >= 0) {   // tabulated offsets: one coalesced 8-byte load per index
+            const int2 *tab = j.ktab + d.ktab_off;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t k = kb + (int64_t)u * blockDim.x + threadIdx.x;
-            oa[u] = -1;
-            ob[u] = 0;
-            if (k < k_end) group_off2(d.k, k, oa[u], ob[u]);
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = kb + (int64_t)u * blockDim.x + threadIdx.x;
+                oa[u] = -1;
+                ob[u] = 0;
+                if (k < k_end) {
+                    const int2 t = __ldg(tab + k);
+                    oa[u] = t.x;
+                    ob[u] = t.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = kb + (int64_t)u * blockDim.x + threadIdx.x;
+                oa[u] = -1;
+                ob[u] = 0;
+                if (k < k_end) group_off2(d.k, k, oa[u], ob[u]);
+            }
         }
         C run[kDotMaxOut];
 #pragma unroll
