@@ -135,13 +135,17 @@ typedef struct {
     double flops, bytes;       /* algorithmic flops (8 * con_serial) and bytes of one contraction */
     int32_t n_warp_progs;      /* warp programs: subtrees of small steps run by one warp each */
     int32_t n_warp_steps;      /* pairwise steps executed inside warp programs */
+    int32_t n_chained;         /* ROWS steps run as continuations of a chain (rows_chains of
+                                  tn_exec_config, on here) */
+    int32_t pad;
 } tn_compile_stats;
 tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_precision prec,
                                 int32_t local_budget, tn_compile_stats *out);
 
 /* The global step list the compiler produces (same inputs as tn_plan_compile_stats): for each
  * entry 8 int64 {kernel class (0 ROWS, 1 TILE, 2 DOTP, 3 DOTF, 5 subtree program), M, N, K,
- * work tiles, dependency level, program steps, program shared-memory bytes}.  At most cap entries
+ * work tiles, dependency level, program steps (ROWS: the entry that continues it in a chain, -1
+ * none), program shared-memory bytes}.  At most cap entries
  * are written to out (may be NULL); *n_out receives the full count.  Errors: as compile_stats. */
 tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_precision prec,
                                 int32_t local_budget, int64_t *out, int32_t cap, int32_t *n_out);
@@ -209,21 +213,26 @@ tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
  *   warp_programs    1: warp programs -- subtrees of small steps run by one warp each; 0: none
  *   tc_min_m/n/k     in the split precisions, a dense step runs on the tensor cores when
  *                    M >= tc_min_m, N >= tc_min_n and K >= tc_min_k
- * Defaults: {-1, 0, 1, 64, 32, 16} (large programs off: on the 24-qubit brickwork benchmark they
+ *   rows_chains      1: a chain of narrow dataflow steps, each consuming the previous one's output
+ *                    as its large operand, runs in one block of the persistent kernel with the
+ *                    tensor kept in shared memory between the steps (complex64 storage); 0: every
+ *                    step writes its output to the arena.  Results are bit-identical either way.
+ * Defaults: {-1, 0, 1, 64, 32, 16, 1} (large programs off: on the 24-qubit brickwork benchmark they
  * measured slower than running fan-in chains as dataflow steps).  Errors: TN_EINVAL. */
 typedef struct {
     int32_t local_budget;
     int32_t big_programs;
     int32_t warp_programs;
     int32_t tc_min_m, tc_min_n, tc_min_k;
+    int32_t rows_chains;
 } tn_exec_config;
 tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
 tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);
 
 /* Autotuner: for the batch (n, nets, plans, prec) -- the same arguments as tn_batch_create --
  * build a batch under each candidate configuration (program kinds on and off, block-program
- * budgets for two and three blocks per SM, no programs; in the split precisions also tensor-core
- * thresholds), time `runs` runs of each with CUDA events after warm-up, keep the fastest
+ * budgets for two and three blocks per SM, no programs, ROWS chains off; in the split precisions
+ * also tensor-core thresholds), time `runs` runs of each with CUDA events after warm-up, keep the fastest
  * configuration in the context and return it.  out_ms (may be NULL) receives its mean device time
  * per run; cand_ms (may be NULL, cap entries) the mean time of every candidate in the order tried,
  * with *n_cand the number of candidates (failed ones: a negative time).  Errors: TN_EINVAL, those

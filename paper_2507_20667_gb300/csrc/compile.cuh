@@ -44,6 +44,8 @@ struct Compiled {
 // programs at all) and large programs (maximal subtrees within big_budget bytes, inputs staged
 // when consumed; none if big_budget <= local_budget).  tc_mode: dense steps (M >= tc_min_m,
 // N >= tc_min_n, K >= tc_min_k) go to the tensor cores, 1 = BF16 split, 2 = TF32 split.
+// rows_chains: link chains of ROWS steps that the persistent kernel runs with the tensor kept in
+// shared memory.
 struct CompileOpts {
     int32_t elem = 8;                 // bytes per complex element (8: complex64, 16: complex128)
     int32_t local_budget = 0;
@@ -51,6 +53,7 @@ struct CompileOpts {
     bool warp_programs = true;
     int32_t tc_mode = 0;
     int32_t tc_min_m = 64, tc_min_n = 32, tc_min_k = 16;
+    bool rows_chains = true;
 };
 
 // Compile (network structure, plan): the global dataflow step list, the subtree programs and the

@@ -35,7 +35,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16};   // programs and tensor-core thresholds
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1};   // programs and tensor-core thresholds
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -521,6 +521,7 @@ tn::CompileOpts tn::compile_opts(const tn_exec_config &cfg, int32_t prec, bool c
     o.tc_min_m = cfg.tc_min_m;
     o.tc_min_n = cfg.tc_min_n;
     o.tc_min_k = cfg.tc_min_k;
+    o.rows_chains = cfg.rows_chains != 0;
     return o;
 }
 
@@ -677,6 +678,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
         StepDesc d;
         std::memset(&d, 0, sizeof(d));
         d.ktab_off = -1;
+        d.chain_next = -1;
         d.M = g.M; d.N = g.N; d.K = g.K;
         d.node_a = g.a; d.node_b = g.b; d.node_c = o;
         d.c_off = (int64_t)(arena_off[o] / esz);
@@ -786,6 +788,30 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
         }
         producer[o] = (int32_t)c.steps.size() - 1;
         level[o] = c.steps.back().level;
+    }
+    // ROWS chains: step t continues step s in the same persistent block, with s's C kept in
+    // shared memory as t's A, when both stage A through shared memory, A of t is C of s (its only
+    // consumer: the plan is a tree), N of s is a power of two (C's rotated layout) and B of t is a
+    // leaf or a program output (complete before the dataflow launch, so the chain never waits
+    // inside).  Steps are in plan order, so s precedes t.
+    if (opt.rows_chains) {
+        std::vector<int32_t> chain_len(c.steps.size(), 1);
+        for (size_t ti = 0; ti < c.steps.size(); ++ti) {
+            StepDesc &t = c.steps[ti];
+            if (t.kind != STEP_ROWS || !(t.flags & FLAG_A_SMEM) || t.dep0 < 0) continue;
+            StepDesc &s = c.steps[t.dep0];
+            if (s.kind != STEP_ROWS || !(s.flags & FLAG_A_SMEM) || s.chain_next >= 0 || s.node_c != t.node_a)
+                continue;
+            if ((s.N & (s.N - 1)) != 0 || s.M * s.N != t.M * t.K) continue;
+            if (t.dep1 >= 0 && c.steps[t.dep1].kind != STEP_LOCAL) continue;
+            if (chain_len[t.dep0] >= kMaxChain) continue;
+            s.chain_next = (int32_t)ti;
+            t.flags |= FLAG_CHAIN_CONT;
+            int32_t lg = 0;
+            while ((1LL << lg) < s.N) ++lg;
+            t.a_lgn = lg;
+            chain_len[ti] = chain_len[t.dep0] + 1;
+        }
     }
     // pass 4: the programs' compact step lists
     c.progs.clear();
@@ -944,7 +970,8 @@ WorkItem tn::dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_
 void tn::work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level) {
     std::vector<std::array<int32_t, 2>> order;   // level, step
     for (size_t s = 0; s < c.steps.size(); ++s)
-        if (c.steps[s].kind != STEP_LOCAL) order.push_back({c.steps[s].level, (int32_t)s});
+        if (c.steps[s].kind != STEP_LOCAL && !(c.steps[s].flags & FLAG_CHAIN_CONT))
+            order.push_back({c.steps[s].level, (int32_t)s});
     std::sort(order.begin(), order.end());
     items.clear();
     item_level.clear();
@@ -1159,6 +1186,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
                     .push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
                 continue;
             }
+            if (d.flags & FLAG_CHAIN_CONT) continue;   // run inside its chain's first step
             const Compiled &cj = b->comp[b->job_comp[o[1]]];
             for (int32_t t = 0; t < d.ntiles; ++t) work.push_back(dataflow_item(cj, (uint32_t)o[1], o[2], t));
         }
@@ -1467,6 +1495,8 @@ tn_status tn_plan_compile_stats(const tn_net *net, const tn_plan *plan, tn_preci
     st.n_local_steps = c.counts[6];
     st.n_warp_progs = c.counts[7];
     st.n_warp_steps = c.counts[8];
+    st.n_chained = 0;
+    for (const StepDesc &d : c.steps) st.n_chained += (d.flags & FLAG_CHAIN_CONT) ? 1 : 0;
     st.max_local_smem = c.dyn_smem;
     st.total_tiles = c.total_tiles;
     st.arena_bytes = c.arena_bytes;
@@ -1493,7 +1523,7 @@ tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_preci
         const StepDesc &d = c.steps[i];
         int64_t *r = out + 8 * (int64_t)i;
         r[0] = d.kind; r[1] = d.M; r[2] = d.N; r[3] = d.K; r[4] = d.ntiles; r[5] = d.level;
-        r[6] = d.kind == STEP_LOCAL ? c.progs[d.tile_rows].n_steps : 0;
+        r[6] = d.kind == STEP_LOCAL ? c.progs[d.tile_rows].n_steps : (d.kind == STEP_ROWS ? d.chain_next : 0);
         r[7] = d.kind == STEP_LOCAL ? c.progs[d.tile_rows].smem_bytes : 0;
     }
     *n_out = n;
@@ -1533,6 +1563,7 @@ tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
     c->cfg = *cfg;
     c->cfg.big_programs = cfg->big_programs ? 1 : 0;
     c->cfg.warp_programs = cfg->warp_programs ? 1 : 0;
+    c->cfg.rows_chains = cfg->rows_chains ? 1 : 0;
     return TN_OK;
 }
 
@@ -1789,14 +1820,15 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
     // programs; in the split precisions the tensor-core thresholds too
     const int32_t b3 = local_smem_budget(c128, 3);
     std::vector<tn_exec_config> cands = {
-        {-1, 1, 1, 64, 32, 16}, {-1, 0, 1, 64, 32, 16}, {-1, 1, 0, 64, 32, 16},
-        {b3, 1, 1, 64, 32, 16}, {b3, 0, 1, 64, 32, 16}, {0, 0, 0, 64, 32, 16}};
+        {-1, 1, 1, 64, 32, 16, 1}, {-1, 0, 1, 64, 32, 16, 1}, {-1, 0, 1, 64, 32, 16, 0},
+        {-1, 1, 0, 64, 32, 16, 1}, {b3, 1, 1, 64, 32, 16, 1}, {b3, 0, 1, 64, 32, 16, 1},
+        {0, 0, 0, 64, 32, 16, 1}};
     if (tc_mode_of(prec)) {
         const int32_t off = 1 << 30;
-        cands.push_back({-1, 1, 1, off, off, off});
-        cands.push_back({-1, 0, 1, off, off, off});
-        cands.push_back({-1, 1, 1, 32, 32, 16});
-        cands.push_back({-1, 0, 1, 32, 32, 16});
+        cands.push_back({-1, 1, 1, off, off, off, 1});
+        cands.push_back({-1, 0, 1, off, off, off, 1});
+        cands.push_back({-1, 1, 1, 32, 32, 16, 1});
+        cands.push_back({-1, 0, 1, 32, 32, 16, 1});
     }
     const tn_exec_config saved = ctx->cfg;
     drop_cached(ctx);

@@ -38,7 +38,9 @@ enum StepFlags : int32_t {
     FLAG_ROOT = 4,      // the step produces the network's value: write the job's result record
     FLAG_NO_C = 8,      // no tensor output (DOTP, or the root's DOTF)
     FLAG_TF32 = 16,     // TC: TF32 split (else BF16 split)
-    FLAG_A_SMEM = 32    // ROWS: A is copied whole into shared memory and C leaves through it
+    FLAG_A_SMEM = 32,   // ROWS: A is copied whole into shared memory and C leaves through it
+    FLAG_CHAIN_CONT = 64  // ROWS (FLAG_A_SMEM): A is the C of the previous step of a chain, which
+                          // the persistent kernel keeps in shared memory; no work item of its own
 };
 
 struct StepDesc {
@@ -54,7 +56,10 @@ struct StepDesc {
     int32_t part_off;              // DOTP / DOTF: offset of the step's partials (in double2)
     int32_t level;                 // longest path from the leaves (scheduling order)
     int32_t ktab_off;              // DOTP: first entry of its shared-index offset table (-1: none)
-    int32_t pad[2];
+    int32_t chain_next;            // ROWS (FLAG_A_SMEM): the step that consumes C next in the same
+                                   // block, C kept in shared memory (-1: C goes to the arena)
+    int32_t a_lgn;                 // FLAG_CHAIN_CONT: log2 of the previous step's N (the row width
+                                   // of A's rotated shared-memory layout)
     Groups m, n, k;
 };
 
@@ -203,6 +208,8 @@ constexpr int kDotMaxOut = 4;
 // (M (N + 1) elements) share kRowsSmemElems elements of the dataflow kernel's dynamic shared memory.
 constexpr int kRowsSmemElems = 9216;
 constexpr int kPersistDynSmem = kRowsSmemElems * 8;
+// Longest chain of ROWS steps one persistent block runs with the tensor kept in shared memory.
+constexpr int kMaxChain = 32;
 constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
 // Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
 // slice (step descriptor, scale slots, intermediates).

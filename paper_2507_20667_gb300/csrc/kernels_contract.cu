@@ -14,8 +14,10 @@
 //                    by a running block and waits only on tiles earlier in the list, which were
 //                    claimed by blocks that are running, so the earliest unfinished tile always
 //                    progresses (co-residency of the grid is not needed).  A block claims its
-//                    next tile while the current one runs.  k_persist<float, true> also runs
-//                    tensor-core tiles (each block then holds 128 TMEM columns).
+//                    next tile while the current one runs.  A chain of narrow ROWS steps is one
+//                    work item, its tensor kept in shared memory between the steps.
+//                    k_persist<float, true> also runs tensor-core tiles (each block then holds
+//                    128 TMEM columns).
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     __shared__ float red[32];
     __shared__ uint32_t s_item;
     __shared__ int32_t s_ok;
+    __shared__ int32_t s_chain[kMaxChain];   // continuation steps of the current ROWS chain
     // Claim-ahead: thread 0 claims the next item while the current one runs, so the claim's round
     // trip is off the critical path.  A block claims items in increasing order and runs them in
     // that order; the earliest unfinished item is therefore always being run (never only held),
@@ -265,7 +268,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         }
         desc_store(dr, d);
         __syncthreads();
-        if (s_ok) {
+        int32_t n_chain = 0;
+        bool chained = false;
+        if constexpr (sizeof(T) == 4) {
+            if (s_ok && d.kind == STEP_ROWS && d.chain_next >= 0) {
+                n_chain = rows_chain(d, j, smem, dyn, red, s_chain);
+                chained = true;
+            }
+        }
+        if (s_ok && !chained) {
             if constexpr (TC) {
                 if (d.kind == STEP_TC) {
                     if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
@@ -281,6 +292,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             atomicAdd(j.done + it.step, 1);
+            for (int32_t c = 0; c < n_chain; ++c) atomicAdd(j.done + s_chain[c], 1);
+            if (!s_ok) {   // a failed chain still completes its steps, so no consumer waits on them
+                int32_t st = d.chain_next;
+                for (int32_t c = 0; st >= 0 && c < kMaxChain; ++c) {
+                    atomicAdd(j.done + st, 1);
+                    st = __ldcg(&j.steps[st].chain_next);
+                }
+            }
             if (prof) {
                 atomicAdd((unsigned long long *)(prof + d.kind), (unsigned long long)(clock64() - t0));
                 atomicAdd((unsigned long long *)(prof + kProfSlots + d.kind), 1ull);

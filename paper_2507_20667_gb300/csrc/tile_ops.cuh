@@ -241,36 +241,64 @@ __device__ void tile_rows(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     if (tile == 0 && threadIdx.x == 0) write_exponent(d, j, eA, eB);
 }
 
+// Rotated shared-memory layout of a chained ROWS step's C (N a power of two): element (m, n) of
+// the dense row-major [M, N] tensor, dense index i = m N + n, sits at m N + ((n + (m >> r)) mod N)
+// with r = max(0, 4 - log2 N).  The threads of a warp each write their own row m; the rotation puts
+// their N-th outputs in 16 different 8-byte bank pairs.  The next step maps its dense A index
+// through the same function.
+__device__ __forceinline__ int32_t rot_index(int32_t i, int32_t lgn) {
+    const int32_t mask = (1 << lgn) - 1, r = lgn >= 4 ? 0 : 4 - lgn;
+    return (i & ~mask) | ((i + (i >> (lgn + r))) & mask);
+}
+
+// Block-wide max of non-negative values, returned to every thread.  Ends with a barrier.
+__device__ __forceinline__ float block_max(float v, float *red) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+    v = warp_max(v);
+    __syncthreads();
+    return v;
+}
+
 // ROWS step whose A fits in shared memory (complex64, FLAG_A_SMEM; the tile covers all M rows):
-// A is copied whole with 16-byte cp.async (coalesced), B densely and scaled into the scratch area;
-// each thread owns R = 32 / NT rows with their accumulators in registers, reading A from shared
-// memory (a row starts its shared index at m mod K when k is contiguous in A, which keeps a warp's
-// reads in different banks); C is then written into the same shared memory with padded rows and
-// leaves it in coalesced order.  HBM traffic: one read of A, one write of C, both coalesced.
-template <int NT>
-__device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red) {
+// A is copied whole with 16-byte cp.async (coalesced) -- or, for a continuation of a chain
+// (A_ROT), is already in shared memory in the rotated layout of width 2^a_lgn -- and B densely and
+// scaled into the scratch area; each thread owns R = 32 / NT rows with their accumulators in
+// registers, reading A from shared memory (a row starts its shared index at m mod K when k is
+// contiguous in A, which keeps a warp's reads in different banks).  C then either stays in shared
+// memory in the rotated layout (c_in_smem: the next step of the chain consumes it; cmax receives
+// the block's max-abs of C) or is written into the same shared memory with padded rows and leaves
+// it in coalesced order.  HBM traffic: one read of A, one write of C, both coalesced (neither
+// for the inner steps of a chain).  Ends with a barrier.
+template <int NT, bool A_ROT>
+__device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red,
+                               float sA, float sB, bool c_in_smem, float &cmax) {
     using C = float2;
     constexpr int R = 32 / NT;
     C *As = reinterpret_cast<C *>(dyn);
     C *Bd = reinterpret_cast<C *>(smem);                              // [K][N + 1], scaled
     int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 1));   // [K] offsets in A
     const int32_t M = (int32_t)d.M, N = (int32_t)d.N, K = (int32_t)d.K, PB = N + 1, MK = M * K;
-    int32_t eA, eB;
-    step_scales(d, j, eA, eB);
-    const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
     const C *__restrict__ A = operand<C>(d, j, true);
     const C *__restrict__ B = operand<C>(d, j, false);
     C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
     const int tid = threadIdx.x;
-    for (int32_t i = tid; 2 * i + 1 < MK; i += blockDim.x)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(As + 2 * i)),
-                     "l"(A + 2 * i)
-                     : "memory");
-    if ((MK & 1) && tid == 0)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(As + MK - 1)),
-                     "l"(A + MK - 1)
-                     : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (!A_ROT) {
+        for (int32_t i = tid; 2 * i + 1 < MK; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(As + 2 * i)),
+                         "l"(A + 2 * i)
+                         : "memory");
+        if ((MK & 1) && tid == 0)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(As + MK - 1)),
+                         "l"(A + MK - 1)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     for (int32_t i = tid; i < K * N; i += blockDim.x) {
         const int32_t k = i / N, n = i - k * N;
         int64_t oa, ob;
@@ -279,8 +307,9 @@ __device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, 
         Bd[k * PB + n] = cscale(ldc(B + ob), sB);
         if (n == 0) kat[k] = (int32_t)oa;
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!A_ROT) asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
+    const int32_t lga = d.a_lgn;
     const bool skew = d.k.n > 0 && d.k.sa[0] == 1;
     const int32_t step = blockDim.x;
     C acc[R][NT];
@@ -302,7 +331,11 @@ __device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, 
         const int32_t ko = kat[k];
         C av[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) av[r] = rows[r] >= 0 ? cscale(As[rows[r] + ko], sA) : make_float2(0.f, 0.f);
+        for (int r = 0; r < R; ++r) {
+            int32_t ia = rows[r] + ko;
+            if (A_ROT) ia = rot_index(ia, lga);
+            av[r] = rows[r] >= 0 ? cscale(As[ia], sA) : make_float2(0.f, 0.f);
+        }
         const C *Bk = Bd + k * PB;
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
@@ -314,6 +347,22 @@ __device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, 
     }
     __syncthreads();   // every thread is done reading A
     float mx = 0.f;
+    if (c_in_smem) {
+        const int32_t lgn = __ffs(N) - 1, rs = lgn >= 4 ? 0 : 4 - lgn;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int32_t m = m0 + r * step;
+            if (m >= M) continue;
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+                if (n < N) {
+                    As[m * N + ((n + (m >> rs)) & (N - 1))] = acc[r][n];
+                    mx = fmaxf(mx, absmax2(acc[r][n]));
+                }
+        }
+        cmax = block_max(mx, red);
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int32_t m = m0 + r * step;
@@ -331,7 +380,62 @@ __device__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, 
         Cp[i] = As[m * PB + (i - m * N)];
     }
     publish_max(mx, j.maxbits + d.node_c, red);
+}
+
+template <bool A_ROT>
+__device__ __forceinline__ void rows_smem_any(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn,
+                                              float *red, float sA, float sB, bool c_in_smem, float &cmax) {
+    if (d.N <= 4) rows_smem_core<4, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
+    else if (d.N <= 8) rows_smem_core<8, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
+    else rows_smem_core<16, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
+}
+
+// A ROWS step staged through shared memory on its own.
+__device__ __forceinline__ void tile_rows_smem(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn,
+                                               float *red) {
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    float cmax = 0.f;
+    rows_smem_any<false>(d, j, smem, dyn, red, pow2<float>(-eA), pow2<float>(-eB), false, cmax);
     if (threadIdx.x == 0) write_exponent(d, j, eA, eB);
+}
+
+// A chain of ROWS steps linked by chain_next, run by one block of the persistent kernel: the first
+// step reads A from the arena, each later one takes the previous step's C, kept in shared memory,
+// as its A, and the last writes its C to the arena.  The per-step power-of-two scaling is
+// unchanged: a continuation's A exponent comes from the block max of the previous C, which is the
+// value the separate steps would publish, so results are bit-identical to running the steps one
+// by one; the exponents of the inner nodes stay in registers and only the last node's max-abs and
+// exponent are written.  d is the block's shared descriptor and is overwritten with each step's;
+// thread 0 writes the indices of the continuation steps to chain[].  Returns their count.
+__device__ __forceinline__ int32_t rows_chain(StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red,
+                                              int32_t *chain) {
+    int32_t eA, eB;
+    step_scales(d, j, eA, eB);
+    int32_t xa = __ldcg(j.exp2 + d.node_a), xb = __ldcg(j.exp2 + d.node_b);
+    int32_t n = 0;
+    while (true) {
+        const int32_t next = d.chain_next;
+        int4 dr[kDescRounds];
+        if (next >= 0) desc_fetch(dr, j.steps + next);
+        float cmax = 0.f;
+        const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
+        if (n == 0) rows_smem_any<false>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax);
+        else rows_smem_any<true>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax);
+        const int32_t xc = xa + eA + xb + eB;
+        if (next < 0) {
+            if (threadIdx.x == 0) j.exp2[d.node_c] = xc;
+            return n;
+        }
+        desc_store(dr, d);   // the step ended with a barrier: nobody reads the old descriptor
+        __syncthreads();
+        if (threadIdx.x == 0) chain[n] = next;
+        ++n;
+        xa = xc;
+        eA = scale_exponent(__float_as_uint(cmax));
+        eB = scale_exponent(__ldcg(j.maxbits + d.node_b));
+        xb = __ldcg(j.exp2 + d.node_b);
+    }
 }
 
 template <typename T>
@@ -339,9 +443,7 @@ __device__ __forceinline__ void tile_rows_dispatch(const StepDesc &d, int64_t ti
                                                    char *smem, float *red, char *dyn) {
     if constexpr (sizeof(T) == 4) {
         if (d.flags & FLAG_A_SMEM) {
-            if (d.N <= 4) tile_rows_smem<4>(d, j, smem, dyn, red);
-            else if (d.N <= 8) tile_rows_smem<8>(d, j, smem, dyn, red);
-            else tile_rows_smem<16>(d, j, smem, dyn, red);
+            tile_rows_smem(d, j, smem, dyn, red);
             return;
         }
     }

@@ -70,13 +70,14 @@ class tn_compile_stats(ctypes.Structure):
                 ("n_dot", ctypes.c_int32), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
                 ("max_local_smem", ctypes.c_int32), ("levels", ctypes.c_int32), ("total_tiles", ctypes.c_int64),
                 ("arena_bytes", ctypes.c_size_t), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
-                ("n_warp_progs", ctypes.c_int32), ("n_warp_steps", ctypes.c_int32)]
+                ("n_warp_progs", ctypes.c_int32), ("n_warp_steps", ctypes.c_int32),
+                ("n_chained", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class tn_exec_config(ctypes.Structure):
     _fields_ = [("local_budget", ctypes.c_int32), ("big_programs", ctypes.c_int32),
                 ("warp_programs", ctypes.c_int32), ("tc_min_m", ctypes.c_int32), ("tc_min_n", ctypes.c_int32),
-                ("tc_min_k", ctypes.c_int32)]
+                ("tc_min_k", ctypes.c_int32), ("rows_chains", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -321,7 +322,7 @@ def tn_plan_export(plan: Plan, n_tensors: int):
 def tn_plan_compile_stats(net: Net, plan: Plan, precision="c64", local_budget=0) -> dict:
     st = tn_compile_stats()
     _check(lib.tn_plan_compile_stats(net, plan, PRECISIONS[precision], int(local_budget), ctypes.byref(st)))
-    return {f: getattr(st, f) for f, _ in tn_compile_stats._fields_}
+    return {f: getattr(st, f) for f, _ in tn_compile_stats._fields_ if f != "pad"}
 
 
 def tn_plan_compile_steps(net: Net, plan: Plan, precision="c64", local_budget=0) -> np.ndarray:
@@ -361,7 +362,7 @@ def tn_ctx_get_config(ctx: Ctx) -> dict:
 
 def tn_ctx_set_config(ctx: Ctx, **fields) -> None:
     """Change fields of the context's execution configuration (local_budget, big_programs,
-    warp_programs, tc_min_m, tc_min_n, tc_min_k); the others keep their values."""
+    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains); the others keep their values."""
     cfg = tn_exec_config()
     _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
     for k, v in fields.items():

@@ -51,3 +51,29 @@ def test_small_step_subtrees_become_warp_programs():
     steps = tnsa.tn_plan_compile_steps(h, plan, "c64", 100000)
     progs = steps[steps[:, 0] == KIND_LOCAL]
     assert (progs[:, 7] <= 100000).all() and (progs[:, 6] >= 1).all()
+
+
+@pytest.mark.parametrize("budget", [0, 4096])
+def test_rows_chains_link_producer_to_consumer(budget):
+    """A chain link s -> t (t continues s in the same block, s's output kept in shared memory) goes
+    forward in the step list, joins ROWS steps only, is taken at most once per step, and stays
+    within the 32-step chain limit; the stats count the continuations."""
+    net, h, plan = _cfg2_like()
+    st = tnsa.tn_plan_compile_stats(h, plan, "c64", budget)
+    steps = tnsa.tn_plan_compile_steps(h, plan, "c64", budget)
+    rows = np.flatnonzero(steps[:, 0] == 0)
+    nxt = {int(i): int(steps[i, 6]) for i in rows if steps[i, 6] >= 0}
+    assert len(nxt) == st["n_chained"] > 0
+    assert len(set(nxt.values())) == len(nxt)
+    for s, t in nxt.items():
+        assert t > s and steps[t, 0] == 0
+        assert steps[s, 1] * steps[s, 2] == steps[t, 1] * steps[t, 3]   # C of s is A of t
+        assert steps[t, 5] > steps[s, 5]
+    heads = set(nxt) - set(nxt.values())
+    for hd in heads:
+        n, s = 1, hd
+        while s in nxt:
+            s, n = nxt[s], n + 1
+        assert n <= 32
+    # complex128 storage never stages A in shared memory, so it has no chains
+    assert tnsa.tn_plan_compile_stats(h, plan, "c128", budget)["n_chained"] == 0

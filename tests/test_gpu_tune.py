@@ -73,3 +73,31 @@ def test_autotune_keeps_the_fastest(tnsa, batch_inputs):
     assert tnsa.tn_ctx_get_config(ctx) == best
     got, _ = _run(tnsa, ctx, hs, plan)
     assert _err(got, ref) <= 1e-5
+
+
+def _run_bits(tnsa, ctx, hs, plan):
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), "c64")
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+    b.close()
+    assert (st == 0).all()
+    return mant, e2
+
+
+@pytest.mark.parametrize("budget", [0, 4096, -1])
+def test_rows_chains_are_bit_identical(tnsa, batch_inputs, budget):
+    """A chain of ROWS steps run in one block with the tensor kept in shared memory computes the
+    same arithmetic in the same order as the separate steps, and carries the per-step scale
+    exponents unchanged: mantissas and exponents agree bit for bit."""
+    hs, plan, ref = batch_inputs
+    if budget >= 0:
+        assert tnsa.tn_plan_compile_stats(hs[0], plan, "c64", budget)["n_chained"] > 0
+    out = []
+    for chains in (1, 0):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_config(ctx, local_budget=budget, rows_chains=chains)
+        out.append(_run_bits(tnsa, ctx, hs, plan))
+    (m1, e1), (m0, e0) = out
+    assert np.array_equal(e1, e0)
+    assert np.array_equal(m1.view(np.uint64), m0.view(np.uint64))
+    assert _err(m1 * np.ldexp(1.0, e1), ref) <= 1e-5
