@@ -414,9 +414,12 @@ __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, f
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
     C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
-    const int32_t N = s.N, K = s.K, M = s.M, PB = N + 1;
-    C *Bd = reinterpret_cast<C *>(scratch);                                  // [K][N + 1], scaled
-    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 1));          // [K] offsets in A
+    // [K][PB] scaled B; complex64 rows are padded to an even length, so they start on 16 bytes and
+    // are read two entries per load
+    constexpr bool PAIRS = sizeof(T) == 4;
+    const int32_t N = s.N, K = s.K, M = s.M, PB = PAIRS ? (N + 2) & ~1 : N + 1;
+    C *Bd = reinterpret_cast<C *>(scratch);
+    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 2));          // [K] offsets in A
     const bool p2 = s.pow2;
     for (int32_t i = threadIdx.x; i < K * N; i += blockDim.x) {
         const int32_t k = i / N, n = i - k * N;
@@ -451,12 +454,28 @@ __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, f
 #pragma unroll
             for (int r = 0; r < R; ++r) av[r] = offA[r] >= 0 ? cscale(A[offA[r] + ko], sA) : cmake((T)0, (T)0);
             const C *Bk = Bd + k * PB;
+            if constexpr (PAIRS) {
+                const float4 *Bk4 = reinterpret_cast<const float4 *>(Bk);
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                if (n >= N) break;
-                const C b = Bk[n];
+                for (int n2 = 0; n2 < NT / 2; ++n2) {
+                    if (2 * n2 >= N) break;
+                    const float4 bb = Bk4[n2];
+                    const C b0 = cmake(bb.x, bb.y), b1 = cmake(bb.z, bb.w);
 #pragma unroll
-                for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
+                    for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2], av[r], b0);
+                    if (2 * n2 + 1 < N) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2 + 1], av[r], b1);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    if (n >= N) break;
+                    const C b = Bk[n];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
+                }
             }
         }
 #pragma unroll

@@ -279,9 +279,12 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
     using C = float2;
     constexpr int R = 32 / NT;
     C *As = reinterpret_cast<C *>(dyn);
-    C *Bd = reinterpret_cast<C *>(smem);                              // [K][N + 1], scaled
-    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 1));   // [K] offsets in A
-    const int32_t M = (int32_t)d.M, N = (int32_t)d.N, K = (int32_t)d.K, PB = N + 1, MK = M * K;
+    // [K][PB] scaled B, PB = N + 1 rounded up to even: rows start on 16 bytes and are read two
+    // entries per load
+    C *Bd = reinterpret_cast<C *>(smem);
+    int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 2));   // [K] offsets in A
+    const int32_t M = (int32_t)d.M, N = (int32_t)d.N, K = (int32_t)d.K, PB = (N + 2) & ~1, MK = M * K;
+    const int32_t PC = N + 1;   // padded C rows (M (N + 1) elements fit by construction)
     const C *__restrict__ A = operand<C>(d, j, true);
     const C *__restrict__ B = operand<C>(d, j, false);
     C *__restrict__ Cp = reinterpret_cast<C *>(j.arena) + d.c_off;
@@ -336,13 +339,18 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
             if (A_ROT) ia = rot_index(ia, lga);
             av[r] = rows[r] >= 0 ? cscale(As[ia], sA) : make_float2(0.f, 0.f);
         }
-        const C *Bk = Bd + k * PB;
+        const float4 *Bk = reinterpret_cast<const float4 *>(Bd + k * PB);
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            if (n >= N) break;
-            const C b = Bk[n];
+        for (int n2 = 0; n2 < NT / 2; ++n2) {
+            if (2 * n2 >= N) break;
+            const float4 bb = Bk[n2];
+            const C b0 = make_float2(bb.x, bb.y), b1 = make_float2(bb.z, bb.w);
 #pragma unroll
-            for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
+            for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2], av[r], b0);
+            if (2 * n2 + 1 < N) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2 + 1], av[r], b1);
+            }
         }
     }
     __syncthreads();   // every thread is done reading A
@@ -370,14 +378,14 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
 #pragma unroll
         for (int n = 0; n < NT; ++n)
             if (n < N) {
-                As[m * PB + n] = acc[r][n];
+                As[m * PC + n] = acc[r][n];
                 mx = fmaxf(mx, absmax2(acc[r][n]));
             }
     }
     __syncthreads();
     for (int32_t i = tid; i < M * N; i += blockDim.x) {
         const int32_t m = i / N;
-        Cp[i] = As[m * PB + (i - m * N)];
+        Cp[i] = As[m * PC + (i - m * N)];
     }
     publish_max(mx, j.maxbits + d.node_c, red);
 }
