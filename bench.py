@@ -66,7 +66,7 @@ def make_workload(batch, seed0=5000):
 def plan_for(tnsa, tni, net_py, net_h):
     return tnsa.tn_plan_create(net_h, k=K_PARTS, mode="directed", iterations=PLAN_ITERS, steps_per_temp=8,
                                seed=PLAN_SEED,
-                               initial_part=tni.qubit_block_partition(net_py, N_QUBITS, K_PARTS))
+                               position=net_py.qubit)
 
 
 class ClockSampler:
@@ -328,8 +328,8 @@ def run_ours(args):
 def _amp_model(tnsa, tni, circ, k, seed, iters):
     net = tni.amplitude_tn(circ, [0] * circ.n_qubits)
     h = tnsa.tn_build(net)
-    init = tni.qubit_block_partition(net, circ.n_qubits, k) if k > 1 else None
-    plan = tnsa.tn_plan_create(h, k=k, iterations=iters, steps_per_temp=8, seed=seed, initial_part=init)
+    pos = net.qubit if k > 1 else None
+    plan = tnsa.tn_plan_create(h, k=k, iterations=iters, steps_per_temp=8, seed=seed, position=pos)
     return net, h, plan, tni.bra_ids(net, circ.n_qubits)
 
 
@@ -442,7 +442,7 @@ def run_cfg5(args):
         zh = tnsa.tn_build(znet)
         try:
             zplan = tnsa.tn_plan_create(zh, k=4, iterations=args.plan_iters, seed=7,
-                                        initial_part=tni.qubit_block_partition(znet, nq, 4))
+                                        position=znet.qubit)
             zz = (znet, zh, zplan, slots)
         except tnsa.TnError:
             zz = None
@@ -535,7 +535,7 @@ def run_cfg3(args):
     nets = [tni.amplitude_tn(circ, x) for x in xs]
     hs = [tnsa.tn_build(t) for t in nets]
     plan = tnsa.tn_plan_create(hs[0], k=8, iterations=args.plan_iters, steps_per_temp=8, seed=7,
-                               initial_part=tni.qubit_block_partition(nets[0], n, 8))
+                               position=nets[0].qubit)
     con_serial, con_dist, mem = tnsa.tn_plan_counts(plan)
     part, steps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
     tree = [(int(l), int(r)) for l, r, o in steps]
@@ -571,7 +571,7 @@ def run_cfg3(args):
     big, bh = tni.amplitude_tn(tni.cfg3()[0], tni.cfg3()[1]), None
     bh = tnsa.tn_build(big)
     bplan = tnsa.tn_plan_create(bh, k=8, iterations=args.plan_iters, steps_per_temp=8, seed=7,
-                                initial_part=tni.qubit_block_partition(big, 40, 8))
+                                position=big.qubit)
     _, _, bmem = tnsa.tn_plan_counts(bplan)
     line = {"metric": METRIC, "value": rows["bf16"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -707,13 +707,13 @@ def run_planner(args):
     rows = []
     for k in args.k_sweep:
         # qubit blocks need at least one qubit per part; beyond that the balanced BFS start is used
-        init = tni.qubit_block_partition(net, N_QUBITS, k) if k <= N_QUBITS else None
+        pos = net.qubit if k <= N_QUBITS else None
         row = {"k": k, "initial": "qubit_block" if init is not None else "bfs"}
         for name, kw in (("initial", dict(iterations=1)),
                          ("sa_naive", dict(mode="naive", iterations=args.plan_iters)),
                          ("sa_directed", dict(mode="directed", iterations=args.plan_iters))):
             t0 = time.perf_counter()
-            plan = tnsa.tn_plan_create(h, k=k, steps_per_temp=8, seed=7, initial_part=init, **kw)
+            plan = tnsa.tn_plan_create(h, k=k, steps_per_temp=8, seed=7, position=pos, **kw)
             sec = time.perf_counter() - t0
             total, crit, mem = tnsa.tn_plan_counts(plan)
             row[name] = {"con_dist_ratio": crit / s_crit, "con_serial_ratio": total / s_total,
@@ -746,9 +746,9 @@ def run_costmodel(args):
     settings = [(1, "directed", 1)] + [(k, mode, iters) for k in args.k_sweep if k > 1
                                        for mode in ("naive", "directed") for iters in (30, 300, 2000)]
     for k, mode, iters in settings:
-        init = tni.qubit_block_partition(nets[0], N_QUBITS, k) if 1 < k <= N_QUBITS else None
+        pos = nets[0].qubit if 1 < k <= N_QUBITS else None
         plan = tnsa.tn_plan_create(hs[0], k=k, mode=mode, iterations=iters, steps_per_temp=8, seed=7,
-                                   initial_part=init)
+                                   position=pos)
         total, crit, mem = tnsa.tn_plan_counts(plan)
         row = {"k": k, "mode": mode, "iterations": iters, "con_serial": total, "con_dist": crit, "mem": mem}
         if mem * 8 * B > 32e9:   # the batch's intermediates would exceed 32 GB: not timed

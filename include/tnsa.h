@@ -98,12 +98,28 @@ typedef struct {
     int32_t restart_threshold;  /* RestartThreshold of Algorithm 1 */
     int32_t fanin_samples;      /* RandomGreedy samples for the fan-in tree (k > 4) */
     uint64_t seed;
-    const int32_t *initial_part;/* nullable: [n_tensors] initial partition in [0, k); NULL = a
-                                   balanced breadth-first split.  Read during tn_plan only. */
+    int32_t initial;            /* tn_initial: how the initial partition (Section 4.2) is formed */
+    int32_t pad0;
+    const int32_t *initial_part;/* TN_INIT_GIVEN: [n_tensors] initial partition in [0, k).
+                                   Read during tn_plan_create only. */
+    const int32_t *position;    /* TN_INIT_QUBIT_BLOCK: [n_tensors] position hint of each tensor,
+                                   >= 0 (for a circuit: the qubit the tensor sits on, a 2-qubit
+                                   gate on its lower qubit).  Read during tn_plan_create only. */
 } tn_plan_opts;
 
+/* Initial partition of the annealing (Section 4.2 starts from a hypergraph partitioner's cut; this
+ * library forms one of its own):
+ *   TN_INIT_BFS          k balanced regions: breadth-first order from tensor 0 (restarting in
+ *                        unvisited components), cut into k contiguous chunks of near-equal size
+ *   TN_INIT_QUBIT_BLOCK  k contiguous blocks of positions: tensor t goes to partition
+ *                        floor(position[t] * k / P) with P = max(position) + 1 (for grid
+ *                        circuits numbered row-major these are blocks of rows)
+ *   TN_INIT_GIVEN        initial_part as given */
+typedef enum { TN_INIT_BFS = 0, TN_INIT_QUBIT_BLOCK = 1, TN_INIT_GIVEN = 2 } tn_initial;
+
 /* Fill opts with the defaults: k = 1, DIRECTED, T0 = 0.1, Tf = 0.001, N = 8, p = 1,
- * iterations = 200, RestartThreshold = 50, 32 fan-in samples, seed = 0, initial_part = NULL. */
+ * iterations = 200, RestartThreshold = 50, 32 fan-in samples, seed = 0, initial = TN_INIT_BFS,
+ * initial_part = position = NULL. */
 void tn_plan_opts_default(tn_plan_opts *opts);
 
 /* Plan a contraction (Section 4): initial partition, simulated-annealing refinement
@@ -111,7 +127,9 @@ void tn_plan_opts_default(tn_plan_opts *opts);
  * term, Section 4.4 and 5.2), a Greedy tree per partition and a fan-in tree over the partition
  * results (exhaustive for k <= 4, RandomGreedy above).  With k = 1 the plan is the Greedy tree.
  * Deterministic for a given seed when time_limit_s <= 0.
- * Errors: TN_EINVAL (bad k or options, invalid initial_part), TN_ENOMEM. */
+ * Errors: TN_EINVAL (bad k or options; TN_INIT_GIVEN without initial_part or with an entry outside
+ * [0, k); TN_INIT_QUBIT_BLOCK without position or with a negative entry; an initial partition
+ * with an empty part), TN_ENOMEM. */
 tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **out);
 
 /* Wrap a caller-chosen tree as a plan.  steps: [n_steps][2] (left, right) node ids, where leaves
@@ -217,14 +235,21 @@ tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
  *                    as its large operand, runs in one block of the persistent kernel with the
  *                    tensor kept in shared memory between the steps (complex64 storage); 0: every
  *                    step writes its output to the arena.  Results are bit-identical either way.
- * Defaults: {-1, 0, 1, 64, 32, 16, 1} (large programs off: on the 24-qubit brickwork benchmark they
- * measured slower than running fan-in chains as dataflow steps).  Errors: TN_EINVAL. */
+ *   wait_limit_us    how long (microseconds, >= 1) a work tile of the persistent kernel waits for
+ *                    the steps producing its operands before it gives up: the tile is skipped, its
+ *                    job's status becomes TN_ETIMEOUT, and a launch-wide abort flag makes every
+ *                    later wait of the launch give up at once, so the launch ends.  The context
+ *                    stays usable.
+ * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000} (large programs off: on the 24-qubit brickwork
+ * benchmark they measured slower than running fan-in chains as dataflow steps).
+ * Errors: TN_EINVAL. */
 typedef struct {
     int32_t local_budget;
     int32_t big_programs;
     int32_t warp_programs;
     int32_t tc_min_m, tc_min_n, tc_min_k;
     int32_t rows_chains;
+    int32_t wait_limit_us;
 } tn_exec_config;
 tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
 tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);
@@ -316,6 +341,17 @@ tn_status tn_batch_last_info(const tn_batch *b, tn_run_info *info);
 tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms);
 void tn_batch_free(tn_batch *b);
 
+/* Diagnostics, for testing the bounded waits: from the next run on, the persistent work list of
+ * the batch leaves out every tile of global step `step` of job `job` (the numbering of
+ * tn_plan_compile_steps), so the tiles consuming that step wait for a producer that never runs
+ * and give up after the context's wait_limit_us (see tn_exec_config): that job -- and any other
+ * job with a tile still waiting when the abort flag rises -- reports TN_ETIMEOUT, every other job
+ * completes normally.  Holds accumulate; step = -1 releases every hold of `job`, job = -1 every
+ * hold of the batch.  Waits for the batch's stream.
+ * Errors: TN_EINVAL (no such job, or the step is not in the persistent work list, or graph
+ * execution mode), TN_ECUDA. */
+tn_status tn_batch_debug_hold(tn_batch *b, int32_t job, int32_t step);
+
 /* Diagnostics: cycle accounting of the persistent kernel (costs a few atomics per work item; off
  * by default).  tn_batch_profile waits for the stream and returns 16 accumulated SM-cycle sums and
  * item counts since profiling was switched on: [0..4] work items of the dataflow kernel by class
@@ -345,7 +381,8 @@ tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_by
  * is the engine's final-reduction kernel offered to callers that cannot allocate device memory
  * while they run -- code whose device memory belongs to a host framework's pool, or serving loops
  * where cudaMalloc / cudaFree would synchronize the device or could fail mid-request.
- *   device       the CUDA device of the vectors; made current by the call
+ *   device       the CUDA device of the vectors; the caller's current device is restored before
+ *                the call returns
  *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream); returns without waiting
  *   d_a, d_b     n complex64 (prec = TN_C64) or complex128 (TN_C128) numbers, interleaved
  *   n            0 <= n <= 2^26; larger n is rejected with TN_EINVAL (the scratch holds one FP64
@@ -355,8 +392,10 @@ tn_status tn_permute(tn_ctx *ctx, const void *d_in, void *d_out, int32_t elem_by
  * until the process exits; all calls share it, so calls whose kernels overlap on the GPU (for
  * example on two streams) race and must be ordered by the caller.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or allocating library routine
- * is called.  Errors: TN_EINVAL, TN_ECUDA. */
+ * first call before any stream capture.  The looked-up address is kept for the life of the
+ * process: after a cudaDeviceReset of that device it is stale, so do not call tn_dot_noalloc on a
+ * device that was reset.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: TN_EINVAL, TN_ECUDA. */
 tn_status tn_dot_noalloc(int32_t device, void *cuda_stream, const void *d_a, const void *d_b,
                          int64_t n, tn_precision prec, double *d_out);
 

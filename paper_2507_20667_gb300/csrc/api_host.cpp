@@ -182,7 +182,10 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->restart_threshold = 50;
     o->fanin_samples = 32;
     o->seed = 0;
+    o->initial = TN_INIT_BFS;
+    o->pad0 = 0;
     o->initial_part = nullptr;
+    o->position = nullptr;
 }
 
 tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **out) {

@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(kThreads) k_dot_sum(const double2 *__restrict_
     }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
+// Device address of the scratch array, looked up once per device with that device current.  The
+// address belongs to the device's primary context as it was at the lookup: a cudaDeviceReset
+// destroys that context (the module is loaded again by the next call and the array may move), so
+// a caller that resets a device must not call tn_dot_noalloc on it afterwards.
 std::mutex g_mu;
 double2 *g_scratch_ptr[kMaxDevices] = {};
 
@@ -124,7 +127,15 @@ extern "C" tn_status tn_dot_noalloc(int32_t device, void *cuda_stream, const voi
     if (prec != TN_C64 && prec != TN_C128)
         return tn::fail(TN_EINVAL, "tn_dot_noalloc takes TN_C64 or TN_C128 vectors");
     if (device < 0 || device >= kMaxDevices) return tn::fail(TN_EINVAL, "device index out of range");
-    cudaError_t e = cudaSetDevice(device);
+    // the call works on `device` and leaves the caller's current device as it found it
+    int caller_device = -1;
+    cudaError_t e = cudaGetDevice(&caller_device);
+    if (e != cudaSuccess) return tn::fail(TN_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    struct Restore {
+        int dev, cur;
+        ~Restore() { if (dev != cur) cudaSetDevice(dev); }
+    } restore{caller_device, device};
+    e = cudaSetDevice(device);
     if (e != cudaSuccess) return tn::fail(TN_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     double2 *scratch = nullptr;
     tn_status s = scratch_for(device, &scratch);

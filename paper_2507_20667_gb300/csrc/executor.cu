@@ -35,7 +35,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1};   // programs and tensor-core thresholds
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000};   // programs, tensor-core thresholds, wait limit
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -62,6 +62,9 @@ struct tn_batch {
     JobPtrs *d_jobs = nullptr;
     WorkItem *d_work = nullptr;
     int64_t n_work = 0;
+    std::vector<WorkItem> h_work;     // the full work list (tn_batch_debug_hold uploads subsets)
+    std::vector<std::pair<int32_t, int32_t>> held;   // (job, step) left out by tn_batch_debug_hold
+    long long wait_ns = 4000000000LL; // a dependency wait of the persistent kernel gives up after this
     WorkItem *d_local = nullptr;      // (job, pseudo-step) of every subtree program
     int32_t n_warp_items = 0;         // warp programs (first in d_local), then block programs
     int32_t n_block_items = 0;
@@ -1024,7 +1027,7 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
         if (e == cudaSuccess) {
             t_enqueue_stage = "dataflow kernel";
             e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->use_tc,
-                                  b->d_prof, st);
+                                  b->wait_ns, b->d_prof, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
@@ -1192,6 +1195,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         }
     }
     b->n_work = (int64_t)work.size();
+    b->wait_ns = (long long)ctx->cfg.wait_limit_us * 1000;
     // warp programs first, longest first (a block of four warps lasts as long as its longest
     // program), then the block programs
     std::stable_sort(warp_items.begin(), warp_items.end(), [&](const WorkItem &x, const WorkItem &y) {
@@ -1305,6 +1309,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
+    b->h_work = std::move(work);
     for (const Compiled &c : b->comp)
         if (c.counts[STEP_TC] > 0) b->use_tc = 1;
     b->grid = persistent_grid(b->c128, b->use_tc);
@@ -1557,7 +1562,8 @@ tn_status tn_ctx_get_config(const tn_ctx *c, tn_exec_config *cfg) {
 
 tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
     if (!c || !cfg) return fail(TN_EINVAL, "NULL argument");
-    if (cfg->local_budget < -1 || cfg->tc_min_m < 1 || cfg->tc_min_n < 1 || cfg->tc_min_k < 1)
+    if (cfg->local_budget < -1 || cfg->tc_min_m < 1 || cfg->tc_min_n < 1 || cfg->tc_min_k < 1 ||
+        cfg->wait_limit_us < 1)
         return fail(TN_EINVAL, "invalid configuration");
     drop_cached(c);
     c->cfg = *cfg;
@@ -1674,6 +1680,38 @@ tn_status tn_batch_profile(tn_batch *b, int64_t *cycles, int64_t *items) {
     long long h[2 * kProfSlots];
     CK(cudaMemcpy(h, b->d_prof, sizeof(h), cudaMemcpyDeviceToHost));
     for (int i = 0; i < kProfSlots; ++i) { cycles[i] = h[i]; items[i] = h[kProfSlots + i]; }
+    return TN_OK;
+}
+
+tn_status tn_batch_debug_hold(tn_batch *b, int32_t job, int32_t step) {
+    if (!b) return fail(TN_EINVAL, "NULL batch");
+    if (b->mode != TN_EXEC_PERSISTENT) return fail(TN_EINVAL, "only the persistent mode has a work list");
+    if (job >= b->n_jobs) return fail(TN_EINVAL, "job index out of range");
+    std::vector<std::pair<int32_t, int32_t>> held;
+    if (job >= 0) {
+        for (const auto &h : b->held)
+            if (h.first != job) held.push_back(h);
+        if (step >= 0) {
+            bool found = false;
+            for (const WorkItem &w : b->h_work) found = found || ((int32_t)w.job == job && (int32_t)w.step == step);
+            if (!found) return fail(TN_EINVAL, "the step has no tile in the persistent work list");
+            for (const auto &h : b->held)
+                if (h.first == job) held.push_back(h);
+            held.push_back({job, step});
+        }
+    }
+    std::vector<WorkItem> kept;
+    kept.reserve(b->h_work.size());
+    for (const WorkItem &w : b->h_work) {
+        bool drop = false;
+        for (const auto &h : held) drop = drop || ((int32_t)w.job == h.first && (int32_t)w.step == h.second);
+        if (!drop) kept.push_back(w);
+    }
+    CK(cudaSetDevice(b->ctx->device));
+    CK(cudaStreamSynchronize(b->ctx->stream));
+    if (!kept.empty()) CK(cudaMemcpy(b->d_work, kept.data(), sizeof(WorkItem) * kept.size(), cudaMemcpyHostToDevice));
+    b->n_work = (int64_t)kept.size();
+    b->held.swap(held);
     return TN_OK;
 }
 
@@ -1841,6 +1879,7 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
     int32_t best = -1;
     tn_status first_err = TN_OK;
     std::string first_msg;
+    for (tn_exec_config &c : cands) c.wait_limit_us = saved.wait_limit_us;
     for (size_t i = 0; i < cands.size(); ++i) {
         ctx->cfg = cands[i];
         tn_batch *b = nullptr;

@@ -180,9 +180,10 @@ constexpr int kProfSlots = 16;
 
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
 // use_tc: the work list holds tensor-core tiles (each block then holds 128 TMEM columns).
+// wait_ns: a dependency wait gives up after about this many nanoseconds (TN_ETIMEOUT).
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
                               int64_t n_work, uint32_t *counter, int32_t grid, int32_t use_tc,
-                              long long *prof, cudaStream_t stream);
+                              long long wait_ns, long long *prof, cudaStream_t stream);
 // Co-resident grid of the persistent kernel, with tensor-core tiles (use_tc) or without.
 int32_t persistent_grid(bool c128, int32_t use_tc);
 // Subtree programs; items: (job, pseudo-step, 0), the n_warp warp programs first (four per

@@ -33,7 +33,6 @@ constexpr int32_t kStatusTimeout = 5;
 // Dynamic shared memory of the complex64 dataflow kernels: staged ROWS steps, and with tensor
 // cores also the operand tiles (used at different times).
 constexpr int32_t kPersistTcDyn = kTcSmem > kPersistDynSmem ? kTcSmem : kPersistDynSmem;
-constexpr long long kSpinLimitNs = 4000000000LL;   // a wait gives up after ~4 s
 
 __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
     uint32_t v;
@@ -45,11 +44,17 @@ __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
 // the wait gave up.  Both counters are read together (one round trip when they are done).  The
 // first wait that gives up raises the launch-wide abort flag, after which every wait returns at
 // once, so a broken dependency costs one time-out, not one per waiting tile.
-__device__ bool wait_deps(const JobPtrs &j, const WorkItem &it, int32_t *abort_flag) {
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+__device__ bool wait_deps(const JobPtrs &j, const WorkItem &it, int32_t *abort_flag, long long limit_ns) {
     const bool d0 = it.dep0 >= 0, d1 = it.dep1 >= 0;
     uint32_t c0 = d0 ? ld_acquire(j.done + it.dep0) : 0u, c1 = d1 ? ld_acquire(j.done + it.dep1) : 0u;
     if ((!d0 || c0 >= it.need0) && (!d1 || c1 >= it.need1)) return true;
-    long long t0 = clock64();
+    const long long t0 = global_ns();
     unsigned ns = 32;
     while (true) {
         if (d0 && c0 < it.need0) c0 = ld_acquire(j.done + it.dep0);
@@ -58,8 +63,8 @@ __device__ bool wait_deps(const JobPtrs &j, const WorkItem &it, int32_t *abort_f
         if (ld_acquire(abort_flag)) return false;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
-        // clock64 counts SM cycles; 2.07 GHz at most, so cycles / 2 is a lower bound in ns
-        if ((clock64() - t0) / 2 > kSpinLimitNs) {
+        // the global timer counts nanoseconds whatever the SM clock
+        if (global_ns() - t0 > limit_ns) {
             atomicExch(abort_flag, 1);
             return false;
         }
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_step_tc(const StepDesc *__restrict
 template <typename T, bool TC>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_persist(const JobPtrs *__restrict__ jobs, const WorkItem *__restrict__ work, int64_t n_work,
-              uint32_t *counter, long long *prof) {
+              uint32_t *counter, long long wait_ns, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
     extern __shared__ __align__(16) char dyn[];
     __shared__ uint64_t tc_bar;
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         if (threadIdx.x == 0) {
             if (prof) t0 = clock64();
             nxt = atomicAdd(counter, 1u);
-            const bool ok = wait_deps(j, it, abort_flag);
+            const bool ok = wait_deps(j, it, abort_flag, wait_ns);
             if (!ok) atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
             s_ok = ok;
             if (prof) {
@@ -452,22 +457,23 @@ int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
 }
 
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work, int64_t n_work,
-                              uint32_t *counter, int32_t grid, int32_t use_tc, long long *prof,
-                              cudaStream_t stream) {
+                              uint32_t *counter, int32_t grid, int32_t use_tc, long long wait_ns,
+                              long long *prof, cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
     if (c128)
-        k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, prof);
+        k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, wait_ns,
+                                                                          prof);
     else if (use_tc) {
         const cudaError_t e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
         if (e != cudaSuccess) return e;
         k_persist<float, true><<<(unsigned)grid, kThreads, kPersistTcDyn, stream>>>(jobs_dev, work, n_work, counter,
-                                                                                    prof);
+                                                                                    wait_ns, prof);
     } else {
         const cudaError_t e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
         if (e != cudaSuccess) return e;
         k_persist<float, false><<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work,
-                                                                                       counter, prof);
+                                                                                       counter, wait_ns, prof);
     }
     return cudaGetLastError();
 }

@@ -516,31 +516,107 @@ bool rebalance(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rn
     return true;
 }
 
+// Natural log of c_new / c_old on exact integer costs; a zero old cost makes any positive new
+// cost infinitely worse.
 double log_ratio(u128 cn, u128 cc) {
     if (cc == 0) return cn == 0 ? 0.0 : INFINITY;
     return std::log((double)cn) - std::log((double)cc);
 }
 
-struct StepResult {
-    State s;
-    int32_t accepted = 0;
+// Metropolis rule of Eq. 4.2 on log-costs: a cheaper state is always taken (the probability
+// exceeds one); a dearer one with probability exp(-log(c_new / c_old) / T).
+bool metropolis_accept(u128 c_new, u128 c_old, double T, Rng &rng) {
+    return std::exp(-log_ratio(c_new, c_old) / T) >= rng.uniform();
+}
+
+// Geometric cooling of Eq. 4.3-4.4: T(x) = T0 (Tf / T0)^x for search progress x in [0, 1].
+struct Cooling {
+    double T0, ratio;
+    Cooling(double t0, double tf) : T0(t0), ratio(tf / t0) {}
+    double at(double x) const { return T0 * std::pow(ratio, x); }
 };
 
-// DoSteps of Algorithm 1 with the acceptance rule of Eq. 4.2.
-void do_steps(const Ctx &c, int32_t nsteps, const State &start, double T, int32_t mode,
-              uint64_t seed, StepResult &res, bool &ovf) {
+// How far the search has come: wall-clock time against a limit, or rounds against a fixed count
+// (the deterministic mode).
+struct SearchBudget {
+    bool timed;
+    double limit_s;
+    int64_t rounds;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double seconds() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    // Progress x of round r, or a negative number when the budget is spent.
+    double progress(int64_t r) const {
+        if (timed) {
+            const double e = seconds();
+            return e >= limit_s ? -1.0 : e / limit_s;
+        }
+        return r >= rounds ? -1.0 : (double)r / (double)rounds;
+    }
+};
+
+// One Markov chain: `moves` rebalancing moves from `start` at fixed temperature T.
+struct Chain {
+    State s;
+    int32_t accepted = 0;
+    bool ovf = false;
+};
+void run_chain(const Ctx &c, const State &start, int32_t moves, double T, int32_t mode, uint64_t seed,
+               Chain &out) {
     Rng rng(seed);
-    res.s = start;
+    out.s = start;
     State cand;
-    for (int32_t j = 0; j < nsteps; ++j) {
-        if (!rebalance(c, res.s, cand, mode, rng, ovf)) break;
-        double p = std::exp(-log_ratio(cand.cost, res.s.cost) / T);
-        if (p >= rng.uniform()) {
-            res.s = std::move(cand);
-            res.accepted++;
+    for (int32_t m = 0; m < moves; ++m) {
+        if (!rebalance(c, out.s, cand, mode, rng, out.ovf)) break;
+        if (metropolis_accept(cand.cost, out.s.cost, T, rng)) {
+            out.s = std::move(cand);
+            out.accepted++;
         }
     }
 }
+
+// One round of the division scheme (Algorithm 1, Section 4.3): p chains start from the same
+// state, each runs ceil(N / p) moves with a seed drawn from (seed, round, chain), and the cheapest
+// end state is kept (lowest chain index on ties, so the result does not depend on scheduling).
+State anneal_round(const Ctx &c, const State &from, int32_t chains, int32_t moves, double T, int32_t mode,
+                   uint64_t seed, int64_t round, int32_t &accepted) {
+    std::vector<Chain> res(chains);
+    auto go = [&](int32_t q) {
+        run_chain(c, from, moves, T, mode, mix64(mix64(seed, (uint64_t)round), (uint64_t)q + 1), res[q]);
+    };
+    if (chains == 1) {
+        go(0);
+    } else {
+        std::vector<std::thread> ts;
+        for (int32_t q = 0; q < chains; ++q) ts.emplace_back(go, q);
+        for (auto &t : ts) t.join();
+    }
+    int32_t win = 0;
+    for (int32_t q = 0; q < chains; ++q) {
+        accepted += res[q].accepted;
+        if (res[q].s.cost < res[win].s.cost) win = q;
+    }
+    return std::move(res[win].s);
+}
+
+// Restart policy (Algorithm 1): remember the cheapest state seen; when `patience` rounds pass
+// without a strictly cheaper state, continue from the remembered one.
+struct BestTracker {
+    State best;
+    int64_t last_gain = -1;
+    int32_t restarts = 0;
+    void observe(State &cur, int64_t round, int32_t patience) {
+        if (cur.cost < best.cost) {
+            best = cur;
+            last_gain = round;
+        } else if (round - last_gain >= patience) {
+            cur = best;
+            last_gain = round;
+            ++restarts;
+        }
+    }
+};
 }  // namespace
 
 tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
@@ -559,13 +635,22 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
     State init;
     init.part.assign(n, 0);
     if (o.k > 1) {
-        if (o.initial_part) {
+        if (o.initial == TN_INIT_GIVEN) {
+            if (!o.initial_part) return fail(TN_EINVAL, "TN_INIT_GIVEN needs initial_part");
             for (int32_t t = 0; t < n; ++t) {
                 if (o.initial_part[t] < 0 || o.initial_part[t] >= o.k)
                     return fail(TN_EINVAL, "initial_part entry out of range");
                 init.part[t] = o.initial_part[t];
             }
-        } else {
+        } else if (o.initial == TN_INIT_QUBIT_BLOCK) {
+            if (!o.position) return fail(TN_EINVAL, "TN_INIT_QUBIT_BLOCK needs a position hint");
+            int64_t span = 0;
+            for (int32_t t = 0; t < n; ++t) {
+                if (o.position[t] < 0) return fail(TN_EINVAL, "negative position hint");
+                span = std::max(span, (int64_t)o.position[t] + 1);
+            }
+            for (int32_t t = 0; t < n; ++t) init.part[t] = (int32_t)((int64_t)o.position[t] * o.k / span);
+        } else if (o.initial == TN_INIT_BFS) {
             // balanced breadth-first split: BFS order from tensor 0 (restarting in unvisited
             // components), cut into k contiguous chunks of near-equal size
             std::vector<std::vector<int32_t>> nb(n);
@@ -583,6 +668,8 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
                 }
             }
             for (int32_t i = 0; i < n; ++i) init.part[order[i]] = (int32_t)((int64_t)i * o.k / n);
+        } else {
+            return fail(TN_EINVAL, "unknown initial partition mode");
         }
     }
     init.parts.resize(o.k);
@@ -594,56 +681,26 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
     for (int32_t k = 0; k < o.k; ++k) rebuild_part(c, init.parts[k], ovf);
     evaluate(c, init, ovf);
 
-    // Algorithm 1 (SimulatedAnnealing) with the division algorithm over p threads
-    State best = init, cur = init;
-    int64_t i = -1, i_best = -1;
-    int32_t accepted = 0, restarts = 0, iters = 0;
+    // Simulated annealing (Section 4.3, Algorithm 1): rounds of parallel chains at a falling
+    // temperature, with restarts from the best state.
+    BestTracker track;
+    track.best = init;
+    int32_t accepted = 0, iters = 0;
     if (o.k > 1) {
-        const double alpha = o.Tf / o.T0;
-        const int32_t p = o.threads;
-        const int32_t np = (o.steps_per_temp + p - 1) / p;
-        auto now = [&] {
-            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        };
-        const bool timed = o.time_limit_s > 0;
-        double t0 = now();
-        while (true) {
-            double elapsed = now() - t0;
-            if (timed ? elapsed >= o.time_limit_s : (i + 1) >= o.iterations) break;
-            ++i;
-            double t = timed ? elapsed / o.time_limit_s : (double)i / (double)o.iterations;
-            double T = o.T0 * std::pow(alpha, t);
-            std::vector<StepResult> res(p);
-            std::vector<char> ovfs(p, 0);
-            auto work = [&](int32_t th) {
-                bool lo = false;
-                uint64_t sd = mix64(mix64(o.seed, (uint64_t)i), (uint64_t)th + 1);
-                do_steps(c, np, cur, T, o.mode, sd, res[th], lo);
-                ovfs[th] = lo;
-            };
-            if (p == 1) work(0);
-            else {
-                std::vector<std::thread> ts;
-                for (int32_t th = 0; th < p; ++th) ts.emplace_back(work, th);
-                for (auto &t : ts) t.join();
-            }
-            int32_t w = 0;   // parmin, ties to the lowest thread index
-            for (int32_t th = 0; th < p; ++th) {
-                accepted += res[th].accepted;
-                if (res[th].s.cost < res[w].s.cost) w = th;
-            }
-            cur = std::move(res[w].s);
+        const Cooling cool(o.T0, o.Tf);
+        const SearchBudget budget{o.time_limit_s > 0, o.time_limit_s, (int64_t)o.iterations};
+        const int32_t moves = (o.steps_per_temp + o.threads - 1) / o.threads;
+        State cur = init;
+        for (int64_t round = 0;; ++round) {
+            const double x = budget.progress(round);
+            if (x < 0) break;
+            cur = anneal_round(c, cur, o.threads, moves, cool.at(x), o.mode, o.seed, round, accepted);
             ++iters;
-            if (cur.cost < best.cost) {
-                i_best = i;
-                best = cur;
-            } else if (i - i_best >= o.restart_threshold) {
-                i_best = i;
-                cur = best;
-                ++restarts;
-            }
+            track.observe(cur, round, o.restart_threshold);
         }
     }
+    const State &best = track.best;
+    const int32_t restarts = track.restarts;
     // assemble the plan from the best state
     out = Plan();
     out.n = n;

@@ -128,6 +128,7 @@ struct tn_server {
     int32_t elem = 8;
     int32_t max_batch = 64;
     CompileOpts copt;                 // compiler options (from the context's configuration)
+    long long wait_ns = 4000000000LL; // dependency-wait limit of the persistent kernel
     char *pool = nullptr;
     size_t pool_bytes = 0;
     Arena arena;
@@ -289,7 +290,7 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     if (e == cudaSuccess && !work.empty())
         e = launch_persistent(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_work),
                               (int64_t)work.size(), reinterpret_cast<uint32_t *>(meta + o_counter),
-                              tc ? S->grid_tc : S->grid, tc ? 1 : 0, nullptr, f.st);
+                              tc ? S->grid_tc : S->grid, tc ? 1 : 0, S->wait_ns, nullptr, f.st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f.h_res, meta + o_res, sizeof(DeviceResult) * (size_t)n, cudaMemcpyDeviceToHost, f.st);
     if (e == cudaSuccess) e = cudaEventRecord(f.ev, f.st);
@@ -426,6 +427,7 @@ tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_byte
         return s;
     }
     S->copt = compile_opts(cfg, prec, S->c128);
+    S->wait_ns = (long long)cfg.wait_limit_us * 1000;
     // full co-resident grids: a second launch's blocks start as the first one's retire
     S->grid = std::max(1, persistent_grid(S->c128, 0));
     S->grid_tc = std::max(1, persistent_grid(S->c128, 1));

@@ -273,13 +273,6 @@ def norm_tn(circ: Circuit) -> Network:
     return b.network()
 
 
-def qubit_block_partition(net: Network, n_qubits: int, k: int) -> np.ndarray:
-    """Initial partition: k contiguous blocks of qubits (row-major for grids); each tensor
-    goes to the block of the qubit it sits on."""
-    q = np.asarray(net.qubit, dtype=np.int64)
-    return ((q * k) // n_qubits).astype(np.int32)
-
-
 def random_network(n_tensors: int, n_extra_edges: int, dim_choices, seed: int,
                    n_open: int = 0) -> Network:
     """A connected random network: a random spanning tree plus extra (multi-)edges, each edge

@@ -20,6 +20,7 @@ TN_OK, TN_EINVAL, TN_ENOMEM, TN_EBUDGET, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED 
 PRECISIONS = {"c128": 0, "c64": 1, "tf32": 2, "bf16": 3}
 EXEC_MODES = {"persistent": 0, "graph": 1}
 MODES = {"naive": 0, "directed": 1}
+INITIAL = {"bfs": 0, "qubit_block": 1, "given": 2}
 
 
 class TnError(RuntimeError):
@@ -44,7 +45,8 @@ class tn_plan_opts(ctypes.Structure):
                 ("Tf", ctypes.c_double), ("steps_per_temp", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("time_limit_s", ctypes.c_double), ("iterations", ctypes.c_int32),
                 ("restart_threshold", ctypes.c_int32), ("fanin_samples", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("initial_part", ctypes.POINTER(ctypes.c_int32))]
+                ("seed", ctypes.c_uint64), ("initial", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("initial_part", ctypes.POINTER(ctypes.c_int32)), ("position", ctypes.POINTER(ctypes.c_int32))]
 
 
 class tn_plan_info(ctypes.Structure):
@@ -77,7 +79,7 @@ class tn_compile_stats(ctypes.Structure):
 class tn_exec_config(ctypes.Structure):
     _fields_ = [("local_budget", ctypes.c_int32), ("big_programs", ctypes.c_int32),
                 ("warp_programs", ctypes.c_int32), ("tc_min_m", ctypes.c_int32), ("tc_min_n", ctypes.c_int32),
-                ("tc_min_k", ctypes.c_int32), ("rows_chains", ctypes.c_int32)]
+                ("tc_min_k", ctypes.c_int32), ("rows_chains", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -131,6 +133,7 @@ _SIGS = {
     "tn_batch_kernel_ms": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "tn_batch_set_tensors": (_I32, [_P, _I32, _P, _P, _P]),
     "tn_batch_set_profiling": (_I32, [_P, _I32]),
+    "tn_batch_debug_hold": (_I32, [_P, _I32, _I32]),
     "tn_batch_profile": (_I32, [_P, _P, _P]),
     "tn_batch_free": (None, [_P]),
     "tn_batch_contract": (_I32, [_P, _I32, _P, _P, _I32, _P, _P]),
@@ -262,7 +265,10 @@ def tn_plan_opts_default() -> tn_plan_opts:
 
 def tn_plan_create(net: Net, k=1, mode="directed", T0=None, Tf=None, steps_per_temp=None, threads=None,
                    time_limit_s=None, iterations=None, restart_threshold=None, fanin_samples=None,
-                   seed=None, initial_part=None) -> Plan:
+                   seed=None, initial_part=None, initial=None, position=None) -> Plan:
+    """initial: "bfs", "qubit_block" (needs `position`, e.g. each tensor's qubit) or "given" (needs
+    `initial_part`); when omitted, "given" if initial_part is passed, else "qubit_block" if position
+    is passed, else "bfs"."""
     o = tn_plan_opts_default()
     o.k = int(k)
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -272,10 +278,15 @@ def tn_plan_create(net: Net, k=1, mode="directed", T0=None, Tf=None, steps_per_t
                       ("seed", seed)):
         if val is not None:
             setattr(o, name, val)
-    keep = None
-    if initial_part is not None:
-        keep = np.ascontiguousarray(initial_part, dtype=np.int32)
-        o.initial_part = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if initial is None:
+        initial = "given" if initial_part is not None else ("qubit_block" if position is not None else "bfs")
+    o.initial = INITIAL[initial] if isinstance(initial, str) else int(initial)
+    keep = []
+    for field, arr in (("initial_part", initial_part), ("position", position)):
+        if arr is not None:
+            a = np.ascontiguousarray(arr, dtype=np.int32)
+            keep.append(a)
+            setattr(o, field, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     out = ctypes.c_void_p()
     _check(lib.tn_plan_create(net, ctypes.byref(o), ctypes.byref(out)))
     return Plan(out.value)
@@ -362,7 +373,8 @@ def tn_ctx_get_config(ctx: Ctx) -> dict:
 
 def tn_ctx_set_config(ctx: Ctx, **fields) -> None:
     """Change fields of the context's execution configuration (local_budget, big_programs,
-    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains); the others keep their values."""
+    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains, wait_limit_us); the others keep their
+    values."""
     cfg = tn_exec_config()
     _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
     for k, v in fields.items():
@@ -422,6 +434,10 @@ def tn_batch_set_tensors(batch: Batch, jobs, tensors, data) -> None:
     t = np.ascontiguousarray(tensors, dtype=np.int32)
     d = np.ascontiguousarray(np.asarray(data, dtype=np.complex128).ravel()).view(np.float64)
     _check(lib.tn_batch_set_tensors(batch, len(j), _ptr(j), _ptr(t), _ptr(d)))
+
+
+def tn_batch_debug_hold(batch: Batch, job: int, step: int) -> None:
+    _check(lib.tn_batch_debug_hold(batch, int(job), int(step)))
 
 
 def tn_batch_set_profiling(batch: Batch, on: bool = True) -> None:

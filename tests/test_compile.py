@@ -21,7 +21,7 @@ def _cfg2_like(n_qubits=16, depth=10, k=4):
     net = tni.amplitude_tn(circ, tni.random_bitstring(n_qubits, 1002))
     h = tnsa.tn_build(net)
     plan = tnsa.tn_plan_create(h, k=k, iterations=200, seed=7,
-                               initial_part=tni.qubit_block_partition(net, n_qubits, k))
+                               position=net.qubit)
     return net, h, plan
 
 

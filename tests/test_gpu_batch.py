@@ -10,8 +10,12 @@
 import numpy as np
 import pytest
 
+from oracle import contract as oc
+from oracle import costs as ocost
+from oracle import greedy as og
 from oracle import statevector as sv
 from paper_2507_20667_gb300 import inputs as tni
+from parity import TOL, amplitude_bitstring, check
 
 pytestmark = pytest.mark.gpu
 
@@ -22,15 +26,9 @@ def tnsa():
     return mod
 
 
-def rel(a, b):
-    return abs(a - b) / abs(b)
-
-
-def amp_err(a, ref, n_qubits):
-    """Error of an amplitude relative to max(|ref|, 2^(-n/2)): the plain relative error for
-    amplitudes at or above the typical magnitude 2^(-n/2) of an n-qubit random circuit, and the
-    error in units of that magnitude for smaller (cancellation-dominated) amplitudes."""
-    return abs(a - ref) / max(abs(ref), 2.0 ** (-n_qubits / 2))
+def oracle_amp(net):
+    steps = og.greedy_steps(list(ocost.leaf_legs(net)), ocost.edge_dims(net))
+    return oc.contract_scalar(net, steps)
 
 
 def amps(tnsa, mant, e2):
@@ -43,7 +41,7 @@ def test_persistent_equals_graph_bitwise(tnsa, prec):
     net = tni.amplitude_tn(circ, x)
     h = tnsa.tn_build(net)
     plan = tnsa.tn_plan_create(h, k=4, iterations=300, seed=7,
-                               initial_part=tni.qubit_block_partition(net, 24, 4))
+                               position=net.qubit)
     out = {}
     for mode in ("persistent", "graph"):
         ctx = tnsa.tn_ctx_create(0)
@@ -55,20 +53,21 @@ def test_persistent_equals_graph_bitwise(tnsa, prec):
 
 def test_one_circuit_many_bitstrings(tnsa):
     circ = tni.brickwork_1d(14, 10, seed=3)
-    xs = [tni.random_bitstring(14, 900 + i) for i in range(64)]
+    psi = sv.simulate(circ).reshape((2,) * 14)
+    xs = [amplitude_bitstring(lambda y: psi[tuple(y)], 14, 900 + i, tni.random_bitstring)[0]
+          for i in range(64)]
     nets = [tni.amplitude_tn(circ, x) for x in xs]
     hs = [tnsa.tn_build(n) for n in nets]
     plan = tnsa.tn_plan_create(hs[0], k=4, iterations=100, seed=1,
-                               initial_part=tni.qubit_block_partition(nets[0], 14, 4))
+                               position=nets[0].qubit)
     ctx = tnsa.tn_ctx_create(0)
     b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), "c64")
     tnsa.tn_batch_run(b)
     mant, e2, st = tnsa.tn_batch_results(b, len(hs))
     assert (st == 0).all()
     got = amps(tnsa, mant, e2)
-    psi = sv.simulate(circ).reshape((2,) * 14)
     for i, x in enumerate(xs):
-        assert amp_err(got[i], psi[tuple(x)], 14) <= 1e-5
+        check(got[i], psi[tuple(x)], TOL["c64"], f"job {i}")
     # bulk update: flip every bit of the first 8 jobs and rerun
     n_t = nets[0].n_tensors
     jobs = np.repeat(np.arange(8, dtype=np.int32), 14)
@@ -82,7 +81,7 @@ def test_one_circuit_many_bitstrings(tnsa):
     mant, e2, st = tnsa.tn_batch_results(b, len(hs))
     got2 = amps(tnsa, mant, e2)
     for i in range(8):
-        assert amp_err(got2[i], psi[tuple(flipped[i])], 14) <= 1e-5
+        check(got2[i], psi[tuple(flipped[i])], TOL["c64"], f"flipped job {i}")
     assert np.array_equal(got2[8:], got[8:])
     with pytest.raises(tnsa.TnError):
         tnsa.tn_batch_set_tensors(b, [len(hs)], [0], np.zeros(2, np.complex128))
@@ -95,21 +94,25 @@ def test_mixed_batch_alone_equals_mix(tnsa):
     nets, hs, plans, refs, nq = [], [], [], [], []
     for i, (circ, k) in enumerate(specs):
         for r in range(3):
-            x = tni.random_bitstring(circ.n_qubits, 70 * i + r) if i < 4 else [r % 2] * 12
+            if i < 4:
+                x, _, _ = amplitude_bitstring(lambda y: sv.amplitude(circ, y), circ.n_qubits, 70 * i + r,
+                                              tni.random_bitstring)
+            else:
+                x = [r % 2] * 12
             net = tni.amplitude_tn(circ, x)
             h = tnsa.tn_build(net)
-            init = tni.qubit_block_partition(net, circ.n_qubits, k) if k > 1 else None
-            plans.append(tnsa.tn_plan_create(h, k=k, iterations=60, seed=i, initial_part=init))
+            pos = net.qubit if k > 1 else None
+            plans.append(tnsa.tn_plan_create(h, k=k, iterations=60, seed=i, position=pos))
             nets.append(net)
             hs.append(h)
             refs.append(sv.amplitude(circ, x))
             nq.append(circ.n_qubits)
     ctx = tnsa.tn_ctx_create(0)
-    for prec, tol in (("c64", 1e-5), ("c128", 1e-12)):
+    for prec in ("c64", "c128"):
         mant, e2 = tnsa.tn_batch_contract(ctx, hs, plans, prec)
         mix = amps(tnsa, mant, e2)
         for i, ref in enumerate(refs):
-            assert amp_err(mix[i], ref, nq[i]) <= tol, (i, mix[i], ref)
+            check(mix[i], ref, TOL[prec], f"{prec} job {i}")
         for i in (0, 4, 8, 13):
             m, e, _ = tnsa.tn_contract(ctx, hs[i], plans[i], prec)
             assert complex(m) * 2.0 ** e == mix[i]      # alone == in the mix, bit for bit
@@ -139,7 +142,8 @@ def test_subtree_programs_match_global_path(tnsa, prec):
     net = tni.amplitude_tn(circ, x)
     h = tnsa.tn_build(net)
     plan = tnsa.tn_plan_create(h, k=4, iterations=300, seed=7,
-                               initial_part=tni.qubit_block_partition(net, 24, 4))
+                               position=net.qubit)
+    ref = oracle_amp(net)
     res = {}
     for budget in (-1, 0, 16384):
         ctx = tnsa.tn_ctx_create(0)
@@ -148,7 +152,5 @@ def test_subtree_programs_match_global_path(tnsa, prec):
         res[budget] = (complex(m) * 2.0 ** e, info)
     assert res[-1][1]["n_local"] >= 1 and res[0][1]["n_local"] == 0
     assert res[16384][1]["n_local"] >= 1
-    tol = 1e-12 if prec == "c128" else 1e-5
-    base = res[0][0]
-    for budget in (-1, 16384):
-        assert abs(res[budget][0] - base) <= tol * abs(base) * 10
+    for budget in (-1, 0, 16384):
+        check(res[budget][0], ref, TOL[prec], f"budget {budget}")

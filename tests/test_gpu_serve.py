@@ -14,6 +14,7 @@ import pytest
 
 from oracle import statevector as sv
 from paper_2507_20667_gb300 import inputs as tni
+from parity import REDRAWS, TOL, check, check_observable
 
 pytestmark = pytest.mark.gpu
 
@@ -31,19 +32,19 @@ def build_models(tnsa):
     h = tnsa.tn_build(net)
     models.append(dict(kind="amp", circ=c1, net=net, h=h, ids=tni.bra_ids(net, 12),
                        plan=tnsa.tn_plan_create(h, k=2, iterations=50, seed=1,
-                                                initial_part=tni.qubit_block_partition(net, 12, 2))))
+                                                position=net.qubit)))
     c2 = tni.grid_2d(4, 4, 6, seed=52)
     net = tni.amplitude_tn(c2, [0] * 16)
     h = tnsa.tn_build(net)
     models.append(dict(kind="amp", circ=c2, net=net, h=h, ids=tni.bra_ids(net, 16),
                        plan=tnsa.tn_plan_create(h, k=4, iterations=50, seed=2,
-                                                initial_part=tni.qubit_block_partition(net, 16, 4))))
+                                                position=net.qubit)))
     c3 = tni.brickwork_1d(10, 6, seed=53)
     net, slots = tni.zz_slots_tn(c3)
     h = tnsa.tn_build(net)
     models.append(dict(kind="zz", circ=c3, net=net, h=h, ids=slots,
                        plan=tnsa.tn_plan_create(h, k=2, iterations=50, seed=3,
-                                                initial_part=tni.qubit_block_partition(net, 10, 2))))
+                                                position=net.qubit)))
     return models
 
 
@@ -104,10 +105,13 @@ def test_continuous_batching_mix_equals_alone(tnsa):
         n = m["circ"].n_qubits
         if what[0] == "amp":
             ref = psi[id(m["circ"])][what[1]]
-            assert abs(got - ref) <= 1e-5 * max(abs(ref), 2.0 ** (-n / 2))
+            if abs(ref) < 1e-3 * 2.0 ** (-n / 2):   # below the redraw threshold: not compared
+                REDRAWS.append(("serve", n, -1, abs(ref) / 2.0 ** (-n / 2)))
+                continue
+            check(got, ref, TOL["c64"], f"amplitude {what[1]}")
         else:
             ref = sv.zz_expectation(m["circ"], *what[1])
-            assert abs(got - ref) <= 1e-5
+            check_observable(got, ref, TOL["c64"], 1.0, f"<Z Z> {what[1]}")
         assert lat > 0
 
 

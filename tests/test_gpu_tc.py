@@ -9,6 +9,8 @@ network in complex128 (CUDA cores) and against numpy.einsum.
 import numpy as np
 import pytest
 
+from parity import TOL, check_scaled
+
 pytestmark = pytest.mark.gpu
 
 
@@ -94,3 +96,72 @@ def test_tc_in_a_batch(tnsa):
     for i, n in enumerate(nets):
         ref = n.exact()
         assert abs(complex(mant[i]) * 2.0 ** int(e2[i]) - ref) <= 1e-4 * abs(ref)
+
+
+class _Bilinear:
+    """u^T (A B) v with A [I, K], B [K, J] and vectors u [I], v [J]: with one-hot u and v the
+    network's value is one element C[i, j] of the product, which the engine computes as a dense
+    tensor-core step followed by two exact selections (sums with a single nonzero term)."""
+    def __init__(self, I, K, J, seed):
+        rng = np.random.default_rng(seed)
+        def rnd(*s):
+            return (rng.standard_normal(s) + 1j * rng.standard_normal(s)) / np.sqrt(2)
+        self.A, self.B = rnd(I, K), rnd(K, J)
+        self.I, self.J = I, J
+        u, v = np.zeros(I, complex), np.zeros(J, complex)
+        u[0] = v[0] = 1
+        self.tensors = [self.A, self.B, u, v]
+        self.degrees = np.array([2, 2, 1, 1], np.int32)
+        self.dims = np.array([I, K, K, J, I, J], np.int64)
+        self.data = np.concatenate([t.ravel() for t in self.tensors]).view(np.float64)
+        # A axis 1 - B axis 0 (K); A axis 0 - u (I); B axis 1 - v (J)
+        self.edges = np.array([[0, 1, 1, 0], [0, 0, 2, 0], [1, 1, 3, 0]], np.int32)
+
+
+def _edge_samples(extent, tile, rng, extra):
+    """Indices on both sides of every tile boundary, the last index, and random ones."""
+    s = {0, extent - 1}
+    for b in range(tile, extent, tile):
+        s.update((b - 1, b))
+    s.update(int(i) for i in rng.integers(0, extent, extra))
+    return sorted(s)
+
+
+@pytest.mark.parametrize("shape", [(200, 40, 100), (136, 48, 72), (1024, 512, 1024)])
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_gemm_elementwise(tnsa, shape, prec):
+    """Elements of the tensor-core product C = A B at sampled (i, j) covering every 128-row and
+    64-column tile edge and the ragged tails (M, N, K not multiples of 128, 64 and 32), each within
+    1e-4 (BF16 split) or 1e-5 (TF32 split) of max |C| against numpy complex128."""
+    I, K, J = shape
+    net = _Bilinear(I, K, J, seed=I + K + J)
+    C = net.A @ net.B
+    scale = np.abs(C).max()
+    rng = np.random.default_rng(I * J)
+    rows = _edge_samples(I, 128, rng, 3)
+    cols = _edge_samples(J, 64, rng, 3)
+    # every sampled row with a random column and every sampled column with a random row, plus the
+    # four corners of the product
+    pairs = sorted({(i, int(rng.integers(0, J))) for i in rows} | {(int(rng.integers(0, I)), j) for j in cols}
+                   | {(0, 0), (0, J - 1), (I - 1, 0), (I - 1, J - 1)})
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_import(h, [(0, 1), (2, 4), (3, 5)])
+    steps = tnsa.tn_plan_compile_steps(h, plan, prec, 0)
+    assert steps[0, 0] == 4, "the product must run as a tensor-core step"
+    ctx = tnsa.tn_ctx_create(0)
+    tnsa.tn_ctx_set_local_budget(ctx, 0)
+    b = tnsa.tn_batch_create(ctx, [h] * len(pairs), [plan] * len(pairs), prec)
+    jobs, tens, data = [], [], []
+    for q, (i, j) in enumerate(pairs):
+        u, v = np.zeros(I, complex), np.zeros(J, complex)
+        u[i] = v[j] = 1
+        jobs += [q, q]
+        tens += [2, 3]
+        data += [u, v]
+    tnsa.tn_batch_set_tensors(b, jobs, tens, np.concatenate(data))
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, len(pairs))
+    assert (st == 0).all()
+    got = mant * np.ldexp(1.0, e2)
+    want = np.array([C[i, j] for i, j in pairs])
+    check_scaled(got, want, scale, TOL[prec], f"{len(pairs)} elements of C")

@@ -11,6 +11,7 @@ import pytest
 
 from oracle import statevector as sv
 from paper_2507_20667_gb300 import inputs as tni
+from parity import TOL, amplitude_bitstring, check_all
 
 pytestmark = pytest.mark.gpu
 
@@ -26,18 +27,19 @@ def tnsa():
 @pytest.fixture(scope="module")
 def batch_inputs(tnsa):
     circ = tni.brickwork_1d(N_Q, 10, seed=11)
-    xs = [tni.random_bitstring(N_Q, 300 + i) for i in range(24)]
+    psi = sv.simulate(circ).reshape((2,) * N_Q)
+    xs = [amplitude_bitstring(lambda y: psi[tuple(y)], N_Q, 300 + i, tni.random_bitstring)[0]
+          for i in range(24)]
     nets = [tni.amplitude_tn(circ, x) for x in xs]
     hs = [tnsa.tn_build(n) for n in nets]
     plan = tnsa.tn_plan_create(hs[0], k=4, iterations=100, seed=3,
-                               initial_part=tni.qubit_block_partition(nets[0], N_Q, 4))
-    psi = sv.simulate(circ).reshape((2,) * N_Q)
+                               position=nets[0].qubit)
     ref = np.array([psi[tuple(x)] for x in xs])
     return hs, plan, ref
 
 
-def _err(got, ref):
-    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 2.0 ** (-N_Q / 2)))
+def _check(got, ref):
+    check_all(got, ref, TOL["c64"])
 
 
 def _run(tnsa, ctx, hs, plan):
@@ -57,7 +59,7 @@ def test_configurations_agree_with_state_vector(tnsa, batch_inputs, cfg):
     ctx = tnsa.tn_ctx_create(0)
     tnsa.tn_ctx_set_config(ctx, **cfg)
     got, info = _run(tnsa, ctx, hs, plan)
-    assert _err(got, ref) <= 1e-5
+    _check(got, ref)
     if cfg.get("warp_programs") == 0 or cfg.get("local_budget") == 0:
         assert info["n_warp_progs"] == 0
     if cfg.get("local_budget") == 0:
@@ -72,7 +74,7 @@ def test_autotune_keeps_the_fastest(tnsa, batch_inputs):
     assert len(ok) >= 2 and ms == pytest.approx(min(ok))
     assert tnsa.tn_ctx_get_config(ctx) == best
     got, _ = _run(tnsa, ctx, hs, plan)
-    assert _err(got, ref) <= 1e-5
+    _check(got, ref)
 
 
 def _run_bits(tnsa, ctx, hs, plan):
@@ -100,4 +102,4 @@ def test_rows_chains_are_bit_identical(tnsa, batch_inputs, budget):
     (m1, e1), (m0, e0) = out
     assert np.array_equal(e1, e0)
     assert np.array_equal(m1.view(np.uint64), m0.view(np.uint64))
-    assert _err(m1 * np.ldexp(1.0, e1), ref) <= 1e-5
+    _check(m1 * np.ldexp(1.0, e1), ref)

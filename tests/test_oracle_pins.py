@@ -20,6 +20,11 @@ from oracle import greedy as og
 from oracle import statevector as sv
 from paper_2507_20667_gb300 import inputs as tni
 
+
+def block_partition(net, n_qubits, k):
+    """k contiguous blocks of qubits; each tensor goes to the block of the qubit it sits on."""
+    return ((np.asarray(net.qubit, dtype=np.int64) * k) // n_qubits).astype(np.int32)
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -237,7 +242,7 @@ def test_costs_ring_closed_form(m):
 def test_costs_identities(seed):
     circ = tni.brickwork_1d(6, 4, seed=seed)
     net = tni.amplitude_tn(circ, tni.random_bitstring(6, seed))
-    part = tni.qubit_block_partition(net, 6, 3)
+    part = block_partition(net, 6, 3)
     # tree: greedy inside each partition, then a left-deep fan-in
     legs = ocost.leaf_legs(net)
     dims = ocost.edge_dims(net)

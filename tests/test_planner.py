@@ -18,6 +18,11 @@ from paper_2507_20667_gb300 import inputs as tni
 from paper_2507_20667_gb300 import tnsa
 
 
+def block_partition(net, n_qubits, k):
+    """k contiguous blocks of qubits; each tensor goes to the block of the qubit it sits on."""
+    return ((np.asarray(net.qubit, dtype=np.int64) * k) // n_qubits).astype(np.int32)
+
+
 def oracle_partition_steps(net, part, k):
     legs = ocost.leaf_legs(net)
     dims = ocost.edge_dims(net)
@@ -74,7 +79,7 @@ def test_sa_postconditions(k, mode, threads):
     circ = tni.brickwork_1d(12, 8, seed=12)
     net = tni.amplitude_tn(circ, tni.random_bitstring(12, 3))
     h = tnsa.tn_build(net)
-    init = tni.qubit_block_partition(net, 12, k)
+    init = block_partition(net, 12, k)
     plan = tnsa.tn_plan_create(h, k=k, mode=mode, iterations=40, steps_per_temp=8, threads=threads,
                                seed=7, initial_part=init)
     part, steps, c, info = check_plan_against_oracle(net, plan, k)
@@ -90,7 +95,7 @@ def test_sa_deterministic_and_seed_sensitive():
     circ = tni.brickwork_1d(10, 8, seed=21)
     net = tni.amplitude_tn(circ, tni.random_bitstring(10, 4))
     h = tnsa.tn_build(net)
-    init = tni.qubit_block_partition(net, 10, 4)
+    init = block_partition(net, 10, 4)
     runs = []
     for seed in (1, 1, 2):
         plan = tnsa.tn_plan_create(h, k=4, iterations=30, steps_per_temp=4, threads=2, seed=seed,
@@ -111,7 +116,7 @@ def test_fanin_exhaustive_k3_is_optimal():
     given partition trees: compare against all three fan-in trees of k = 3 in the oracle."""
     net = tni.amplitude_tn(tni.brickwork_1d(6, 4, seed=5), tni.random_bitstring(6, 6))
     h = tnsa.tn_build(net)
-    init = tni.qubit_block_partition(net, 6, 3)
+    init = block_partition(net, 6, 3)
     plan = tnsa.tn_plan_create(h, k=3, iterations=0, initial_part=init)
     part, steps, c, info = check_plan_against_oracle(net, plan, 3)
     n = net.n_tensors
@@ -209,3 +214,41 @@ def test_build_rejects_malformed():
         tnsa.tn_plan_create(h, k=0)
     with pytest.raises(tnsa.TnError):
         tnsa.tn_plan_create(h, k=ok.n_tensors + 1)
+
+
+def _circuits_cfg1_to_cfg4():
+    yield tni.cfg1()[0], 1
+    yield tni.cfg2()[0], 4
+    yield tni.cfg3(small=True)[0], 8
+    yield tni.cfg3()[0], 8
+    for circ, k, xs in tni.cfg4_circuits():
+        yield circ, k
+
+
+def test_qubit_block_initial_partition_in_library():
+    """TN_INIT_QUBIT_BLOCK (the library's initial partition, Section 4.2's starting cut) equals the
+    k contiguous qubit blocks on every workload circuit; with no annealing rounds it is the plan's
+    partition."""
+    for circ, k in _circuits_cfg1_to_cfg4():
+        for kk in sorted({k, 2, 3}):
+            net = tni.amplitude_tn(circ, np.zeros(circ.n_qubits, np.int32))
+            h = tnsa.tn_build(net)
+            plan = tnsa.tn_plan_create(h, k=kk, iterations=0, initial="qubit_block", position=net.qubit)
+            part, _, _ = tnsa.tn_plan_export(plan, net.n_tensors)
+            assert np.array_equal(part, block_partition(net, circ.n_qubits, kk)), (circ.n_qubits, kk)
+
+
+def test_initial_partition_errors():
+    net = tni.amplitude_tn(tni.brickwork_1d(6, 3, seed=1), np.zeros(6, np.int32))
+    h = tnsa.tn_build(net)
+    for kw in ({"initial": "given"}, {"initial": "qubit_block"},
+               {"initial": "qubit_block", "position": -np.ones(net.n_tensors, np.int32)},
+               {"initial": "given", "initial_part": np.full(net.n_tensors, 5, np.int32)},
+               {"initial": 7}):
+        with pytest.raises(tnsa.TnError) as ei:
+            tnsa.tn_plan_create(h, k=3, iterations=0, **kw)
+        assert ei.value.status == tnsa.TN_EINVAL
+    # a block with no tensor in it: positions 0 and 5 only, k = 3
+    pos = np.where(np.arange(net.n_tensors) % 2 == 0, 0, 5).astype(np.int32)
+    with pytest.raises(tnsa.TnError):
+        tnsa.tn_plan_create(h, k=3, iterations=0, position=pos)

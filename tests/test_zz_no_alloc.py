@@ -1,11 +1,13 @@
-"""The allocation-free inner product (tn_dot_noalloc) against the existing entry point.
+"""The allocation-free inner product (tn_dot_noalloc) against numpy and the existing entry point.
 
 tn_dot_noalloc serves callers that must not allocate device memory while they run (their device
 memory belongs to a host framework's pool, or a serving loop cannot afford cudaMalloc's implicit
 synchronization or its failure mid-request).  Its scratch is a fixed device array shared by all
 calls, so this test calls it twice in a row on the same array and compares both results with
-tn_contract on the same two vectors written as a two-tensor network (one shared leg).  This file
-is collected last, so a run that stops at the first failure has run every other test before it.
+numpy (complex128 products of the vectors as stored on the device, so independent of every GPU
+path) and with tn_contract on the same two vectors written as a two-tensor network (one shared
+leg).  This file is collected last, so a run that stops at the first failure has run every other
+test before it.
 """
 import numpy as np
 import pytest
@@ -39,12 +41,16 @@ def test_dot_noalloc_matches_contract(prec):
     dt = torch.complex64 if prec == "c64" else torch.complex128
     d_a = torch.from_numpy(a).to(dt).cuda()
     d_b = torch.from_numpy(b).to(dt).cuda()
+    # numpy: the vectors as the device holds them, multiplied and summed in complex128
+    exact = complex(np.dot(d_a.cpu().numpy().astype(np.complex128), d_b.cpu().numpy().astype(np.complex128)))
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
         tnsa.tn_dot_noalloc(0, stream, d_a.data_ptr(), d_b.data_ptr(), n, prec, out.data_ptr())
         torch.cuda.synchronize()
+        assert torch.cuda.current_device() == 0        # the caller's current device is kept
         got = complex(out[0].item(), out[1].item())
+        assert abs(got - exact) <= TOL[prec] * abs(exact), (call, got, exact)
         assert abs(got - ref) <= TOL[prec] * abs(ref), (call, got, ref)
 
 
@@ -56,3 +62,12 @@ def test_dot_noalloc_rejects_oversize():
     with pytest.raises(tnsa.TnError) as ei:
         tnsa.tn_dot_noalloc(0, 0, buf.data_ptr(), buf.data_ptr(), 2 ** 26 + 1, "c64", out.data_ptr())
     assert ei.value.status == tnsa.TN_EINVAL
+
+
+def test_dot_noalloc_empty_vector():
+    import torch
+    from paper_2507_20667_gb300 import tnsa
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    tnsa.tn_dot_noalloc(0, 0, 0, 0, 0, "c64", out.data_ptr())
+    torch.cuda.synchronize()
+    assert out.tolist() == [0.0, 0.0]
