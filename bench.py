@@ -673,12 +673,16 @@ def run_tcgemm(args):
         for _ in range(reps):
             tnsa.tn_batch_run(b)
         ms = tnsa.tn_batch_kernel_ms(b, reps)
+        times = tnsa.tn_batch_kernel_times(b, reps)
         info = tnsa.tn_batch_last_info(b)
-        r = {"ms": ms, "algorithmic_tflops": 8 * mnk / ms / 1e9, "tensor_core_steps": info["n_tc"]}
+        r = {"ms": ms, "algorithmic_tflops": 8 * mnk / ms / 1e9, "tensor_core_steps": info["n_tc"],
+             "kernel_ms": times}
         if prec != "c64":
-            executed = 24 * mnk / ms / 1e9
             peak = bf16_peak if prec == "bf16" else bf16_peak / 2   # TF32 dense rate is half of BF16
-            r.update({"executed_tflops": executed, "tensor_frac": executed / peak})
+            executed = 24 * mnk / ms / 1e9
+            gemm = 24 * mnk / times["tc_gemm"] / 1e9 if times["tc_gemm"] > 0 else None
+            r.update({"executed_tflops": executed, "tensor_frac": executed / peak,
+                      "gemm_kernel_executed_tflops": gemm, "gemm_kernel_frac": gemm / peak if gemm else None})
         res[prec] = r
         b.close()
         ctx.close()

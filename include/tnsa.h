@@ -335,10 +335,17 @@ tn_status tn_batch_results(tn_batch *b, double *amps, int32_t *exp2, int32_t *st
 tn_status tn_batch_footprint(const tn_batch *b, size_t *bytes);
 tn_status tn_batch_last_info(const tn_batch *b, tn_run_info *info);
 
-/* Mean device duration (CUDA events recorded around the launch on the context's stream) of the
- * persistent contraction kernel over the last n_runs runs, 1 <= n_runs <= 256; waits for them.
+/* Mean device duration (CUDA events recorded on the context's stream before the first and after
+ * the last contraction kernel of a run) over the last n_runs runs, 1 <= n_runs <= 256; waits for
+ * them.
  * Errors: TN_EINVAL, TN_EUNSUPPORTED (graph mode), TN_ECUDA. */
 tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms);
+
+/* The same device time split by kernel class (CUDA events recorded between the launches of each
+ * run): mean_ms[0] warp programs, [1] block and large programs, [2] tensor-core operand packing,
+ * [3] tensor-core GEMM, [4] persistent dataflow launches (summed over the dependency phases).
+ * Errors: as tn_batch_kernel_ms. */
+tn_status tn_batch_kernel_times(const tn_batch *b, int32_t n_runs, double *mean_ms);
 void tn_batch_free(tn_batch *b);
 
 /* Diagnostics, for testing the bounded waits: from the next run on, the persistent work list of

@@ -60,6 +60,10 @@ struct CompileOpts {
 // arena plan of one contraction.
 tn_status compile(Compiled &c, const Net &net, const Plan &plan, const CompileOpts &o);
 
+// Reference counting of contexts by the objects made from them (tn_ctx_free defers the delete).
+void ctx_retain(tn_ctx *c);
+void ctx_release(tn_ctx *c);
+
 // Tensor-core mode of a precision (0: CUDA cores only).
 int32_t tc_mode_of(int32_t prec);
 
@@ -69,7 +73,25 @@ CompileOpts compile_opts(const tn_exec_config &cfg, int32_t prec, bool c128);
 // The dataflow work item of tile `tile` of step `step` (with the step's dependencies).
 WorkItem dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_t tile);
 
-// Sorted work items (level, step, tile) of one compiled structure, subtree programs excluded.
-void work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level);
+// Dependency phases.  A dense tensor-core step runs in its own pack and GEMM launches, so the
+// persistent dataflow launches are cut at them: phase(TC step) = 1 + the largest phase of its
+// producers, phase(other step) = the largest phase of its producers (programs: 0).  A run is, for
+// p = 0, 1, ...: the pack and GEMM launches of the TC steps of phase p (none for p = 0), then the
+// persistent launch of the other steps of phase p.  Returns the number of phases.
+int32_t step_phases(const Compiled &c, std::vector<int32_t> &phase);
+
+// Per phase of one compiled structure (job index 0): the dataflow work items sorted by (level,
+// step, tile) with their levels, the pack units and the GEMM tiles of its tensor-core steps.
+struct PhaseTemplate {
+    std::vector<WorkItem> work;
+    std::vector<int32_t> level;
+    std::vector<WorkItem> pack, gemm;
+};
+void phase_templates(const Compiled &c, std::vector<PhaseTemplate> &out);
+
+// The pack units and GEMM tiles of one tensor-core step of one job, as ranges of a run's lists.
+struct TcRange {
+    int32_t job, step, pack0, n_pack, gemm0, n_gemm;
+};
 
 }  // namespace tn

@@ -6,11 +6,13 @@
 // plan share one compiled list and differ only in their leaves.
 //
 // A batch is a set of jobs (independent contractions).  It is executed either by the subtree-
-// program kernel plus the persistent dataflow kernel (two launches for all jobs; the default) or,
-// as a reference mode, by one launch per step and job recorded into a CUDA graph.  A program is a
-// batch of one job.
+// program kernels plus the persistent dataflow kernel -- one launch of each for all jobs, and for
+// every dependency phase of dense tensor-core steps a pack launch, a grouped GEMM launch and one
+// more dataflow launch (the default) -- or, as a reference mode, by one launch per step and job
+// recorded into a CUDA graph.  A program is a batch of one job.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <new>
@@ -39,7 +41,24 @@ struct tn_ctx {
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
+    // Batches, programs and servers made from the context hold a reference; tn_ctx_free only marks
+    // the context, which is deleted when its last dependent is freed (garbage collectors may free
+    // a context before the batches that use it).
+    std::atomic<int32_t> refs{0};
+    bool freed = false;
 };
+
+namespace tn {
+void ctx_retain(tn_ctx *c) { c->refs.fetch_add(1); }
+void ctx_destroy_now(tn_ctx *c) {
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+void ctx_release(tn_ctx *c) {
+    if (c && c->refs.fetch_sub(1) == 1 && c->freed) ctx_destroy_now(c);
+}
+}  // namespace tn
 
 struct tn_batch {
     tn_ctx *ctx = nullptr;
@@ -62,6 +81,16 @@ struct tn_batch {
     JobPtrs *d_jobs = nullptr;
     WorkItem *d_work = nullptr;
     int64_t n_work = 0;
+    // dependency phases (step_phases): per phase the range of its dataflow items in d_work and of
+    // its tensor-core pack units and GEMM tiles in d_pack / d_gemm (persistent mode)
+    struct Phase {
+        int64_t work0 = 0, n_work = 0;
+        int32_t pack0 = 0, n_pack = 0, gemm0 = 0, n_gemm = 0;
+    };
+    std::vector<Phase> phases;
+    WorkItem *d_pack = nullptr, *d_gemm = nullptr;
+    std::vector<TcRange> tc_ranges;   // every tensor-core step's units and tiles (both modes)
+    std::vector<int32_t> h_work_phase;
     std::vector<WorkItem> h_work;     // the full work list (tn_batch_debug_hold uploads subsets)
     std::vector<std::pair<int32_t, int32_t>> held;   // (job, step) left out by tn_batch_debug_hold
     long long wait_ns = 4000000000LL; // a dependency wait of the persistent kernel gives up after this
@@ -77,16 +106,17 @@ struct tn_batch {
     size_t footprint = 0, arena_total = 0;
     int32_t grid = 0;
     int32_t dyn_smem = 0;             // dynamic shared memory of the subtree-program kernel
-    int32_t use_tc = 0;               // the dataflow kernel runs tensor-core tiles
     long long *d_prof = nullptr;      // optional per-kind cycle counters (tn_batch_set_profiling)
     // host
     double *h_pinned = nullptr;
     DeviceResult *h_res = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // ring of event pairs around the dominant kernel (persistent mode), one pair per run
+    // ring of per-run event lists (persistent mode): one event at the start of the contraction
+    // kernels and one after every launch slot -- warp programs, block and large programs, then per
+    // phase the pack, GEMM and dataflow launches (a slot whose launch is empty records no time)
     static constexpr int kRing = 256;
-    cudaEvent_t kev[kRing][2] = {};
+    std::vector<cudaEvent_t> kev[kRing];
     int64_t runs = 0;
     // pending tensor updates (tn_batch_set_tensors): headers {dst element offset, count, src
     // element offset} and complex128 values, staged in pinned memory, applied on the device
@@ -769,11 +799,15 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             c.steps.push_back(d);
             c.counts[STEP_ROWS]++;
         } else if (use_tc && M >= opt.tc_min_m && N >= opt.tc_min_n && K >= opt.tc_min_k) {
-            // dense step on the tensor cores: 128 x 64 complex output tiles, BF16 or TF32 split
+            // dense step on the tensor cores: operands packed into split images, then 128 x 128
+            // complex output tiles, BF16 or TF32 split
             d.kind = STEP_TC;
             if (tc_mode == 2) d.flags |= FLAG_TF32;
-            const int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
-            if (tiles > 0x7fffffffLL) return fail(TN_EUNSUPPORTED, "step too large");
+            if (d.m.n > 0 && d.m.sa[0] == 1 && !(d.k.n > 0 && d.k.sa[0] == 1)) d.flags |= FLAG_A_MCONT;
+            if (d.n.n > 0 && d.n.sa[0] == 1) d.flags |= FLAG_B_NCONT;
+            const int64_t tiles = ((M + kTcRows - 1) / kTcRows) * ((N + kTcCols - 1) / kTcCols);
+            if (tiles > 0x7fffffffLL || tc_pack_units(M, N, K, tc_mode == 2) > 0x7fffffffLL)
+                return fail(TN_EUNSUPPORTED, "step too large");
             d.ntiles = (int32_t)tiles;
             c.steps.push_back(d);
             c.counts[STEP_TC]++;
@@ -815,6 +849,19 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             t.a_lgn = lg;
             chain_len[ti] = chain_len[t.dep0] + 1;
         }
+    }
+    // packed operand images of the tensor-core steps: after the intermediates, never reused
+    {
+        size_t img = align_up(c.arena_bytes, 1024);
+        for (StepDesc &d : c.steps) {
+            if (d.kind != STEP_TC) continue;
+            size_t a_bytes = 0;
+            const size_t all = tc_image_bytes(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0, &a_bytes);
+            d.img_a = (int64_t)img;
+            d.img_b = (int64_t)(img + a_bytes);
+            img = align_up(img + all, 1024);
+        }
+        c.arena_bytes = img;
     }
     // pass 4: the programs' compact step lists
     c.progs.clear();
@@ -970,19 +1017,44 @@ WorkItem tn::dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_
     return w;
 }
 
-void tn::work_template(const Compiled &c, std::vector<WorkItem> &items, std::vector<int32_t> &item_level) {
-    std::vector<std::array<int32_t, 2>> order;   // level, step
+int32_t tn::step_phases(const Compiled &c, std::vector<int32_t> &phase) {
+    phase.assign(c.steps.size(), 0);
+    int32_t top = 0;
+    for (size_t s = 0; s < c.steps.size(); ++s) {   // producers precede their consumers
+        const StepDesc &d = c.steps[s];
+        int32_t p = 0;
+        if (d.dep0 >= 0) p = std::max(p, phase[d.dep0]);
+        if (d.dep1 >= 0) p = std::max(p, phase[d.dep1]);
+        if (d.kind == STEP_TC) ++p;
+        phase[s] = p;
+        top = std::max(top, p);
+    }
+    return top + 1;
+}
+
+void tn::phase_templates(const Compiled &c, std::vector<PhaseTemplate> &out) {
+    std::vector<int32_t> phase;
+    const int32_t np = step_phases(c, phase);
+    out.assign(np, PhaseTemplate());
+    std::vector<std::array<int32_t, 3>> order;   // phase, level, step
     for (size_t s = 0; s < c.steps.size(); ++s)
         if (c.steps[s].kind != STEP_LOCAL && !(c.steps[s].flags & FLAG_CHAIN_CONT))
-            order.push_back({c.steps[s].level, (int32_t)s});
+            order.push_back({phase[s], c.steps[s].level, (int32_t)s});
     std::sort(order.begin(), order.end());
-    items.clear();
-    item_level.clear();
-    for (auto &o : order)
-        for (int32_t t = 0; t < c.steps[o[1]].ntiles; ++t) {
-            items.push_back(dataflow_item(c, 0u, o[1], t));
-            item_level.push_back(o[0]);
+    for (auto &o : order) {
+        const StepDesc &d = c.steps[o[2]];
+        PhaseTemplate &pt = out[o[0]];
+        if (d.kind == STEP_TC) {
+            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0);
+            for (int64_t u = 0; u < units; ++u) pt.pack.push_back({0u, (uint32_t)o[2], (uint32_t)u});
+            for (int32_t t = 0; t < d.ntiles; ++t) pt.gemm.push_back({0u, (uint32_t)o[2], (uint32_t)t});
+            continue;
         }
+        for (int32_t t = 0; t < d.ntiles; ++t) {
+            pt.work.push_back(dataflow_item(c, 0u, o[2], t));
+            pt.level.push_back(o[1]);
+        }
+    }
 }
 
 namespace {
@@ -1000,10 +1072,23 @@ tn_status upload_leaves(tn_batch *b, int32_t job) {
     return TN_OK;
 }
 
+// Ranges of the phases' dataflow items in a work list built phase by phase (item i in phase ph[i]).
+void set_phase_ranges(tn_batch *b, const std::vector<int32_t> &ph) {
+    for (tn_batch::Phase &p : b->phases) p.work0 = p.n_work = 0;
+    for (size_t i = 0; i < ph.size(); ++i) {
+        tn_batch::Phase &p = b->phases[ph[i]];
+        if (p.n_work == 0) p.work0 = (int64_t)i;
+        p.n_work++;
+    }
+}
+
 // The stage of the last enqueue_run that failed (for the error message).
 thread_local const char *t_enqueue_stage = "";
 
 cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
+    // a non-sticky error left by an earlier runtime call of this thread (another library's, say)
+    // would otherwise be reported by the launch checks below
+    (void)cudaGetLastError();
     t_enqueue_stage = "reset";
     cudaError_t e = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
     if (e == cudaSuccess) {
@@ -1012,30 +1097,67 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
     }
     if (e != cudaSuccess) return e;
     if (b->mode == TN_EXEC_PERSISTENT) {
-        cudaEvent_t *ev = b->kev[b->runs % tn_batch::kRing];
-        if (!ev[0]) {
-            e = cudaEventCreate(&ev[0]);
-            if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+        std::vector<cudaEvent_t> &ev = b->kev[b->runs % tn_batch::kRing];
+        const size_t n_ev = 3 + 3 * b->phases.size();
+        while (ev.size() < n_ev) {
+            cudaEvent_t x = nullptr;
+            e = cudaEventCreate(&x);
             if (e != cudaSuccess) return e;
+            ev.push_back(x);
         }
-        e = cudaEventRecord(ev[0], st);
+        size_t k = 0;
+        e = cudaEventRecord(ev[k++], st);
+        if (e == cudaSuccess) {
+            t_enqueue_stage = "warp programs";
+            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, 0, 0, b->dyn_smem, b->dyn_big,
+                             b->d_prof, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
         if (e == cudaSuccess) {
             t_enqueue_stage = "subtree programs";
-            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, b->n_block_items, b->n_big_items,
+            e = launch_local(b->c128, b->d_jobs, b->d_local + b->n_warp_items, 0, b->n_block_items, b->n_big_items,
                              b->dyn_smem, b->dyn_big, b->d_prof, st);
         }
-        if (e == cudaSuccess) {
-            t_enqueue_stage = "dataflow kernel";
-            e = launch_persistent(b->c128, b->d_jobs, b->d_work, b->n_work, b->d_counter, b->grid, b->use_tc,
-                                  b->wait_ns, b->d_prof, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
+        const bool tf32 = b->prec == TN_TF32_SPLIT;
+        for (size_t p = 0; e == cudaSuccess && p < b->phases.size(); ++p) {
+            const tn_batch::Phase &ph = b->phases[p];
+            uint32_t *cnt = b->d_counter + 3 * p;
+            if (ph.n_pack > 0) {
+                t_enqueue_stage = "tensor-core operand packing";
+                e = launch_tc_pack(tf32, b->d_jobs, b->d_pack + ph.pack0, ph.n_pack, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
+            if (e == cudaSuccess && ph.n_gemm > 0) {
+                t_enqueue_stage = "tensor-core GEMM";
+                e = launch_tc_gemm(tf32, b->d_jobs, b->d_gemm + ph.gemm0, ph.n_gemm, reinterpret_cast<int32_t *>(cnt + 2),
+                                   b->wait_ns, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
+            if (e == cudaSuccess && ph.n_work > 0) {
+                t_enqueue_stage = "dataflow kernel";
+                e = launch_persistent(b->c128, b->d_jobs, b->d_work + ph.work0, ph.n_work, cnt, b->grid, b->wait_ns,
+                                      b->d_prof, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         b->runs++;
     } else {
+        const bool tf32 = b->prec == TN_TF32_SPLIT;
+        size_t r = 0;   // tensor-core ranges, in (job, step) order
         for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb) {
             const Compiled &c = b->comp[b->job_comp[jb]];
-            for (size_t s = 0; e == cudaSuccess && s < c.steps.size(); ++s)
+            for (size_t s = 0; e == cudaSuccess && s < c.steps.size(); ++s) {
+                if (c.steps[s].kind == STEP_TC) {
+                    const TcRange &tr = b->tc_ranges[r++];
+                    e = launch_tc_pack(tf32, b->d_jobs, b->d_pack + tr.pack0, tr.n_pack, st);
+                    if (e == cudaSuccess)
+                        e = launch_tc_gemm(tf32, b->d_jobs, b->d_gemm + tr.gemm0, tr.n_gemm,
+                                           reinterpret_cast<int32_t *>(b->d_counter + 2), b->wait_ns, st);
+                    continue;
+                }
                 e = launch_step(b->c128, c.steps[s], (int32_t)s, b->jobs[jb], std::max(b->dyn_smem, b->dyn_big), st);
+            }
         }
     }
     for (int32_t jb = 0; e == cudaSuccess && jb < b->n_jobs; ++jb)
@@ -1063,8 +1185,8 @@ tn_status record_graph(tn_batch *b) {
 void batch_destroy(tn_batch *b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    for (auto &pair : b->kev)
-        for (cudaEvent_t e : pair)
+    for (auto &list : b->kev)
+        for (cudaEvent_t e : list)
             if (e) cudaEventDestroy(e);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
@@ -1074,7 +1196,9 @@ void batch_destroy(tn_batch *b) {
     if (b->h_upd) cudaFreeHost(b->h_upd);
     if (b->d_upd) cudaFree(b->d_upd);
     if (b->d_prof) cudaFree(b->d_prof);
+    tn_ctx *ctx = b->ctx;
     delete b;
+    ctx_release(ctx);
 }
 
 tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const tn_plan *const *plans,
@@ -1105,6 +1229,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     tn_batch *b = new (std::nothrow) tn_batch;
     if (!b) return fail(TN_ENOMEM, "allocating the batch");
     b->ctx = ctx;
+    ctx_retain(ctx);
     b->prec = prec;
     b->c128 = (prec == TN_C128);
     b->elem = b->c128 ? 16 : 8;
@@ -1167,34 +1292,75 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->arena_total += c.arena_bytes;
     }
     const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
-    // work list: (job, step, tile) in (level, job, step, tile) order
-    std::vector<WorkItem> work, local_items, warp_items, big_items;
-    if (b->mode == TN_EXEC_PERSISTENT) {
+    // work lists per dependency phase (step_phases): dataflow items in (level, job, step, tile)
+    // order, and the pack units and GEMM tiles of the tensor-core steps in (job, step) order
+    std::vector<WorkItem> work, packs, gemms, local_items, warp_items, big_items;
+    std::vector<int32_t> work_phase;
+    {
+        std::vector<std::vector<int32_t>> phase_of(b->comp.size());
+        int32_t np = 1;
+        for (size_t ci = 0; ci < b->comp.size(); ++ci) np = std::max(np, step_phases(b->comp[ci], phase_of[ci]));
         int64_t total = 0;
         for (int32_t i = 0; i < n; ++i) total += b->comp[b->job_comp[i]].total_tiles;
         if (total >= 0xffffffffLL) { batch_destroy(b); return fail(TN_EUNSUPPORTED, "too many work tiles"); }
-        std::vector<std::array<int32_t, 3>> order;   // level, job, step
         for (int32_t i = 0; i < n; ++i) {
             const Compiled &c = b->comp[b->job_comp[i]];
-            for (size_t s = 0; s < c.steps.size(); ++s) order.push_back({c.steps[s].level, i, (int32_t)s});
-        }
-        std::sort(order.begin(), order.end());
-        work.reserve((size_t)total);
-        for (auto &o : order) {
-            const StepDesc &d = b->comp[b->job_comp[o[1]]].steps[o[2]];
-            if (d.kind == STEP_LOCAL) {
-                const Compiled &c = b->comp[b->job_comp[o[1]]];
+            for (size_t st = 0; st < c.steps.size(); ++st) {
+                const StepDesc &d = c.steps[st];
+                if (d.kind != STEP_LOCAL) continue;
                 const LocalProg &P = c.progs[d.tile_rows];
                 (P.kind == PROG_WARP ? warp_items : P.kind == PROG_BIG ? big_items : local_items)
-                    .push_back({(uint32_t)o[1], (uint32_t)o[2], 0u});
-                continue;
+                    .push_back({(uint32_t)i, (uint32_t)st, 0u});
             }
-            if (d.flags & FLAG_CHAIN_CONT) continue;   // run inside its chain's first step
-            const Compiled &cj = b->comp[b->job_comp[o[1]]];
-            for (int32_t t = 0; t < d.ntiles; ++t) work.push_back(dataflow_item(cj, (uint32_t)o[1], o[2], t));
+        }
+        auto add_tc = [&](int32_t job, int32_t st) {
+            const StepDesc &d = b->comp[b->job_comp[job]].steps[st];
+            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0);
+            TcRange r{job, st, (int32_t)packs.size(), (int32_t)units, (int32_t)gemms.size(), d.ntiles};
+            for (int64_t u = 0; u < units; ++u) packs.push_back({(uint32_t)job, (uint32_t)st, (uint32_t)u});
+            for (int32_t t = 0; t < d.ntiles; ++t) gemms.push_back({(uint32_t)job, (uint32_t)st, (uint32_t)t});
+            b->tc_ranges.push_back(r);
+        };
+        if (b->mode == TN_EXEC_PERSISTENT) {
+            work.reserve((size_t)total);
+            b->phases.assign(np, tn_batch::Phase());
+            for (int32_t p = 0; p < np; ++p) {
+                tn_batch::Phase &ph = b->phases[p];
+                std::vector<std::array<int32_t, 3>> order;   // level, job, step
+                for (int32_t i = 0; i < n; ++i) {
+                    const Compiled &c = b->comp[b->job_comp[i]];
+                    const std::vector<int32_t> &phs = phase_of[b->job_comp[i]];
+                    for (size_t st = 0; st < c.steps.size(); ++st)
+                        if (phs[st] == p && c.steps[st].kind != STEP_LOCAL && !(c.steps[st].flags & FLAG_CHAIN_CONT))
+                            order.push_back({c.steps[st].level, i, (int32_t)st});
+                }
+                std::sort(order.begin(), order.end());
+                ph.pack0 = (int32_t)packs.size();
+                ph.gemm0 = (int32_t)gemms.size();
+                for (auto &o : order)
+                    if (b->comp[b->job_comp[o[1]]].steps[o[2]].kind == STEP_TC) add_tc(o[1], o[2]);
+                ph.n_pack = (int32_t)packs.size() - ph.pack0;
+                ph.n_gemm = (int32_t)gemms.size() - ph.gemm0;
+                for (auto &o : order) {
+                    const Compiled &cj = b->comp[b->job_comp[o[1]]];
+                    const StepDesc &d = cj.steps[o[2]];
+                    if (d.kind == STEP_TC) continue;
+                    for (int32_t t = 0; t < d.ntiles; ++t) {
+                        work.push_back(dataflow_item(cj, (uint32_t)o[1], o[2], t));
+                        work_phase.push_back(p);
+                    }
+                }
+            }
+        } else {
+            for (int32_t i = 0; i < n; ++i) {
+                const Compiled &c = b->comp[b->job_comp[i]];
+                for (size_t st = 0; st < c.steps.size(); ++st)
+                    if (c.steps[st].kind == STEP_TC) add_tc(i, (int32_t)st);
+            }
         }
     }
     b->n_work = (int64_t)work.size();
+    set_phase_ranges(b, work_phase);
     b->wait_ns = (long long)ctx->cfg.wait_limit_us * 1000;
     // warp programs first, longest first (a block of four warps lasts as long as its longest
     // program), then the block programs
@@ -1209,6 +1375,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     local_items.insert(local_items.end(), big_items.begin(), big_items.end());
     const size_t o_work = carve(sizeof(WorkItem) * work.size());
     const size_t o_litems = carve(sizeof(WorkItem) * local_items.size());
+    const size_t o_pack = carve(sizeof(WorkItem) * packs.size());
+    const size_t o_gemm = carve(sizeof(WorkItem) * gemms.size());
     // reset region: results, maxbits, done, counter
     const size_t o_reset = off;
     const size_t o_res = carve(sizeof(DeviceResult) * (size_t)n);
@@ -1218,7 +1386,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         o_max[i] = carve(sizeof(uint32_t) * (size_t)c.n_nodes);
         o_done[i] = carve(sizeof(int32_t) * c.steps.size());
     }
-    const size_t o_counter = carve(2 * sizeof(uint32_t));   // claim counter, abort flag
+    // per phase: the dataflow launch's claim counter and abort flag, the GEMM launch's abort flag
+    const size_t o_counter = carve(3 * sizeof(uint32_t) * std::max<size_t>(b->phases.size(), 1));
     b->reset_bytes = off - o_reset;
     b->footprint = off;
     if (ctx->budget && b->footprint > ctx->budget) {
@@ -1245,6 +1414,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->d_jobs = reinterpret_cast<JobPtrs *>(base + o_jobs);
     b->d_work = reinterpret_cast<WorkItem *>(base + o_work);
     b->d_local = reinterpret_cast<WorkItem *>(base + o_litems);
+    b->d_pack = reinterpret_cast<WorkItem *>(base + o_pack);
+    b->d_gemm = reinterpret_cast<WorkItem *>(base + o_gemm);
     b->d_reset = base + o_reset;
     b->d_res = reinterpret_cast<DeviceResult *>(base + o_res);
     b->d_counter = reinterpret_cast<uint32_t *>(base + o_counter);
@@ -1306,13 +1477,16 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     if (e == cudaSuccess && !local_items.empty())
         e = cudaMemcpyAsync(b->d_local, local_items.data(), sizeof(WorkItem) * local_items.size(),
                             cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !packs.empty())
+        e = cudaMemcpyAsync(b->d_pack, packs.data(), sizeof(WorkItem) * packs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !gemms.empty())
+        e = cudaMemcpyAsync(b->d_gemm, gemms.data(), sizeof(WorkItem) * gemms.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) { batch_destroy(b); return fail(TN_ECUDA, cudaGetErrorString(e)); }
     b->h_work = std::move(work);
-    for (const Compiled &c : b->comp)
-        if (c.counts[STEP_TC] > 0) b->use_tc = 1;
-    b->grid = persistent_grid(b->c128, b->use_tc);
+    b->h_work_phase = std::move(work_phase);
+    b->grid = persistent_grid(b->c128);
     if (b->grid <= 0) { batch_destroy(b); return fail(TN_ECUDA, "occupancy query failed"); }
     tn_status s = TN_OK;
     for (int32_t i = 0; i < n && s == TN_OK; ++i) s = upload_leaves(b, i);
@@ -1339,12 +1513,18 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     b->info.dyn_smem = b->dyn_smem;
     b->info.arena_bytes = b->arena_total;
     if (b->mode == TN_EXEC_PERSISTENT) {
-        // leaf conversion, warp programs, block programs, dataflow
-        b->info.launches = 2 + (b->n_warp_items > 0 ? 1 : 0) + (b->n_block_items > 0 ? 1 : 0) +
+        // leaf conversion, warp programs, block programs, large programs; per phase the pack,
+        // GEMM and dataflow launches
+        b->info.launches = 1 + (b->n_warp_items > 0 ? 1 : 0) + (b->n_block_items > 0 ? 1 : 0) +
                            (b->n_big_items > 0 ? 1 : 0);
+        for (const tn_batch::Phase &ph : b->phases)
+            b->info.launches += (ph.n_pack > 0) + (ph.n_gemm > 0) + (ph.n_work > 0);
     } else {
         int32_t l = 1;
-        for (int32_t i = 0; i < n; ++i) l += (int32_t)b->comp[b->job_comp[i]].steps.size();
+        for (int32_t i = 0; i < n; ++i) {
+            const Compiled &c = b->comp[b->job_comp[i]];
+            l += (int32_t)c.steps.size() + c.counts[STEP_TC];   // a tensor-core step: pack and GEMM
+        }
         b->info.launches = l;
     }
     for (int32_t i = 0; i < n; ++i)
@@ -1590,9 +1770,12 @@ void tn_ctx_free(tn_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    batch_destroy(c->cached);
-    if (c->own_stream) cudaStreamDestroy(c->stream);
-    delete c;
+    tn_batch *cached = c->cached;
+    c->cached = nullptr;
+    c->freed = true;
+    c->refs.fetch_add(1);      // keep the context alive while its cached batch is destroyed
+    batch_destroy(cached);
+    ctx_release(c);            // deletes it now unless other batches, programs or servers remain
 }
 
 tn_status tn_ctx_device(const tn_ctx *c, int32_t *device) {
@@ -1701,16 +1884,22 @@ tn_status tn_batch_debug_hold(tn_batch *b, int32_t job, int32_t step) {
         }
     }
     std::vector<WorkItem> kept;
+    std::vector<int32_t> kept_phase;
     kept.reserve(b->h_work.size());
-    for (const WorkItem &w : b->h_work) {
+    for (size_t i = 0; i < b->h_work.size(); ++i) {
+        const WorkItem &w = b->h_work[i];
         bool drop = false;
         for (const auto &h : held) drop = drop || ((int32_t)w.job == h.first && (int32_t)w.step == h.second);
-        if (!drop) kept.push_back(w);
+        if (!drop) {
+            kept.push_back(w);
+            kept_phase.push_back(b->h_work_phase[i]);
+        }
     }
     CK(cudaSetDevice(b->ctx->device));
     CK(cudaStreamSynchronize(b->ctx->stream));
     if (!kept.empty()) CK(cudaMemcpy(b->d_work, kept.data(), sizeof(WorkItem) * kept.size(), cudaMemcpyHostToDevice));
     b->n_work = (int64_t)kept.size();
+    set_phase_ranges(b, kept_phase);
     b->held.swap(held);
     return TN_OK;
 }
@@ -1759,14 +1948,40 @@ tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms)
         return fail(TN_EINVAL, "n_runs must be in [1, min(256, runs so far)]");
     CK(cudaSetDevice(b->ctx->device));
     double total = 0;
+    const size_t n_ev = 3 + 3 * b->phases.size();
     for (int64_t r = b->runs - n_runs; r < b->runs; ++r) {
-        cudaEvent_t const *ev = b->kev[r % tn_batch::kRing];
-        CK(cudaEventSynchronize(ev[1]));
+        const std::vector<cudaEvent_t> &ev = b->kev[r % tn_batch::kRing];
+        if (ev.size() < n_ev) return fail(TN_EINVAL, "no timing of that run");
+        CK(cudaEventSynchronize(ev[n_ev - 1]));
         float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[n_ev - 1]));
         total += ms;
     }
     *mean_ms = total / n_runs;
+    return TN_OK;
+}
+
+tn_status tn_batch_kernel_times(const tn_batch *b, int32_t n_runs, double *mean_ms) {
+    if (!b || !mean_ms) return fail(TN_EINVAL, "NULL argument");
+    if (b->mode != TN_EXEC_PERSISTENT) return fail(TN_EUNSUPPORTED, "only the persistent mode is timed per run");
+    if (n_runs < 1 || n_runs > tn_batch::kRing || n_runs > b->runs)
+        return fail(TN_EINVAL, "n_runs must be in [1, min(256, runs so far)]");
+    CK(cudaSetDevice(b->ctx->device));
+    double acc[5] = {0, 0, 0, 0, 0};
+    const size_t n_ev = 3 + 3 * b->phases.size();
+    for (int64_t r = b->runs - n_runs; r < b->runs; ++r) {
+        const std::vector<cudaEvent_t> &ev = b->kev[r % tn_batch::kRing];
+        if (ev.size() < n_ev) return fail(TN_EINVAL, "no timing of that run");
+        CK(cudaEventSynchronize(ev[n_ev - 1]));
+        for (size_t i = 0; i + 1 < n_ev; ++i) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            // slots: 0 warp programs, 1 block and large programs, then (pack, GEMM, dataflow) per phase
+            const int cls = i < 2 ? (int)i : 2 + (int)((i - 2) % 3);
+            acc[cls] += ms;
+        }
+    }
+    for (int c = 0; c < 5; ++c) mean_ms[c] = acc[c] / n_runs;
     return TN_OK;
 }
 

@@ -39,13 +39,16 @@ enum StepFlags : int32_t {
     FLAG_NO_C = 8,      // no tensor output (DOTP, or the root's DOTF)
     FLAG_TF32 = 16,     // TC: TF32 split (else BF16 split)
     FLAG_A_SMEM = 32,   // ROWS: A is copied whole into shared memory and C leaves through it
-    FLAG_CHAIN_CONT = 64  // ROWS (FLAG_A_SMEM): A is the C of the previous step of a chain, which
+    FLAG_CHAIN_CONT = 64, // ROWS (FLAG_A_SMEM): A is the C of the previous step of a chain, which
                           // the persistent kernel keeps in shared memory; no work item of its own
+    FLAG_A_MCONT = 128,   // TC: A's row index is its contiguous one (the pack reads rows fastest)
+    FLAG_B_NCONT = 256    // TC: B's column index is its contiguous one
 };
 
 struct StepDesc {
     int64_t M, N, K;
     int64_t a_off, b_off, c_off;   // element offsets into the leaf buffer or the arena
+    int64_t img_a, img_b;          // TC: byte offsets in the arena of the packed operand images
     int32_t node_a, node_b, node_c;
     int32_t kind;
     int32_t flags;
@@ -179,13 +182,32 @@ cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t strea
 constexpr int kProfSlots = 16;
 
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
-// use_tc: the work list holds tensor-core tiles (each block then holds 128 TMEM columns).
 // wait_ns: a dependency wait gives up after about this many nanoseconds (TN_ETIMEOUT).
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work,
-                              int64_t n_work, uint32_t *counter, int32_t grid, int32_t use_tc,
+                              int64_t n_work, uint32_t *counter, int32_t grid,
                               long long wait_ns, long long *prof, cudaStream_t stream);
-// Co-resident grid of the persistent kernel, with tensor-core tiles (use_tc) or without.
-int32_t persistent_grid(bool c128, int32_t use_tc);
+// Co-resident grid of the persistent kernel.
+int32_t persistent_grid(bool c128);
+
+// ---- dense steps on the tensor cores (kernels_tc.cu) ------------------------------------------
+// A dense step C [M, N] = A [M, K] B [K, N] (complex64 storage, BF16 or TF32 split) runs as a pack
+// launch -- every operand k-block gathered, scaled, split into hi / lo and written as a
+// shared-memory image -- and a GEMM launch over 128 x 128 complex output tiles.  Images: A tile t,
+// k-block kb at img_a + (t KB + kb) 2 kTcImgA (hi plane, then lo); B'' likewise with kTcImgB.
+constexpr int kTcRows = 128;               // rows of C per GEMM tile (tensor-memory lanes)
+constexpr int kTcCols = 128;               // complex columns of C per GEMM tile (256 real)
+constexpr uint32_t kTcImgA = 128 * 64;     // one plane of an A k-block: 128 rows x 64 bytes
+constexpr uint32_t kTcImgB = 256 * 64;     // one plane of a B'' k-block: 256 rows x 64 bytes
+// units: (job, step, unit) with unit < (ceil(M/128) + ceil(N/128)) KB (tc_pack_units).
+cudaError_t launch_tc_pack(bool tf32, const JobPtrs *jobs_dev, const WorkItem *units, int32_t n_units,
+                           cudaStream_t stream);
+// tiles: (job, step, tile) with tile < ceil(M/128) ceil(N/128); each completed tile adds one to
+// the job's done[step].  abort_flag: a zeroed device int32 (the launch-wide abort flag).
+cudaError_t launch_tc_gemm(bool tf32, const JobPtrs *jobs_dev, const WorkItem *tiles, int32_t n_tiles,
+                           int32_t *abort_flag, long long wait_ns, cudaStream_t stream);
+int64_t tc_pack_units(int64_t M, int64_t N, int64_t K, bool tf32);
+// Bytes of a step's operand images (a_bytes: the A part, may be NULL).
+size_t tc_image_bytes(int64_t M, int64_t N, int64_t K, bool tf32, size_t *a_bytes);
 // Subtree programs; items: (job, pseudo-step, 0), the n_warp warp programs first (four per
 // block of kWarpThreads), then the n_block block programs (one per block, `dyn_smem` bytes), then
 // the n_big large programs (one per block, `dyn_big` bytes).

@@ -16,13 +16,11 @@
 //                    progresses (co-residency of the grid is not needed).  A block claims its
 //                    next tile while the current one runs.  A chain of narrow ROWS steps is one
 //                    work item, its tensor kept in shared memory between the steps.
-//                    k_persist<float, true> also runs tensor-core tiles (each block then holds
-//                    128 TMEM columns).
+// Dense tensor-core steps run in their own pack and GEMM launches (kernels_tc.cu).
 #include <cstdint>
 
 #include "kernels.cuh"
 #include "local_ops.cuh"
-#include "tc_ops.cuh"
 #include "tile_ops.cuh"
 
 namespace tn {
@@ -30,9 +28,6 @@ namespace tn {
 namespace {
 
 constexpr int32_t kStatusTimeout = 5;
-// Dynamic shared memory of the complex64 dataflow kernels: staged ROWS steps, and with tensor
-// cores also the operand tiles (used at different times).
-constexpr int32_t kPersistTcDyn = kTcSmem > kPersistDynSmem ? kTcSmem : kPersistDynSmem;
 
 __device__ __forceinline__ uint32_t ld_acquire(const int32_t *p) {
     uint32_t v;
@@ -168,30 +163,6 @@ __global__ void __launch_bounds__(kThreads) k_local(const JobPtrs *__restrict__ 
     }
 }
 
-// Tensor-memory accumulator and mbarrier of one block (tensor-core tiles only).
-__device__ __forceinline__ void tc_setup(TcState &tc, uint32_t *tmem_slot, uint64_t *bar, int32_t *abort_flag) {
-    if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, kTcCols);
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    tc.tmem = *tmem_slot;
-    tc.bar = bar;
-    tc.phase = 0;
-    tc.abort_flag = abort_flag;
-    tc.pending = false;
-}
-
-// Frees the block's tensor memory; after a wait that gave up, first waits (bounded) once more for
-// the MMAs that may still be in flight.
-__device__ __forceinline__ void tc_teardown(TcState &tc) {
-    if (tc.pending) mbar_wait(tc.bar, tc.phase, kTcWaitLimit);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, kTcCols);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ steps, int32_t step,
                                                    JobPtrs job) {
@@ -203,38 +174,13 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ 
     run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
 }
 
-// One tensor-core step (graph execution mode): one block per 128 x 64 output tile.
-__global__ void __launch_bounds__(kThreads) k_step_tc(const StepDesc *__restrict__ steps, int32_t step,
-                                                      JobPtrs job) {
-    extern __shared__ __align__(16) char dyn[];
-    __shared__ StepDesc d;
-    __shared__ __align__(16) char smem[Scratch<float>::bytes];
-    __shared__ float red[32];
-    __shared__ uint64_t tc_bar;
-    __shared__ uint32_t tc_tmem;
-    __shared__ int32_t tc_abort;
-    load_desc(d, steps + step);
-    if (threadIdx.x == 0) tc_abort = 0;
-    TcState tc;
-    tc_setup(tc, &tc_tmem, &tc_bar, &tc_abort);
-    const bool ok = tile_tc(d, blockIdx.x, job, dyn, smem, red, tc);
-    if (!ok && threadIdx.x == 0) atomicExch(&static_cast<DeviceResult *>(job.result)->status, kStatusTimeout);
-    tc_teardown(tc);
-}
-
-// Persistent dataflow kernel.  TC: the work list holds tensor-core tiles (complex64 storage
-// only); it is a separate instantiation so that the CUDA-core variant carries no tensor-memory
-// code and keeps two blocks per SM.
-template <typename T, bool TC>
+// Persistent dataflow kernel.
+template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_persist(const JobPtrs *__restrict__ jobs, const WorkItem *__restrict__ work, int64_t n_work,
               uint32_t *counter, long long wait_ns, long long *prof) {
     int32_t *abort_flag = reinterpret_cast<int32_t *>(counter + 1);
     extern __shared__ __align__(16) char dyn[];
-    __shared__ uint64_t tc_bar;
-    __shared__ uint32_t tc_tmem;
-    TcState tc;
-    if constexpr (TC) tc_setup(tc, &tc_tmem, &tc_bar, abort_flag);
     __shared__ StepDesc d;
     __shared__ __align__(16) char smem[Scratch<T>::bytes];
     __shared__ float red[32];
@@ -281,18 +227,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                 chained = true;
             }
         }
-        if (s_ok && !chained) {
-            if constexpr (TC) {
-                if (d.kind == STEP_TC) {
-                    if (!tc.pending && !tile_tc(d, it.tile, j, dyn, smem, red, tc) && threadIdx.x == 0)
-                        atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
-                } else {
-                    run_tile<T>(d, it.tile, j, smem, red, dyn);
-                }
-            } else {
-                run_tile<T>(d, it.tile, j, smem, red, dyn);
-            }
-        }
+        if (s_ok && !chained) run_tile<T>(d, it.tile, j, smem, red, dyn);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -311,7 +246,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
             }
         }
     }
-    if constexpr (TC) tc_teardown(tc);
 }
 
 // Scatter staged tensor updates {dst offset, count, src offset} into the complex128 leaves.
@@ -354,14 +288,7 @@ cudaError_t allow_dyn_smem(K kernel, int32_t bytes) {
 
 cudaError_t launch_step(bool c128, const StepDesc &h, int32_t step, const JobPtrs &job, int32_t dyn_smem,
                         cudaStream_t stream) {
-    if (h.ntiles <= 0) return cudaErrorInvalidValue;
-    if (h.kind == STEP_TC) {
-        if (c128) return cudaErrorInvalidValue;
-        cudaError_t e = allow_dyn_smem(k_step_tc, kTcSmem);
-        if (e != cudaSuccess) return e;
-        k_step_tc<<<(unsigned)h.ntiles, kThreads, kTcSmem, stream>>>(job.steps, step, job);
-        return cudaGetLastError();
-    }
+    if (h.ntiles <= 0 || h.kind == STEP_TC) return cudaErrorInvalidValue;   // TC: launch_tc_pack / _gemm
     const int32_t dyn = h.kind == STEP_LOCAL ? dyn_smem : ((h.flags & FLAG_A_SMEM) ? kPersistDynSmem : 0);
     cudaError_t e = c128 ? allow_dyn_smem(k_step<double>, dyn) : allow_dyn_smem(k_step<float>, dyn);
     if (e != cudaSuccess) return e;
@@ -385,28 +312,17 @@ cudaError_t launch_scatter_updates(const int64_t *hdr, const double2 *vals, int6
     return cudaGetLastError();
 }
 
-int32_t persistent_grid(bool c128, int32_t use_tc) {
+int32_t persistent_grid(bool c128) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     cudaError_t e;
     if (c128) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double, false>, kThreads, 0);
-    } else if (use_tc) {
-        // the occupancy query reports one block per SM for a kernel that allocates tensor memory;
-        // registers and shared memory allow two (as for the CUDA-core instantiation, which has the
-        // same footprint), and two blocks use 2 x 128 of the SM's 512 TMEM columns
-        e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
-        if (e == cudaSuccess) e = allow_dyn_smem(k_persist<float, false>, kPersistTcDyn);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads,
-                                                              kPersistTcDyn);
-        if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0);
     } else {
-        e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
+        e = allow_dyn_smem(k_persist<float>, kPersistDynSmem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads,
-                                                              kPersistDynSmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, kPersistDynSmem);
     }
     if (e != cudaSuccess) return 0;
     return sms * per_sm;
@@ -457,23 +373,17 @@ int32_t local_smem_budget(bool c128, int32_t blocks_per_sm) {
 }
 
 cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem *work, int64_t n_work,
-                              uint32_t *counter, int32_t grid, int32_t use_tc, long long wait_ns,
-                              long long *prof, cudaStream_t stream) {
+                              uint32_t *counter, int32_t grid, long long wait_ns, long long *prof,
+                              cudaStream_t stream) {
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
-    if (c128)
-        k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, wait_ns,
-                                                                          prof);
-    else if (use_tc) {
-        const cudaError_t e = allow_dyn_smem(k_persist<float, true>, kPersistTcDyn);
-        if (e != cudaSuccess) return e;
-        k_persist<float, true><<<(unsigned)grid, kThreads, kPersistTcDyn, stream>>>(jobs_dev, work, n_work, counter,
-                                                                                    wait_ns, prof);
+    if (c128) {
+        k_persist<double><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, wait_ns, prof);
     } else {
-        const cudaError_t e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
+        const cudaError_t e = allow_dyn_smem(k_persist<float>, kPersistDynSmem);
         if (e != cudaSuccess) return e;
-        k_persist<float, false><<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work,
-                                                                                       counter, wait_ns, prof);
+        k_persist<float><<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work, counter,
+                                                                               wait_ns, prof);
     }
     return cudaGetLastError();
 }

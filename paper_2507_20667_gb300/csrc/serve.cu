@@ -83,13 +83,12 @@ struct Model {
     void *dev = nullptr;              // step tables
     std::vector<double> leaves;       // base complex128 leaves (interleaved)
     std::vector<int64_t> leaf_off;
-    std::vector<WorkItem> tmpl;       // global work items (job field unused)
-    std::vector<int32_t> tmpl_level;
+    std::vector<PhaseTemplate> ph;    // per dependency phase: dataflow items, TC units and tiles
+    size_t n_items = 0;               // work items of all phases (dataflow, pack, GEMM)
     std::vector<int32_t> local_steps; // pseudo-steps of block programs
     std::vector<int32_t> warp_steps;  // pseudo-steps of warp programs
     std::vector<int32_t> big_steps;   // pseudo-steps of large programs
     size_t o_leaf = 0, o_arena = 0, o_part = 0, o_exp = 0, job_bytes = 0;
-    int32_t max_level = 0;
 };
 
 struct Request {
@@ -141,7 +140,7 @@ struct tn_server {
     Flight fl[2];
     std::thread worker;
     std::atomic<bool> stop{false};
-    int32_t dyn_smem = 0, dyn_big = 0, grid = 0, grid_tc = 0;
+    int32_t dyn_smem = 0, dyn_big = 0, grid = 0;
     bool any_tc = false;
     std::string worker_error;
     tn_serve_stats stats{};
@@ -180,21 +179,43 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
         l64[i] = leaf_total;
         leaf_total += S->models[f.reqs[i].model]->leaf_off.back();
     }
-    std::vector<WorkItem> work, local;
-    int32_t max_level = 0;
-    for (int32_t i = 0; i < n; ++i) max_level = std::max(max_level, S->models[f.reqs[i].model]->max_level);
-    // merge the jobs' work templates level by level (all jobs' level-1 tiles first, ...)
-    std::vector<size_t> cursor(n, 0);
-    for (int32_t lv = 0; lv <= max_level; ++lv)
+    std::vector<WorkItem> work, local, packs, gemms;
+    int32_t n_phases = 1;
+    for (int32_t i = 0; i < n; ++i) n_phases = std::max(n_phases, (int32_t)S->models[f.reqs[i].model]->ph.size());
+    // per phase: the TC units and tiles of all jobs, then the jobs' dataflow items merged level by
+    // level (all jobs' level-1 tiles first, ...)
+    struct Range { size_t w0, nw, p0, np, g0, ng; };
+    std::vector<Range> ranges(n_phases);
+    for (int32_t p = 0; p < n_phases; ++p) {
+        Range &r = ranges[p];
+        r.p0 = packs.size();
+        r.g0 = gemms.size();
+        r.w0 = work.size();
+        int32_t max_level = 0;
         for (int32_t i = 0; i < n; ++i) {
             const Model &m = *S->models[f.reqs[i].model];
-            size_t &c = cursor[i];
-            while (c < m.tmpl.size() && m.tmpl_level[c] == lv) {
-                WorkItem w = m.tmpl[c++];
-                w.job = (uint32_t)i;
-                work.push_back(w);
-            }
+            if (p >= (int32_t)m.ph.size()) continue;
+            for (WorkItem w : m.ph[p].pack) { w.job = (uint32_t)i; packs.push_back(w); }
+            for (WorkItem w : m.ph[p].gemm) { w.job = (uint32_t)i; gemms.push_back(w); }
+            for (int32_t lv : m.ph[p].level) max_level = std::max(max_level, lv);
         }
+        std::vector<size_t> cursor(n, 0);
+        for (int32_t lv = 0; lv <= max_level; ++lv)
+            for (int32_t i = 0; i < n; ++i) {
+                const Model &m = *S->models[f.reqs[i].model];
+                if (p >= (int32_t)m.ph.size()) continue;
+                const PhaseTemplate &pt = m.ph[p];
+                size_t &c = cursor[i];
+                while (c < pt.work.size() && pt.level[c] == lv) {
+                    WorkItem w = pt.work[c++];
+                    w.job = (uint32_t)i;
+                    work.push_back(w);
+                }
+            }
+        r.np = packs.size() - r.p0;
+        r.ng = gemms.size() - r.g0;
+        r.nw = work.size() - r.w0;
+    }
     // warp programs first, then block programs (launch_local's item order)
     for (int32_t i = 0; i < n; ++i)
         for (int32_t s : S->models[f.reqs[i].model]->warp_steps) local.push_back({(uint32_t)i, (uint32_t)s, 0u});
@@ -211,6 +232,8 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     const size_t o_jobs = carve(sizeof(JobPtrs) * (size_t)n);
     const size_t o_work = carve(sizeof(WorkItem) * work.size());
     const size_t o_local = carve(sizeof(WorkItem) * local.size());
+    const size_t o_pack = carve(sizeof(WorkItem) * packs.size());
+    const size_t o_gemm = carve(sizeof(WorkItem) * gemms.size());
     const size_t upload_bytes = off;
     const size_t o_reset = off;
     const size_t o_res = carve(sizeof(DeviceResult) * (size_t)n);
@@ -220,7 +243,7 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
         o_max[i] = carve(sizeof(uint32_t) * (size_t)m.c.n_nodes);
         o_done[i] = carve(sizeof(int32_t) * m.c.steps.size());
     }
-    const size_t o_counter = carve(2 * sizeof(uint32_t));
+    const size_t o_counter = carve(3 * sizeof(uint32_t) * (size_t)n_phases);   // per phase: claim, abort x 2
     const size_t reset_bytes = off - o_reset;
     char *meta = S->pool + meta_off;
     // host staging
@@ -276,10 +299,10 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     }
     if (!work.empty()) std::memcpy(f.h_stage + o_work, work.data(), sizeof(WorkItem) * work.size());
     if (!local.empty()) std::memcpy(f.h_stage + o_local, local.data(), sizeof(WorkItem) * local.size());
+    if (!packs.empty()) std::memcpy(f.h_stage + o_pack, packs.data(), sizeof(WorkItem) * packs.size());
+    if (!gemms.empty()) std::memcpy(f.h_stage + o_gemm, gemms.data(), sizeof(WorkItem) * gemms.size());
     int32_t max_leaves = 0;
     for (int32_t i = 0; i < n; ++i) max_leaves = std::max(max_leaves, S->models[f.reqs[i].model]->c.n);
-    bool tc = false;
-    for (int32_t i = 0; i < n; ++i) tc = tc || S->models[f.reqs[i].model]->c.counts[STEP_TC] > 0;
     const JobPtrs *d_jobs = reinterpret_cast<const JobPtrs *>(meta + o_jobs);
     cudaError_t e = cudaMemcpyAsync(meta, f.h_stage, upload_bytes, cudaMemcpyHostToDevice, f.st);
     if (e == cudaSuccess) e = cudaMemsetAsync(meta + o_reset, 0, reset_bytes, f.st);
@@ -287,10 +310,19 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     if (e == cudaSuccess)
         e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), n_warp, n_block,
                          n_big, S->dyn_smem, S->dyn_big, nullptr, f.st);
-    if (e == cudaSuccess && !work.empty())
-        e = launch_persistent(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_work),
-                              (int64_t)work.size(), reinterpret_cast<uint32_t *>(meta + o_counter),
-                              tc ? S->grid_tc : S->grid, tc ? 1 : 0, S->wait_ns, nullptr, f.st);
+    const bool tf32 = S->prec == TN_TF32_SPLIT;
+    for (int32_t p = 0; e == cudaSuccess && p < n_phases; ++p) {
+        const Range &r = ranges[p];
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(meta + o_counter) + 3 * p;
+        if (r.np > 0)
+            e = launch_tc_pack(tf32, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_pack) + r.p0, (int32_t)r.np, f.st);
+        if (e == cudaSuccess && r.ng > 0)
+            e = launch_tc_gemm(tf32, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_gemm) + r.g0, (int32_t)r.ng,
+                               reinterpret_cast<int32_t *>(cnt + 2), S->wait_ns, f.st);
+        if (e == cudaSuccess && r.nw > 0)
+            e = launch_persistent(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_work) + r.w0,
+                                  (int64_t)r.nw, cnt, S->grid, S->wait_ns, nullptr, f.st);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f.h_res, meta + o_res, sizeof(DeviceResult) * (size_t)n, cudaMemcpyDeviceToHost, f.st);
     if (e == cudaSuccess) e = cudaEventRecord(f.ev, f.st);
@@ -303,8 +335,8 @@ size_t meta_bytes(tn_server *S, const std::vector<Request> &reqs) {
     for (const Request &r : reqs) {
         const Model &m = *S->models[r.model];
         b += sizeof(double2) * (size_t)m.leaf_off.back() + sizeof(JobPtrs) +
-             sizeof(WorkItem) * (m.tmpl.size() + m.local_steps.size() + m.warp_steps.size() + m.big_steps.size()) +
-             sizeof(DeviceResult) +
+             sizeof(WorkItem) * (m.n_items + m.local_steps.size() + m.warp_steps.size() + m.big_steps.size()) +
+             sizeof(DeviceResult) + 3 * sizeof(uint32_t) * m.ph.size() +
              sizeof(uint32_t) * (size_t)m.c.n_nodes + sizeof(int32_t) * m.c.steps.size() + 5 * 256;
     }
     return b + 16 * 256;
@@ -415,6 +447,7 @@ tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_byte
     tn_server *S = new (std::nothrow) tn_server;
     if (!S) return fail(TN_ENOMEM, "allocating the server");
     S->ctx = ctx;
+    ctx_retain(ctx);
     S->device = dev;
     S->prec = prec;
     S->c128 = prec == TN_C128;
@@ -424,16 +457,17 @@ tn_status tn_serve_create(tn_ctx *ctx, tn_precision prec, size_t hbm_budget_byte
     s = tn_ctx_get_config(ctx, &cfg);
     if (s != TN_OK) {
         delete S;
+        ctx_release(ctx);
         return s;
     }
     S->copt = compile_opts(cfg, prec, S->c128);
     S->wait_ns = (long long)cfg.wait_limit_us * 1000;
     // full co-resident grids: a second launch's blocks start as the first one's retire
-    S->grid = std::max(1, persistent_grid(S->c128, 0));
-    S->grid_tc = std::max(1, persistent_grid(S->c128, 1));
+    S->grid = std::max(1, persistent_grid(S->c128));
     cudaError_t e = cudaMalloc(&S->pool, hbm_budget_bytes);
     if (e != cudaSuccess) {
         delete S;
+        ctx_release(ctx);
         return fail(e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA, cudaGetErrorString(e));
     }
     S->pool_bytes = hbm_budget_bytes;
@@ -475,7 +509,8 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
     if (s != TN_OK) return s;
     m->leaves = net->impl.data;
     m->leaf_off = net->impl.data_off;
-    work_template(m->c, m->tmpl, m->tmpl_level);
+    phase_templates(m->c, m->ph);
+    for (const PhaseTemplate &pt : m->ph) m->n_items += pt.work.size() + pt.pack.size() + pt.gemm.size();
     for (size_t st = 0; st < m->c.steps.size(); ++st)
         if (m->c.steps[st].kind == STEP_LOCAL)
         {
@@ -483,7 +518,6 @@ tn_status tn_serve_register(tn_server *S, const tn_net *net, const tn_plan *plan
             (kind == PROG_WARP ? m->warp_steps : kind == PROG_BIG ? m->big_steps : m->local_steps)
                 .push_back((int32_t)st);
         }
-    for (int32_t lv : m->tmpl_level) m->max_level = std::max(m->max_level, lv);
     // per-request device bytes: storage leaves, arena, partials, exponents
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off = align256(off + std::max<size_t>(bytes, 16)); return o; };
@@ -622,7 +656,9 @@ void tn_serve_free(tn_server *S) {
     for (auto &m : S->models)
         if (m->dev) cudaFree(m->dev);
     if (S->pool) cudaFree(S->pool);
+    tn_ctx *ctx = S->ctx;
     delete S;
+    ctx_release(ctx);
 }
 
 }  // extern "C"

@@ -171,9 +171,7 @@ template <typename T> struct Scratch {
     // offset table and FP64 partials
     static constexpr int mm = (TK_MM * (257 + 65) * (int)sizeof(C) + (256 + 64) * 4 + TK_MM * 8 + 15) / 16 * 16;
     static constexpr int local = mm > 1024 * 8 + (kThreads / 32) * 16 ? mm : 1024 * 8 + (kThreads / 32) * 16;
-    static constexpr int tc = (128 + 64 + 32 + 32) * (int)sizeof(int64_t);   // tensor-core tile offsets
-    static constexpr int m0 = rows > tc ? rows : tc;
-    static constexpr int m1 = m0 > tile ? m0 : tile;
+    static constexpr int m1 = rows > tile ? rows : tile;
     static constexpr int m2 = dot > local ? dot : local;
     static constexpr int bytes = m1 > m2 ? m1 : m2;
 };

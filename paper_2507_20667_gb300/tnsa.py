@@ -134,6 +134,7 @@ _SIGS = {
     "tn_batch_set_tensors": (_I32, [_P, _I32, _P, _P, _P]),
     "tn_batch_set_profiling": (_I32, [_P, _I32]),
     "tn_batch_debug_hold": (_I32, [_P, _I32, _I32]),
+    "tn_batch_kernel_times": (_I32, [_P, _I32, _P]),
     "tn_batch_profile": (_I32, [_P, _P, _P]),
     "tn_batch_free": (None, [_P]),
     "tn_batch_contract": (_I32, [_P, _I32, _P, _P, _I32, _P, _P]),
@@ -462,6 +463,13 @@ def tn_batch_last_info(batch: Batch) -> dict:
     i = tn_run_info()
     _check(lib.tn_batch_last_info(batch, ctypes.byref(i)))
     return i.as_dict()
+
+
+def tn_batch_kernel_times(batch: Batch, n_runs: int) -> dict:
+    """Mean device time (ms) per kernel class over the last n_runs runs."""
+    out = np.zeros(5, np.float64)
+    _check(lib.tn_batch_kernel_times(batch, int(n_runs), _ptr(out)))
+    return dict(zip(("warp_programs", "block_programs", "tc_pack", "tc_gemm", "dataflow"), out.tolist()))
 
 
 def tn_batch_kernel_ms(batch: Batch, n_runs: int) -> float:

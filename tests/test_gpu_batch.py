@@ -130,8 +130,10 @@ def test_batch_kernel_timing(tnsa):
     ms = tnsa.tn_batch_kernel_ms(b, 3)
     assert 0 < ms < 1000
     info = tnsa.tn_batch_last_info(b)
-    # leaf conversion and the dataflow kernel, plus one launch per program kind present
-    expect = 2 + (info["n_warp_progs"] > 0) + (info["n_local"] > 0)
+    # leaf conversion, one launch per program kind present, and the dataflow kernel when any step
+    # is left outside the programs
+    expect = 1 + (info["n_warp_progs"] > 0) + (info["n_local"] > 0) + \
+        (info["n_gather"] + info["n_tile"] + info["n_dot"] > 0)
     assert info["launches"] == expect and info["flops"] > 0 and info["bytes"] > 0
 
 
@@ -154,3 +156,19 @@ def test_subtree_programs_match_global_path(tnsa, prec):
     assert res[16384][1]["n_local"] >= 1
     for budget in (-1, 0, 16384):
         check(res[budget][0], ref, TOL[prec], f"budget {budget}")
+
+
+def test_context_freed_before_its_batch(tnsa):
+    """Garbage collectors may free a context before the batches made from it: the context then
+    lives on until its last batch is freed, and the batch keeps working meanwhile."""
+    circ, x = tni.cfg1()
+    h = tnsa.tn_build(tni.amplitude_tn(circ, x))
+    plan = tnsa.tn_plan_create(h, k=1)
+    ctx = tnsa.tn_ctx_create(0)
+    b = tnsa.tn_batch_create(ctx, [h], [plan], "c64")
+    ctx.close()
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, 1)
+    assert st[0] == 0
+    check(complex(mant[0]) * 2.0 ** int(e2[0]), sv.amplitude(circ, x), TOL["c64"])
+    b.close()
