@@ -119,6 +119,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cores():
+    """Host cores available to this process (what nproc prints)."""
+    try:
+        return int(subprocess.run(["nproc"], capture_output=True, text=True, check=True).stdout.strip())
+    except (OSError, ValueError, subprocess.CalledProcessError):
+        return len(os.sched_getaffinity(0))
+
+
+def kernel_sources_sha():
+    """Hash of the engine's kernel and runtime sources: DRAM-traffic counters taken from ncu stay
+    valid only while it is unchanged."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_20667_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "*"))):
+        if p.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+            with open(p, "rb") as f:
+                h.update(os.path.basename(p).encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the contraction kernels
+# of one run of the headline workload, from one ncu capture of `bench.py` at the default batch
+# (profiles/launches_brickwork24_batch2432.md); valid for the kernel sources with this hash.
+TRAFFIC = {"sources_sha": None, "batch": 2432, "bytes_per_run": None}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -137,22 +165,33 @@ def oracle_tree(net):
     return steps, ocost.Tree(net, steps).con_serial()
 
 
-def oracle_sample(nets, budget_s=12.0, min_amps=1):
-    """The oracle as it stands on the host cores -- its own Greedy tree, its complex128 C
-    contractor -- on whole amplitudes of the same workload until the time budget is used."""
+def oracle_rate(nets, tree, budget_s, min_amps=1):
+    """Whole amplitudes per second of the oracle's complex128 C contractor along `tree` on the
+    host cores, over nets[0], nets[1], ... until the time budget is used."""
     from oracle import contract as oc
-    tree, con_serial = oracle_tree(nets[0])
     t0 = time.perf_counter()
     done = 0
     while done < min_amps or (time.perf_counter() - t0 < budget_s and done < len(nets)):
         oc.contract_scalar(nets[done % len(nets)], tree)
         done += 1
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": done * 8 * con_serial / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} whole amplitudes of the step's workload (complex128 C contractor on the "
-                      f"oracle's own Greedy tree, con_serial {con_serial}), {dt:.1f} s",
-            "amps_per_s": done / dt}
+    return done, dt
+
+
+def oracle_sample(nets, plan_tree, plan_con_serial, budget_s=12.0):
+    """The oracle as it stands on the host cores, on whole amplitudes of the same workload: along
+    the engine's own simulated-annealing tree (the same tree the GPU contracts), and along the
+    oracle's own serial Greedy tree."""
+    cores = host_cores()
+    done, dt = oracle_rate(nets, plan_tree, 0.75 * budget_s)
+    own_tree, own_con = oracle_tree(nets[0])
+    done2, dt2 = oracle_rate(nets, own_tree, 0.25 * budget_s)
+    return {"value": done * 8 * plan_con_serial / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} whole amplitudes of the step's workload along the same SA tree as the GPU "
+                      f"(con_serial {plan_con_serial}), complex128 C contractor, {dt:.1f} s",
+            "amps_per_s": done / dt,
+            "oracle_own_greedy_tree": {"amps_per_s": done2 / dt2, "con_serial": own_con,
+                                       "tflops": done2 * 8 * own_con / dt2 / 1e12, "amplitudes": done2}}
 
 
 def dist_env():
@@ -192,7 +231,15 @@ def run_reference(args):
     if rank != 0:
         return
     circ, xs, nets = make_workload(max(args.steps + args.warmup, 1))
-    tree, con_serial = oracle_tree(nets[0])
+    # the tree: the configuration's simulated-annealing plan (the library's host planner, exported),
+    # the same tree the GPU arm contracts; the oracle contracts along it
+    from paper_2507_20667_gb300 import inputs as tni
+    from paper_2507_20667_gb300 import tnsa
+    h = tnsa.tn_build(nets[0])
+    plan = plan_for(tnsa, tni, nets[0], h)
+    con_serial = tnsa.tn_plan_counts(plan)[0]
+    part, psteps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+    tree = [(int(l), int(r)) for l, r, o in psteps]
     from oracle import contract as oc
     for i in range(args.warmup):
         oc.contract_scalar(nets[i], tree)
@@ -201,16 +248,59 @@ def run_reference(args):
         oc.contract_scalar(nets[args.warmup + i], tree)
     dt = time.perf_counter() - t0
     value = args.steps * 8 * con_serial / dt / 1e12
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = host_cores()
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": workload_config(args.batch), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} whole amplitudes, one per step"},
+                             "sample": f"{args.steps} whole amplitudes, one per step, complex128 C contractor "
+                                       f"along the configuration's SA tree (con_serial {con_serial})"},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "amps_per_s": args.steps / dt}
     print(json.dumps(line), flush=True)
+
+
+def other_configs(args, tnsa, tni, budget_s=4.0):
+    """cfg1 (10-qubit brickwork depth 8, k = 1 Greedy tree) and the 4x5 depth-8 grid instance of
+    cfg3 (k = 8 SA partitions): a GPU batch (complex64, CUDA events) against the oracle on the
+    host cores along the same tree, with the largest plain relative error of the GPU amplitudes
+    against the oracle over a sample."""
+    import torch
+    from oracle import contract as oc
+    out = {}
+    for name, (circ, x0), k in (("cfg1_brickwork10_d8", tni.cfg1(), 1), ("cfg3_grid4x5_d8", tni.cfg3(small=True), 8)):
+        n = circ.n_qubits
+        B = 512
+        nets = [tni.amplitude_tn(circ, tni.random_bitstring(n, 8000 + i)) for i in range(B)]
+        hs = [tnsa.tn_build(t) for t in nets]
+        plan = tnsa.tn_plan_create(hs[0], k=k, iterations=200 if k > 1 else 0, steps_per_temp=8, seed=7,
+                                   position=nets[0].qubit if k > 1 else None)
+        con_serial = tnsa.tn_plan_counts(plan)[0]
+        ctx = tnsa.tn_ctx_create(0)
+        b = tnsa.tn_batch_create(ctx, hs, [plan] * B, "c64")
+        for _ in range(3):
+            tnsa.tn_batch_run(b)
+        reps = 10
+        for _ in range(reps):
+            tnsa.tn_batch_run(b)
+        ms = tnsa.tn_batch_kernel_ms(b, reps)
+        mant, e2, st = tnsa.tn_batch_results(b, B)
+        part, psteps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+        tree = [(int(l), int(r)) for l, r, o in psteps]
+        done, dt = oracle_rate(nets, tree, budget_s)
+        errs = []
+        for i in range(min(done, B)):
+            ref = oc.contract_scalar(nets[i], tree)
+            got = complex(mant[i]) * 2.0 ** int(e2[i])
+            errs.append(abs(got - ref) / abs(ref))
+        b.close()
+        ctx.close()
+        out[name] = {"batch": B, "gpu_amps_per_s": B / (ms * 1e-3), "gpu_tflops": B * 8 * con_serial / ms / 1e9,
+                     "oracle_amps_per_s": done / dt, "oracle_cores": host_cores(), "oracle_amplitudes": done,
+                     "max_rel_err_c64_vs_oracle": max(errs) if errs else None, "compared": len(errs),
+                     "con_serial": con_serial}
+    return out
 
 
 def run_ours(args):
@@ -270,6 +360,7 @@ def run_ours(args):
     barrier(ws)
     ms = ev0.elapsed_time(ev1)
     kernel_ms = tnsa.tn_batch_kernel_ms(batch, min(args.steps, 256))
+    class_ms = tnsa.tn_batch_kernel_times(batch, min(args.steps, 256))
     value, sec = replica_throughput(args.steps * flops_per_step / 1e12, ms * 1e-3, ws)
     ms_per_step = 1e3 * sec / args.steps
 
@@ -300,7 +391,20 @@ def run_ours(args):
         return
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_step / (kernel_ms * 1e-3) / 1e9
-    cpu = oracle_sample(nets, budget_s=args.cpu_seconds) if not args.skip_cpu else None
+    sha = kernel_sources_sha()
+    traffic = (TRAFFIC["bytes_per_run"] * B / TRAFFIC["batch"]
+               if TRAFFIC["bytes_per_run"] and TRAFFIC["sources_sha"] == sha else None)
+    per_kernel = {}
+    for cls, key in (("warp_programs", "bytes_warp"), ("block_programs", "bytes_block"), ("tc_gemm", "bytes_tc"),
+                     ("dataflow", "bytes_flow")):
+        t = class_ms[cls]
+        per_kernel[cls] = {"ms": t, "algorithmic_bytes": info[key],
+                           "achieved_gbs": info[key] / (t * 1e-3) / 1e9 if t > 0 and info[key] > 0 else None}
+    cpu = None
+    if not args.skip_cpu:
+        part, psteps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
+        cpu = oracle_sample(nets, [(int(l), int(r)) for l, r, o in psteps], con_serial, budget_s=args.cpu_seconds)
+    others = other_configs(args, tnsa, tni) if not args.skip_cpu else None
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision if args.precision != "bf16" else "bf16-split",
@@ -309,10 +413,11 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                     "amps_per_s": ws * e2e_steps * B / dt, "steps": e2e_steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "contraction kernels of one run (k_warp warp programs, k_local block "
                                    "programs, k_persist dataflow steps), events around all of them",
-                         "kernel_ms": kernel_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
+                         "kernel_ms": kernel_ms, "peak_kind": f"{peak_kind} hbm_gbs", "sources_sha": sha,
+                         "per_kernel": per_kernel},
             "gpu_launches": info["launches"] * args.steps,
             "exec": {"warp_programs": info["n_warp_progs"], "block_programs": info["n_local"],
                      "steps_in_programs": info["n_local_steps"],
@@ -321,7 +426,8 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem},
             "tuning": tuning,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu,
+            "other_configs": others}
     print(json.dumps(line), flush=True)
 
 
@@ -807,10 +913,10 @@ def main():
     ap.add_argument("--queries-per-circuit", type=int, default=16)
     ap.add_argument("--plan-iters", type=int, default=100)
     ap.add_argument("--max-batch", type=int, default=256)
-    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--duration", type=float, default=20.0)
-    ap.add_argument("--warmup-s", type=float, default=3.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--warmup-s", type=float, default=5.0)
     args = ap.parse_args()
     if args.workload == "cfg3" and args.impl == "ours":
         return run_cfg3(args)

@@ -278,6 +278,9 @@ typedef struct {
     int32_t n_local_steps;     /* steps executed inside subtree and warp programs */
     int32_t dyn_smem;          /* dynamic shared memory per block of the contraction kernels */
     int32_t n_warp_progs;      /* warp programs (one warp each) */
+    /* the algorithmic bytes above split by the kernel class that executes each step: warp
+     * programs, block and large programs, tensor-core GEMM, persistent dataflow kernel */
+    double bytes_warp, bytes_block, bytes_tc, bytes_flow;
 } tn_run_info;
 
 /* Compile (net, plan, precision) into a device program: per-step layouts, index maps, kernel

@@ -24,6 +24,9 @@ struct Compiled {
     int32_t dyn_smem = 0;            // largest shared-memory need of a block (or warp) program
     int32_t dyn_big = 0;             // largest shared-memory need of a large program
     double flops = 0, bytes = 0;
+    // algorithmic bytes by the kernel class that executes the step: [0] warp programs, [1] block
+    // and large programs, [2] tensor-core GEMM, [3] dataflow kernel
+    double bytes_cls[4] = {0, 0, 0, 0};
     // by StepKind ([5] = all programs); [6] = steps inside block and large programs; [7] = warp
     // programs, [8] = steps inside warp programs; [9] = large programs
     int32_t counts[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};

@@ -850,6 +850,17 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             chain_len[ti] = chain_len[t.dep0] + 1;
         }
     }
+    // algorithmic bytes by executing kernel class
+    for (int32_t st = 0; st < n - 1; ++st) {
+        const int32_t o = n + st;
+        const Geom &g = geo[st];
+        const double bb = (double)(size[g.a] + size[g.b] + size[o]) * (double)esz;
+        int cls = 3;
+        if (wprog_of[o] >= 0) cls = 0;
+        else if (prog_of[o] >= 0) cls = 1;
+        else if (producer[o] >= 0 && c.steps[producer[o]].kind == STEP_TC) cls = 2;
+        c.bytes_cls[cls] += bb;
+    }
     // packed operand images of the tensor-core steps: after the intermediates, never reused
     {
         size_t img = align_up(c.arena_bytes, 1024);
@@ -1502,6 +1513,10 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         const Compiled &c = b->comp[b->job_comp[i]];
         b->info.flops += c.flops;
         b->info.bytes += c.bytes;
+        b->info.bytes_warp += c.bytes_cls[0];
+        b->info.bytes_block += c.bytes_cls[1];
+        b->info.bytes_tc += c.bytes_cls[2];
+        b->info.bytes_flow += c.bytes_cls[3];
         b->info.n_gather += c.counts[STEP_ROWS];
         b->info.n_tile += c.counts[STEP_TILE];
         b->info.n_dot += c.counts[STEP_DOTP];

@@ -61,7 +61,9 @@ class tn_run_info(ctypes.Structure):
                 ("n_tile", ctypes.c_int32), ("n_dot", ctypes.c_int32), ("n_tc", ctypes.c_int32),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("arena_bytes", ctypes.c_size_t),
                 ("h2d_bytes", ctypes.c_double), ("n_local", ctypes.c_int32), ("n_local_steps", ctypes.c_int32),
-                ("dyn_smem", ctypes.c_int32), ("n_warp_progs", ctypes.c_int32)]
+                ("dyn_smem", ctypes.c_int32), ("n_warp_progs", ctypes.c_int32),
+                ("bytes_warp", ctypes.c_double), ("bytes_block", ctypes.c_double), ("bytes_tc", ctypes.c_double),
+                ("bytes_flow", ctypes.c_double)]
 
     def as_dict(self):
         return {f: (getattr(self, f)) for f, _ in self._fields_}
