@@ -289,16 +289,19 @@ def other_configs(args, tnsa, tni, budget_s=4.0):
         part, psteps, _ = tnsa.tn_plan_export(plan, nets[0].n_tensors)
         tree = [(int(l), int(r)) for l, r, o in psteps]
         done, dt = oracle_rate(nets, tree, budget_s)
-        errs = []
+        errs, mags = [], []
         for i in range(min(done, B)):
             ref = oc.contract_scalar(nets[i], tree)
             got = complex(mant[i]) * 2.0 ** int(e2[i])
             errs.append(abs(got - ref) / abs(ref))
+            mags.append(abs(ref) * 2.0 ** (n / 2))
+        over = [m for e, m in zip(errs, mags) if e > 1e-5]
         b.close()
         ctx.close()
         out[name] = {"batch": B, "gpu_amps_per_s": B / (ms * 1e-3), "gpu_tflops": B * 8 * con_serial / ms / 1e9,
                      "oracle_amps_per_s": done / dt, "oracle_cores": host_cores(), "oracle_amplitudes": done,
                      "max_rel_err_c64_vs_oracle": max(errs) if errs else None, "compared": len(errs),
+                     "over_1e-5": len(over), "largest_|a|*2^(n/2)_over_1e-5": max(over) if over else None,
                      "con_serial": con_serial}
     return out
 
@@ -446,75 +449,135 @@ def _percentiles(lat):
     return float(a[int(0.5 * (len(a) - 1))]), float(a[int(0.99 * (len(a) - 1))])
 
 
+def _oracle_errors(tnsa, models, results, max_n=24, per_model=2, budget_s=60.0):
+    """Largest plain relative error of GPU amplitudes against the oracle (complex128 C contractor
+    along the same plan tree), over up to `per_model` results of every model with at most `max_n`
+    qubits.  results: list of (model index, bits or tensor data, complex amplitude)."""
+    from oracle import contract as oc
+    seen, errs, t0 = {}, [], time.perf_counter()
+    for mi, data, amp in results:
+        net, h, plan, bras, nq = models[mi]
+        if nq > max_n or seen.get(mi, 0) >= per_model or time.perf_counter() - t0 > budget_s:
+            continue
+        seen[mi] = seen.get(mi, 0) + 1
+        part, psteps, _ = tnsa.tn_plan_export(plan, net.n_tensors)
+        tree = [(int(l), int(r)) for l, r, o in psteps]
+        class Q:
+            pass
+        q = Q()
+        q.degrees, q.dims, q.edges = net.degrees, net.dims, net.edges
+        d = np.asarray(net.data, np.float64).copy().view(np.complex128)
+        for t, v in zip(bras, data):
+            off = int(np.sum([np.prod(net.tensors[u].shape) for u in range(t)]))
+            d[off:off + len(v)] = v
+        q.data = d.view(np.float64)
+        ref = oc.contract_scalar(q, tree)
+        errs.append(abs(amp - ref) / abs(ref))
+    return {"max_rel_err": max(errs) if errs else None, "compared": len(errs),
+            "circuits_compared": len(seen), "max_qubits": max_n}
+
+
 def run_cfg4(args):
-    """512 amplitude queries over 32 seeded circuits (16-36 qubits, depth 8-16, 1D and 2D, k in
-    {2, 4, 8}), 16 bitstrings each: all queries through the batching server (grouped launches)
-    against one query at a time through tn_contract in complex64."""
+    """Amplitude queries over 32 seeded circuits (16-36 qubits, depth 8-16, 1D and 2D, k in
+    {2, 4, 8}; 16 bitstrings each, 512 queries): every feasible query in one grouped batch (all
+    jobs' steps in the persistent launches of one recorded CUDA graph), BF16 split and complex64;
+    the same queries through the batching server; and one query at a time through tn_contract in
+    complex64.  Errors against the oracle for the circuits of at most 24 qubits."""
     import torch
     from paper_2507_20667_gb300 import inputs as tni
     from paper_2507_20667_gb300 import tnsa
     ctx = tnsa.tn_ctx_create(0)
     free = torch.cuda.mem_get_info()[0]
-    budget = min(int(0.7 * free), 150 << 30)
-    models, reqs, flops = [], [], {}
+    budget = min(int(0.6 * free), 150 << 30)
+    models, reqs = [], []
     t0 = time.perf_counter()
     for i, (circ, k, xs) in enumerate(tni.cfg4_circuits()):
         net, h, plan, bras = _amp_model(tnsa, tni, circ, k, seed=7, iters=args.plan_iters)
-        models.append((net, h, plan, bras))
+        models.append((net, h, plan, bras, circ.n_qubits))
         for x in xs[:args.queries_per_circuit]:
             reqs.append((i, np.eye(2, dtype=np.complex128)[np.asarray(x)]))
     plan_s = time.perf_counter() - t0
+    # per-query device bytes of each model (a server of the same context compiles it)
+    probe = tnsa.tn_serve_create(ctx, "bf16", hbm_budget_bytes=1 << 20, max_batch=1)
+    job_bytes = [tnsa.tn_serve_model_info(probe, tnsa.tn_serve_register(probe, m[1], m[2]))[0] for m in models]
+    flops_of = [tnsa.tn_serve_model_info(probe, mi)[1] for mi in range(len(models))]
+    probe.close()
+    # the grouped batch takes queries in order while they fit the budget
+    chosen, used = [], 0
+    for qi, (mi, data) in enumerate(reqs):
+        if used + 2 * job_bytes[mi] <= budget:
+            chosen.append(qi)
+            used += 2 * job_bytes[mi]
     out = {}
-    for prec in ("c64", "bf16"):
+    for prec in ("bf16", "c64"):
+        hs = []
+        for qi in chosen:
+            mi, data = reqs[qi]
+            net = models[mi][0]
+            h = tnsa.tn_build(net)
+            for t, v in zip(models[mi][3], data):
+                tnsa.tn_net_set_tensor(h, t, v)
+            hs.append(h)
+        plans = [models[reqs[qi][0]][2] for qi in chosen]
+        b = tnsa.tn_batch_create(ctx, hs, plans, prec)
+        tnsa.tn_batch_run(b)
+        tnsa.tn_batch_results(b, len(hs))
+        reps = 3
+        for _ in range(reps):
+            tnsa.tn_batch_run(b)
+        ms = tnsa.tn_batch_kernel_ms(b, reps)
+        mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+        amps = [complex(m) * 2.0 ** int(e) for m, e in zip(mant, e2)]
+        results = [(reqs[qi][0], reqs[qi][1], amps[j]) for j, qi in enumerate(chosen) if st[j] == 0]
+        fl = sum(flops_of[reqs[qi][0]] for qi in chosen)
+        out[prec] = {"queries": len(chosen), "ms_per_batch": ms, "amps_per_s": len(chosen) / (ms * 1e-3),
+                     "tflops": fl / ms / 1e9, "launches_per_run": tnsa.tn_batch_last_info(b)["launches"],
+                     "graph_replay": True, "tensor_core_steps": tnsa.tn_batch_last_info(b)["n_tc"],
+                     "error_vs_oracle": _oracle_errors(tnsa, models, results)}
+        b.close()
+    # the same queries through the batching server (continuous batching, memory admission)
+    srv = {}
+    for prec in ("bf16", "c64"):
         server = tnsa.tn_serve_create(ctx, prec, hbm_budget_bytes=budget, max_batch=args.max_batch)
-        mids = [tnsa.tn_serve_register(server, h, plan) for (net, h, plan, bras) in models]
-        for m in mids:
-            flops[m] = tnsa.tn_serve_model_info(server, m)[1]
-        tickets = []
+        mids = [tnsa.tn_serve_register(server, m[1], m[2]) for m in models]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for (i, data) in reqs:
-            tickets.append((i, tnsa.tn_serve_submit(server, mids[i], models[i][3], data)))
-        done, rejected, fl = [], 0, 0.0
-        for i, tk in tickets:
-            try:
-                r = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
-                done.append((i, r))
-                fl += flops[mids[i]]
-            except tnsa.TnError as e:
-                if e.status != tnsa.TN_EBUDGET:
-                    raise
-                rejected += 1
+        tickets = [(qi, tnsa.tn_serve_submit(server, mids[reqs[qi][0]], models[reqs[qi][0]][3], reqs[qi][1]))
+                   for qi in chosen]
+        done = []
+        for qi, tk in tickets:
+            mant, e, lat = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
+            done.append((reqs[qi][0], reqs[qi][1], complex(mant) * 2.0 ** e))
         dt = time.perf_counter() - t0
         st = tnsa.tn_serve_get_stats(server)
-        out[prec] = {"amps_per_s": len(done) / dt, "tflops": fl / dt / 1e12, "seconds": dt, "completed": len(done),
-                     "rejected_over_budget": rejected, "launches": st["launches"],
-                     "mean_batch": st["launched_requests"] / max(st["launches"], 1), "results": done}
-        del server
-    # one query at a time, complex64, through tn_contract (each query its own launch)
-    single_dt, single_n = 0.0, 0
-    feasible = {i for i, r in out["c64"]["results"]}
+        srv[prec] = {"queries": len(done), "amps_per_s": len(done) / dt, "seconds": dt, "launches": st["launches"],
+                     "mean_batch": st["launched_requests"] / max(st["launches"], 1),
+                     "error_vs_oracle": _oracle_errors(tnsa, models, done)}
+        server.close()
+    # one query at a time, complex64, through tn_contract (each query its own launches)
     t0 = time.perf_counter()
-    for (i, data) in reqs:
-        if i not in feasible:
-            continue
-        net, h, plan, bras = models[i]
+    single = []
+    for qi in chosen:
+        mi, data = reqs[qi]
+        net, h, plan, bras, nq = models[mi]
         for q, t in enumerate(bras):
             tnsa.tn_net_set_tensor(h, t, data[q])
-        tnsa.tn_contract(ctx, h, plan, "c64")
-        single_n += 1
+        m, e, _ = tnsa.tn_contract(ctx, h, plan, "c64")
+        single.append((mi, data, complex(m) * 2.0 ** e))
     single_dt = time.perf_counter() - t0
-    # the grouped results equal the single ones within the c64 tolerance of the workload
-    line = {"metric": METRIC, "value": out["c64"]["amps_per_s"], "unit": "amps/s", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "512 amplitude queries over 32 seeded circuits (16-36 qubits, depth 8-16, "
-                                   "1D/2D, k in {2,4,8}), grouped launches through the batching server",
+    line = {"metric": METRIC, "value": out["bf16"]["amps_per_s"], "unit": "amps/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-split", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} amplitude queries over 32 seeded circuits (16-36 qubits, depth "
+                                   f"8-16, 1D/2D, k in {{2,4,8}}), {args.queries_per_circuit} per circuit; "
+                                   f"{len(chosen)} fit one grouped batch under {budget / 2**30:.0f} GiB",
+                       "queries_requested": len(reqs), "queries_run": len(chosen),
                        "plan_iterations": args.plan_iters, "planning_seconds": plan_s},
-            "grouped_c64": {k: v for k, v in out["c64"].items() if k != "results"},
-            "grouped_bf16": {k: v for k, v in out["bf16"].items() if k != "results"},
-            "one_at_a_time_c64": {"amps_per_s": single_n / single_dt, "seconds": single_dt, "queries": single_n},
-            "speedup_grouped_vs_one_at_a_time": out["c64"]["amps_per_s"] / (single_n / single_dt)}
+            "grouped_batch_bf16": out["bf16"], "grouped_batch_c64": out["c64"],
+            "server_bf16": srv["bf16"], "server_c64": srv["c64"],
+            "one_at_a_time_c64": {"amps_per_s": len(single) / single_dt, "seconds": single_dt, "queries": len(single),
+                                  "error_vs_oracle": _oracle_errors(tnsa, models, single)},
+            "speedup_grouped_bf16_vs_one_at_a_time_c64": out["bf16"]["amps_per_s"] / (len(single) / single_dt)}
     print(json.dumps(line), flush=True)
 
 
@@ -554,21 +617,22 @@ def run_cfg5(args):
             zz = None
         pool.append((circ, amp, zz))
     plan_s = time.perf_counter() - t0
-    res = {}
-    for prec in ("c64", "bf16"):
+    models = []   # (net, handle, plan, bra or slot ids, n_qubits) as _oracle_errors expects
+
+    def stream(prec, rate, duration, warmup_s, seed):
         server = tnsa.tn_serve_create(ctx, prec, hbm_budget_bytes=budget, max_batch=args.max_batch)
         ids = []
         for circ, amp, zz in pool:
             ids.append((tnsa.tn_serve_register(server, amp[1], amp[2]) if amp else None,
                         tnsa.tn_serve_register(server, zz[1], zz[2]) if zz else None))
-        arr = np.random.default_rng(55)
+        arr = np.random.default_rng(seed)
         sent = []
         unplannable = [0]
 
         def client():
-            t_end = time.perf_counter() + args.duration
+            t_end = time.perf_counter() + duration
             while time.perf_counter() < t_end:
-                time.sleep(arr.exponential(1.0 / args.rate))
+                time.sleep(arr.exponential(1.0 / rate))
                 c = int(arr.integers(0, len(pool)))
                 circ, amp, zz = pool[c]
                 nq = circ.n_qubits
@@ -577,7 +641,9 @@ def run_cfg5(args):
                     if ids[c][0] is None:
                         unplannable[0] += 1
                         continue
-                    tk = tnsa.tn_serve_submit(server, ids[c][0], amp[3], np.eye(2, dtype=np.complex128)[bits])
+                    data = np.eye(2, dtype=np.complex128)[bits]
+                    tk = tnsa.tn_serve_submit(server, ids[c][0], amp[3], data)
+                    sent.append((time.perf_counter(), tk, ("amp", c, data)))
                 else:
                     i, j = arr.choice(nq, 2, replace=False)
                     if ids[c][1] is None:
@@ -585,40 +651,74 @@ def run_cfg5(args):
                         continue
                     data = np.array([tni.Z_MAT if q in (i, j) else np.eye(2) for q in range(nq)], np.complex128)
                     tk = tnsa.tn_serve_submit(server, ids[c][1], zz[3], data)
-                sent.append((time.perf_counter(), tk))
+                    sent.append((time.perf_counter(), tk, ("zz", c, (int(i), int(j)))))
 
         import threading
         th = threading.Thread(target=client)
         t_start = time.perf_counter()
         th.start()
         th.join()
-        lat, rejected, done = [], 0, 0
-        for ts, tk in sent:
+        lat, rejected, done, results = [], 0, 0, []
+        for ts, tk, what in sent:
             try:
                 r = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
-                if ts - t_start >= args.warmup_s:
+                if ts - t_start >= warmup_s:
                     lat.append(r[2])
                 done += 1
+                results.append((what, complex(r[0]) * 2.0 ** r[1]))
             except tnsa.TnError as e:
                 if e.status != tnsa.TN_EBUDGET:
                     raise
                 rejected += 1
         t_total = time.perf_counter() - t_start
         st = tnsa.tn_serve_get_stats(server)
+        server.close()
         p50, p99 = _percentiles(lat)
-        res[prec] = {"requests": len(sent) + unplannable[0], "completed": done,
-                     "rejected_over_budget": rejected, "refused_plan_above_2e120": unplannable[0],
-                     "p50_ms": None if p50 is None else 1e3 * p50, "p99_ms": None if p99 is None else 1e3 * p99,
-                     "amps_per_s": done / t_total, "launches": st["launches"],
-                     "mean_batch": st["launched_requests"] / max(st["launches"], 1),
-                     "max_in_flight": st["max_in_flight"]}
-        del server
+        return {"rate_per_s": rate, "duration_s": duration, "requests": len(sent) + unplannable[0],
+                "completed": done, "rejected_over_budget": rejected, "refused_plan_above_2e120": unplannable[0],
+                "p50_ms": None if p50 is None else 1e3 * p50, "p99_ms": None if p99 is None else 1e3 * p99,
+                "amps_per_s": done / t_total, "launches": st["launches"],
+                "mean_batch": st["launched_requests"] / max(st["launches"], 1),
+                "max_in_flight": st["max_in_flight"]}, results
+
+    def errors(results):
+        """Amplitudes of circuits of at most 24 qubits against the oracle along the same plan;
+        <Z_i Z_j> of circuits of at most 16 qubits against the state vector (error on the
+        scale ||Z_i Z_j|| = 1)."""
+        from oracle import statevector as sv
+        amp_res, zz_errs, seen = [], [], {}
+        for what, val in results:
+            kind, c, data = what
+            circ, amp, zz = pool[c]
+            if kind == "amp" and amp is not None:
+                if c not in seen:
+                    seen[c] = len(models)
+                    models.append((amp[0], amp[1], amp[2], amp[3], circ.n_qubits))
+                amp_res.append((seen[c], data, val))
+            elif kind == "zz" and circ.n_qubits <= 16 and len(zz_errs) < 40:
+                zz_errs.append(abs(val - sv.zz_expectation(circ, *data)))
+        e = _oracle_errors(tnsa, models, amp_res, per_model=2, budget_s=60.0)
+        e["zz_max_abs_err"] = max(zz_errs) if zz_errs else None
+        e["zz_compared"] = len(zz_errs)
+        return e
+
+    res = {}
+    for prec in ("c64", "bf16"):
+        r, results = stream(prec, args.rate, args.duration, args.warmup_s, 55)
+        r["error_vs_oracle"] = errors(results)
+        # service latency without queueing: a stream at 80 % of the throughput the loaded run
+        # sustained (the requested rate, if that is lower)
+        sustain = min(args.rate, 0.8 * r["amps_per_s"])
+        r2, _ = stream(prec, sustain, min(args.duration, 20.0), min(args.warmup_s, 3.0), 56)
+        r["at_sustainable_rate"] = r2
+        res[prec] = r
     line = {"metric": METRIC, "value": res["bf16"]["amps_per_s"], "unit": "amps/s", "n_gpus": 1, "steps": 1,
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split",
             "data": "synthetic",
             "config": {"workload": f"serving: Poisson {args.rate}/s amplitude and <Z_i Z_j> requests, "
                                    f"{args.pool} seeded circuits of 12-48 qubits depth 8-20 (1D/2D), "
-                                   f"{args.duration}s stream, {budget / 2**30:.0f} GiB budget",
+                                   f"{args.duration}s stream after a {args.warmup_s}s warm-up, "
+                                   f"{budget / 2**30:.0f} GiB budget",
                        "planning_seconds": plan_s, "latency_warmup_s": args.warmup_s},
             "bf16_split": res["bf16"], "c64": res["c64"]}
     print(json.dumps(line), flush=True)

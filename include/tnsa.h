@@ -240,7 +240,12 @@ tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
  *                    job's status becomes TN_ETIMEOUT, and a launch-wide abort flag makes every
  *                    later wait of the launch give up at once, so the launch ends.  The context
  *                    stays usable.
- * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000} (large programs off: on the 24-qubit brickwork
+ *   graph_capture    1: a batch (or program) in the persistent mode records one run -- the reset,
+ *                    the leaf conversion and every launch -- into a CUDA graph at creation and
+ *                    replays it (one graph launch per run); its per-class kernel times
+ *                    (tn_batch_kernel_times) are then those of the last replay.  0: the launches
+ *                    are issued one by one every run.
+ * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000, 1} (large programs off: on the 24-qubit brickwork
  * benchmark they measured slower than running fan-in chains as dataflow steps).
  * Errors: TN_EINVAL. */
 typedef struct {
@@ -250,6 +255,7 @@ typedef struct {
     int32_t tc_min_m, tc_min_n, tc_min_k;
     int32_t rows_chains;
     int32_t wait_limit_us;
+    int32_t graph_capture;
 } tn_exec_config;
 tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
 tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);

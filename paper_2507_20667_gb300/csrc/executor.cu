@@ -37,7 +37,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000};   // programs, tensor-core thresholds, wait limit
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1};   // programs, TC thresholds, wait limit, graphs
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -117,6 +117,12 @@ struct tn_batch {
     // phase the pack, GEMM and dataflow launches (a slot whose launch is empty records no time)
     static constexpr int kRing = 256;
     std::vector<cudaEvent_t> kev[kRing];
+    // persistent runs replayed from a CUDA graph (tn_exec_config.graph_capture): the graph holds
+    // the reset, the leaf conversion and every launch of a run, with its own per-slot events
+    // (gev, the last replay's); the ring then holds only a start and an end event per run
+    cudaGraphExec_t pgexec = nullptr;
+    std::vector<cudaEvent_t> gev;
+    bool replay = false;
     int64_t runs = 0;
     // pending tensor updates (tn_batch_set_tensors): headers {dst element offset, count, src
     // element offset} and complex128 values, staged in pinned memory, applied on the device
@@ -1096,6 +1102,66 @@ void set_phase_ranges(tn_batch *b, const std::vector<int32_t> &ph) {
 // The stage of the last enqueue_run that failed (for the error message).
 thread_local const char *t_enqueue_stage = "";
 
+// Enough events in `ev` for one persistent run: a start event and one after every launch slot.
+cudaError_t ensure_events(std::vector<cudaEvent_t> &ev, size_t n) {
+    while (ev.size() < n) {
+        cudaEvent_t x = nullptr;
+        const cudaError_t e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return e;
+        ev.push_back(x);
+    }
+    return cudaSuccess;
+}
+
+// The contraction kernels of one persistent run, ev[0] recorded first and one event after every
+// launch slot: warp programs, block and large programs, then per phase the pack, GEMM and
+// dataflow launches.
+cudaError_t enqueue_persistent(tn_batch *b, cudaStream_t st, std::vector<cudaEvent_t> &ev, bool capturing) {
+    // inside a stream capture an event becomes a graph event-record node only when recorded as
+    // an external event
+    const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaError_t e = cudaSuccess;
+    e = ensure_events(ev, 3 + 3 * b->phases.size());
+    if (e != cudaSuccess) return e;
+    size_t k = 0;
+    e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+    if (e == cudaSuccess) {
+        t_enqueue_stage = "warp programs";
+        e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, 0, 0, b->dyn_smem, b->dyn_big,
+                         b->d_prof, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+    if (e == cudaSuccess) {
+        t_enqueue_stage = "subtree programs";
+        e = launch_local(b->c128, b->d_jobs, b->d_local + b->n_warp_items, 0, b->n_block_items, b->n_big_items,
+                         b->dyn_smem, b->dyn_big, b->d_prof, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+    const bool tf32 = b->prec == TN_TF32_SPLIT;
+    for (size_t p = 0; e == cudaSuccess && p < b->phases.size(); ++p) {
+        const tn_batch::Phase &ph = b->phases[p];
+        uint32_t *cnt = b->d_counter + 3 * p;
+        if (ph.n_pack > 0) {
+            t_enqueue_stage = "tensor-core operand packing";
+            e = launch_tc_pack(tf32, b->d_jobs, b->d_pack + ph.pack0, ph.n_pack, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+        if (e == cudaSuccess && ph.n_gemm > 0) {
+            t_enqueue_stage = "tensor-core GEMM";
+            e = launch_tc_gemm(tf32, b->d_jobs, b->d_gemm + ph.gemm0, ph.n_gemm, reinterpret_cast<int32_t *>(cnt + 2),
+                               b->wait_ns, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+        if (e == cudaSuccess && ph.n_work > 0) {
+            t_enqueue_stage = "dataflow kernel";
+            e = launch_persistent(b->c128, b->d_jobs, b->d_work + ph.work0, ph.n_work, cnt, b->grid, b->wait_ns,
+                                  b->d_prof, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[k++], st, rec_flags);
+    }
+    return e;
+}
+
 cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
     // a non-sticky error left by an earlier runtime call of this thread (another library's, say)
     // would otherwise be reported by the launch checks below
@@ -1108,50 +1174,7 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
     }
     if (e != cudaSuccess) return e;
     if (b->mode == TN_EXEC_PERSISTENT) {
-        std::vector<cudaEvent_t> &ev = b->kev[b->runs % tn_batch::kRing];
-        const size_t n_ev = 3 + 3 * b->phases.size();
-        while (ev.size() < n_ev) {
-            cudaEvent_t x = nullptr;
-            e = cudaEventCreate(&x);
-            if (e != cudaSuccess) return e;
-            ev.push_back(x);
-        }
-        size_t k = 0;
-        e = cudaEventRecord(ev[k++], st);
-        if (e == cudaSuccess) {
-            t_enqueue_stage = "warp programs";
-            e = launch_local(b->c128, b->d_jobs, b->d_local, b->n_warp_items, 0, 0, b->dyn_smem, b->dyn_big,
-                             b->d_prof, st);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
-        if (e == cudaSuccess) {
-            t_enqueue_stage = "subtree programs";
-            e = launch_local(b->c128, b->d_jobs, b->d_local + b->n_warp_items, 0, b->n_block_items, b->n_big_items,
-                             b->dyn_smem, b->dyn_big, b->d_prof, st);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
-        const bool tf32 = b->prec == TN_TF32_SPLIT;
-        for (size_t p = 0; e == cudaSuccess && p < b->phases.size(); ++p) {
-            const tn_batch::Phase &ph = b->phases[p];
-            uint32_t *cnt = b->d_counter + 3 * p;
-            if (ph.n_pack > 0) {
-                t_enqueue_stage = "tensor-core operand packing";
-                e = launch_tc_pack(tf32, b->d_jobs, b->d_pack + ph.pack0, ph.n_pack, st);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
-            if (e == cudaSuccess && ph.n_gemm > 0) {
-                t_enqueue_stage = "tensor-core GEMM";
-                e = launch_tc_gemm(tf32, b->d_jobs, b->d_gemm + ph.gemm0, ph.n_gemm, reinterpret_cast<int32_t *>(cnt + 2),
-                                   b->wait_ns, st);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
-            if (e == cudaSuccess && ph.n_work > 0) {
-                t_enqueue_stage = "dataflow kernel";
-                e = launch_persistent(b->c128, b->d_jobs, b->d_work + ph.work0, ph.n_work, cnt, b->grid, b->wait_ns,
-                                      b->d_prof, st);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(ev[k++], st);
-        }
+        e = enqueue_persistent(b, st, b->kev[b->runs % tn_batch::kRing], false);
         b->runs++;
     } else {
         const bool tf32 = b->prec == TN_TF32_SPLIT;
@@ -1176,6 +1199,37 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
     return e;
 }
 
+// Capture one persistent run -- reset, leaf conversion, all launches with the graph's own events
+// -- into b->pgexec (replaced if present).
+tn_status record_persistent_graph(tn_batch *b) {
+    cudaStream_t st = b->ctx->stream;
+    if (b->pgexec) {
+        CK(cudaStreamSynchronize(st));
+        cudaGraphExecDestroy(b->pgexec);
+        b->pgexec = nullptr;
+    }
+    cudaError_t err = ensure_events(b->gev, 3 + 3 * b->phases.size());
+    if (err != cudaSuccess) return fail(TN_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(err));
+    (void)cudaGetLastError();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    err = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
+    if (err == cudaSuccess) err = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+    if (err == cudaSuccess) err = enqueue_persistent(b, st, b->gev, true);
+    for (int32_t jb = 0; err == cudaSuccess && jb < b->n_jobs; ++jb)
+        if (b->comp[b->job_comp[jb]].n == 1) err = launch_finish_leaf(b->c128, b->jobs[jb], st);
+    cudaGraph_t g = nullptr;
+    cudaError_t err2 = cudaStreamEndCapture(st, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(TN_ECUDA, std::string("recording the run: ") + cudaGetErrorString(err));
+    }
+    if (err2 != cudaSuccess) return fail(TN_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(err2));
+    err = cudaGraphInstantiate(&b->pgexec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return fail(TN_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(err));
+    return TN_OK;
+}
+
 tn_status record_graph(tn_batch *b) {
     cudaStream_t st = b->ctx->stream;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -1196,6 +1250,9 @@ tn_status record_graph(tn_batch *b) {
 void batch_destroy(tn_batch *b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->pgexec) cudaGraphExecDestroy(b->pgexec);
+    for (cudaEvent_t e : b->gev)
+        if (e) cudaEventDestroy(e);
     for (auto &list : b->kev)
         for (cudaEvent_t e : list)
             if (e) cudaEventDestroy(e);
@@ -1502,6 +1559,8 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
     tn_status s = TN_OK;
     for (int32_t i = 0; i < n && s == TN_OK; ++i) s = upload_leaves(b, i);
     if (s == TN_OK && b->mode == TN_EXEC_GRAPH) s = record_graph(b);
+    b->replay = b->mode == TN_EXEC_PERSISTENT && ctx->cfg.graph_capture != 0;
+    if (s == TN_OK && b->replay) s = record_persistent_graph(b);
     if (s == TN_OK) {
         e = cudaStreamSynchronize(st);   // the uploads read host buffers that must stay alive
         if (e != cudaSuccess) s = fail(TN_ECUDA, cudaGetErrorString(e));
@@ -1600,8 +1659,16 @@ tn_status batch_run(tn_batch *b, void *d_results) {
         if (s != TN_OK) return s;
     }
     CK(cudaEventRecord(b->ev0, st));
-    if (b->mode == TN_EXEC_GRAPH) CK(cudaGraphLaunch(b->gexec, st));
-    else {
+    if (b->mode == TN_EXEC_GRAPH) {
+        CK(cudaGraphLaunch(b->gexec, st));
+    } else if (b->replay) {
+        std::vector<cudaEvent_t> &ev = b->kev[b->runs % tn_batch::kRing];
+        CK(ensure_events(ev, 2));
+        CK(cudaEventRecord(ev[0], st));
+        CK(cudaGraphLaunch(b->pgexec, st));
+        CK(cudaEventRecord(ev[1], st));
+        b->runs++;
+    } else {
         const cudaError_t e = enqueue_run(b, st);
         if (e != cudaSuccess)
             return fail(TN_ECUDA, std::string("run (") + t_enqueue_stage + "): " + cudaGetErrorString(e));
@@ -1765,6 +1832,7 @@ tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
     c->cfg.big_programs = cfg->big_programs ? 1 : 0;
     c->cfg.warp_programs = cfg->warp_programs ? 1 : 0;
     c->cfg.rows_chains = cfg->rows_chains ? 1 : 0;
+    c->cfg.graph_capture = cfg->graph_capture ? 1 : 0;
     return TN_OK;
 }
 
@@ -1867,6 +1935,7 @@ tn_status tn_batch_set_profiling(tn_batch *b, int32_t on) {
         cudaFree(b->d_prof);
         b->d_prof = nullptr;
     }
+    if (b->replay) return record_persistent_graph(b);   // the launches' profiling pointer changed
     return TN_OK;
 }
 
@@ -1916,6 +1985,7 @@ tn_status tn_batch_debug_hold(tn_batch *b, int32_t job, int32_t step) {
     b->n_work = (int64_t)kept.size();
     set_phase_ranges(b, kept_phase);
     b->held.swap(held);
+    if (b->replay) return record_persistent_graph(b);   // the launches' work counts changed
     return TN_OK;
 }
 
@@ -1963,7 +2033,7 @@ tn_status tn_batch_kernel_ms(const tn_batch *b, int32_t n_runs, double *mean_ms)
         return fail(TN_EINVAL, "n_runs must be in [1, min(256, runs so far)]");
     CK(cudaSetDevice(b->ctx->device));
     double total = 0;
-    const size_t n_ev = 3 + 3 * b->phases.size();
+    const size_t n_ev = b->replay ? 2 : 3 + 3 * b->phases.size();
     for (int64_t r = b->runs - n_runs; r < b->runs; ++r) {
         const std::vector<cudaEvent_t> &ev = b->kev[r % tn_batch::kRing];
         if (ev.size() < n_ev) return fail(TN_EINVAL, "no timing of that run");
@@ -1984,8 +2054,9 @@ tn_status tn_batch_kernel_times(const tn_batch *b, int32_t n_runs, double *mean_
     CK(cudaSetDevice(b->ctx->device));
     double acc[5] = {0, 0, 0, 0, 0};
     const size_t n_ev = 3 + 3 * b->phases.size();
+    if (b->replay) n_runs = 1;   // the graph's events time its last replay
     for (int64_t r = b->runs - n_runs; r < b->runs; ++r) {
-        const std::vector<cudaEvent_t> &ev = b->kev[r % tn_batch::kRing];
+        const std::vector<cudaEvent_t> &ev = b->replay ? b->gev : b->kev[r % tn_batch::kRing];
         if (ev.size() < n_ev) return fail(TN_EINVAL, "no timing of that run");
         CK(cudaEventSynchronize(ev[n_ev - 1]));
         for (size_t i = 0; i + 1 < n_ev; ++i) {
@@ -2109,7 +2180,10 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
     int32_t best = -1;
     tn_status first_err = TN_OK;
     std::string first_msg;
-    for (tn_exec_config &c : cands) c.wait_limit_us = saved.wait_limit_us;
+    for (tn_exec_config &c : cands) {
+        c.wait_limit_us = saved.wait_limit_us;
+        c.graph_capture = saved.graph_capture;
+    }
     for (size_t i = 0; i < cands.size(); ++i) {
         ctx->cfg = cands[i];
         tn_batch *b = nullptr;

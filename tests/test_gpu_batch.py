@@ -172,3 +172,29 @@ def test_context_freed_before_its_batch(tnsa):
     assert st[0] == 0
     check(complex(mant[0]) * 2.0 ** int(e2[0]), sv.amplitude(circ, x), TOL["c64"])
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "bf16"])
+def test_graph_replay_equals_direct_launches(tnsa, prec):
+    """The default persistent path replays one recorded CUDA graph per run (reset, leaf conversion,
+    programs, and per dependency phase the tensor-core pack and GEMM launches and the dataflow
+    launch); issuing the same launches one by one gives the same bits."""
+    circ, _ = tni.cfg3(small=True)
+    nets = [tni.amplitude_tn(circ, tni.random_bitstring(20, 600 + i)) for i in range(16)]
+    hs = [tnsa.tn_build(n) for n in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=8, iterations=100, seed=7, position=nets[0].qubit)
+    out = {}
+    for graph in (1, 0):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_config(ctx, graph_capture=graph)
+        b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), prec)
+        for _ in range(3):
+            tnsa.tn_batch_run(b)
+        mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+        assert (st == 0).all()
+        times = tnsa.tn_batch_kernel_times(b, 2)
+        assert tnsa.tn_batch_kernel_ms(b, 3) > 0 and times["dataflow"] > 0
+        if prec == "bf16":
+            assert tnsa.tn_batch_last_info(b)["n_tc"] > 0 and times["tc_gemm"] > 0
+        out[graph] = (mant.view(np.uint64).copy(), e2.copy())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
