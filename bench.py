@@ -502,39 +502,52 @@ def run_cfg4(args):
     job_bytes = [tnsa.tn_serve_model_info(probe, tnsa.tn_serve_register(probe, m[1], m[2]))[0] for m in models]
     flops_of = [tnsa.tn_serve_model_info(probe, mi)[1] for mi in range(len(models))]
     probe.close()
-    # the grouped batch takes queries in order while they fit the budget
-    chosen, used = [], 0
-    for qi, (mi, data) in enumerate(reqs):
-        if used + 2 * job_bytes[mi] <= budget:
-            chosen.append(qi)
-            used += 2 * job_bytes[mi]
+    # every query whose job fits the budget on its own runs; the queries are grouped, in order of
+    # their per-job bytes, into as few batches as the budget allows (each batch one graph replay)
+    chosen = [qi for qi, (mi, data) in enumerate(reqs) if 2 * job_bytes[mi] <= budget]
+    refused = len(reqs) - len(chosen)
+    chosen.sort(key=lambda qi: (job_bytes[reqs[qi][0]], qi))
+    groups, cur, used = [], [], 0
+    for qi in chosen:
+        jb = 2 * job_bytes[reqs[qi][0]]
+        if cur and used + jb > budget:
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append(qi)
+        used += jb
+    if cur:
+        groups.append(cur)
     out = {}
     for prec in ("bf16", "c64"):
-        hs = []
-        for qi in chosen:
-            mi, data = reqs[qi]
-            net = models[mi][0]
-            h = tnsa.tn_build(net)
-            for t, v in zip(models[mi][3], data):
-                tnsa.tn_net_set_tensor(h, t, v)
-            hs.append(h)
-        plans = [models[reqs[qi][0]][2] for qi in chosen]
-        b = tnsa.tn_batch_create(ctx, hs, plans, prec)
-        tnsa.tn_batch_run(b)
-        tnsa.tn_batch_results(b, len(hs))
-        reps = 3
-        for _ in range(reps):
+        total_ms, results, n_tc, launches = 0.0, [], 0, 0
+        for grp in groups:
+            hs = []
+            for qi in grp:
+                mi, data = reqs[qi]
+                h = tnsa.tn_build(models[mi][0])
+                for t, v in zip(models[mi][3], data):
+                    tnsa.tn_net_set_tensor(h, t, v)
+                hs.append(h)
+            plans = [models[reqs[qi][0]][2] for qi in grp]
+            b = tnsa.tn_batch_create(ctx, hs, plans, prec)
             tnsa.tn_batch_run(b)
-        ms = tnsa.tn_batch_kernel_ms(b, reps)
-        mant, e2, st = tnsa.tn_batch_results(b, len(hs))
-        amps = [complex(m) * 2.0 ** int(e) for m, e in zip(mant, e2)]
-        results = [(reqs[qi][0], reqs[qi][1], amps[j]) for j, qi in enumerate(chosen) if st[j] == 0]
+            tnsa.tn_batch_results(b, len(hs))
+            reps = 2
+            for _ in range(reps):
+                tnsa.tn_batch_run(b)
+            total_ms += tnsa.tn_batch_kernel_ms(b, reps)
+            mant, e2, st = tnsa.tn_batch_results(b, len(hs))
+            info = tnsa.tn_batch_last_info(b)
+            n_tc += info["n_tc"]
+            launches += info["launches"]
+            results += [(reqs[qi][0], reqs[qi][1], complex(mant[j]) * 2.0 ** int(e2[j]))
+                        for j, qi in enumerate(grp) if st[j] == 0]
+            b.close()
         fl = sum(flops_of[reqs[qi][0]] for qi in chosen)
-        out[prec] = {"queries": len(chosen), "ms_per_batch": ms, "amps_per_s": len(chosen) / (ms * 1e-3),
-                     "tflops": fl / ms / 1e9, "launches_per_run": tnsa.tn_batch_last_info(b)["launches"],
-                     "graph_replay": True, "tensor_core_steps": tnsa.tn_batch_last_info(b)["n_tc"],
+        out[prec] = {"queries": len(chosen), "batches": len(groups), "ms_all_batches": total_ms,
+                     "amps_per_s": len(chosen) / (total_ms * 1e-3), "tflops": fl / total_ms / 1e9,
+                     "launches_per_run": launches, "graph_replay": True, "tensor_core_steps": n_tc,
                      "error_vs_oracle": _oracle_errors(tnsa, models, results)}
-        b.close()
     # the same queries through the batching server (continuous batching, memory admission)
     srv = {}
     for prec in ("bf16", "c64"):
@@ -570,8 +583,9 @@ def run_cfg4(args):
             "dtype": "bf16-split", "data": "synthetic",
             "config": {"workload": f"{len(reqs)} amplitude queries over 32 seeded circuits (16-36 qubits, depth "
                                    f"8-16, 1D/2D, k in {{2,4,8}}), {args.queries_per_circuit} per circuit; "
-                                   f"{len(chosen)} fit one grouped batch under {budget / 2**30:.0f} GiB",
-                       "queries_requested": len(reqs), "queries_run": len(chosen),
+                                   f"{len(chosen)} feasible in {len(groups)} grouped batches under "
+                                   f"{budget / 2**30:.0f} GiB, {refused} refused (one job above the budget)",
+                       "queries_requested": len(reqs), "queries_run": len(chosen), "queries_refused": refused,
                        "plan_iterations": args.plan_iters, "planning_seconds": plan_s},
             "grouped_batch_bf16": out["bf16"], "grouped_batch_c64": out["c64"],
             "server_bf16": srv["bf16"], "server_c64": srv["c64"],
@@ -630,7 +644,7 @@ def run_cfg5(args):
         unplannable = [0]
 
         def client():
-            t_end = time.perf_counter() + duration
+            t_end = time.perf_counter() + warmup_s + duration
             while time.perf_counter() < t_end:
                 time.sleep(arr.exponential(1.0 / rate))
                 c = int(arr.integers(0, len(pool)))
@@ -658,26 +672,40 @@ def run_cfg5(args):
         t_start = time.perf_counter()
         th.start()
         th.join()
-        lat, rejected, done, results = [], 0, 0, []
+        # drain: poll until every request completed or the drain deadline passed; a request still
+        # open then has a latency of at least its wait so far (censored)
+        t_stream_end = time.perf_counter()
+        deadline = t_stream_end + args.drain_s
+        lat, rejected, done, results, open_, t_last = [], 0, 0, [], 0, t_stream_end
         for ts, tk, what in sent:
             try:
-                r = tnsa.tn_serve_poll(server, tk, timeout_s=600.0)
-                if ts - t_start >= warmup_s:
-                    lat.append(r[2])
-                done += 1
-                results.append((what, complex(r[0]) * 2.0 ** r[1]))
+                r = tnsa.tn_serve_poll(server, tk, timeout_s=max(0.0, deadline - time.perf_counter()))
             except tnsa.TnError as e:
                 if e.status != tnsa.TN_EBUDGET:
                     raise
                 rejected += 1
-        t_total = time.perf_counter() - t_start
+                continue
+            if r is None:
+                open_ += 1
+                if ts - t_start >= warmup_s:
+                    lat.append(float("inf"))
+                continue
+            t_last = time.perf_counter()
+            if ts - t_start >= warmup_s:
+                lat.append(r[2])
+            done += 1
+            results.append((what, complex(r[0]) * 2.0 ** r[1]))
+        t_total = t_last - t_start
         st = tnsa.tn_serve_get_stats(server)
         server.close()
         p50, p99 = _percentiles(lat)
+        fmt = lambda p: None if p is None else (1e3 * p if math.isfinite(p) else
+                                                f"> {1e3 * (deadline - t_start):.0f} (censored at the drain deadline)")
         return {"rate_per_s": rate, "duration_s": duration, "requests": len(sent) + unplannable[0],
-                "completed": done, "rejected_over_budget": rejected, "refused_plan_above_2e120": unplannable[0],
-                "p50_ms": None if p50 is None else 1e3 * p50, "p99_ms": None if p99 is None else 1e3 * p99,
-                "amps_per_s": done / t_total, "launches": st["launches"],
+                "completed": done, "open_at_deadline": open_, "rejected_over_budget": rejected,
+                "refused_plan_above_2e120": unplannable[0],
+                "p50_ms": fmt(p50), "p99_ms": fmt(p99),
+                "amps_per_s": done / max(t_total, 1e-9), "launches": st["launches"],
                 "mean_batch": st["launched_requests"] / max(st["launches"], 1),
                 "max_in_flight": st["max_in_flight"]}, results
 
@@ -708,7 +736,7 @@ def run_cfg5(args):
         r["error_vs_oracle"] = errors(results)
         # service latency without queueing: a stream at 80 % of the throughput the loaded run
         # sustained (the requested rate, if that is lower)
-        sustain = min(args.rate, 0.8 * r["amps_per_s"])
+        sustain = max(0.5, min(args.rate, 0.8 * r["amps_per_s"]))
         r2, _ = stream(prec, sustain, min(args.duration, 20.0), min(args.warmup_s, 3.0), 56)
         r["at_sustainable_rate"] = r2
         res[prec] = r
@@ -768,17 +796,47 @@ def run_cfg3(args):
         errs = []
         for i in check:
             got = complex(mant[i]) * 2.0 ** int(e2[i])
-            errs.append(abs(got - refs[i]) / max(abs(refs[i]), 2.0 ** (-n / 2)))
+            errs.append(abs(got - refs[i]) / abs(refs[i]))
         rows[prec] = {"ms_per_step": ms, "amps_per_s": B / (ms * 1e-3), "tflops": B * 8.0 * con_serial / (ms * 1e-3) / 1e12,
                       "max_err_vs_oracle": max(errs), "status_ok": bool((st == 0).all()),
                       "tensor_core_steps": info["n_tc"], "launches": info["launches"]}
         b.close()
         ctx.close()
-    big, bh = tni.amplitude_tn(tni.cfg3()[0], tni.cfg3()[1]), None
+    # the full-size 5x8 depth-12 grid: its plan is sliced (Section 4.1) to a per-slice memory that
+    # fits a batch of slices on the device; a sample of slices is contracted and timed, and the
+    # time of all slices projected from it
+    big = tni.amplitude_tn(tni.cfg3()[0], tni.cfg3()[1])
     bh = tnsa.tn_build(big)
     bplan = tnsa.tn_plan_create(bh, k=8, iterations=args.plan_iters, steps_per_temp=8, seed=7,
                                 position=big.qubit)
-    _, _, bmem = tnsa.tn_plan_counts(bplan)
+    btotal, bcrit, bmem = tnsa.tn_plan_counts(bplan)
+    sl = tnsa.tn_plan_slice(bh, bplan, 1 << 26, max_edges=96)
+    full = {"mem_elements": bmem, "con_serial": btotal, "con_dist": bcrit, "fits_hbm_unsliced": bmem * 8 < 250e9,
+            "sliced_edges": len(sl["edges"]), "n_slices": sl["n_slices"], "slice_mem_elements": sl["slice_mem"],
+            "slice_con": sl["slice_con"], "total_con_sliced": sl["total_con"],
+            "redundant_ops_ratio": sl["total_con"] / max(btotal, 1)}
+    if sl["slice_mem"] <= (1 << 26) and sl["n_slices"] <= (1 << 40):
+        ctx = tnsa.tn_ctx_create(0, stream=stream.cuda_stream)
+        sample = int(min(sl["n_slices"], 64))
+        try:
+            tnsa.tn_contract_sliced(ctx, bh, bplan, sl["edges"], "bf16", max_jobs=32, slice_count=min(sample, 32))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tnsa.tn_contract_sliced(ctx, bh, bplan, sl["edges"], "bf16", max_jobs=32, first_slice=0,
+                                    slice_count=sample)
+            dt = time.perf_counter() - t0
+            full.update({"timed_slices": sample, "seconds_per_slice": dt / sample,
+                         "projected_seconds_all_slices": dt / sample * sl["n_slices"],
+                         "sliced_tflops": sample * 8.0 * sl["slice_con"] / dt / 1e12})
+        except tnsa.TnError as e:
+            full["sample_error"] = str(e)
+        ctx.close()
+    else:
+        # too many slices to sample: the projection uses the BF16 throughput of the 4x5 instance
+        rate = rows["bf16"]["tflops"] * 1e12
+        full.update({"timed_slices": 0, "projection_rate_tflops": rows["bf16"]["tflops"],
+                     "projected_seconds_all_slices": 8.0 * sl["total_con"] / rate,
+                     "projected_seconds_unsliced_if_it_fit": 8.0 * btotal / rate})
     line = {"metric": METRIC, "value": rows["bf16"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-split", "data": "synthetic",
@@ -786,7 +844,7 @@ def run_cfg3(args):
                                    "precision sweep with the error against the complex128 oracle",
                        "plan": {"con_serial": con_serial, "con_dist": con_dist, "mem": mem}},
             "precisions": rows,
-            "full_size_5x8_depth12": {"mem_elements": bmem, "fits_hbm": bmem * 8 < 250e9}}
+            "full_size_5x8_depth12": full}
     print(json.dumps(line), flush=True)
 
 
@@ -1017,6 +1075,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--warmup-s", type=float, default=5.0)
+    ap.add_argument("--drain-s", type=float, default=60.0)
     args = ap.parse_args()
     if args.workload == "cfg3" and args.impl == "ours":
         return run_cfg3(args)

@@ -105,6 +105,11 @@ typedef struct {
     const int32_t *position;    /* TN_INIT_QUBIT_BLOCK: [n_tensors] position hint of each tensor,
                                    >= 0 (for a circuit: the qubit the tensor sits on, a 2-qubit
                                    gate on its lower qubit).  Read during tn_plan_create only. */
+    int32_t fanin_device;       /* >= 0: for k > 4 the RandomGreedy fan-in trees of every annealing
+                                   step are evaluated on this CUDA device, the chains advancing in
+                                   lockstep with one batched launch per step (the plan is the same
+                                   as with host evaluation); -1: on the host */
+    int32_t pad1;
 } tn_plan_opts;
 
 /* Initial partition of the annealing (Section 4.2 starts from a hypergraph partitioner's cut; this
@@ -119,7 +124,7 @@ typedef enum { TN_INIT_BFS = 0, TN_INIT_QUBIT_BLOCK = 1, TN_INIT_GIVEN = 2 } tn_
 
 /* Fill opts with the defaults: k = 1, DIRECTED, T0 = 0.1, Tf = 0.001, N = 8, p = 1,
  * iterations = 200, RestartThreshold = 50, 32 fan-in samples, seed = 0, initial = TN_INIT_BFS,
- * initial_part = position = NULL. */
+ * initial_part = position = NULL, fanin_device = -1. */
 void tn_plan_opts_default(tn_plan_opts *opts);
 
 /* Plan a contraction (Section 4): initial partition, simulated-annealing refinement
@@ -174,6 +179,22 @@ tn_status tn_plan_compile_steps(const tn_net *net, const tn_plan *plan, tn_preci
 tn_status tn_plan_counts(const tn_plan *plan, tn_u128 *total_ops, tn_u128 *crit_ops,
                          tn_u128 *mem_elems);
 
+/* EvaluateState (Section 4.4) for many candidate states at once: for each of n_states partitions
+ * of the network into k parts (parts: [n_states][n_tensors], entries in [0, k), no part empty) the
+ * counts of the plan tn_plan_create would assemble from it -- a Greedy tree per partition and the
+ * fan-in tree over the partition results (every merge order for k <= 4, else the best of
+ * fanin_samples RandomGreedy samples) -- written to con_serial, con_dist and mem ([n_states]
+ * each, Eq. 3.2, 3.5, 3.1; any may be NULL).  device >= 0 evaluates the fan-in trees of k > 4 on
+ * that CUDA device in one batched launch, device = -1 on the host; both give the same counts,
+ * which equal tn_plan_counts of tn_plan_create with the state as TN_INIT_GIVEN and no annealing.
+ * saturated ([n_states], may be NULL) is set to 1 for a state whose sizes or costs reach 2^120
+ * (its counts are then lower bounds).
+ * Errors: TN_EINVAL (bad k or parts), TN_EUNSUPPORTED (device evaluation of k > 256 or of more
+ * than 2048 cut legs), TN_ECUDA, TN_ENOMEM. */
+tn_status tn_plan_eval_states(const tn_net *net, int32_t k, int32_t fanin_samples, int32_t device,
+                              int32_t n_states, const int32_t *parts, tn_u128 *con_serial,
+                              tn_u128 *con_dist, tn_u128 *mem, int32_t *saturated);
+
 typedef struct {
     tn_u128 con_serial, con_dist, con_par, mem; /* Eq. 3.2, 3.5, 3.4, 3.1 */
     tn_u128 initial_con_dist;                   /* con_dist of the initial partition */
@@ -190,6 +211,21 @@ tn_status tn_plan_get_info(const tn_plan *plan, tn_plan_info *info);
 tn_status tn_plan_export(const tn_plan *plan, int32_t *part_of_tensor, int32_t *steps,
                          int32_t *step_part, int32_t *n_steps);
 void tn_plan_free(tn_plan *plan);
+
+/* Slicing on top of partitioning (Section 4.1; Section 6 names it as the way past the memory
+ * limit).  Fixing the index of every edge of a set S splits the contraction into prod_{e in S} n(e)
+ * slices, each the same network with n(e) = 1 on S, contracted along the plan's tree; the value is
+ * the sum of the slices.  tn_plan_slice chooses S greedily for the plan's tree: while its mem
+ * (Eq. 3.1) is above target_mem elements and fewer than max_edges are chosen, it slices the leg of
+ * the peak-memory step (the step maximising |v| + |c1| + |c2| and its children's legs) that lowers
+ * mem the most (ties: fewer total operations, then the smaller edge id).  Writes the chosen edge
+ * ids to edges (increasing, at most max_edges), their number to *n_edges, and the counts: slices,
+ * per-slice con_serial (Eq. 3.2) and mem, and the total operations of all slices (slices x
+ * per-slice; the excess over the unsliced con_serial is the redundant work).  Counts may be NULL.
+ * Errors: TN_EINVAL, TN_EUNSUPPORTED (more than 2^100 slices). */
+tn_status tn_plan_slice(const tn_net *net, const tn_plan *plan, tn_u128 target_mem, int32_t max_edges,
+                        int32_t *edges, int32_t *n_edges, tn_u128 *n_slices, tn_u128 *slice_con,
+                        tn_u128 *slice_mem, tn_u128 *total_con);
 
 /* ------------------------------------------------------------------ contraction on the GPU */
 
@@ -245,7 +281,13 @@ tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
  *                    replays it (one graph launch per run); its per-class kernel times
  *                    (tn_batch_kernel_times) are then those of the last replay.  0: the launches
  *                    are issued one by one every run.
- * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000, 1} (large programs off: on the 24-qubit brickwork
+ *   schedule         order of the persistent kernel's work list (every order is a topological one,
+ *                    so the claim-in-order scheme stays deadlock-free): 0 by dependency level (all
+ *                    jobs' level-1 tiles, then level 2, ...); 1 critical path first: by decreasing
+ *                    weight of the path from the step to the root, sum of 2^vc (the path sums of
+ *                    Eq. 3.4, whose maximum is con_par), so the steps on the longest weighted
+ *                    paths are claimed first.
+ * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0} (large programs off: on the 24-qubit brickwork
  * benchmark they measured slower than running fan-in chains as dataflow steps).
  * Errors: TN_EINVAL. */
 typedef struct {
@@ -256,6 +298,7 @@ typedef struct {
     int32_t rows_chains;
     int32_t wait_limit_us;
     int32_t graph_capture;
+    int32_t schedule;
 } tn_exec_config;
 tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
 tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);
@@ -313,6 +356,19 @@ void tn_program_free(tn_program *prog);
  * Errors: as tn_program_create / tn_program_run; TN_ETIMEOUT if a device wait gave up. */
 tn_status tn_contract(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
                       double out_amp[2], int32_t *out_exp2, tn_run_info *info);
+
+/* Sliced contraction: the slices of the closed network (n_sliced edges, none an open leg) run as
+ * the jobs of a batch of at most max_jobs jobs -- one compiled plan (the plan's tree on the sliced
+ * structure), each job's tensors on sliced edges replaced by its slice -- and their values are
+ * summed in FP64; the amplitude is returned as for tn_contract, and the number of slices in
+ * *n_slices (may be NULL).  Slices are numbered in mixed radix over `sliced` (the first edge
+ * slowest); first_slice and slice_count (0 = all) select a range, whose partial sum is returned
+ * (for timing a sample of a large slicing).  Blocks until done.
+ * Errors: TN_EINVAL, TN_EUNSUPPORTED (more than 2^40 slices), those of tn_batch_create and
+ * tn_batch_run, TN_ETIMEOUT. */
+tn_status tn_contract_sliced(tn_ctx *ctx, const tn_net *net, const tn_plan *plan, tn_precision prec,
+                             int32_t n_sliced, const int32_t *sliced, int32_t max_jobs, int64_t first_slice,
+                             int64_t slice_count, double out_amp[2], int32_t *out_exp2, int64_t *n_slices);
 
 /* ------------------------------------------------------------------ batches (many contractions) */
 

@@ -186,6 +186,8 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->pad0 = 0;
     o->initial_part = nullptr;
     o->position = nullptr;
+    o->fanin_device = -1;
+    o->pad1 = 0;
 }
 
 tn_status tn_plan_create(const tn_net *net, const tn_plan_opts *opts, tn_plan **out) {
@@ -235,6 +237,22 @@ tn_status tn_plan_counts(const tn_plan *p, tn_u128 *total_ops, tn_u128 *crit_ops
     if (total_ops) *total_ops = to_abi(p->impl.con_serial);
     if (crit_ops) *crit_ops = to_abi(p->impl.con_dist);
     if (mem_elems) *mem_elems = to_abi(p->impl.mem);
+    return TN_OK;
+}
+
+tn_status tn_plan_eval_states(const tn_net *net, int32_t k, int32_t fanin_samples, int32_t device,
+                              int32_t n_states, const int32_t *parts, tn_u128 *con_serial,
+                              tn_u128 *con_dist, tn_u128 *mem, int32_t *saturated) {
+    if (!net) return fail(TN_EINVAL, "NULL net");
+    std::vector<StateCounts> out;
+    tn_status s = eval_states(net->impl, k, fanin_samples, device, n_states, parts, out);
+    if (s != TN_OK) return s;
+    for (int32_t q = 0; q < n_states; ++q) {
+        if (con_serial) con_serial[q] = to_abi(out[q].con_serial);
+        if (con_dist) con_dist[q] = to_abi(out[q].con_dist);
+        if (mem) mem[q] = to_abi(out[q].mem);
+        if (saturated) saturated[q] = out[q].saturated ? 1 : 0;
+    }
     return TN_OK;
 }
 

@@ -76,6 +76,11 @@ CompileOpts compile_opts(const tn_exec_config &cfg, int32_t prec, bool c128);
 // The dataflow work item of tile `tile` of step `step` (with the step's dependencies).
 WorkItem dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_t tile);
 
+// Weight of the path from every global step to the root: the sum of M N K (2^vc of Eq. 3.3) over
+// the step and its consumers up to the root -- the path sums whose maximum over the leaves is
+// con_par (Eq. 3.4).  Programs count as zero.
+void path_weights(const Compiled &c, std::vector<double> &path);
+
 // Dependency phases.  A dense tensor-core step runs in its own pack and GEMM launches, so the
 // persistent dataflow launches are cut at them: phase(TC step) = 1 + the largest phase of its
 // producers, phase(other step) = the largest phase of its producers (programs: 0).  A run is, for

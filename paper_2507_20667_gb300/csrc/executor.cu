@@ -17,6 +17,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -37,7 +38,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1};   // programs, TC thresholds, wait limit, graphs
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0};   // programs, TC, wait limit, graphs, order
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -1034,6 +1035,21 @@ WorkItem tn::dataflow_item(const Compiled &c, uint32_t job, int32_t step, int32_
     return w;
 }
 
+void tn::path_weights(const Compiled &c, std::vector<double> &path) {
+    const size_t ns = c.steps.size();
+    std::vector<int32_t> consumer(ns, -1);
+    for (size_t s = 0; s < ns; ++s) {
+        if (c.steps[s].dep0 >= 0) consumer[c.steps[s].dep0] = (int32_t)s;
+        if (c.steps[s].dep1 >= 0) consumer[c.steps[s].dep1] = (int32_t)s;
+    }
+    path.assign(ns, 0.0);
+    for (size_t s = ns; s-- > 0;) {   // consumers follow their producers
+        const StepDesc &d = c.steps[s];
+        const double w = d.kind == STEP_LOCAL ? 0.0 : (double)d.M * (double)d.N * (double)d.K;
+        path[s] = w + (consumer[s] >= 0 ? path[consumer[s]] : 0.0);
+    }
+}
+
 int32_t tn::step_phases(const Compiled &c, std::vector<int32_t> &phase) {
     phase.assign(c.steps.size(), 0);
     int32_t top = 0;
@@ -1392,29 +1408,45 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         if (b->mode == TN_EXEC_PERSISTENT) {
             work.reserve((size_t)total);
             b->phases.assign(np, tn_batch::Phase());
+            // order key of every step: its dependency level, or (critical path first) minus the
+            // weight of its path to the root
+            std::vector<std::vector<double>> key(b->comp.size());
+            for (size_t ci = 0; ci < b->comp.size(); ++ci) {
+                const Compiled &c = b->comp[ci];
+                key[ci].assign(c.steps.size(), 0.0);
+                if (ctx->cfg.schedule == 1) {
+                    std::vector<double> path;
+                    path_weights(c, path);
+                    for (size_t st = 0; st < c.steps.size(); ++st) key[ci][st] = -path[st];
+                } else {
+                    for (size_t st = 0; st < c.steps.size(); ++st) key[ci][st] = c.steps[st].level;
+                }
+            }
             for (int32_t p = 0; p < np; ++p) {
                 tn_batch::Phase &ph = b->phases[p];
-                std::vector<std::array<int32_t, 3>> order;   // level, job, step
+                std::vector<std::tuple<double, int32_t, int32_t>> order;   // key, job, step
                 for (int32_t i = 0; i < n; ++i) {
                     const Compiled &c = b->comp[b->job_comp[i]];
                     const std::vector<int32_t> &phs = phase_of[b->job_comp[i]];
                     for (size_t st = 0; st < c.steps.size(); ++st)
                         if (phs[st] == p && c.steps[st].kind != STEP_LOCAL && !(c.steps[st].flags & FLAG_CHAIN_CONT))
-                            order.push_back({c.steps[st].level, i, (int32_t)st});
+                            order.emplace_back(key[b->job_comp[i]][st], i, (int32_t)st);
                 }
                 std::sort(order.begin(), order.end());
                 ph.pack0 = (int32_t)packs.size();
                 ph.gemm0 = (int32_t)gemms.size();
                 for (auto &o : order)
-                    if (b->comp[b->job_comp[o[1]]].steps[o[2]].kind == STEP_TC) add_tc(o[1], o[2]);
+                    if (b->comp[b->job_comp[std::get<1>(o)]].steps[std::get<2>(o)].kind == STEP_TC)
+                        add_tc(std::get<1>(o), std::get<2>(o));
                 ph.n_pack = (int32_t)packs.size() - ph.pack0;
                 ph.n_gemm = (int32_t)gemms.size() - ph.gemm0;
                 for (auto &o : order) {
-                    const Compiled &cj = b->comp[b->job_comp[o[1]]];
-                    const StepDesc &d = cj.steps[o[2]];
+                    const int32_t job = std::get<1>(o), st = std::get<2>(o);
+                    const Compiled &cj = b->comp[b->job_comp[job]];
+                    const StepDesc &d = cj.steps[st];
                     if (d.kind == STEP_TC) continue;
                     for (int32_t t = 0; t < d.ntiles; ++t) {
-                        work.push_back(dataflow_item(cj, (uint32_t)o[1], o[2], t));
+                        work.push_back(dataflow_item(cj, (uint32_t)job, st, t));
                         work_phase.push_back(p);
                     }
                 }
@@ -1833,6 +1865,7 @@ tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
     c->cfg.warp_programs = cfg->warp_programs ? 1 : 0;
     c->cfg.rows_chains = cfg->rows_chains ? 1 : 0;
     c->cfg.graph_capture = cfg->graph_capture ? 1 : 0;
+    if (cfg->schedule < 0 || cfg->schedule > 1) return fail(TN_EINVAL, "schedule must be 0 or 1");
     return TN_OK;
 }
 
@@ -2183,6 +2216,12 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
     for (tn_exec_config &c : cands) {
         c.wait_limit_us = saved.wait_limit_us;
         c.graph_capture = saved.graph_capture;
+        c.schedule = 0;
+    }
+    {   // the critical-path-first order with the default program configuration
+        tn_exec_config cp = cands[1];
+        cp.schedule = 1;
+        cands.push_back(cp);
     }
     for (size_t i = 0; i < cands.size(); ++i) {
         ctx->cfg = cands[i];

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <queue>
 #include <thread>
 
@@ -201,141 +202,177 @@ uint64_t mix64(uint64_t h, uint64_t v) {
     return h * 0xff51afd7ed558ccdull;
 }
 
-// Evaluate a fan-in merge sequence: con_dist (Eq. 3.5, comm = 0) and the fan-in con / mem.
-FanIn eval_fanin(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
-                 const std::vector<std::pair<int32_t, int32_t>> &steps,
-                 const std::vector<int64_t> &edim, bool &ovf) {
-    const int32_t k = (int32_t)roots.size();
-    std::vector<Legs> legs(roots);
-    legs.resize(2 * k - 1);
-    std::vector<u128> cost(2 * k - 1, 0), size(2 * k - 1, 0);
-    std::vector<int32_t> parent(2 * k - 1, -1);
-    FanIn f;
-    f.steps = steps;
-    for (int32_t i = 0; i < k; ++i) size[i] = legs_size(legs[i], edim, ovf);
-    for (size_t s = 0; s < steps.size(); ++s) {
-        int32_t a = steps[s].first, b = steps[s].second, o = k + (int32_t)s;
-        legs_symdiff(legs[a], legs[b], legs[o]);
-        size[o] = legs_size(legs[o], edim, ovf);
-        cost[o] = union_size(legs[a], legs[b], edim, ovf);
-        parent[a] = parent[b] = o;
-        f.con += cost[o];
-        u128 m = size[o] + size[a] + size[b];
-        if (m > f.mem) f.mem = m;
-    }
-    for (int32_t i = 0; i < k; ++i) {
-        u128 c = part_con[i];
-        for (int32_t v = parent[i]; v >= 0; v = parent[v]) c += cost[v];
-        if (c > f.con_dist) f.con_dist = c;
-    }
-    return f;
-}
+}  // namespace
 
-bool fanin_better(const FanIn &a, const FanIn &b) {
-    if (a.con_dist != b.con_dist) return a.con_dist < b.con_dist;
-    return a.con < b.con;
-}
-
-void enumerate_fanin(std::vector<int32_t> &alive, int32_t next,
-                     std::vector<std::pair<int32_t, int32_t>> &cur, const std::vector<Legs> &roots,
-                     const std::vector<u128> &part_con, const std::vector<int64_t> &edim,
-                     FanIn &best, bool &have, bool &ovf) {
-    if (alive.size() == 1) {
-        FanIn f = eval_fanin(roots, part_con, cur, edim, ovf);
-        if (!have || fanin_better(f, best)) { best = f; have = true; }
-        return;
-    }
-    for (size_t x = 0; x < alive.size(); ++x)
-        for (size_t y = x + 1; y < alive.size(); ++y) {
-            int32_t a = alive[x], b = alive[y];
-            std::vector<int32_t> rest;
-            for (int32_t v : alive) if (v != a && v != b) rest.push_back(v);
-            rest.push_back(next);
-            cur.emplace_back(std::min(a, b), std::max(a, b));
-            enumerate_fanin(rest, next + 1, cur, roots, part_con, edim, best, have, ovf);
-            cur.pop_back();
+// The fan-in problem in the shared bitset form: compact edge ids are the union of the roots'
+// legs in increasing edge order.
+void fanin_input(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
+                 const std::vector<int64_t> &edim, uint64_t seed, FaninInput &in) {
+    in.k = (int32_t)roots.size();
+    in.seed = seed;
+    in.part_con = part_con;
+    std::vector<int32_t> ids;
+    for (const Legs &r : roots) ids.insert(ids.end(), r.begin(), r.end());
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    in.W = std::max<int32_t>(1, (int32_t)((ids.size() + 63) / 64));
+    in.unit = true;
+    for (int32_t e : ids) in.unit = in.unit && edim[e] == 2;
+    in.roots.assign((size_t)in.k * in.W, 0);
+    for (int32_t i = 0; i < in.k; ++i)
+        for (int32_t e : roots[i]) {
+            const size_t x = (size_t)(std::lower_bound(ids.begin(), ids.end(), e) - ids.begin());
+            in.roots[(size_t)i * in.W + x / 64] |= 1ull << (x % 64);
         }
+    in.dims.clear();
+    if (!in.unit) {
+        in.dims.assign((size_t)64 * in.W, 1);
+        for (size_t x = 0; x < ids.size(); ++x) in.dims[x] = edim[ids[x]];
+    }
 }
 
-// One (possibly noisy) Greedy pass over the partition results (RandomGreedy sample).
-std::vector<std::pair<int32_t, int32_t>> noisy_greedy(const std::vector<Legs> &roots,
-                                                      const std::vector<int64_t> &edim,
-                                                      double tau, Rng *rng, bool &ovf) {
-    const int32_t k = (int32_t)roots.size();
-    std::vector<Legs> legs(roots);
-    legs.resize(2 * k - 1);
-    std::vector<u128> size(2 * k - 1, 0);
-    std::vector<char> alive(2 * k - 1, 0);
-    for (int32_t i = 0; i < k; ++i) { size[i] = legs_size(legs[i], edim, ovf); alive[i] = 1; }
-    std::vector<std::pair<int32_t, int32_t>> steps;
-    int32_t next = k;
-    for (int32_t it = 0; it < k - 1; ++it) {
-        double best = 0;
-        int32_t bi = -1, bj = -1;
-        for (int32_t i = 0; i < next; ++i) {
-            if (!alive[i]) continue;
-            for (int32_t j = i + 1; j < next; ++j) {
-                if (!alive[j] || !legs_intersect(legs[i], legs[j])) continue;
-                Legs r;
-                legs_symdiff(legs[i], legs[j], r);
-                i128 obj = (i128)size[i] + (i128)size[j] - (i128)legs_size(r, edim, ovf);
-                double sc = (double)obj;
-                if (rng) {
-                    double u = rng->uniform();
-                    double g = -std::log(-std::log(u + 1e-300) + 1e-300);  // Gumbel(0, 1)
-                    sc += tau * std::max(std::fabs(sc), 1.0) * g;
-                }
-                if (bi < 0 || sc > best) { best = sc; bi = i; bj = j; }
+namespace {
+// One Greedy pass (a RandomGreedy sample; noiseless when !noisy) over the k roots in legs[0..k):
+// repeatedly merge the connected pair of live nodes that comes first in fanin::pair_before order
+// (scores are fixed per pair, so a heap with lazy deletion holds them); a set with no connected
+// pair merges its two smallest nodes (size, then id).  steps[2 s], steps[2 s + 1] = merge s.
+void greedy_pass(int k, const fanin::Dims &d, bool noisy, uint64_t seed, uint64_t *legs, u128 *size,
+                 uint8_t *alive, int16_t *steps, bool &sat) {
+    const int W = d.W;
+    struct Cand {
+        i128 score;
+        int32_t i, j;
+    };
+    auto later = [](const Cand &a, const Cand &b) { return fanin::pair_before(b.score, b.i, b.j, a.score, a.i, a.j); };
+    std::priority_queue<Cand, std::vector<Cand>, decltype(later)> heap(later);
+    auto push = [&](int i, int j) {
+        const uint64_t *li = legs + (size_t)i * W, *lj = legs + (size_t)j * W;
+        if (!fanin::intersects(li, lj, W)) return;
+        const i128 obj = (i128)size[i] + (i128)size[j] - (i128)fanin::set_size(li, lj, 1, d, sat);
+        heap.push(Cand{fanin::pair_score(obj, noisy, seed, (uint32_t)i, (uint32_t)j), i, j});
+    };
+    for (int i = 0; i < k; ++i) {
+        size[i] = fanin::set_size(legs + (size_t)i * W, legs + (size_t)i * W, 0, d, sat);
+        alive[i] = 1;
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j) push(i, j);
+    for (int it = 0; it < k - 1; ++it) {
+        const int next = k + it;
+        int bi = -1, bj = -1;
+        while (!heap.empty()) {
+            const Cand c = heap.top();
+            heap.pop();
+            if (alive[c.i] && alive[c.j]) {
+                bi = c.i;
+                bj = c.j;
+                break;
             }
         }
-        if (bi < 0) {
-            int32_t a = -1, b = -1;
-            for (int32_t v = 0; v < next; ++v) {
+        if (bi < 0) {   // no connected pair: the two smallest (size, then id)
+            int a = -1, b = -1;
+            for (int v = 0; v < next; ++v) {
                 if (!alive[v]) continue;
-                if (a < 0 || size[v] < size[a]) { b = a; a = v; }
-                else if (b < 0 || size[v] < size[b]) b = v;
+                if (a < 0 || size[v] < size[a]) {
+                    b = a;
+                    a = v;
+                } else if (b < 0 || size[v] < size[b]) {
+                    b = v;
+                }
             }
             bi = std::min(a, b);
             bj = std::max(a, b);
         }
-        legs_symdiff(legs[bi], legs[bj], legs[next]);
-        size[next] = legs_size(legs[next], edim, ovf);
+        uint64_t *ln = legs + (size_t)next * W;
+        for (int w = 0; w < W; ++w) ln[w] = legs[(size_t)bi * W + w] ^ legs[(size_t)bj * W + w];
+        size[next] = fanin::set_size(ln, ln, 0, d, sat);
         alive[bi] = alive[bj] = 0;
         alive[next] = 1;
-        steps.emplace_back(bi, bj);
-        ++next;
+        steps[2 * it] = (int16_t)bi;
+        steps[2 * it + 1] = (int16_t)bj;
+        for (int x = 0; x < next; ++x)
+            if (alive[x]) push(x, next);
     }
-    return steps;
+}
+
+// Every merge order of k <= 4 roots (recursively: each pair of the live nodes, then the rest).
+void enumerate_orders(std::vector<int32_t> &live, int32_t next, std::vector<int16_t> &cur,
+                      const std::function<void(const std::vector<int16_t> &)> &visit) {
+    if (live.size() == 1) {
+        visit(cur);
+        return;
+    }
+    for (size_t x = 0; x < live.size(); ++x)
+        for (size_t y = x + 1; y < live.size(); ++y) {
+            const int32_t a = live[x], b = live[y];
+            std::vector<int32_t> rest;
+            for (int32_t v : live) if (v != a && v != b) rest.push_back(v);
+            rest.push_back(next);
+            cur.push_back((int16_t)std::min(a, b));
+            cur.push_back((int16_t)std::max(a, b));
+            enumerate_orders(rest, next + 1, cur, visit);
+            cur.resize(cur.size() - 2);
+        }
 }
 }  // namespace
 
 // The fan-in (reduction) tree of Section 4.4: for k <= 4 every merge order is tried; above that
-// RandomGreedy keeps the best of `samples` Greedy paths (sample 0 noiseless, the others with
-// Gumbel noise on the objective).  Best = smallest con_dist, then smallest fan-in con, then first.
+// RandomGreedy keeps the best of `samples` Greedy passes (sample 0 noiseless, the others with the
+// integer perturbation of fanin::pair_score).  Best = smallest con_dist, then smallest fan-in con,
+// then first.  The batched GPU evaluator (fanin_eval.cu) makes the same choices.
+FanIn fanin_host(const FaninInput &in, int samples, int sample, bool &ovf) {
+    const int32_t k = in.k;
+    FanIn out;
+    if (k == 1) {
+        out.con_dist = in.part_con[0];
+        return out;
+    }
+    const fanin::Dims d{in.W, in.unit ? 1 : 0, in.dims.empty() ? nullptr : in.dims.data()};
+    const size_t nn = 2 * (size_t)k - 1;
+    std::vector<uint64_t> legs(nn * in.W, 0);
+    std::copy(in.roots.begin(), in.roots.end(), legs.begin());
+    std::vector<u128> size(nn), cost(nn);
+    std::vector<int16_t> parent(nn), steps(2 * (size_t)(k - 1));
+    std::vector<uint8_t> alive(nn);
+    fanin::Counts best{0, 0, 0, false};
+    std::vector<int16_t> best_steps;
+    bool have = false, sat = false;
+    auto consider = [&](const std::vector<int16_t> &st) {
+        const fanin::Counts c = fanin::eval_steps(k, in.part_con.data(), st.data(), d, legs.data(), size.data(),
+                                                  parent.data(), cost.data());
+        sat = sat || c.sat;
+        if (!have || fanin::better(c, best)) {
+            best = c;
+            best_steps = st;
+            have = true;
+        }
+    };
+    if (k <= 4) {
+        std::vector<int32_t> live(k);
+        for (int32_t i = 0; i < k; ++i) live[i] = i;
+        std::vector<int16_t> cur;
+        enumerate_orders(live, k, cur, consider);
+    } else {
+        const int s0 = sample >= 0 ? sample : 0, s1 = sample >= 0 ? sample + 1 : std::max(samples, 1);
+        for (int smp = s0; smp < s1; ++smp) {
+            greedy_pass(k, d, smp > 0, smp > 0 ? fanin::sample_seed(in.seed, smp) : 0, legs.data(), size.data(),
+                        alive.data(), steps.data(), sat);
+            consider(steps);
+        }
+    }
+    if (sat) ovf = true;
+    out.con_dist = best.con_dist;
+    out.con = best.con;
+    out.mem = best.mem;
+    for (int32_t t = 0; t + 1 < k; ++t) out.steps.emplace_back(best_steps[2 * t], best_steps[2 * t + 1]);
+    return out;
+}
+
 FanIn fanin_tree(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
                  const std::vector<int64_t> &edim, int samples, uint64_t seed, bool &ovf) {
-    const int32_t k = (int32_t)roots.size();
-    if (k == 1) {
-        FanIn f;
-        f.con_dist = part_con[0];
-        return f;
-    }
-    FanIn best;
-    bool have = false;
-    if (k <= 4) {
-        std::vector<int32_t> alive(k);
-        for (int32_t i = 0; i < k; ++i) alive[i] = i;
-        std::vector<std::pair<int32_t, int32_t>> cur;
-        enumerate_fanin(alive, k, cur, roots, part_con, edim, best, have, ovf);
-        return best;
-    }
-    Rng rng(seed);
-    for (int s = 0; s < std::max(samples, 1); ++s) {
-        auto steps = noisy_greedy(roots, edim, 0.5, s == 0 ? nullptr : &rng, ovf);
-        FanIn f = eval_fanin(roots, part_con, steps, edim, ovf);
-        if (!have || fanin_better(f, best)) { best = f; have = true; }
-    }
-    return best;
+    FaninInput in;
+    fanin_input(roots, part_con, edim, seed, in);
+    return fanin_host(in, samples, -1, ovf);
 }
 
 // ------------------------------------------------------------------------------------ counts
@@ -410,7 +447,8 @@ struct PartState {
 struct State {
     std::vector<int32_t> part;
     std::vector<PartState> parts;
-    FanIn fan;
+    FanIn fan;                      // its steps are left empty when a device evaluated the state
+    int32_t fan_sample = -1;        // then: the winning RandomGreedy sample
     u128 cost = 0;                  // con_dist
 };
 
@@ -419,6 +457,8 @@ struct Ctx {
     int32_t k;
     int32_t samples;
     bool ovf = false;
+    int32_t device = -1;            // >= 0: fan-in trees of k > 4 evaluated in batches on this GPU
+    FaninWorkspace *ws = nullptr;
 };
 
 void rebuild_part(const Ctx &c, PartState &ps, bool &ovf) {
@@ -431,7 +471,7 @@ void rebuild_part(const Ctx &c, PartState &ps, bool &ovf) {
 // EvaluateState (Section 4.4): Greedy trees are kept per partition; the fan-in tree and con_dist
 // follow from the partition results.  The fan-in sampling seed is a hash of the partition roots,
 // so the cost is a function of the state alone.
-void evaluate(const Ctx &c, State &s, bool &ovf) {
+void state_fanin(const Ctx &c, const State &s, FaninInput &in) {
     std::vector<Legs> roots(c.k);
     std::vector<u128> pc(c.k);
     uint64_t h = 0x1234567ull;
@@ -441,15 +481,51 @@ void evaluate(const Ctx &c, State &s, bool &ovf) {
         for (int32_t e : roots[k]) h = mix64(h, (uint64_t)e * 131 + (uint64_t)k);
         h = mix64(h, (uint64_t)pc[k] ^ (uint64_t)(pc[k] >> 64));
     }
-    s.fan = fanin_tree(roots, pc, c.net.edim, c.samples, h, ovf);
+    fanin_input(roots, pc, c.net.edim, h, in);
+}
+
+void evaluate(const Ctx &c, State &s, bool &ovf) {
+    FaninInput in;
+    state_fanin(c, s, in);
+    s.fan = fanin_host(in, c.samples, -1, ovf);
+    s.fan_sample = -1;
     s.cost = s.fan.con_dist;
+}
+
+// Evaluate many states' fan-in trees on the context's device in one launch (k > 4).
+tn_status evaluate_batch(const Ctx &c, std::vector<State *> &states, std::vector<char> *sat = nullptr) {
+    std::vector<FaninInput> ins(states.size());
+    for (size_t q = 0; q < states.size(); ++q) state_fanin(c, *states[q], ins[q]);
+    std::vector<FaninBest> best;
+    tn_status st = fanin_eval_device(c.device, ins, c.samples, best, *c.ws);
+    if (st != TN_OK) return st;
+    for (size_t q = 0; q < states.size(); ++q) {
+        State &s = *states[q];
+        s.fan = FanIn();
+        s.fan.con_dist = best[q].counts.con_dist;
+        s.fan.con = best[q].counts.con;
+        s.fan.mem = best[q].counts.mem;
+        s.fan_sample = best[q].sample;
+        s.cost = s.fan.con_dist;
+        if (sat) (*sat)[q] = best[q].counts.sat ? 1 : 0;
+    }
+    return TN_OK;
+}
+
+// The merge steps of a state evaluated on a device (the winning sample, replayed on the host).
+void fill_fanin_steps(const Ctx &c, State &s, bool &ovf) {
+    if (s.fan_sample < 0 || c.k <= 1) return;
+    FaninInput in;
+    state_fanin(c, s, in);
+    s.fan = fanin_host(in, c.samples, s.fan_sample, ovf);
+    s.fan_sample = -1;
 }
 
 // Rebalance (Algorithm 2): pick a source partition with at least two tensors, a node v of its tree
 // other than the root (so the source never empties), the tensors under v, and a target partition
 // (uniform for NAIVE; for DIRECTED the argmax of Eq. 4.5 between legs(v) and the target's root,
 // ties to the lowest index); move the tensors and rebuild both Greedy trees and the fan-in tree.
-bool rebalance(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rng, bool &ovf) {
+bool propose(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rng, bool &ovf) {
     std::vector<int32_t> cand;
     for (int32_t k = 0; k < c.k; ++k)
         if (cur.parts[k].members.size() >= 2) cand.push_back(k);
@@ -512,6 +588,12 @@ bool rebalance(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rn
     dm.swap(merged);
     rebuild_part(c, nxt.parts[src], ovf);
     rebuild_part(c, nxt.parts[dst], ovf);
+    return true;
+}
+
+// A move and the evaluation of the state it leads to.
+bool rebalance(const Ctx &c, const State &cur, State &nxt, int32_t mode, Rng &rng, bool &ovf) {
+    if (!propose(c, cur, nxt, mode, rng, ovf)) return false;
     evaluate(c, nxt, ovf);
     return true;
 }
@@ -579,6 +661,50 @@ void run_chain(const Ctx &c, const State &start, int32_t moves, double T, int32_
 // One round of the division scheme (Algorithm 1, Section 4.3): p chains start from the same
 // state, each runs ceil(N / p) moves with a seed drawn from (seed, round, chain), and the cheapest
 // end state is kept (lowest chain index on ties, so the result does not depend on scheduling).
+// The same round with the fan-in trees evaluated on a device: the chains advance in lockstep, every
+// chain proposing its next move, then one batched launch evaluates all proposals, then every
+// chain applies the Metropolis rule.  Each chain draws the same random numbers in the same order
+// as in anneal_round and the device evaluation equals the host's, so the result is the same.
+tn_status anneal_round_device(const Ctx &c, const State &from, int32_t chains, int32_t moves, double T,
+                              int32_t mode, uint64_t seed, int64_t round, int32_t &accepted, State &out) {
+    std::vector<Chain> res(chains);
+    std::vector<Rng> rngs;
+    std::vector<char> live(chains, 1);
+    for (int32_t q = 0; q < chains; ++q) {
+        res[q].s = from;
+        rngs.emplace_back(mix64(mix64(seed, (uint64_t)round), (uint64_t)q + 1));
+    }
+    std::vector<State> cand(chains);
+    for (int32_t m = 0; m < moves; ++m) {
+        std::vector<State *> batch;
+        std::vector<int32_t> who;
+        for (int32_t q = 0; q < chains; ++q) {
+            if (!live[q]) continue;
+            if (!propose(c, res[q].s, cand[q], mode, rngs[q], res[q].ovf)) {
+                live[q] = 0;
+                continue;
+            }
+            batch.push_back(&cand[q]);
+            who.push_back(q);
+        }
+        if (batch.empty()) break;
+        tn_status st = evaluate_batch(c, batch);
+        if (st != TN_OK) return st;
+        for (int32_t q : who)
+            if (metropolis_accept(cand[q].cost, res[q].s.cost, T, rngs[q])) {
+                res[q].s = std::move(cand[q]);
+                res[q].accepted++;
+            }
+    }
+    int32_t win = 0;
+    for (int32_t q = 0; q < chains; ++q) {
+        accepted += res[q].accepted;
+        if (res[q].s.cost < res[win].s.cost) win = q;
+    }
+    out = std::move(res[win].s);
+    return TN_OK;
+}
+
 State anneal_round(const Ctx &c, const State &from, int32_t chains, int32_t moves, double T, int32_t mode,
                    uint64_t seed, int64_t round, int32_t &accepted) {
     std::vector<Chain> res(chains);
@@ -619,6 +745,91 @@ struct BestTracker {
 };
 }  // namespace
 
+tn_status eval_states(const Net &net, int32_t k, int32_t samples, int32_t device, int32_t n_states,
+                      const int32_t *parts, std::vector<StateCounts> &out) {
+    if (k < 1 || k > net.n) return fail(TN_EINVAL, "k must satisfy 1 <= k <= n_tensors");
+    if (n_states < 0 || (n_states > 0 && !parts)) return fail(TN_EINVAL, "NULL parts");
+    Ctx c{net, k, samples};
+    FaninWorkspace ws;
+    struct WsGuard {
+        FaninWorkspace &w;
+        ~WsGuard() { fanin_workspace_free(w); }
+    } ws_guard{ws};
+    if (device >= 0 && k > 4) {
+        c.device = device;
+        c.ws = &ws;
+    }
+    std::vector<State> st(n_states);
+    std::vector<char> ovfs(n_states, 0);
+    // partition trees on the host, in parallel over states
+    auto build = [&](int32_t lo, int32_t hi, bool *bad) {
+        for (int32_t q = lo; q < hi; ++q) {
+            State &s = st[q];
+            s.part.assign(parts + (size_t)q * net.n, parts + (size_t)(q + 1) * net.n);
+            s.parts.assign(k, PartState());
+            for (int32_t t = 0; t < net.n; ++t) {
+                if (s.part[t] < 0 || s.part[t] >= k) { *bad = true; return; }
+                s.parts[s.part[t]].members.push_back(t);
+            }
+            for (int32_t p = 0; p < k; ++p) {
+                if (s.parts[p].members.empty()) { *bad = true; return; }
+                bool ov = false;
+                rebuild_part(c, s.parts[p], ov);
+                if (ov) ovfs[q] = 1;
+            }
+        }
+    };
+    const int32_t nt = std::max<int32_t>(1, std::min<int32_t>((int32_t)std::thread::hardware_concurrency(), 16));
+    std::vector<std::thread> ts;
+    std::vector<char> bad(nt, 0);
+    for (int32_t w = 0; w < nt; ++w) {
+        const int32_t lo = (int32_t)((int64_t)n_states * w / nt), hi = (int32_t)((int64_t)n_states * (w + 1) / nt);
+        ts.emplace_back([&, lo, hi, w] {
+            bool b = false;
+            build(lo, hi, &b);
+            bad[w] = b;
+        });
+    }
+    for (auto &t : ts) t.join();
+    for (char b : bad)
+        if (b) return fail(TN_EINVAL, "a state has a partition index outside [0, k) or an empty partition");
+    if (c.device >= 0) {
+        std::vector<State *> ptr;
+        for (State &s : st) ptr.push_back(&s);
+        std::vector<char> fsat(n_states, 0);
+        tn_status r = evaluate_batch(c, ptr, &fsat);
+        if (r != TN_OK) return r;
+        for (int32_t q = 0; q < n_states; ++q) ovfs[q] = ovfs[q] || fsat[q];
+    } else {
+        std::vector<std::thread> ev;
+        for (int32_t w = 0; w < nt; ++w) {
+            const int32_t lo = (int32_t)((int64_t)n_states * w / nt), hi = (int32_t)((int64_t)n_states * (w + 1) / nt);
+            ev.emplace_back([&, lo, hi] {
+                for (int32_t q = lo; q < hi; ++q) {
+                    bool ov = false;
+                    evaluate(c, st[q], ov);
+                    if (ov) ovfs[q] = 1;
+                }
+            });
+        }
+        for (auto &t : ev) t.join();
+    }
+    out.assign(n_states, StateCounts());
+    for (int32_t q = 0; q < n_states; ++q) {
+        StateCounts &r = out[q];
+        u128 con = st[q].fan.con, mem = st[q].fan.mem;
+        for (const PartState &ps : st[q].parts) {
+            con += ps.tree.con;
+            mem = std::max(mem, ps.tree.mem);
+        }
+        r.con_serial = con;
+        r.con_dist = st[q].cost;
+        r.mem = mem;
+        r.saturated = ovfs[q] || con >= kSizeCap || st[q].cost >= kSizeCap || mem >= kSizeCap;
+    }
+    return TN_OK;
+}
+
 tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
     auto t_start = std::chrono::steady_clock::now();
     const int32_t n = net.n;
@@ -630,6 +841,15 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
     if (o.mode != TN_SA_NAIVE && o.mode != TN_SA_DIRECTED) return fail(TN_EINVAL, "unknown SA mode");
     Ctx c{net, o.k, o.fanin_samples};
     bool ovf = false;
+    FaninWorkspace ws;
+    struct WsGuard {
+        FaninWorkspace &w;
+        ~WsGuard() { fanin_workspace_free(w); }
+    } ws_guard{ws};
+    if (o.fanin_device >= 0 && o.k > 4) {
+        c.device = o.fanin_device;
+        c.ws = &ws;
+    }
 
     // initial partitioning
     State init;
@@ -679,7 +899,13 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
     // Sizes and costs saturate at 2^120 during the search: a saturated state is merely very
     // expensive, so the annealing can still move away from it.  Only the final plan must fit.
     for (int32_t k = 0; k < o.k; ++k) rebuild_part(c, init.parts[k], ovf);
-    evaluate(c, init, ovf);
+    if (c.device >= 0) {
+        std::vector<State *> one{&init};
+        tn_status st = evaluate_batch(c, one);
+        if (st != TN_OK) return st;
+    } else {
+        evaluate(c, init, ovf);
+    }
 
     // Simulated annealing (Section 4.3, Algorithm 1): rounds of parallel chains at a falling
     // temperature, with restarts from the best state.
@@ -694,12 +920,21 @@ tn_status plan_run(const Net &net, const tn_plan_opts &o, Plan &out) {
         for (int64_t round = 0;; ++round) {
             const double x = budget.progress(round);
             if (x < 0) break;
-            cur = anneal_round(c, cur, o.threads, moves, cool.at(x), o.mode, o.seed, round, accepted);
+            if (c.device >= 0) {
+                State nxt;
+                tn_status st = anneal_round_device(c, cur, o.threads, moves, cool.at(x), o.mode, o.seed, round,
+                                                   accepted, nxt);
+                if (st != TN_OK) return st;
+                cur = std::move(nxt);
+            } else {
+                cur = anneal_round(c, cur, o.threads, moves, cool.at(x), o.mode, o.seed, round, accepted);
+            }
             ++iters;
             track.observe(cur, round, o.restart_threshold);
         }
     }
-    const State &best = track.best;
+    State &best = track.best;
+    fill_fanin_steps(c, best, ovf);
     const int32_t restarts = track.restarts;
     // assemble the plan from the best state
     out = Plan();

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "tnsa.h"
+#include "fanin_core.cuh"
 
 namespace tn {
 
@@ -67,6 +68,38 @@ struct FanIn {
 FanIn fanin_tree(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
                  const std::vector<int64_t> &edim, int samples, uint64_t seed, bool &ovf);
 
+// A fan-in problem in the shared bitset form (fanin_core.cuh): the k roots' legs over compact
+// edge ids (the union of the roots' legs, in increasing edge order), their dimensions, the
+// partition results' con and the sampling seed.
+struct FaninInput {
+    int32_t k = 0, W = 0;
+    bool unit = true;                   // every compact edge has dimension 2
+    std::vector<uint64_t> roots;        // [k][W]
+    std::vector<int64_t> dims;          // [64 W] (empty when unit)
+    std::vector<u128> part_con;         // [k]
+    uint64_t seed = 0;
+};
+void fanin_input(const std::vector<Legs> &roots, const std::vector<u128> &part_con,
+                 const std::vector<int64_t> &edim, uint64_t seed, FaninInput &in);
+// The fan-in tree on the host: every merge order for k <= 4, else the best of `samples`
+// RandomGreedy samples; `sample` >= 0 evaluates that single sample only (k > 4).
+FanIn fanin_host(const FaninInput &in, int samples, int sample, bool &ovf);
+
+// The best sample of a batched evaluation.
+struct FaninBest {
+    fanin::Counts counts{0, 0, 0, false};
+    int32_t sample = 0;
+};
+// Device buffers and stream kept across batched evaluations.
+struct FaninWorkspace {
+    void *d_buf = nullptr, *h_buf = nullptr, *stream = nullptr;
+    size_t cap = 0;
+};
+// Batched fan-in evaluation on a CUDA device (k > 4): bit-identical to fanin_host.
+tn_status fanin_eval_device(int32_t device, const std::vector<FaninInput> &ins, int32_t samples,
+                            std::vector<FaninBest> &result, FaninWorkspace &ws);
+void fanin_workspace_free(FaninWorkspace &ws);
+
 struct Plan {
     int32_t n = 0, k = 1;
     std::vector<int32_t> part;                       // partition of each tensor
@@ -85,6 +118,16 @@ uint64_t next_uid();
 tn_status plan_finalize(const Net &net, Plan &plan);
 
 tn_status plan_run(const Net &net, const tn_plan_opts &opts, Plan &out);
+
+// EvaluateState (Section 4.4) for many partitions at once: each state's Greedy partition trees
+// (host threads) and fan-in tree (on `device` in one batched launch when k > 4 and device >= 0,
+// else on the host); the counts of the plan the planner would assemble from it.
+struct StateCounts {
+    u128 con_serial = 0, con_dist = 0, mem = 0;
+    bool saturated = false;     // some size or cost reached 2^120: the counts are lower bounds
+};
+tn_status eval_states(const Net &net, int32_t k, int32_t samples, int32_t device, int32_t n_states,
+                      const int32_t *parts, std::vector<StateCounts> &out);
 
 }  // namespace tn
 

@@ -46,7 +46,8 @@ class tn_plan_opts(ctypes.Structure):
                 ("time_limit_s", ctypes.c_double), ("iterations", ctypes.c_int32),
                 ("restart_threshold", ctypes.c_int32), ("fanin_samples", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("initial", ctypes.c_int32), ("pad0", ctypes.c_int32),
-                ("initial_part", ctypes.POINTER(ctypes.c_int32)), ("position", ctypes.POINTER(ctypes.c_int32))]
+                ("initial_part", ctypes.POINTER(ctypes.c_int32)), ("position", ctypes.POINTER(ctypes.c_int32)),
+                ("fanin_device", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
 
 class tn_plan_info(ctypes.Structure):
@@ -82,7 +83,7 @@ class tn_exec_config(ctypes.Structure):
     _fields_ = [("local_budget", ctypes.c_int32), ("big_programs", ctypes.c_int32),
                 ("warp_programs", ctypes.c_int32), ("tc_min_m", ctypes.c_int32), ("tc_min_n", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("rows_chains", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("graph_capture", ctypes.c_int32)]
+                ("graph_capture", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -105,6 +106,9 @@ _SIGS = {
     "tn_plan_create": (_I32, [_P, ctypes.POINTER(tn_plan_opts), ctypes.POINTER(_P)]),
     "tn_plan_import": (_I32, [_P, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
     "tn_plan_counts": (_I32, [_P, ctypes.POINTER(tn_u128), ctypes.POINTER(tn_u128), ctypes.POINTER(tn_u128)]),
+    "tn_plan_eval_states": (_I32, [_P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P]),
+    "tn_plan_slice": (_I32, [_P, _P, tn_u128, _I32, _P, _P, _P, _P, _P, _P]),
+    "tn_contract_sliced": (_I32, [_P, _P, _P, _I32, _I32, _P, _I32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
     "tn_plan_get_info": (_I32, [_P, ctypes.POINTER(tn_plan_info)]),
     "tn_plan_export": (_I32, [_P, _P, _P, _P, _P]),
     "tn_plan_free": (None, [_P]),
@@ -269,7 +273,7 @@ def tn_plan_opts_default() -> tn_plan_opts:
 
 def tn_plan_create(net: Net, k=1, mode="directed", T0=None, Tf=None, steps_per_temp=None, threads=None,
                    time_limit_s=None, iterations=None, restart_threshold=None, fanin_samples=None,
-                   seed=None, initial_part=None, initial=None, position=None) -> Plan:
+                   seed=None, initial_part=None, initial=None, position=None, fanin_device=None) -> Plan:
     """initial: "bfs", "qubit_block" (needs `position`, e.g. each tensor's qubit) or "given" (needs
     `initial_part`); when omitted, "given" if initial_part is passed, else "qubit_block" if position
     is passed, else "bfs"."""
@@ -279,7 +283,7 @@ def tn_plan_create(net: Net, k=1, mode="directed", T0=None, Tf=None, steps_per_t
     for name, val in (("T0", T0), ("Tf", Tf), ("steps_per_temp", steps_per_temp), ("threads", threads),
                       ("time_limit_s", time_limit_s), ("iterations", iterations),
                       ("restart_threshold", restart_threshold), ("fanin_samples", fanin_samples),
-                      ("seed", seed)):
+                      ("seed", seed), ("fanin_device", fanin_device)):
         if val is not None:
             setattr(o, name, val)
     if initial is None:
@@ -307,6 +311,50 @@ def tn_plan_import(net: Net, steps, part=None, k=None) -> Plan:
     _check(lib.tn_plan_import(net, kk, _ptr(pa) if pa is not None else None, len(st), _ptr(st),
                               ctypes.byref(out)))
     return Plan(out.value)
+
+
+def tn_plan_eval_states(net: Net, k: int, parts, fanin_samples: int = 32, device: int = -1):
+    """Counts of many states (parts: [n_states, n_tensors]): (con_serial, con_dist, mem,
+    saturated) as lists of Python ints / bools."""
+    p = np.ascontiguousarray(np.asarray(parts, dtype=np.int32))
+    n_states = p.shape[0] if p.ndim == 2 else 0
+    cs = (tn_u128 * max(n_states, 1))()
+    cd = (tn_u128 * max(n_states, 1))()
+    mm = (tn_u128 * max(n_states, 1))()
+    sat = np.zeros(max(n_states, 1), np.int32)
+    _check(lib.tn_plan_eval_states(net, int(k), int(fanin_samples), int(device), n_states, _ptr(p),
+                                   ctypes.cast(cs, ctypes.c_void_p), ctypes.cast(cd, ctypes.c_void_p),
+                                   ctypes.cast(mm, ctypes.c_void_p), _ptr(sat)))
+    return ([cs[i].value() for i in range(n_states)], [cd[i].value() for i in range(n_states)],
+            [mm[i].value() for i in range(n_states)], [bool(x) for x in sat[:n_states]])
+
+
+def _u128(x: int) -> tn_u128:
+    return tn_u128(x & (2 ** 64 - 1), x >> 64)
+
+
+def tn_plan_slice(net: Net, plan: Plan, target_mem: int, max_edges: int = 64) -> dict:
+    """Edges to slice so that the plan's per-slice mem is at most target_mem, with the counts."""
+    edges = np.zeros(max(max_edges, 1), np.int32)
+    n = ctypes.c_int32()
+    ns, sc, sm, tc = tn_u128(), tn_u128(), tn_u128(), tn_u128()
+    _check(lib.tn_plan_slice(net, plan, _u128(int(target_mem)), int(max_edges), _ptr(edges), ctypes.byref(n),
+                             ctypes.byref(ns), ctypes.byref(sc), ctypes.byref(sm), ctypes.byref(tc)))
+    return {"edges": edges[:n.value].tolist(), "n_slices": ns.value(), "slice_con": sc.value(),
+            "slice_mem": sm.value(), "total_con": tc.value()}
+
+
+def tn_contract_sliced(ctx: Ctx, net: Net, plan: Plan, sliced, precision="c64", max_jobs=1024, first_slice=0,
+                       slice_count=0):
+    """(mantissa, exp2, number of slices) of the sliced contraction (slice_count 0: all slices)."""
+    e = np.ascontiguousarray(np.asarray(sliced, dtype=np.int32))
+    amp = np.zeros(2, np.float64)
+    ex = ctypes.c_int32()
+    ns = ctypes.c_int64()
+    _check(lib.tn_contract_sliced(ctx, net, plan, PRECISIONS[precision], len(e), _ptr(e) if len(e) else None,
+                                  int(max_jobs), int(first_slice), int(slice_count), _ptr(amp), ctypes.byref(ex),
+                                  ctypes.byref(ns)))
+    return complex(amp[0], amp[1]), ex.value, ns.value
 
 
 def tn_plan_counts(plan: Plan):
@@ -377,8 +425,8 @@ def tn_ctx_get_config(ctx: Ctx) -> dict:
 
 def tn_ctx_set_config(ctx: Ctx, **fields) -> None:
     """Change fields of the context's execution configuration (local_budget, big_programs,
-    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains, wait_limit_us, graph_capture); the
-    others keep their values."""
+    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains, wait_limit_us, graph_capture, schedule);
+    the others keep their values."""
     cfg = tn_exec_config()
     _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
     for k, v in fields.items():

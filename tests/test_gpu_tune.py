@@ -103,3 +103,17 @@ def test_rows_chains_are_bit_identical(tnsa, batch_inputs, budget):
     assert np.array_equal(e1, e0)
     assert np.array_equal(m1.view(np.uint64), m0.view(np.uint64))
     _check(m1 * np.ldexp(1.0, e1), ref)
+
+
+def test_critical_path_schedule_is_bit_identical(tnsa, batch_inputs):
+    """The critical-path-first work order (path sums of Eq. 3.4) changes only when tiles run, not
+    what they compute: the results equal the level order's bit for bit."""
+    hs, plan, ref = batch_inputs
+    out = []
+    for sched in (0, 1):
+        ctx = tnsa.tn_ctx_create(0)
+        tnsa.tn_ctx_set_config(ctx, schedule=sched, local_budget=4096)
+        out.append(_run_bits(tnsa, ctx, hs, plan))
+    (m0, e0), (m1, e1) = out
+    assert np.array_equal(e0, e1) and np.array_equal(m0.view(np.uint64), m1.view(np.uint64))
+    _check(m1 * np.ldexp(1.0, e1), ref)
