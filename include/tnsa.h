@@ -287,8 +287,10 @@ tn_status tn_ctx_set_local_budget(tn_ctx *ctx, int32_t bytes);
  *                    weight of the path from the step to the root, sum of 2^vc (the path sums of
  *                    Eq. 3.4, whose maximum is con_par), so the steps on the longest weighted
  *                    paths are claimed first.
- * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0} (large programs off: on the 24-qubit brickwork
- * benchmark they measured slower than running fan-in chains as dataflow steps).
+ *   tc_tile_n        output tile width of the tensor-core steps, complex columns: 64 or 128; 0
+ *                    chooses 64 for a step with N <= 64 and 128 otherwise
+ * Defaults: {-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0, 0} (large programs off: on the 24-qubit
+ * brickwork benchmark they measured slower than running fan-in chains as dataflow steps).
  * Errors: TN_EINVAL. */
 typedef struct {
     int32_t local_budget;
@@ -299,14 +301,16 @@ typedef struct {
     int32_t wait_limit_us;
     int32_t graph_capture;
     int32_t schedule;
+    int32_t tc_tile_n;
 } tn_exec_config;
 tn_status tn_ctx_get_config(const tn_ctx *ctx, tn_exec_config *cfg);
 tn_status tn_ctx_set_config(tn_ctx *ctx, const tn_exec_config *cfg);
 
 /* Autotuner: for the batch (n, nets, plans, prec) -- the same arguments as tn_batch_create --
  * build a batch under each candidate configuration (program kinds on and off, block-program
- * budgets for two and three blocks per SM, no programs, ROWS chains off; in the split precisions
- * also tensor-core thresholds), time `runs` runs of each with CUDA events after warm-up, keep the fastest
+ * budgets for two and three blocks per SM, no programs, ROWS chains off, the critical-path-first
+ * work order; in the split precisions also tensor-core thresholds and the tensor-core tile width
+ * -- the tile shapes of the dense steps), time `runs` runs of each with CUDA events after warm-up, keep the fastest
  * configuration in the context and return it.  out_ms (may be NULL) receives its mean device time
  * per run; cand_ms (may be NULL, cap entries) the mean time of every candidate in the order tried,
  * with *n_cand the number of candidates (failed ones: a negative time).  Errors: TN_EINVAL, those

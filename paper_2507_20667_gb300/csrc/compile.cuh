@@ -56,6 +56,7 @@ struct CompileOpts {
     bool warp_programs = true;
     int32_t tc_mode = 0;
     int32_t tc_min_m = 64, tc_min_n = 32, tc_min_k = 16;
+    int32_t tc_tile_n = 0;            // dense-step tile width: 0 automatic (64 if N <= 64), 64, 128
     bool rows_chains = true;
 };
 

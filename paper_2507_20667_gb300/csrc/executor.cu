@@ -38,7 +38,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0};   // programs, TC, wait limit, graphs, order
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0, 0};   // programs, TC, waits, graphs, order, TC tile
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -562,6 +562,7 @@ tn::CompileOpts tn::compile_opts(const tn_exec_config &cfg, int32_t prec, bool c
     o.tc_min_n = cfg.tc_min_n;
     o.tc_min_k = cfg.tc_min_k;
     o.rows_chains = cfg.rows_chains != 0;
+    o.tc_tile_n = cfg.tc_tile_n;
     return o;
 }
 
@@ -812,8 +813,11 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             if (tc_mode == 2) d.flags |= FLAG_TF32;
             if (d.m.n > 0 && d.m.sa[0] == 1 && !(d.k.n > 0 && d.k.sa[0] == 1)) d.flags |= FLAG_A_MCONT;
             if (d.n.n > 0 && d.n.sa[0] == 1) d.flags |= FLAG_B_NCONT;
-            const int64_t tiles = ((M + kTcRows - 1) / kTcRows) * ((N + kTcCols - 1) / kTcCols);
-            if (tiles > 0x7fffffffLL || tc_pack_units(M, N, K, tc_mode == 2) > 0x7fffffffLL)
+            // output tile width: 64 complex columns when the step is that narrow (or forced)
+            const int nc = opt.tc_tile_n == 64 || (opt.tc_tile_n == 0 && N <= 64) ? 64 : kTcColsMax;
+            d.tile_rows = nc;
+            const int64_t tiles = ((M + kTcRows - 1) / kTcRows) * ((N + nc - 1) / nc);
+            if (tiles > 0x7fffffffLL || tc_pack_units(M, N, K, tc_mode == 2, nc) > 0x7fffffffLL)
                 return fail(TN_EUNSUPPORTED, "step too large");
             d.ntiles = (int32_t)tiles;
             c.steps.push_back(d);
@@ -874,7 +878,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
         for (StepDesc &d : c.steps) {
             if (d.kind != STEP_TC) continue;
             size_t a_bytes = 0;
-            const size_t all = tc_image_bytes(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0, &a_bytes);
+            const size_t all = tc_image_bytes(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0, d.tile_rows, &a_bytes);
             d.img_a = (int64_t)img;
             d.img_b = (int64_t)(img + a_bytes);
             img = align_up(img + all, 1024);
@@ -1078,7 +1082,7 @@ void tn::phase_templates(const Compiled &c, std::vector<PhaseTemplate> &out) {
         const StepDesc &d = c.steps[o[2]];
         PhaseTemplate &pt = out[o[0]];
         if (d.kind == STEP_TC) {
-            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0);
+            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0, d.tile_rows);
             for (int64_t u = 0; u < units; ++u) pt.pack.push_back({0u, (uint32_t)o[2], (uint32_t)u});
             for (int32_t t = 0; t < d.ntiles; ++t) pt.gemm.push_back({0u, (uint32_t)o[2], (uint32_t)t});
             continue;
@@ -1399,7 +1403,7 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         }
         auto add_tc = [&](int32_t job, int32_t st) {
             const StepDesc &d = b->comp[b->job_comp[job]].steps[st];
-            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0);
+            const int64_t units = tc_pack_units(d.M, d.N, d.K, (d.flags & FLAG_TF32) != 0, d.tile_rows);
             TcRange r{job, st, (int32_t)packs.size(), (int32_t)units, (int32_t)gemms.size(), d.ntiles};
             for (int64_t u = 0; u < units; ++u) packs.push_back({(uint32_t)job, (uint32_t)st, (uint32_t)u});
             for (int32_t t = 0; t < d.ntiles; ++t) gemms.push_back({(uint32_t)job, (uint32_t)st, (uint32_t)t});
@@ -1866,6 +1870,8 @@ tn_status tn_ctx_set_config(tn_ctx *c, const tn_exec_config *cfg) {
     c->cfg.rows_chains = cfg->rows_chains ? 1 : 0;
     c->cfg.graph_capture = cfg->graph_capture ? 1 : 0;
     if (cfg->schedule < 0 || cfg->schedule > 1) return fail(TN_EINVAL, "schedule must be 0 or 1");
+    if (cfg->tc_tile_n != 0 && cfg->tc_tile_n != 64 && cfg->tc_tile_n != 128)
+        return fail(TN_EINVAL, "tc_tile_n must be 0, 64 or 128");
     return TN_OK;
 }
 
@@ -2217,11 +2223,17 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
         c.wait_limit_us = saved.wait_limit_us;
         c.graph_capture = saved.graph_capture;
         c.schedule = 0;
+        c.tc_tile_n = 0;
     }
     {   // the critical-path-first order with the default program configuration
         tn_exec_config cp = cands[1];
         cp.schedule = 1;
         cands.push_back(cp);
+    }
+    if (tc_mode_of(prec)) {   // 128-column tiles for every dense step
+        tn_exec_config wide = cands[1];
+        wide.tc_tile_n = 128;
+        cands.push_back(wide);
     }
     for (size_t i = 0; i < cands.size(); ++i) {
         ctx->cfg = cands[i];

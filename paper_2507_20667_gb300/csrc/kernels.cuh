@@ -178,7 +178,9 @@ cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t strea
 // of each work item, thread 0), prof[kProfSlots + slot] counts items.  Slots 0..4: work items by
 // StepKind (dependency wait excluded); 5: block programs; 6: large programs; 8: waves of small
 // steps; 9: waves with block-wide steps (block programs); 10: warp programs (lane 0's view);
-// 12: dependency waits; 13: waves with block-wide steps (large programs).
+// 12: dependency waits; 13: waves with block-wide steps (large programs); 14: waiting for the
+// inputs of large programs; ROWS steps staged through shared memory, by phase: 7 operand staging,
+// 11 the multiply-add loop, 15 the epilogue.
 constexpr int kProfSlots = 16;
 
 // counter: two zeroed 32-bit words, the work claim counter and the launch-wide abort flag.
@@ -192,22 +194,23 @@ int32_t persistent_grid(bool c128);
 // ---- dense steps on the tensor cores (kernels_tc.cu) ------------------------------------------
 // A dense step C [M, N] = A [M, K] B [K, N] (complex64 storage, BF16 or TF32 split) runs as a pack
 // launch -- every operand k-block gathered, scaled, split into hi / lo and written as a
-// shared-memory image -- and a GEMM launch over 128 x 128 complex output tiles.  Images: A tile t,
-// k-block kb at img_a + (t KB + kb) 2 kTcImgA (hi plane, then lo); B'' likewise with kTcImgB.
+// shared-memory image -- and a GEMM launch over output tiles of 128 rows x NC complex columns,
+// NC = 64 or 128 per step (StepDesc.tile_rows).  Images: A tile t, k-block kb at
+// img_a + (t KB + kb) 2 kTcImgA (hi plane, then lo); B'' likewise with planes of tc_img_b(NC).
 constexpr int kTcRows = 128;               // rows of C per GEMM tile (tensor-memory lanes)
-constexpr int kTcCols = 128;               // complex columns of C per GEMM tile (256 real)
+constexpr int kTcColsMax = 128;            // complex columns of C per GEMM tile, at most (256 real)
 constexpr uint32_t kTcImgA = 128 * 64;     // one plane of an A k-block: 128 rows x 64 bytes
-constexpr uint32_t kTcImgB = 256 * 64;     // one plane of a B'' k-block: 256 rows x 64 bytes
-// units: (job, step, unit) with unit < (ceil(M/128) + ceil(N/128)) KB (tc_pack_units).
+__host__ __device__ constexpr uint32_t tc_img_b(int nc) { return (uint32_t)(2 * nc * 64); }   // 2 NC rows x 64 B
+// units: (job, step, unit) with unit < (ceil(M/128) + ceil(N/NC)) KB (tc_pack_units).
 cudaError_t launch_tc_pack(bool tf32, const JobPtrs *jobs_dev, const WorkItem *units, int32_t n_units,
                            cudaStream_t stream);
-// tiles: (job, step, tile) with tile < ceil(M/128) ceil(N/128); each completed tile adds one to
+// tiles: (job, step, tile) with tile < ceil(M/128) ceil(N/NC); each completed tile adds one to
 // the job's done[step].  abort_flag: a zeroed device int32 (the launch-wide abort flag).
 cudaError_t launch_tc_gemm(bool tf32, const JobPtrs *jobs_dev, const WorkItem *tiles, int32_t n_tiles,
                            int32_t *abort_flag, long long wait_ns, cudaStream_t stream);
-int64_t tc_pack_units(int64_t M, int64_t N, int64_t K, bool tf32);
+int64_t tc_pack_units(int64_t M, int64_t N, int64_t K, bool tf32, int nc);
 // Bytes of a step's operand images (a_bytes: the A part, may be NULL).
-size_t tc_image_bytes(int64_t M, int64_t N, int64_t K, bool tf32, size_t *a_bytes);
+size_t tc_image_bytes(int64_t M, int64_t N, int64_t K, bool tf32, int nc, size_t *a_bytes);
 // Subtree programs; items: (job, pseudo-step, 0), the n_warp warp programs first (four per
 // block of kWarpThreads), then the n_block block programs (one per block, `dyn_smem` bytes), then
 // the n_big large programs (one per block, `dyn_big` bytes).
@@ -233,7 +236,7 @@ constexpr int kRowsSmemElems = 9216;
 constexpr int kPersistDynSmem = kRowsSmemElems * 8;
 // Longest chain of ROWS steps one persistent block runs with the tensor kept in shared memory.
 constexpr int kMaxChain = 32;
-constexpr int kDotChunk = 2048;                         // shared indices per DOTP tile
+constexpr int kDotChunk = 8192;                         // shared indices per DOTP tile
 // Warp programs: blocks of kWarpThreads, each warp with a private kWarpSlice-byte shared-memory
 // slice (step descriptor, scale slots, intermediates).
 constexpr int kWarpThreads = 128;

@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepDesc *__restrict__ 
     run_item<T>(d, blockIdx.x, job, smem, red, dyn, nullptr);
 }
 
-// Persistent dataflow kernel.
-template <typename T>
+// Persistent dataflow kernel.  PROF: the variant with cycle accounting (prof non-null).
+template <typename T, bool PROF>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
     k_persist(const JobPtrs *__restrict__ jobs, const WorkItem *__restrict__ work, int64_t n_work,
               uint32_t *counter, long long wait_ns, long long *prof) {
@@ -205,12 +205,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         desc_fetch(dr, j.steps + it.step);
         long long t0 = 0;
         if (threadIdx.x == 0) {
-            if (prof) t0 = clock64();
+            if (PROF) t0 = clock64();
             nxt = atomicAdd(counter, 1u);
             const bool ok = wait_deps(j, it, abort_flag, wait_ns);
             if (!ok) atomicExch(&static_cast<DeviceResult *>(j.result)->status, kStatusTimeout);
             s_ok = ok;
-            if (prof) {
+            if (PROF) {
                 const long long t1 = clock64();
                 atomicAdd((unsigned long long *)(prof + 12), (unsigned long long)(t1 - t0));
                 atomicAdd((unsigned long long *)(prof + kProfSlots + 12), 1ull);
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
         bool chained = false;
         if constexpr (sizeof(T) == 4) {
             if (s_ok && d.kind == STEP_ROWS && d.chain_next >= 0) {
-                n_chain = rows_chain(d, j, smem, dyn, red, s_chain);
+                n_chain = rows_chain<PROF>(d, j, smem, dyn, red, s_chain, prof);
                 chained = true;
             }
         }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1)
                     st = __ldcg(&j.steps[st].chain_next);
                 }
             }
-            if (prof) {
+            if (PROF) {
                 atomicAdd((unsigned long long *)(prof + d.kind), (unsigned long long)(clock64() - t0));
                 atomicAdd((unsigned long long *)(prof + kProfSlots + d.kind), 1ull);
             }
@@ -318,11 +318,11 @@ int32_t persistent_grid(bool c128) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     cudaError_t e;
     if (c128) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<double, false>, kThreads, 0);
     } else {
-        e = allow_dyn_smem(k_persist<float>, kPersistDynSmem);
+        e = allow_dyn_smem(k_persist<float, false>, kPersistDynSmem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float>, kThreads, kPersistDynSmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<float, false>, kThreads, kPersistDynSmem);
     }
     if (e != cudaSuccess) return 0;
     return sms * per_sm;
@@ -378,12 +378,17 @@ cudaError_t launch_persistent(bool c128, const JobPtrs *jobs_dev, const WorkItem
     if (n_work <= 0) return cudaSuccess;
     if (grid > n_work) grid = (int32_t)n_work;
     if (c128) {
-        k_persist<double><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter, wait_ns, prof);
+        if (prof)
+            k_persist<double, true><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter,
+                                                                            wait_ns, prof);
+        else
+            k_persist<double, false><<<(unsigned)grid, kThreads, 0, stream>>>(jobs_dev, work, n_work, counter,
+                                                                             wait_ns, nullptr);
     } else {
-        const cudaError_t e = allow_dyn_smem(k_persist<float>, kPersistDynSmem);
+        auto kern = prof ? k_persist<float, true> : k_persist<float, false>;
+        const cudaError_t e = allow_dyn_smem(kern, kPersistDynSmem);
         if (e != cudaSuccess) return e;
-        k_persist<float><<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work, counter,
-                                                                               wait_ns, prof);
+        kern<<<(unsigned)grid, kThreads, kPersistDynSmem, stream>>>(jobs_dev, work, n_work, counter, wait_ns, prof);
     }
     return cudaGetLastError();
 }

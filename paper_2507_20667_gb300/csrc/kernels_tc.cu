@@ -11,10 +11,10 @@
 //                A_real B''^T is C [M, N] with (Re, Im) interleaved (the real 4M form).  Tails
 //                (rows, columns, shared indices past the step's extent) are zero.
 //  * k_tc_gemm   one CTA per SM, warp-specialised: warp 0 streams the k-block images of a
-//                128-row x 128-complex-column tile with bulk copies into a 4-stage shared-memory
-//                ring (mbarrier transaction counts), warp 1 issues the MMAs -- per k-block
-//                hi*hi, hi*lo and lo*hi, each as two K-slices -- into a 128 x 256 FP32 accumulator
-//                in tensor memory and releases each stage with tcgen05.commit, and warps 2-5 read
+//                128-row x NC-complex-column tile (NC = 64 or 128) with bulk copies into a 4-stage
+//                shared-memory ring (mbarrier transaction counts), warp 1 issues the MMAs -- per
+//                k-block hi*hi, hi*lo and lo*hi, each as two K-slices -- into a 128 x 2NC FP32
+//                accumulator in tensor memory and releases each stage with tcgen05.commit, and warps 2-5 read
 //                the accumulator (tcgen05.ld) into complex64 C, publish the tile's max-abs and
 //                mark the tile complete.  The producer runs up to four k-blocks ahead of the MMAs,
 //                across tile boundaries.
@@ -36,7 +36,7 @@ constexpr int32_t kStatusTimeout = 5;
 constexpr int kPackThreads = 256;
 constexpr int kGemmThreads = 192;      // warp 0 producer, warp 1 MMA issuer, warps 2-5 epilogue
 constexpr int kStages = 4;
-constexpr uint32_t kStageBytes = 2 * kTcImgA + 2 * kTcImgB;   // A hi, A lo, B'' hi, B'' lo
+constexpr uint32_t kStageBytes = 2 * kTcImgA + 2 * tc_img_b(kTcColsMax);   // A hi, A lo, B'' hi, B'' lo
 constexpr uint32_t kAccCols = 256;                             // 128 x 256 FP32 accumulator
 constexpr int kBarBytes = 256;
 constexpr int kGemmSmem = kStages * (int)kStageBytes + kBarBytes + 1024;   // + alignment slack
@@ -84,13 +84,16 @@ __global__ void __launch_bounds__(kPackThreads) k_tc_pack(const JobPtrs *__restr
     const JobPtrs &j = jobs[u.job];
     load_desc(d, j.steps + u.step);
     const int64_t M = d.M, N = d.N, K = d.K;
+    const int NC = d.tile_rows;
     const int64_t KB = (K + KC - 1) / KC, MT = (M + kTcRows - 1) / kTcRows;
     const bool side_a = (int64_t)u.tile < MT * KB;
     const int64_t v = side_a ? (int64_t)u.tile : (int64_t)u.tile - MT * KB;
     const int64_t t = v / KB, kb = v % KB;
-    const int64_t extent = side_a ? M : N, r0 = t * kTcRows, k0 = kb * KC;
+    const int rows = side_a ? kTcRows : NC;   // operand rows of the unit (B: complex columns)
+    const int64_t extent = side_a ? M : N, r0 = t * rows, k0 = kb * KC;
     const Groups &g = side_a ? d.m : d.n;
-    for (int i = threadIdx.x; i < kTcRows; i += kPackThreads) roff[i] = (r0 + i < extent) ? group_off(g, r0 + i) : -1;
+    for (int i = threadIdx.x; i < kTcRows; i += kPackThreads)
+        roff[i] = (i < rows && r0 + i < extent) ? group_off(g, r0 + i) : -1;
     for (int i = threadIdx.x; i < KC; i += kPackThreads) {
         int64_t oa = -1, ob = -1;
         if (k0 + i < K) group_off2(d.k, k0 + i, oa, ob);
@@ -118,12 +121,13 @@ __global__ void __launch_bounds__(kPackThreads) k_tc_pack(const JobPtrs *__restr
     }
     __syncthreads();
     // split and write, shared index fastest (a warp covers whole 64-byte rows)
-    const uint32_t plane = side_a ? kTcImgA : kTcImgB;
+    const uint32_t plane = side_a ? kTcImgA : tc_img_b(NC);
     char *img = j.arena + (side_a ? d.img_a : d.img_b) + (size_t)(t * KB + kb) * 2 * plane;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int e = threadIdx.x + q * kPackThreads;
         const int r = e / KC, kk = e % KC;
+        if (r >= rows) continue;   // a B unit of NC = 64 columns fills half the tile
         const float2 y = tile[r * LD + kk];
         if (side_a) {
             put_pair<TF32>(img, plane, (uint32_t)r, (uint32_t)kk, y.x, y.y);
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(kPackThreads) k_tc_pack(const JobPtrs *__restr
 // Geometry of one GEMM tile, read by every role from the step descriptor.
 struct TileGeo {
     int64_t M, N, KB, mt, nt;
+    int NC;
     const char *img_a, *img_b;
 };
 
@@ -149,11 +154,12 @@ __device__ __forceinline__ TileGeo tile_geo(const JobPtrs &j, const WorkItem &w)
     g.M = __ldcg(&d->M);
     g.N = __ldcg(&d->N);
     g.KB = (__ldcg(&d->K) + KC - 1) / KC;
-    const int64_t NT = (g.N + kTcCols - 1) / kTcCols;
+    g.NC = __ldcg(&d->tile_rows);
+    const int64_t NT = (g.N + g.NC - 1) / g.NC;
     g.mt = (int64_t)w.tile / NT;
     g.nt = (int64_t)w.tile % NT;
     g.img_a = j.arena + __ldcg(&d->img_a) + (size_t)(g.mt * g.KB) * 2 * kTcImgA;
-    g.img_b = j.arena + __ldcg(&d->img_b) + (size_t)(g.nt * g.KB) * 2 * kTcImgB;
+    g.img_b = j.arena + __ldcg(&d->img_b) + (size_t)(g.nt * g.KB) * 2 * tc_img_b(g.NC);
     return g;
 }
 
@@ -216,9 +222,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     break;
                 }
                 char *st = ring + s * kStageBytes;
-                mbar_arrive_expect_tx(full + s, kStageBytes);
+                const uint32_t bb = 2 * tc_img_b(g.NC);
+                mbar_arrive_expect_tx(full + s, 2 * kTcImgA + bb);
                 bulk_g2s(st, g.img_a + (size_t)kb * 2 * kTcImgA, 2 * kTcImgA, full + s);
-                bulk_g2s(st + 2 * kTcImgA, g.img_b + (size_t)kb * 2 * kTcImgB, 2 * kTcImgB, full + s);
+                bulk_g2s(st + 2 * kTcImgA, g.img_b + (size_t)kb * bb, bb, full + s);
             }
         }
         // the copies this CTA started land before it exits
@@ -226,7 +233,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (uint32_t i = first; i < it; ++i) mbar_drain(full + i % kStages, (i / kStages) & 1u, wait_ns);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
-        const uint32_t idesc = TF32 ? idesc_tf32(kTcRows, 2 * kTcCols) : idesc_bf16(kTcRows, 2 * kTcCols);
         uint32_t it = 0, tl = 0;
         bool ok = true;
         for (int32_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tl) {
@@ -238,6 +244,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc_fence_after();
+            const uint32_t idesc = TF32 ? idesc_tf32(kTcRows, 2 * g.NC) : idesc_bf16(kTcRows, 2 * g.NC);
             for (int64_t kb = 0; kb < g.KB; ++kb, ++it) {
                 const uint32_t s = it % kStages;
                 if (!mbar_wait(full + s, (it / kStages) & 1u, wait_ns, abort_flag)) {
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tc_fence_after();
                 const uint32_t a = smem_u32(ring + s * kStageBytes);
                 const uint64_t ah = smem_desc_sw64(a), al = smem_desc_sw64(a + kTcImgA);
-                const uint64_t bh = smem_desc_sw64(a + 2 * kTcImgA), bl = smem_desc_sw64(a + 2 * kTcImgA + kTcImgB);
+                const uint64_t bh = smem_desc_sw64(a + 2 * kTcImgA), bl = smem_desc_sw64(a + 2 * kTcImgA + tc_img_b(g.NC));
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // two 32-byte K-slices of the 64-byte rows
                     const uint64_t adv = (uint64_t)(h * 32 >> 4);
@@ -289,10 +296,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int64_t N = g.N;
             float2 *__restrict__ Cp = reinterpret_cast<float2 *>(j.arena) + __ldcg(&d->c_off);
             float mx = 0.f;
-            for (int c = 0; c < 2 * kTcCols / 16; ++c) {
+            for (int c = 0; c < 2 * g.NC / 16; ++c) {
                 float v[16];
                 tc_ld16(tmem + ((32u * quarter) << 16) + (uint32_t)(16 * c), v);
-                const int64_t n0 = g.nt * kTcCols + 8 * c;
+                const int64_t n0 = g.nt * g.NC + 8 * c;
                 if (m < g.M) {
                     float2 *row = Cp + m * N;
                     if (n0 + 8 <= N && ((m * N + n0) & 1) == 0) {
@@ -372,15 +379,15 @@ cudaError_t launch_tc_gemm(bool tf32, const JobPtrs *jobs_dev, const WorkItem *t
     return cudaGetLastError();
 }
 
-int64_t tc_pack_units(int64_t M, int64_t N, int64_t K, bool tf32) {
+int64_t tc_pack_units(int64_t M, int64_t N, int64_t K, bool tf32, int nc) {
     const int64_t KC = tf32 ? 8 : 16, KB = (K + KC - 1) / KC;
-    return ((M + kTcRows - 1) / kTcRows + (N + kTcCols - 1) / kTcCols) * KB;
+    return ((M + kTcRows - 1) / kTcRows + (N + nc - 1) / nc) * KB;
 }
 
-size_t tc_image_bytes(int64_t M, int64_t N, int64_t K, bool tf32, size_t *a_bytes) {
+size_t tc_image_bytes(int64_t M, int64_t N, int64_t K, bool tf32, int nc, size_t *a_bytes) {
     const int64_t KC = tf32 ? 8 : 16, KB = (K + KC - 1) / KC;
     const size_t a = (size_t)((M + kTcRows - 1) / kTcRows) * (size_t)KB * 2 * kTcImgA;
-    const size_t b = (size_t)((N + kTcCols - 1) / kTcCols) * (size_t)KB * 2 * kTcImgB;
+    const size_t b = (size_t)((N + nc - 1) / nc) * (size_t)KB * 2 * tc_img_b(nc);
     if (a_bytes) *a_bytes = a;
     return a + b;
 }

@@ -271,9 +271,23 @@ __device__ __forceinline__ float block_max(float v, float *red) {
 // the block's max-abs of C) or is written into the same shared memory with padded rows and leaves
 // it in coalesced order.  HBM traffic: one read of A, one write of C, both coalesced (neither
 // for the inner steps of a chain).  Ends with a barrier.
-template <int NT, bool A_ROT>
+// Phase cycle accounting of the profiling variant of the dataflow kernel (PROF), compiled out of
+// the other one.
+template <bool PROF>
+__device__ __forceinline__ void prof_phase(long long *prof, int slot, long long &t) {
+    if (PROF && threadIdx.x == 0) {
+        const long long t1 = clock64();
+        atomicAdd((unsigned long long *)(prof + slot), (unsigned long long)(t1 - t));
+        atomicAdd((unsigned long long *)(prof + kProfSlots + slot), 1ull);
+        t = t1;
+    }
+}
+
+template <int NT, bool A_ROT, bool PROF>
 __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red,
-                               float sA, float sB, bool c_in_smem, float &cmax) {
+                               float sA, float sB, bool c_in_smem, float &cmax, long long *prof) {
+    long long tp = 0;
+    if (PROF && threadIdx.x == 0) tp = clock64();
     using C = float2;
     constexpr int R = 32 / NT;
     C *As = reinterpret_cast<C *>(dyn);
@@ -310,6 +324,7 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
     }
     if (!A_ROT) asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
+    prof_phase<PROF>(prof, 7, tp);
     const int32_t lga = d.a_lgn;
     const bool skew = d.k.n > 0 && d.k.sa[0] == 1;
     const int32_t step = blockDim.x;
@@ -352,6 +367,7 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
         }
     }
     __syncthreads();   // every thread is done reading A
+    prof_phase<PROF>(prof, 11, tp);
     float mx = 0.f;
     if (c_in_smem) {
         const int32_t lgn = __ffs(N) - 1, rs = lgn >= 4 ? 0 : 4 - lgn;
@@ -367,6 +383,7 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
                 }
         }
         cmax = block_max(mx, red);
+        prof_phase<PROF>(prof, 15, tp);
         return;
     }
 #pragma unroll
@@ -386,14 +403,16 @@ __device__ void rows_smem_core(const StepDesc &d, const JobPtrs &j, char *smem, 
         Cp[i] = As[m * PC + (i - m * N)];
     }
     publish_max(mx, j.maxbits + d.node_c, red);
+    prof_phase<PROF>(prof, 15, tp);
 }
 
-template <bool A_ROT>
+template <bool A_ROT, bool PROF>
 __device__ __forceinline__ void rows_smem_any(const StepDesc &d, const JobPtrs &j, char *smem, char *dyn,
-                                              float *red, float sA, float sB, bool c_in_smem, float &cmax) {
-    if (d.N <= 4) rows_smem_core<4, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
-    else if (d.N <= 8) rows_smem_core<8, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
-    else rows_smem_core<16, A_ROT>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax);
+                                              float *red, float sA, float sB, bool c_in_smem, float &cmax,
+                                              long long *prof) {
+    if (d.N <= 4) rows_smem_core<4, A_ROT, PROF>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax, prof);
+    else if (d.N <= 8) rows_smem_core<8, A_ROT, PROF>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax, prof);
+    else rows_smem_core<16, A_ROT, PROF>(d, j, smem, dyn, red, sA, sB, c_in_smem, cmax, prof);
 }
 
 // A ROWS step staged through shared memory on its own.
@@ -402,7 +421,7 @@ __device__ __forceinline__ void tile_rows_smem(const StepDesc &d, const JobPtrs 
     int32_t eA, eB;
     step_scales(d, j, eA, eB);
     float cmax = 0.f;
-    rows_smem_any<false>(d, j, smem, dyn, red, pow2<float>(-eA), pow2<float>(-eB), false, cmax);
+    rows_smem_any<false, false>(d, j, smem, dyn, red, pow2<float>(-eA), pow2<float>(-eB), false, cmax, nullptr);
     if (threadIdx.x == 0) write_exponent(d, j, eA, eB);
 }
 
@@ -414,8 +433,9 @@ __device__ __forceinline__ void tile_rows_smem(const StepDesc &d, const JobPtrs 
 // by one; the exponents of the inner nodes stay in registers and only the last node's max-abs and
 // exponent are written.  d is the block's shared descriptor and is overwritten with each step's;
 // thread 0 writes the indices of the continuation steps to chain[].  Returns their count.
+template <bool PROF>
 __device__ __forceinline__ int32_t rows_chain(StepDesc &d, const JobPtrs &j, char *smem, char *dyn, float *red,
-                                              int32_t *chain) {
+                                              int32_t *chain, long long *prof) {
     int32_t eA, eB;
     step_scales(d, j, eA, eB);
     int32_t xa = __ldcg(j.exp2 + d.node_a), xb = __ldcg(j.exp2 + d.node_b);
@@ -426,8 +446,8 @@ __device__ __forceinline__ int32_t rows_chain(StepDesc &d, const JobPtrs &j, cha
         if (next >= 0) desc_fetch(dr, j.steps + next);
         float cmax = 0.f;
         const float sA = pow2<float>(-eA), sB = pow2<float>(-eB);
-        if (n == 0) rows_smem_any<false>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax);
-        else rows_smem_any<true>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax);
+        if (n == 0) rows_smem_any<false, PROF>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax, prof);
+        else rows_smem_any<true, PROF>(d, j, smem, dyn, red, sA, sB, next >= 0, cmax, prof);
         const int32_t xc = xa + eA + xb + eB;
         if (next < 0) {
             if (threadIdx.x == 0) j.exp2[d.node_c] = xc;

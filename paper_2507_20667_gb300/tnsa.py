@@ -83,7 +83,7 @@ class tn_exec_config(ctypes.Structure):
     _fields_ = [("local_budget", ctypes.c_int32), ("big_programs", ctypes.c_int32),
                 ("warp_programs", ctypes.c_int32), ("tc_min_m", ctypes.c_int32), ("tc_min_n", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("rows_chains", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("graph_capture", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+                ("graph_capture", ctypes.c_int32), ("schedule", ctypes.c_int32), ("tc_tile_n", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -425,8 +425,8 @@ def tn_ctx_get_config(ctx: Ctx) -> dict:
 
 def tn_ctx_set_config(ctx: Ctx, **fields) -> None:
     """Change fields of the context's execution configuration (local_budget, big_programs,
-    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains, wait_limit_us, graph_capture, schedule);
-    the others keep their values."""
+    warp_programs, tc_min_m, tc_min_n, tc_min_k, rows_chains, wait_limit_us, graph_capture, schedule,
+    tc_tile_n); the others keep their values."""
     cfg = tn_exec_config()
     _check(lib.tn_ctx_get_config(ctx, ctypes.byref(cfg)))
     for k, v in fields.items():

@@ -127,12 +127,14 @@ def _edge_samples(extent, tile, rng, extra):
     return sorted(s)
 
 
-@pytest.mark.parametrize("shape", [(200, 40, 100), (136, 48, 72), (1024, 512, 1024)])
+@pytest.mark.parametrize("shape,tile", [((200, 40, 100), 0), ((200, 40, 100), 64), ((136, 48, 72), 128),
+                                        ((136, 48, 60), 0), ((1024, 512, 1024), 0)])
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
-def test_tc_gemm_elementwise(tnsa, shape, prec):
+def test_tc_gemm_elementwise(tnsa, shape, tile, prec):
     """Elements of the tensor-core product C = A B at sampled (i, j) covering every 128-row and
     64-column tile edge and the ragged tails (M, N, K not multiples of 128, 64 and 32), each within
-    1e-4 (BF16 split) or 1e-5 (TF32 split) of max |C| against numpy complex128."""
+    1e-4 (BF16 split) or 1e-5 (TF32 split) of max |C| against numpy complex128; output tiles of 64
+    and of 128 complex columns (tile 0: 64 when N <= 64)."""
     I, K, J = shape
     net = _Bilinear(I, K, J, seed=I + K + J)
     C = net.A @ net.B
@@ -149,7 +151,7 @@ def test_tc_gemm_elementwise(tnsa, shape, prec):
     steps = tnsa.tn_plan_compile_steps(h, plan, prec, 0)
     assert steps[0, 0] == 4, "the product must run as a tensor-core step"
     ctx = tnsa.tn_ctx_create(0)
-    tnsa.tn_ctx_set_local_budget(ctx, 0)
+    tnsa.tn_ctx_set_config(ctx, local_budget=0, tc_tile_n=tile)
     b = tnsa.tn_batch_create(ctx, [h] * len(pairs), [plan] * len(pairs), prec)
     jobs, tens, data = [], [], []
     for q, (i, j) in enumerate(pairs):
