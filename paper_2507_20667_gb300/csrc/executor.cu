@@ -76,6 +76,7 @@ struct tn_batch {
     std::vector<int64_t> leaf64_off;  // per job, element offset into d_leaf64
     int64_t leaf_elems_total = 0;
     int32_t max_leaves = 0;
+    int64_t max_leaf_elems = 0;      // the largest leaf of any job
     // device memory: one allocation, carved
     void *d_block = nullptr;
     double2 *d_leaf64 = nullptr;
@@ -778,6 +779,19 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
                 }
                 if (fits && t0 <= 0x7fffffffULL) p.ktab_off = (int32_t)t0;
                 else c.ktab.resize(t0);
+                // one complex64 tile over a vector operand read in a permuted order: stage the more
+                // permuted one (counted in breaks of unit stride along k) in shared memory
+                if (p.ktab_off >= 0 && elem == 8 && p.ntiles == 1 && K <= kRowsSmemElems) {
+                    int64_t brk_a = 0, brk_b = 0;
+                    for (int64_t k = 1; k < K; ++k) {
+                        const int2 u = c.ktab[t0 + (size_t)k - 1], v = c.ktab[t0 + (size_t)k];
+                        brk_a += v.x != u.x + 1;
+                        brk_b += v.y != u.y + 1;
+                    }
+                    const bool a_ok = M == 1 && !(p.flags & FLAG_A_LEAF), b_ok = N == 1 && !(p.flags & FLAG_B_LEAF);
+                    if (b_ok && brk_b > 0 && (brk_b >= brk_a || !a_ok)) p.flags |= FLAG_DOT_SMEM_B;
+                    else if (a_ok && brk_a > 0) p.flags |= FLAG_DOT_SMEM_A;
+                }
             }
             c.steps.push_back(p);
             StepDesc f = d;
@@ -1190,7 +1204,7 @@ cudaError_t enqueue_run(tn_batch *b, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
     if (e == cudaSuccess) {
         t_enqueue_stage = "leaf conversion";
-        e = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+        e = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, b->max_leaf_elems, st);
     }
     if (e != cudaSuccess) return e;
     if (b->mode == TN_EXEC_PERSISTENT) {
@@ -1233,7 +1247,7 @@ tn_status record_persistent_graph(tn_batch *b) {
     (void)cudaGetLastError();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     err = cudaMemsetAsync(b->d_reset, 0, b->reset_bytes, st);
-    if (err == cudaSuccess) err = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, st);
+    if (err == cudaSuccess) err = launch_leaf_convert(b->c128, b->d_jobs, b->n_jobs, b->max_leaves, b->max_leaf_elems, st);
     if (err == cudaSuccess) err = enqueue_persistent(b, st, b->gev, true);
     for (int32_t jb = 0; err == cudaSuccess && jb < b->n_jobs; ++jb)
         if (b->comp[b->job_comp[jb]].n == 1) err = launch_finish_leaf(b->c128, b->jobs[jb], st);
@@ -1367,6 +1381,10 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
         b->leaf64_off[i] = leaf_total;
         leaf_total += b->comp[b->job_comp[i]].leaf_off.back();
         b->max_leaves = std::max(b->max_leaves, b->comp[b->job_comp[i]].n);
+        {
+            const std::vector<int64_t> &lo = b->comp[b->job_comp[i]].leaf_off;
+            for (size_t t = 0; t + 1 < lo.size(); ++t) b->max_leaf_elems = std::max(b->max_leaf_elems, lo[t + 1] - lo[t]);
+        }
     }
     b->leaf_elems_total = leaf_total;
     const size_t o_leaf64 = carve(sizeof(double2) * (size_t)leaf_total);

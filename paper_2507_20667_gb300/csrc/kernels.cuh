@@ -42,7 +42,10 @@ enum StepFlags : int32_t {
     FLAG_CHAIN_CONT = 64, // ROWS (FLAG_A_SMEM): A is the C of the previous step of a chain, which
                           // the persistent kernel keeps in shared memory; no work item of its own
     FLAG_A_MCONT = 128,   // TC: A's row index is its contiguous one (the pack reads rows fastest)
-    FLAG_B_NCONT = 256    // TC: B's column index is its contiguous one
+    FLAG_B_NCONT = 256,   // TC: B's column index is its contiguous one
+    FLAG_DOT_SMEM_A = 512,  // DOTP (complex64, one tile, M = 1): A, read in a permuted order, is
+                            // first copied whole and coalesced into shared memory
+    FLAG_DOT_SMEM_B = 1024  // the same for B (N = 1)
 };
 
 struct StepDesc {
@@ -169,8 +172,9 @@ struct WorkItem {
 static_assert(sizeof(WorkItem) == 32, "work items are 32 bytes");
 
 // Launchers (all enqueue on `stream`, return the launch error).
+// max_leaf_elems: the largest leaf of any job (selects the conversion for large leaves).
 cudaError_t launch_leaf_convert(bool c128, const JobPtrs *jobs_dev, int32_t n_jobs,
-                                int32_t max_leaves, cudaStream_t stream);
+                                int32_t max_leaves, int64_t max_leaf_elems, cudaStream_t stream);
 cudaError_t launch_step(bool c128, const StepDesc &h_desc, int32_t step, const JobPtrs &job,
                         int32_t dyn_smem, cudaStream_t stream);
 cudaError_t launch_finish_leaf(bool c128, const JobPtrs &job, cudaStream_t stream);

@@ -13,11 +13,18 @@
 //  * k_tc_gemm   one CTA per SM, warp-specialised: warp 0 streams the k-block images of a
 //                128-row x NC-complex-column tile (NC = 64 or 128) with bulk copies into a 4-stage
 //                shared-memory ring (mbarrier transaction counts), warp 1 issues the MMAs -- per
-//                k-block hi*hi, hi*lo and lo*hi, each as two K-slices -- into a 128 x 2NC FP32
-//                accumulator in tensor memory and releases each stage with tcgen05.commit, and warps 2-5 read
-//                the accumulator (tcgen05.ld) into complex64 C, publish the tile's max-abs and
-//                mark the tile complete.  The producer runs up to four k-blocks ahead of the MMAs,
-//                across tile boundaries.
+//                k-block hi*hi, hi*lo and lo*hi, each as two K-slices -- and releases each stage
+//                with tcgen05.commit, and warps 2-9 add the accumulator into FP32 registers
+//                (tcgen05.ld), write complex64 C, publish the tile's max-abs and mark the tile
+//                complete.  The tensor-memory accumulator holds at most kSegBlocks k-blocks: a long
+//                shared index is summed in segments, each accumulated by the tensor cores into one
+//                of two 128 x 2NC FP32 buffers and then added, rounding to nearest, into the
+//                epilogue's registers while the next segment accumulates in the other buffer.  The
+//                tensor cores' own accumulation does not round to nearest (measured: the product
+//                drifts toward zero by about 2^-25 of its value per accumulated MMA), so bounding
+//                the MMAs per buffer bounds that drift whatever K is.  The producer runs up to four
+//                k-blocks ahead of the MMAs, across tile boundaries, and a tile's epilogue overlaps
+//                the next tile's MMAs.
 //
 // Every mbarrier wait is bounded and gives up when the launch-wide abort flag rises; a role that
 // gives up marks its job TN_ETIMEOUT, and before the CTA exits the producer waits (bounded) for
@@ -34,14 +41,18 @@ namespace {
 
 constexpr int32_t kStatusTimeout = 5;
 constexpr int kPackThreads = 256;
-constexpr int kGemmThreads = 192;      // warp 0 producer, warp 1 MMA issuer, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // warp 0 producer, warp 1 MMA issuer, warps 2-9 epilogue
 constexpr int kStages = 4;
 constexpr uint32_t kStageBytes = 2 * kTcImgA + 2 * tc_img_b(kTcColsMax);   // A hi, A lo, B'' hi, B'' lo
-constexpr uint32_t kAccCols = 256;                             // 128 x 256 FP32 accumulator
+constexpr uint32_t kAccBuf = 256;                              // 128 x 256 FP32 accumulator buffer
+constexpr uint32_t kAccCols = 2 * kAccBuf;                     // two buffers: all 512 TMEM columns
+constexpr int kSegBlocks = 8;                                  // k-blocks per accumulation segment
 constexpr int kBarBytes = 256;
 constexpr int kGemmSmem = kStages * (int)kStageBytes + kBarBytes + 1024;   // + alignment slack
 static_assert(kStageBytes % 1024 == 0, "stage images keep 1024-byte alignment");
-static_assert((2 * kStages + 3) * 8 + 4 <= kBarBytes, "barrier area");
+static_assert((2 * kStages + 5) * 8 + 12 <= kBarBytes, "barrier area");
+static_assert(2 * kTcColsMax <= (int)kAccBuf, "a tile's accumulator fits one buffer");
 static_assert(kGemmSmem <= 227 * 1024, "shared memory per CTA");
 
 template <bool TF32> struct TcK { static constexpr int KC = TF32 ? 8 : 16; };   // complex k per k-block
@@ -183,21 +194,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     char *ring = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * kStageBytes);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;
-    uint64_t *acc_empty = acc_full + 1;
-    uint64_t *drain = acc_empty + 1;
+    uint64_t *acc_full = empty + kStages;    // [2] a segment is accumulated in buffer b
+    uint64_t *acc_empty = acc_full + 2;      // [2] the epilogue has read buffer b
+    uint64_t *drain = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
-    uint32_t *tiles_seen = tmem_slot + 1;   // epilogue-warp tickets: four per completed tile
+    // epilogue-warp tickets, counted per buffer of a tile's last segment: kEpiWarps per completed
+    // tile.  Every ticket of a tile precedes, on its buffer's counter, every ticket of a later tile:
+    // that tile's last segment reuses the buffer only after all warps released its previous use,
+    // which each warp does after its tickets of the earlier tiles.
+    uint32_t *tickets = tmem_slot + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full + b, 1);
+            mbar_init(acc_empty + b, kEpiWarps);
+            tickets[b] = 0;
+        }
         mbar_init(drain, 1);
-        *tiles_seen = 0;
         mbar_init_fence();
     }
     if (warp == 1) tmem_alloc(tmem_slot, kAccCols);
@@ -232,108 +249,142 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0u;
         for (uint32_t i = first; i < it; ++i) mbar_drain(full + i % kStages, (i / kStages) & 1u, wait_ns);
     } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        uint32_t it = 0, tl = 0;
+        // ---- MMA issuer: segment sg accumulates into buffer sg % 2
+        uint32_t it = 0, sg = 0;
         bool ok = true;
-        for (int32_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++tl) {
+        for (int32_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const WorkItem w = tiles[t];
             const JobPtrs &j = jobs[w.job];
             const TileGeo g = tile_geo<TF32>(j, w);
-            if (!mbar_wait(acc_empty, (tl & 1u) ^ 1u, wait_ns, abort_flag)) {
-                mark_timeout(j);
-                break;
-            }
-            tc_fence_after();
             const uint32_t idesc = TF32 ? idesc_tf32(kTcRows, 2 * g.NC) : idesc_bf16(kTcRows, 2 * g.NC);
-            for (int64_t kb = 0; kb < g.KB; ++kb, ++it) {
-                const uint32_t s = it % kStages;
-                if (!mbar_wait(full + s, (it / kStages) & 1u, wait_ns, abort_flag)) {
+            for (int64_t kb0 = 0; kb0 < g.KB && ok; kb0 += kSegBlocks, ++sg) {
+                const uint32_t b = sg & 1u;
+                if (!mbar_wait(acc_empty + b, ((sg >> 1) & 1u) ^ 1u, wait_ns, abort_flag)) {
                     mark_timeout(j);
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a = smem_u32(ring + s * kStageBytes);
-                const uint64_t ah = smem_desc_sw64(a), al = smem_desc_sw64(a + kTcImgA);
-                const uint64_t bh = smem_desc_sw64(a + 2 * kTcImgA), bl = smem_desc_sw64(a + 2 * kTcImgA + tc_img_b(g.NC));
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {   // two 32-byte K-slices of the 64-byte rows
-                    const uint64_t adv = (uint64_t)(h * 32 >> 4);
-                    const uint32_t acc = (kb > 0 || h > 0) ? 1u : 0u;
-                    if constexpr (TF32) {
-                        tc_mma_tf32(tmem, ah + adv, bh + adv, idesc, acc);
-                        tc_mma_tf32(tmem, ah + adv, bl + adv, idesc, 1u);
-                        tc_mma_tf32(tmem, al + adv, bh + adv, idesc, 1u);
-                    } else {
-                        tc_mma_bf16(tmem, ah + adv, bh + adv, idesc, acc);
-                        tc_mma_bf16(tmem, ah + adv, bl + adv, idesc, 1u);
-                        tc_mma_bf16(tmem, al + adv, bh + adv, idesc, 1u);
+                const uint32_t dst = tmem + b * kAccBuf;
+                const int64_t kb1 = kb0 + kSegBlocks < g.KB ? kb0 + kSegBlocks : g.KB;
+                for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
+                    const uint32_t s = it % kStages;
+                    if (!mbar_wait(full + s, (it / kStages) & 1u, wait_ns, abort_flag)) {
+                        mark_timeout(j);
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(ring + s * kStageBytes);
+                    const uint64_t ah = smem_desc_sw64(a), al = smem_desc_sw64(a + kTcImgA);
+                    const uint64_t bh = smem_desc_sw64(a + 2 * kTcImgA),
+                                   bl = smem_desc_sw64(a + 2 * kTcImgA + tc_img_b(g.NC));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {   // two 32-byte K-slices of the 64-byte rows
+                        const uint64_t adv = (uint64_t)(h * 32 >> 4);
+                        const uint32_t acc = (kb > kb0 || h > 0) ? 1u : 0u;
+                        if constexpr (TF32) {
+                            tc_mma_tf32(dst, ah + adv, bh + adv, idesc, acc);
+                            tc_mma_tf32(dst, ah + adv, bl + adv, idesc, 1u);
+                            tc_mma_tf32(dst, al + adv, bh + adv, idesc, 1u);
+                        } else {
+                            tc_mma_bf16(dst, ah + adv, bh + adv, idesc, acc);
+                            tc_mma_bf16(dst, ah + adv, bl + adv, idesc, 1u);
+                            tc_mma_bf16(dst, al + adv, bh + adv, idesc, 1u);
+                        }
+                    }
+                    tc_commit(empty + s);   // the stage is free once these MMAs have read it
                 }
-                tc_commit(empty + s);   // the stage is free once these MMAs have read it
+                if (!ok) break;
+                tc_commit(acc_full + b);    // the segment's partial sums are complete
             }
-            if (!ok) break;
-            tc_commit(acc_full);        // the tile's accumulator is complete
         }
         // every MMA this CTA issued completes before tensor memory is freed
         tc_commit(drain);
         mbar_drain(drain, 0u, wait_ns);
     } else if (warp >= 2) {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its 32 rows of the tile), and
+        // half (w - 2) / 4 of the tile's 2 NC FP32 columns
         const uint32_t quarter = (uint32_t)(warp & 3);
-        uint32_t tl = 0;
-        for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tl) {
+        const int half = (warp - 2) >> 2;
+        uint32_t sg = 0;
+        for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
             const WorkItem w = tiles[t];
             const JobPtrs &j = jobs[w.job];
             const TileGeo g = tile_geo<TF32>(j, w);
             const StepDesc *d = j.steps + w.step;
-            if (!mbar_wait(acc_full, tl & 1u, wait_ns, abort_flag)) {
-                mark_timeout(j);
-                break;
+            const int nch = g.NC / 16;   // 16-column chunks of a half: 4 or 8
+            float sum[8 * 16];
+#pragma unroll
+            for (int i = 0; i < 8 * 16; ++i) sum[i] = 0.f;
+            bool ok = true;
+            uint32_t b = 0;
+            for (int64_t kb0 = 0; kb0 < g.KB; kb0 += kSegBlocks, ++sg) {
+                b = sg & 1u;
+                if (!mbar_wait(acc_full + b, (sg >> 1) & 1u, wait_ns, abort_flag)) {
+                    mark_timeout(j);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + ((32u * quarter) << 16) + b * kAccBuf + (uint32_t)(half * g.NC);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (c < nch) {
+                        float v[16];
+                        tc_ld16(base + (uint32_t)(16 * c), v);
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) sum[16 * c + p] += v[p];
+                    }
+                }
+                if (kb0 + kSegBlocks < g.KB) {   // not the tile's last segment: release the buffer now
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acc_empty + b);
+                }
             }
-            tc_fence_after();
+            if (!ok) break;
             const int64_t m = g.mt * kTcRows + 32 * quarter + lane;
             const int64_t N = g.N;
             float2 *__restrict__ Cp = reinterpret_cast<float2 *>(j.arena) + __ldcg(&d->c_off);
             float mx = 0.f;
-            for (int c = 0; c < 2 * g.NC / 16; ++c) {
-                float v[16];
-                tc_ld16(tmem + ((32u * quarter) << 16) + (uint32_t)(16 * c), v);
-                const int64_t n0 = g.nt * g.NC + 8 * c;
-                if (m < g.M) {
-                    float2 *row = Cp + m * N;
-                    if (n0 + 8 <= N && ((m * N + n0) & 1) == 0) {
 #pragma unroll
-                        for (int p = 0; p < 4; ++p)
-                            *reinterpret_cast<float4 *>(row + n0 + 2 * p) =
-                                make_float4(v[4 * p], v[4 * p + 1], v[4 * p + 2], v[4 * p + 3]);
+            for (int c = 0; c < 8; ++c) {
+                if (c >= nch || m >= g.M) continue;
+                const float *v = sum + 16 * c;
+                const int64_t n0 = g.nt * g.NC + half * (g.NC / 2) + 8 * c;
+                float2 *row = Cp + m * N;
+                if (n0 + 8 <= N && ((m * N + n0) & 1) == 0) {
 #pragma unroll
-                        for (int p = 0; p < 16; ++p) mx = fmaxf(mx, fabsf(v[p]));
-                    } else {
+                    for (int p = 0; p < 4; ++p)
+                        *reinterpret_cast<float4 *>(row + n0 + 2 * p) =
+                            make_float4(v[4 * p], v[4 * p + 1], v[4 * p + 2], v[4 * p + 3]);
 #pragma unroll
-                        for (int p = 0; p < 8; ++p)
-                            if (n0 + p < N) {
-                                row[n0 + p] = make_float2(v[2 * p], v[2 * p + 1]);
-                                mx = fmaxf(mx, fmaxf(fabsf(v[2 * p]), fabsf(v[2 * p + 1])));
-                            }
-                    }
+                    for (int p = 0; p < 16; ++p) mx = fmaxf(mx, fabsf(v[p]));
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        if (n0 + p < N) {
+                            row[n0 + p] = make_float2(v[2 * p], v[2 * p + 1]);
+                            mx = fmaxf(mx, fmaxf(fabsf(v[2 * p]), fabsf(v[2 * p + 1])));
+                        }
                 }
             }
             mx = warp_max(mx);
             if (lane == 0) {
                 if (mx > 0.f) atomicMax(j.maxbits + __ldcg(&d->node_c), __float_as_uint(mx));
-                // the fourth epilogue warp to finish the tile publishes it (no block barrier: a warp
+                // the last epilogue warp to finish the tile publishes it (no block barrier: a warp
                 // that gave up on a wait must not hold the others)
                 __threadfence();
-                if (atomicAdd(tiles_seen, 1u) % 4u == 3u) {
+                if (atomicAdd(tickets + b, 1u) % (uint32_t)kEpiWarps == (uint32_t)kEpiWarps - 1u) {
                     __threadfence();
                     atomicAdd(j.done + w.step, 1);
                 }
             }
-            // release the accumulator only now, so the next tile's tickets follow this tile's
+            // release the last segment's buffer only after the ticket (see tickets above)
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+            if (lane == 0) mbar_arrive(acc_empty + b);
         }
     }
     tc_fence_before();

@@ -586,7 +586,7 @@ __device__ __forceinline__ void local_reduce(const LocalStep &s, const LocalSmem
 
 // Runs local program `prog` of job `j` in the calling block.  `dyn` is the block's dynamic shared
 // memory, laid out by local_layout().
-template <typename T>
+template <typename T, bool PROF = false>
 __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scratch, long long *prof) {
     // scratch: the block's static tile scratch -- dense B / offset tables, then FP64 partials
     double2 *red64 = reinterpret_cast<double2 *>(scratch + kKTab * sizeof(int2));
@@ -612,7 +612,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     long long tp = 0;
-    if (prof && threadIdx.x == 0) tp = clock64();
+    if (PROF && threadIdx.x == 0) tp = clock64();
     // large programs: each wave's inputs are copied asynchronously one wave ahead (the compiler
     // places them clear of the previous wave's operands and results)
     const bool lazy = P.kind == PROG_BIG;
@@ -632,7 +632,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
             cp_async_commit();
             cp_async_wait_prev();   // this wave's inputs have landed (the next wave's may be in flight)
             __syncthreads();
-            if (prof && threadIdx.x == 0) {   // slot 14: waiting for the inputs of large programs
+            if (PROF && threadIdx.x == 0) {   // slot 14: waiting for the inputs of large programs
                 const long long t1 = clock64();
                 atomicAdd((unsigned long long *)(prof + 14), (unsigned long long)(t1 - tp));
                 atomicAdd((unsigned long long *)(prof + kProfSlots + 14), 1ull);
@@ -661,7 +661,7 @@ __device__ void run_local(int32_t prog, const JobPtrs &j, char *dyn, char *scrat
             __syncthreads();   // scratch (dense B / offset table) is reused by the next big step
         }
         __syncthreads();
-        if (prof && threadIdx.x == 0) {
+        if (PROF && threadIdx.x == 0) {
             const long long t1 = clock64();
             // 8: waves of small steps only, 9: waves with block-wide steps, 13: those of large programs
             const int slot = W.n_big ? (P.kind == PROG_BIG ? 13 : 9) : 8;

@@ -302,11 +302,16 @@ cudaError_t launch(tn_server *S, Flight &f, const std::vector<size_t> &job_off, 
     if (!packs.empty()) std::memcpy(f.h_stage + o_pack, packs.data(), sizeof(WorkItem) * packs.size());
     if (!gemms.empty()) std::memcpy(f.h_stage + o_gemm, gemms.data(), sizeof(WorkItem) * gemms.size());
     int32_t max_leaves = 0;
-    for (int32_t i = 0; i < n; ++i) max_leaves = std::max(max_leaves, S->models[f.reqs[i].model]->c.n);
+    int64_t max_leaf_elems = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const Model &m = *S->models[f.reqs[i].model];
+        max_leaves = std::max(max_leaves, m.c.n);
+        for (size_t t = 0; t + 1 < m.leaf_off.size(); ++t) max_leaf_elems = std::max(max_leaf_elems, m.leaf_off[t + 1] - m.leaf_off[t]);
+    }
     const JobPtrs *d_jobs = reinterpret_cast<const JobPtrs *>(meta + o_jobs);
     cudaError_t e = cudaMemcpyAsync(meta, f.h_stage, upload_bytes, cudaMemcpyHostToDevice, f.st);
     if (e == cudaSuccess) e = cudaMemsetAsync(meta + o_reset, 0, reset_bytes, f.st);
-    if (e == cudaSuccess) e = launch_leaf_convert(S->c128, d_jobs, n, max_leaves, f.st);
+    if (e == cudaSuccess) e = launch_leaf_convert(S->c128, d_jobs, n, max_leaves, max_leaf_elems, f.st);
     if (e == cudaSuccess)
         e = launch_local(S->c128, d_jobs, reinterpret_cast<const WorkItem *>(meta + o_local), n_warp, n_block,
                          n_big, S->dyn_smem, S->dyn_big, nullptr, f.st);

@@ -598,7 +598,7 @@ __device__ void tile_gemm(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
 // reproducible.  The root step of a closed network (M = N = 1) always takes this path: the final
 // reduction of the amplitude is FP64.
 template <typename T>
-__device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem) {
+__device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, char *smem, char *dyn) {
     using C = cx_t<T>;
     double2(*red)[kDotMaxOut] = reinterpret_cast<double2(*)[kDotMaxOut]>(smem);
     int64_t *rowA = reinterpret_cast<int64_t *>(smem + (kThreads / 32) * kDotMaxOut * sizeof(double2));
@@ -613,6 +613,25 @@ __device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
     const T sA = pow2<T>(-eA), sB = pow2<T>(-eB);
     const C *__restrict__ A = operand<C>(d, j, true);
     const C *__restrict__ B = operand<C>(d, j, false);
+    // an operand whose offsets are permuted along k (complex64 only) is copied whole -- K elements,
+    // 16-byte aligned in the arena -- with coalesced 16-byte copies, then gathered from shared
+    // memory with plain loads (Xs)
+    const bool sm_a = sizeof(T) == 4 && (d.flags & FLAG_DOT_SMEM_A) != 0;
+    const bool sm_b = sizeof(T) == 4 && (d.flags & FLAG_DOT_SMEM_B) != 0;
+    C *Xs = reinterpret_cast<C *>(dyn);
+    if (sm_a || sm_b) {
+        const C *src = sm_a ? A : B;
+        const int32_t K = (int32_t)d.K;
+        for (int32_t i = threadIdx.x; 2 * i + 1 < K; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(Xs + 2 * i)),
+                         "l"(src + 2 * i)
+                         : "memory");
+        if ((K & 1) && threadIdx.x == 0) Xs[K - 1] = ldc(src + K - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+    }
     double2 acc[kDotMaxOut];
 #pragma unroll
     for (int i = 0; i < kDotMaxOut; ++i) acc[i] = make_double2(0, 0);
@@ -655,7 +674,9 @@ __device__ void tile_dotp(const StepDesc &d, int64_t tile, const JobPtrs &j, cha
             for (int i = 0; i < kDotMaxOut; ++i) {
                 if (i < MN) {
                     const int m = i / N, n = i - m * N;
-                    const C a = cscale(ldc(A + oa[u] + rowA[m]), sA), b = cscale(ldc(B + ob[u] + colB[n]), sB);
+                    const C av = sm_a ? Xs[oa[u] + rowA[m]] : ldc(A + oa[u] + rowA[m]);
+                    const C bv = sm_b ? Xs[ob[u] + colB[n]] : ldc(B + ob[u] + colB[n]);
+                    const C a = cscale(av, sA), b = cscale(bv, sB);
                     cfma(run[i], a, b);
                 }
             }
@@ -743,7 +764,7 @@ __device__ __forceinline__ void run_tile(const StepDesc &d, int64_t tile, const 
             }
             tile_gemm<T, kTileM, kTileN>(d, tile, j, smem, red);
             break;
-        case STEP_DOTP: tile_dotp<T>(d, tile, j, smem); break;
+        case STEP_DOTP: tile_dotp<T>(d, tile, j, smem, dyn); break;
         case STEP_DOTF: tile_dotf<T>(d, j, smem); break;
         default: break;
     }

@@ -464,15 +464,23 @@ def tn_batch_create(ctx: Ctx, nets, plans, precision="c64") -> Batch:
     pp, keep_p = _handle_array(plans)
     out = ctypes.c_void_p()
     _check(lib.tn_batch_create(ctx, len(nets), pn, pp, PRECISIONS[precision], ctypes.byref(out)))
-    return Batch(out.value, keep=(ctx, tuple(nets), tuple(plans)))
+    b = Batch(out.value, keep=(ctx, tuple(nets), tuple(plans)))
+    b.n_jobs = len(nets)
+    return b
 
 
 def tn_batch_run(batch: Batch, d_results: int = 0) -> None:
     _check(lib.tn_batch_run(batch, ctypes.c_void_p(d_results) if d_results else None))
 
 
-def tn_batch_results(batch: Batch, n: int):
-    """Returns (mantissas complex128 [n], exp2 int32 [n], status int32 [n])."""
+def tn_batch_results(batch: Batch, n: int = None):
+    """Returns (mantissas complex128 [n], exp2 int32 [n], status int32 [n]) for all n jobs of the
+    batch (the call writes every job's result, so n must be the batch's job count)."""
+    jobs = getattr(batch, "n_jobs", None)
+    if n is None:
+        n = jobs
+    elif jobs is not None and n != jobs:
+        raise ValueError(f"the batch has {jobs} jobs, not {n}: every job's result is written")
     amps = np.zeros(2 * n, np.float64)
     e = np.zeros(n, np.int32)
     st = np.zeros(n, np.int32)

@@ -198,3 +198,19 @@ def test_graph_replay_equals_direct_launches(tnsa, prec):
             assert tnsa.tn_batch_last_info(b)["n_tc"] > 0 and times["tc_gemm"] > 0
         out[graph] = (mant.view(np.uint64).copy(), e2.copy())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_results_buffer_must_hold_every_job(tnsa):
+    """tn_batch_results writes the result of every job of the batch: the binding refuses a count
+    other than the batch's (a shorter host buffer would be overrun)."""
+    circ, x = tni.cfg1()
+    hs = [tnsa.tn_build(tni.amplitude_tn(circ, x)) for _ in range(3)]
+    plan = tnsa.tn_plan_create(hs[0], k=1)
+    ctx = tnsa.tn_ctx_create(0)
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * 3, "c64")
+    tnsa.tn_batch_run(b)
+    with pytest.raises(ValueError):
+        tnsa.tn_batch_results(b, 2)
+    mant, e2, st = tnsa.tn_batch_results(b)
+    assert len(mant) == 3 and (st == 0).all()
+    b.close()

@@ -167,3 +167,40 @@ def test_tc_gemm_elementwise(tnsa, shape, tile, prec):
     got = mant * np.ldexp(1.0, e2)
     want = np.array([C[i, j] for i, j in pairs])
     check_scaled(got, want, scale, TOL[prec], f"{len(pairs)} elements of C")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_long_k_does_not_drift(tnsa, prec):
+    """A long shared index (K = 16384: 1024 BF16 or 2048 TF32 k-blocks) is accumulated in segments
+    whose partial sums are added in FP32 on the CUDA cores, so the tensor cores' non-nearest
+    accumulation cannot shrink the product systematically: the mean radial error of sampled
+    elements, Re((got - want) conj(want)) / |want|^2, stays at the size of one segment's drift
+    (below 5e-6), where a single accumulator over all of K drifted by -1e-4 (BF16) and -2e-4
+    (TF32)."""
+    I, K, J = 128, 16384, 128
+    net = _Bilinear(I, K, J, seed=K)
+    C = net.A @ net.B
+    rng = np.random.default_rng(K)
+    pairs = [(int(rng.integers(0, I)), int(rng.integers(0, J))) for _ in range(64)]
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_import(h, [(0, 1), (2, 4), (3, 5)])
+    ctx = tnsa.tn_ctx_create(0)
+    tnsa.tn_ctx_set_config(ctx, local_budget=0)
+    b = tnsa.tn_batch_create(ctx, [h] * len(pairs), [plan] * len(pairs), prec)
+    jobs, tens, data = [], [], []
+    for q, (i, j) in enumerate(pairs):
+        u, v = np.zeros(I, complex), np.zeros(J, complex)
+        u[i] = v[j] = 1
+        jobs += [q, q]
+        tens += [2, 3]
+        data += [u, v]
+    tnsa.tn_batch_set_tensors(b, jobs, tens, np.concatenate(data))
+    tnsa.tn_batch_run(b)
+    mant, e2, st = tnsa.tn_batch_results(b, len(pairs))
+    assert (st == 0).all()
+    assert tnsa.tn_batch_last_info(b)["n_tc"] == len(pairs)
+    got = mant * np.ldexp(1.0, e2)
+    want = np.array([C[i, j] for i, j in pairs])
+    radial = np.real((got - want) * np.conj(want)) / np.abs(want) ** 2
+    assert abs(radial.mean()) < 5e-6, f"mean radial error {radial.mean():.3e}"
+    check_scaled(got, want, np.abs(C).max(), TOL[prec], f"{len(pairs)} elements of C, K = {K}")
