@@ -132,6 +132,7 @@ struct tn_batch {
     std::vector<double> upd_val;
     char *h_upd = nullptr;
     size_t h_upd_cap = 0;
+    cudaEvent_t upd_ev = nullptr;     // recorded after the copy out of h_upd (it may be refilled then)
     char *d_upd = nullptr;
     size_t d_upd_cap = 0;
     size_t last_h2d = 0;
@@ -303,6 +304,42 @@ bool make_lgroups(const std::vector<int64_t> &dim, const std::vector<int64_t> &s
     }
     if (!g.pow2) pow2 = false;
     return true;
+}
+
+// Tabulate the index maps of a small step with at most kTabOut outputs and kTabK shared indices
+// (LFLAG_TAB): the warp then reads each offset instead of decoding the index over the leg groups.
+// The decode is the one the kernels perform (digits by shift and mask, or by division).
+void tabulate_small(LocalStep &ls) {
+    if (!(ls.flags & LFLAG_SMALL) || (int64_t)ls.M * ls.N > kTabOut || ls.K > kTabK) return;
+    auto dec = [&](int32_t n, const int32_t *dim, const int32_t *str, const uint8_t *lsb, int32_t idx) {
+        int64_t off = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            int64_t d;
+            if (ls.pow2) {
+                d = (idx >> lsb[i]) & (dim[i] - 1);
+            } else {
+                d = idx % dim[i];
+                idx /= dim[i];
+            }
+            off += d * str[i];
+        }
+        return off;
+    };
+    uint32_t t[kTabOut + kTabK] = {};
+    for (int32_t o = 0; o < ls.M * ls.N; ++o) {
+        const int64_t a = dec(ls.nm, ls.m_dim, ls.m_str, ls.m_lsb, o / ls.N);
+        const int64_t b = dec(ls.nn, ls.n_dim, ls.n_str, ls.n_lsb, o % ls.N);
+        if (a > 0xffff || b > 0xffff) return;
+        t[o] = (uint32_t)a | ((uint32_t)b << 16);
+    }
+    for (int32_t k = 0; k < ls.K; ++k) {
+        const int64_t a = dec(ls.nk, ls.k_dim, ls.k_sa, ls.k_lsb, k);
+        const int64_t b = dec(ls.nk, ls.k_dim, ls.k_sb, ls.k_lsb, k);
+        if (a > 0xffff || b > 0xffff) return;
+        t[kTabOut + k] = (uint32_t)a | ((uint32_t)b << 16);
+    }
+    std::memcpy(reinterpret_cast<char *>(&ls) + offsetof(LocalStep, m_dim), t, sizeof(t));
+    ls.flags |= LFLAG_TAB;
 }
 
 struct LocalPlan {
@@ -977,6 +1014,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
                 ls.mode = LMODE_REDUCE;
             }
             if (lp.small[si]) ls.flags |= LFLAG_SMALL;
+            tabulate_small(ls);
             c.lsteps.push_back(ls);
         }
         if (P.kind == PROG_BIG) {
@@ -1028,6 +1066,7 @@ tn_status tn::compile(Compiled &c, const Net &net, const Plan &plan, const Compi
             make_lgroups(g.kd, g.ksa, g.ksb, true, ls.k_dim, ls.k_sa, ls.k_sb, ls.k_lsb, ls.nk, p2);
             ls.pow2 = p2 ? 1 : 0;
             ls.mode = LMODE_ROWS;
+            tabulate_small(ls);
             c.lsteps.push_back(ls);
         }
         c.dyn_smem = std::max(c.dyn_smem, (int32_t)kWarpSlice);
@@ -1296,6 +1335,7 @@ void batch_destroy(tn_batch *b) {
     if (b->h_pinned) cudaFreeHost(b->h_pinned);
     if (b->h_res) cudaFreeHost(b->h_res);
     if (b->h_upd) cudaFreeHost(b->h_upd);
+    if (b->upd_ev) cudaEventDestroy(b->upd_ev);
     if (b->d_upd) cudaFree(b->d_upd);
     if (b->d_prof) cudaFree(b->d_prof);
     tn_ctx *ctx = b->ctx;
@@ -1668,7 +1708,10 @@ tn_status apply_updates(tn_batch *b, cudaStream_t st) {
     if (n_upd == 0) return TN_OK;
     const size_t hdr_bytes = align_up(sizeof(int64_t) * b->upd_hdr.size(), 16);
     const size_t bytes = hdr_bytes + sizeof(double) * b->upd_val.size();
-    CK(cudaStreamSynchronize(st));   // the staging buffers may still be read by a previous copy
+    // the pinned staging buffer may still be read by the previous update's copy: wait for that copy
+    // alone, not for the runs queued behind it
+    if (!b->upd_ev) CK(cudaEventCreateWithFlags(&b->upd_ev, cudaEventDisableTiming));
+    else CK(cudaEventSynchronize(b->upd_ev));
     if (bytes > b->h_upd_cap) {
         if (b->h_upd) cudaFreeHost(b->h_upd);
         b->h_upd = nullptr;
@@ -1687,6 +1730,7 @@ tn_status apply_updates(tn_batch *b, cudaStream_t st) {
     std::memcpy(b->h_upd, b->upd_hdr.data(), sizeof(int64_t) * b->upd_hdr.size());
     std::memcpy(b->h_upd + hdr_bytes, b->upd_val.data(), sizeof(double) * b->upd_val.size());
     CK(cudaMemcpyAsync(b->d_upd, b->h_upd, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(b->upd_ev, st));
     CK(launch_scatter_updates(reinterpret_cast<const int64_t *>(b->d_upd),
                               reinterpret_cast<const double2 *>(b->d_upd + hdr_bytes), (int64_t)n_upd,
                               b->d_leaf64, st));

@@ -1,6 +1,7 @@
 // Device step descriptors, job tables and kernel launchers of the contraction engine.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -77,9 +78,13 @@ enum LocalMode : uint8_t { LMODE_ROWS = 0, LMODE_GEMM = 1, LMODE_REDUCE = 2 };
 enum LocalFlags : int32_t {
     LFLAG_JOB_ROOT = 1,     // (program, step) produces the job's amplitude
     LFLAG_SMALL = 2,        // (step) small enough for one warp
+    LFLAG_TAB = 4,          // (small step, M N <= 16, K <= 16) the index maps are tabulated: the
+                            // bytes of the group fields from m_dim on hold kTabWords packed
+                            // offsets (low 16 bits in A, high 16 in B), outputs then shared indices
     LFLAG_C_OUT = 16        // (warp programs) C is the program's result: written to the job's
                             // arena at root_c_off
 };
+constexpr int kTabOut = 16, kTabK = 16;
 
 // A wave of a program: steps [first, first + n_small) run one per warp, then n_big steps use the
 // whole block; the steps of a wave are independent of each other.
@@ -102,6 +107,8 @@ struct LocalStep {
     uint8_t pad[2];
 };
 static_assert(sizeof(LocalStep) == 224, "LocalStep layout");
+static_assert(offsetof(LocalStep, m_lsb) - offsetof(LocalStep, m_dim) >= 4 * (kTabOut + kTabK),
+              "the tabulated offsets fit the group fields");
 
 struct LocalProg {
     int32_t first_step, n_steps;        // into the job's LocalStep array

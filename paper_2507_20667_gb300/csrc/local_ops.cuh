@@ -179,6 +179,9 @@ __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A
     const T sA = fold ? (T)1 : pow2<T>(-eA);
     const T sB = fold ? pow2<T>(-es) : pow2<T>(-eB);
     const int32_t N = s.N, K = s.K, O = s.M * s.N;
+    const bool tab = (s.flags & LFLAG_TAB) != 0;
+    const uint32_t *tbl = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(&s) +
+                                                             offsetof(LocalStep, m_dim));
     int32_t S = 1;
     while (S * 2 * O <= 32 && S < K) S *= 2;
     const int32_t sub = lane & (S - 1), per_pass = 32 / S;
@@ -188,7 +191,11 @@ __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A
         const int32_t o = o0 + lane / S;
         const bool act = o < O;
         int32_t oa = 0, ob = 0;
-        if (act) {
+        if (act && tab) {
+            const uint32_t t = tbl[o];
+            oa = (int32_t)(t & 0xffffu);
+            ob = (int32_t)(t >> 16);
+        } else if (act) {
             const int32_t m = o / N, n = o - m * N;
             oa = lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, p2, m);
             ob = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, p2, n);
@@ -197,9 +204,13 @@ __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A
         for (int32_t k0 = 0; k0 < K; k0 += 32) {
             uint32_t packed = 0;
             if (k0 + lane < K) {
-                int32_t ka, kb;
-                lgroup_off2(s, k0 + lane, ka, kb);
-                packed = (uint32_t)ka | ((uint32_t)kb << 16);
+                if (tab) {
+                    packed = tbl[kTabOut + lane];   // K <= kTabK: one pass, k0 = 0
+                } else {
+                    int32_t ka, kb;
+                    lgroup_off2(s, k0 + lane, ka, kb);
+                    packed = (uint32_t)ka | ((uint32_t)kb << 16);
+                }
             }
             const int32_t kn = min(32, K - k0);
             for (int32_t kk = 0; kk < kn; kk += S) {
