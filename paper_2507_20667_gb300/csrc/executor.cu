@@ -38,7 +38,7 @@ struct tn_ctx {
     bool own_stream = false;
     size_t budget = 0;
     int32_t mode = 0;                 // tn_exec_mode
-    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 0, 0};   // programs, TC, waits, graphs, order, TC tile
+    tn_exec_config cfg{-1, 0, 1, 64, 32, 16, 1, 4000000, 1, 1, 0};   // programs, TC, waits, graphs, order, TC tile
     tn_batch *cached = nullptr;       // batch of one reused by tn_contract, keyed by the unique
     uint64_t cached_net = 0, cached_plan = 0;   // ids of the net and plan (never by address)
     tn_precision cached_prec = TN_C64;
@@ -2284,13 +2284,13 @@ tn_status tn_ctx_autotune(tn_ctx *ctx, int32_t n, const tn_net *const *nets, con
     for (tn_exec_config &c : cands) {
         c.wait_limit_us = saved.wait_limit_us;
         c.graph_capture = saved.graph_capture;
-        c.schedule = 0;
+        c.schedule = 1;
         c.tc_tile_n = 0;
     }
-    {   // the critical-path-first order with the default program configuration
-        tn_exec_config cp = cands[1];
-        cp.schedule = 1;
-        cands.push_back(cp);
+    {   // the dependency-level order with the default program configuration
+        tn_exec_config lv = cands[1];
+        lv.schedule = 0;
+        cands.push_back(lv);
     }
     if (tc_mode_of(prec)) {   // 128-column tiles for every dense step
         tn_exec_config wide = cands[1];
