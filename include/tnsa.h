@@ -67,7 +67,9 @@ typedef struct tn_batch tn_batch;
  *   degree     [n_tensors] degree d_v >= 0 of each tensor (0 = scalar)
  *   dims       concatenation of every tensor's dims n_v (sum of degree entries, each >= 1)
  *   data       concatenation of every tensor's entries, complex128 interleaved (re, im),
- *              row-major; 2 * sum_v |T_v| doubles
+ *              row-major; 2 * sum_v |T_v| doubles, each finite and below 2^127 in magnitude
+ *              (each tensor's max-abs is tracked in FP32 by the per-step scaling;
+ *              intermediates may grow without bound)
  *   n_edges, edges  the edge list; every (u, a) slot must be named exactly once, the dims at both
  *              ends must agree (n_{u,a} = n_{v,b}), and u != v (no self-loops).  Several edges
  *              between the same two tensors are allowed.
@@ -77,8 +79,9 @@ tn_status tn_build(int32_t n_tensors, const int32_t *degree, const int64_t *dims
                    const double *data, int32_t n_edges, const tn_edge *edges, tn_net **out);
 
 /* Replace the entries of tensor t (same shape), e.g. a new bitstring's bra tensors.
- * data: |T_t| complex128 interleaved.  Programs built from this net pick the change up at their
- * next run (the leaves are re-uploaded).  Errors: TN_EINVAL. */
+ * data: |T_t| complex128 interleaved, each part finite and below 2^127 in magnitude.  Programs
+ * built from this net pick the change up at their next run (the leaves are re-uploaded).
+ * Errors: TN_EINVAL. */
 tn_status tn_net_set_tensor(tn_net *net, int32_t t, const double *data);
 
 /* Number of tensors, edges, and whether every leg is bound (a closed network). */
@@ -393,8 +396,11 @@ tn_status tn_batch_run(tn_batch *b, void *d_results);
 
 /* Replace the entries of tensor tensor[i] of job job[i] (same shape) for i < count, in the batch's
  * resident copy only (the nets are not modified).  data: the new entries back to back, complex128
- * interleaved.  The values are staged on the host and applied on the device by the next
- * tn_batch_run, in one copy and one scatter kernel.  Errors: TN_EINVAL (nothing is staged). */
+ * interleaved, each part finite and below 2^127 in magnitude.  The values are written into pinned
+ * host memory (two staging sets used in turn, so the call may overlap a run in flight: it waits
+ * only for the copy out of the set it refills, made two runs earlier) and applied on the device by
+ * the next tn_batch_run, in two copies and one scatter kernel.  Errors: TN_EINVAL (nothing is
+ * staged), TN_ENOMEM, TN_ECUDA. */
 tn_status tn_batch_set_tensors(tn_batch *b, int32_t count, const int32_t *job, const int32_t *tensor,
                                const double *data);
 
@@ -505,7 +511,8 @@ tn_status tn_serve_register(tn_server *s, const tn_net *net, const tn_plan *plan
 /* Device bytes one request of `model` holds while in flight, and its algorithmic flops. */
 tn_status tn_serve_model_info(tn_server *s, int32_t model, size_t *job_bytes, double *flops);
 /* Queue a request: `count` tensors of the model replaced by `data` (their entries back to back,
- * complex128 interleaved; copied).  Thread-safe, returns at once with a ticket.  Errors: TN_EINVAL. */
+ * complex128 interleaved, each part finite and below 2^127 in magnitude; copied).  Thread-safe,
+ * returns at once with a ticket.  Errors: TN_EINVAL. */
 tn_status tn_serve_submit(tn_server *s, int32_t model, int32_t count, const int32_t *tensors,
                           const double *data, uint64_t *ticket);
 /* Wait up to timeout_s (0 = do not wait) for a ticket.  *done = 0 if not finished yet; otherwise

@@ -85,6 +85,10 @@ tn_status tn_build(int32_t n_tensors, const int32_t *degree, const int64_t *dims
             }
         }
         if (!data) { delete h; return fail(TN_EINVAL, "NULL data"); }
+        if (!entries_in_range(data, 2 * (size_t)net.data_off[n_tensors])) {
+            delete h;
+            return fail(TN_EINVAL, "tensor entries must be finite and below 2^127 in magnitude");
+        }
         net.data.assign(data, data + 2 * net.data_off[n_tensors]);
         net.edges.assign(edges, edges + n_edges);
         net.edim.assign(n_edges, 0);
@@ -152,6 +156,8 @@ tn_status tn_net_set_tensor(tn_net *h, int32_t t, const double *data) {
     if (!h || !data) return fail(TN_EINVAL, "NULL argument");
     Net &net = h->impl;
     if (t < 0 || t >= net.n) return fail(TN_EINVAL, "tensor index out of range");
+    if (!entries_in_range(data, 2 * (size_t)(net.data_off[t + 1] - net.data_off[t])))
+        return fail(TN_EINVAL, "tensor entries must be finite and below 2^127 in magnitude");
     std::memcpy(&net.data[2 * net.data_off[t]], data,
                 sizeof(double) * 2 * (size_t)(net.data_off[t + 1] - net.data_off[t]));
     net.version++;

@@ -128,11 +128,20 @@ struct tn_batch {
     int64_t runs = 0;
     // pending tensor updates (tn_batch_set_tensors): headers {dst element offset, count, src
     // element offset} and complex128 values, staged in pinned memory, applied on the device
-    std::vector<int64_t> upd_hdr;
-    std::vector<double> upd_val;
-    char *h_upd = nullptr;
-    size_t h_upd_cap = 0;
-    cudaEvent_t upd_ev = nullptr;     // recorded after the copy out of h_upd (it may be refilled then)
+    // staged tensor updates, written by tn_batch_set_tensors straight into pinned host memory: two
+    // staging sets used in turn, so a set is refilled only once the copy of the run before last
+    // out of it has completed (its event), and the filling overlaps the run in flight
+    struct Pinned {
+        char *p = nullptr;
+        size_t size = 0, cap = 0;
+    };
+    struct Stage {
+        Pinned hdr, val;              // {dst offset, count, src offset} per update; the values
+        cudaEvent_t ev = nullptr;     // recorded after the copies out of this set
+        bool copying = false;
+    };
+    Stage stage[2];
+    int32_t cur_stage = 0;
     char *d_upd = nullptr;
     size_t d_upd_cap = 0;
     size_t last_h2d = 0;
@@ -1334,8 +1343,11 @@ void batch_destroy(tn_batch *b) {
     if (b->d_block) cudaFree(b->d_block);
     if (b->h_pinned) cudaFreeHost(b->h_pinned);
     if (b->h_res) cudaFreeHost(b->h_res);
-    if (b->h_upd) cudaFreeHost(b->h_upd);
-    if (b->upd_ev) cudaEventDestroy(b->upd_ev);
+    for (tn_batch::Stage &sg : b->stage) {
+        if (sg.hdr.p) cudaFreeHost(sg.hdr.p);
+        if (sg.val.p) cudaFreeHost(sg.val.p);
+        if (sg.ev) cudaEventDestroy(sg.ev);
+    }
     if (b->d_upd) cudaFree(b->d_upd);
     if (b->d_prof) cudaFree(b->d_prof);
     tn_ctx *ctx = b->ctx;
@@ -1704,21 +1716,11 @@ tn_status batch_create(tn_ctx *ctx, int32_t n, const tn_net *const *nets, const 
 // Copy the pending tensor updates to the device in one transfer and scatter them into the
 // resident complex128 leaves.
 tn_status apply_updates(tn_batch *b, cudaStream_t st) {
-    const size_t n_upd = b->upd_hdr.size() / 3;
+    tn_batch::Stage &sg = b->stage[b->cur_stage];
+    const size_t n_upd = sg.hdr.size / (3 * sizeof(int64_t));
     if (n_upd == 0) return TN_OK;
-    const size_t hdr_bytes = align_up(sizeof(int64_t) * b->upd_hdr.size(), 16);
-    const size_t bytes = hdr_bytes + sizeof(double) * b->upd_val.size();
-    // the pinned staging buffer may still be read by the previous update's copy: wait for that copy
-    // alone, not for the runs queued behind it
-    if (!b->upd_ev) CK(cudaEventCreateWithFlags(&b->upd_ev, cudaEventDisableTiming));
-    else CK(cudaEventSynchronize(b->upd_ev));
-    if (bytes > b->h_upd_cap) {
-        if (b->h_upd) cudaFreeHost(b->h_upd);
-        b->h_upd = nullptr;
-        b->h_upd_cap = 0;
-        CK(cudaMallocHost(&b->h_upd, bytes));
-        b->h_upd_cap = bytes;
-    }
+    const size_t hdr_bytes = align_up(sg.hdr.size, 16);
+    const size_t bytes = hdr_bytes + sg.val.size;
     if (bytes > b->d_upd_cap) {
         if (b->d_upd) cudaFree(b->d_upd);
         b->d_upd = nullptr;
@@ -1727,16 +1729,18 @@ tn_status apply_updates(tn_batch *b, cudaStream_t st) {
         if (e != cudaSuccess) return fail(TN_ENOMEM, cudaGetErrorString(e));
         b->d_upd_cap = bytes;
     }
-    std::memcpy(b->h_upd, b->upd_hdr.data(), sizeof(int64_t) * b->upd_hdr.size());
-    std::memcpy(b->h_upd + hdr_bytes, b->upd_val.data(), sizeof(double) * b->upd_val.size());
-    CK(cudaMemcpyAsync(b->d_upd, b->h_upd, bytes, cudaMemcpyHostToDevice, st));
-    CK(cudaEventRecord(b->upd_ev, st));
+    if (!sg.ev) CK(cudaEventCreateWithFlags(&sg.ev, cudaEventDisableTiming));
+    CK(cudaMemcpyAsync(b->d_upd, sg.hdr.p, sg.hdr.size, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_upd + hdr_bytes, sg.val.p, sg.val.size, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(sg.ev, st));
+    sg.copying = true;
     CK(launch_scatter_updates(reinterpret_cast<const int64_t *>(b->d_upd),
                               reinterpret_cast<const double2 *>(b->d_upd + hdr_bytes), (int64_t)n_upd,
                               b->d_leaf64, st));
     b->last_h2d += bytes;
-    b->upd_hdr.clear();
-    b->upd_val.clear();
+    sg.hdr.size = 0;
+    sg.val.size = 0;
+    b->cur_stage ^= 1;
     return TN_OK;
 }
 
@@ -2090,29 +2094,61 @@ tn_status tn_batch_debug_hold(tn_batch *b, int32_t job, int32_t step) {
     return TN_OK;
 }
 
+// Grow a pinned staging buffer to hold `need` bytes, keeping its contents.
+static tn_status pinned_reserve(tn_batch::Pinned &buf, size_t need) {
+    if (need <= buf.cap) return TN_OK;
+    size_t cap = std::max<size_t>(need, 2 * buf.cap);
+    char *p = nullptr;
+    cudaError_t e = cudaMallocHost(&p, cap);
+    if (e != cudaSuccess) return fail(TN_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    if (buf.size) std::memcpy(p, buf.p, buf.size);
+    if (buf.p) cudaFreeHost(buf.p);
+    buf.p = p;
+    buf.cap = cap;
+    return TN_OK;
+}
+
 tn_status tn_batch_set_tensors(tn_batch *b, int32_t count, const int32_t *job, const int32_t *tensor,
                                const double *data) {
     if (!b || (count > 0 && (!job || !tensor || !data))) return fail(TN_EINVAL, "NULL argument");
     if (count < 0) return fail(TN_EINVAL, "count must be >= 0");
-    size_t src = 0;
-    const size_t hdr0 = b->upd_hdr.size(), val0 = b->upd_val.size();
+    // validate everything first: a rejected call stages nothing
+    size_t n_val = 0;
     for (int32_t i = 0; i < count; ++i) {
-        if (job[i] < 0 || job[i] >= b->n_jobs) {
-            b->upd_hdr.resize(hdr0); b->upd_val.resize(val0);
-            return fail(TN_EINVAL, "job index out of range");
-        }
+        if (job[i] < 0 || job[i] >= b->n_jobs) return fail(TN_EINVAL, "job index out of range");
         const Compiled &c = b->comp[b->job_comp[job[i]]];
-        if (tensor[i] < 0 || tensor[i] >= c.n) {
-            b->upd_hdr.resize(hdr0); b->upd_val.resize(val0);
-            return fail(TN_EINVAL, "tensor index out of range");
-        }
-        const int64_t off = c.leaf_off[tensor[i]], cnt = c.leaf_off[tensor[i] + 1] - off;
-        b->upd_hdr.push_back(b->leaf64_off[job[i]] + off);
-        b->upd_hdr.push_back(cnt);
-        b->upd_hdr.push_back((int64_t)(b->upd_val.size() / 2));
-        b->upd_val.insert(b->upd_val.end(), data + src, data + src + 2 * cnt);
-        src += 2 * (size_t)cnt;
+        if (tensor[i] < 0 || tensor[i] >= c.n) return fail(TN_EINVAL, "tensor index out of range");
+        n_val += 2 * (size_t)(c.leaf_off[tensor[i] + 1] - c.leaf_off[tensor[i]]);
     }
+    if (count == 0) return TN_OK;
+    if (!entries_in_range(data, n_val))
+        return fail(TN_EINVAL, "tensor entries must be finite and below 2^127 in magnitude");
+    tn_batch::Stage &sg = b->stage[b->cur_stage];
+    if (sg.copying) {   // the copy out of this set, two runs ago, must be done before it is refilled
+        CK(cudaSetDevice(b->ctx->device));
+        CK(cudaEventSynchronize(sg.ev));
+        sg.copying = false;
+    }
+    tn_status s = pinned_reserve(sg.hdr, sg.hdr.size + 3 * sizeof(int64_t) * (size_t)count);
+    if (s == TN_OK) s = pinned_reserve(sg.val, sg.val.size + sizeof(double) * n_val);
+    if (s != TN_OK) return s;
+    int64_t *hdr = reinterpret_cast<int64_t *>(sg.hdr.p + sg.hdr.size);
+    double *val = reinterpret_cast<double *>(sg.val.p + sg.val.size);
+    int64_t vpos = (int64_t)(sg.val.size / (2 * sizeof(double)));   // complex entries staged so far
+    size_t src = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const Compiled &c = b->comp[b->job_comp[job[i]]];
+        const int64_t off = c.leaf_off[tensor[i]], cnt = c.leaf_off[tensor[i] + 1] - off;
+        hdr[3 * i] = b->leaf64_off[job[i]] + off;
+        hdr[3 * i + 1] = cnt;
+        hdr[3 * i + 2] = vpos;
+        std::memcpy(val, data + src, sizeof(double) * 2 * (size_t)cnt);
+        val += 2 * cnt;
+        src += 2 * (size_t)cnt;
+        vpos += cnt;
+    }
+    sg.hdr.size += 3 * sizeof(int64_t) * (size_t)count;
+    sg.val.size += sizeof(double) * n_val;
     return TN_OK;
 }
 

@@ -602,6 +602,8 @@ tn_status tn_serve_submit(tn_server *S, int32_t model, int32_t count, const int3
             vals += 2 * (size_t)(m.leaf_off[tensors[i] + 1] - m.leaf_off[tensors[i]]);
         }
         r.tensors.assign(tensors, tensors + count);
+        if (!entries_in_range(data, vals))
+            return fail(TN_EINVAL, "tensor entries must be finite and below 2^127 in magnitude");
         r.data.assign(data, data + vals);
         r.model = model;
         r.ticket = S->next_ticket++;

@@ -37,7 +37,9 @@ template <typename C> __device__ __forceinline__ C cscale(C v, decltype(C::x) s)
 __device__ __forceinline__ int32_t scale_exponent(uint32_t bits) {
     if (bits == 0u) return 0;
     int32_t e = (int32_t)((bits >> 23) & 0xffu);
-    return e == 0 ? -126 : e - 126;
+    // a max-abs of 2^126 or more keeps e = 126, so that the scale 2^-e stays a normal float (the
+    // scaled values then stay below 4); the exponent bookkeeping uses the same e
+    return e == 0 ? -126 : (e - 126 > 126 ? 126 : e - 126);
 }
 
 // Exact 2^e built from the IEEE-754 exponent field (e within the normal range of T; the scale

@@ -20,6 +20,16 @@ void set_error(const std::string &msg);
 
 inline tn_u128 to_abi(u128 x) { return tn_u128{(uint64_t)x, (uint64_t)(x >> 64)}; }
 
+// Tensor entries the engine accepts: finite, with |Re| and |Im| below 2^127.  The per-step scaling
+// tracks each tensor's max-abs in FP32, so larger leaf entries (possible only in complex128) would
+// saturate it; intermediates of any size are fine (every step rescales its operands).
+constexpr double kMaxEntry = 170141183460469231731687303715884105728.0;   // 2^127
+inline bool entries_in_range(const double *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(p[i] < kMaxEntry && p[i] > -kMaxEntry)) return false;   // NaN fails both
+    return true;
+}
+
 // Sorted set of edge ids (the legs of a tensor, Eq. 2.2 / Eq. 2.6).
 using Legs = std::vector<int32_t>;
 

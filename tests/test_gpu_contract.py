@@ -266,3 +266,44 @@ def test_rows_steps_with_odd_width(tnsa, ctx):
         if found == 4:
             break
     assert found >= 1
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_large_leaves_max_abs_across_slices(tnsa, ctx, prec):
+    """Two vectors of 50000 entries (leaves above 64 entries are converted by blocks per slice of
+    the leaf, whose max-abs values merge into one): their entries are about 2^60, except one near
+    the end of each at 0.75 * 2^127, just below the largest entry the boundary accepts.  Scaled by
+    the max-abs of the small entries alone, the product of the two large ones would overflow
+    complex64; the true max-abs of the whole leaf keeps it finite, and a max-abs of 2^126 or more
+    still gives a normal scale factor (the scale exponent stops at 126).  The dot product is
+    compared with numpy on the stored values."""
+    L = 50000
+    rng = np.random.default_rng(11)
+    big, small = 127, 60
+
+    def vec():
+        v = (rng.standard_normal(L) + 1j * rng.standard_normal(L)) * 2.0 ** small
+        v[L - 7] = (0.75 + 0.5j) * 2.0 ** big
+        return v
+
+    class Dot:
+        pass
+    net = Dot()
+    u, v = vec(), vec()
+    net.degrees = np.array([1, 1], np.int32)
+    net.dims = np.array([L, L], np.int64)
+    net.edges = np.array([[0, 0, 1, 0]], np.int32)
+    net.data = np.concatenate([u, v]).view(np.float64)
+    h = tnsa.tn_build(net)
+    plan = tnsa.tn_plan_import(h, [(0, 1)])
+    m, e, _ = tnsa.tn_contract(ctx, h, plan, prec)
+    m = complex(m)
+    assert np.isfinite(m.real) and np.isfinite(m.imag)
+    st = np.complex64 if prec == "c64" else np.complex128
+    us, vs = u.astype(st).astype(np.complex128), v.astype(st).astype(np.complex128)
+
+    def down(z):   # exact scaling by 2^-big, so that the products stay inside the float64 range
+        return np.ldexp(z.real, -big) + 1j * np.ldexp(z.imag, -big)
+    ref = np.dot(down(us), down(vs))
+    got = complex(np.ldexp(m.real, int(e) - 2 * big), np.ldexp(m.imag, int(e) - 2 * big))
+    check(got, ref, TOL[prec], f"{prec} dot of {L} entries")

@@ -216,6 +216,34 @@ def test_build_rejects_malformed():
         tnsa.tn_plan_create(h, k=ok.n_tensors + 1)
 
 
+def test_entries_out_of_range_are_rejected():
+    """Tensor entries must be finite with |Re|, |Im| below 2^127 (the max-abs of every tensor is
+    tracked in FP32): tn_build and tn_net_set_tensor reject NaN, infinities and 2^127, and accept
+    the largest double below it."""
+    ok = tni.amplitude_tn(tni.brickwork_1d(3, 2, seed=1), [0, 1, 0])
+    h = tnsa.tn_build(ok)
+    n0 = ok.tensors[0].size
+
+    class Net:
+        pass
+
+    for bad in (np.nan, np.inf, -np.inf, 2.0 ** 127, -(2.0 ** 127)):
+        b = Net()
+        b.degrees, b.dims, b.edges = ok.degrees, ok.dims, ok.edges
+        d = np.array(ok.data, np.float64)
+        d[1] = bad
+        b.data = d
+        with pytest.raises(tnsa.TnError):
+            tnsa.tn_build(b)
+        v = np.zeros(n0, np.complex128)
+        v[0] = complex(bad, 0.0)
+        with pytest.raises(tnsa.TnError):
+            tnsa.tn_net_set_tensor(h, 0, v)
+    v = np.zeros(n0, np.complex128)
+    v[0] = np.nextafter(2.0 ** 127, 0.0)
+    tnsa.tn_net_set_tensor(h, 0, v)
+
+
 def _circuits_cfg1_to_cfg4():
     yield tni.cfg1()[0], 1
     yield tni.cfg2()[0], 4
