@@ -161,6 +161,23 @@ __device__ __forceinline__ void stage_inputs_async(const JobPtrs &j, const LeafR
     }
 }
 
+// Error-free transformations (Knuth's TwoSum; the FMA form of Dekker's TwoProduct, as used by
+// Ogita, Rump and Oishi for accurate dot products), written with round-to-nearest intrinsics so
+// that the compiler neither contracts nor reorders them: a + b = s + err and a * b = p + err
+// exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &err) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// A sum kept as an unevaluated pair hi + lo (about 44 significant bits); adds x = xh + xl.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float xh, float xl) {
+    float s, t;
+    two_sum(hi, xh, s, t);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(xl, t));
+}
+
 // A small step computed by one warp: C = A * B with A, B and C at any address (shared memory, or
 // global memory in warp programs).  S lanes share an output (S a power of two, S <= 32 / outputs,
 // S <= K) and split its shared index; their partial sums are combined with xor shuffles.  The
@@ -168,7 +185,12 @@ __device__ __forceinline__ void stage_inputs_async(const JobPtrs &j, const LeafR
 // packed in 16 bits each (program operands have fewer than 2^16 elements) -- and are broadcast
 // with a shuffle.  The operand scales 2^-eA and 2^-eB are applied together on the B side when
 // their product is a normal number (products then round exactly as with separate scaling), else
-// separately.  Returns the warp-wide max-abs of C (every lane).
+// separately.  In complex64 each output is accumulated as hi + lo pairs from exact products and
+// exact pairwise sums, and rounded once when it is stored: these steps are most of a circuit's
+// steps, and with plain FP32 multiply-adds their several roundings per output (rather than the one
+// of storing it) tripled the error of small amplitudes; the extra arithmetic costs about 3 % of
+// the time of a batch of 24-qubit brickwork amplitudes, where these steps are latency-bound.
+// Returns the warp-wide max-abs of C (every lane).
 template <typename T>
 __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A, const cx_t<T> *B, cx_t<T> *Cp,
                                             int32_t eA, int32_t eB) {
@@ -201,6 +223,7 @@ __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A
             ob = lgroup_off(s.nn, s.n_dim, s.n_str, s.n_lsb, p2, n);
         }
         C acc = cmake((T)0, (T)0);
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;   // complex64: the sums as hi + lo pairs
         for (int32_t k0 = 0; k0 < K; k0 += 32) {
             uint32_t packed = 0;
             if (k0 + lane < K) {
@@ -219,13 +242,37 @@ __device__ __forceinline__ float small_core(const LocalStep &s, const cx_t<T> *A
                 if (act && k < kn) {
                     const C a = A[oa + (int32_t)(p & 0xffffu)];
                     const C b = B[ob + (int32_t)(p >> 16)];
-                    cfma(acc, fold ? a : cscale(a, sA), cscale(b, sB));
+                    const C as = fold ? a : cscale(a, sA), bs = cscale(b, sB);
+                    if constexpr (sizeof(T) == 4) {
+                        // exact products, then exact sums of pairs: Re and Im of a * b as hi + lo
+                        const float p1 = __fmul_rn(as.x, bs.x), e1 = __fmaf_rn(as.x, bs.x, -p1);
+                        const float p2 = __fmul_rn(as.y, bs.y), e2 = __fmaf_rn(as.y, bs.y, -p2);
+                        const float p3 = __fmul_rn(as.x, bs.y), e3 = __fmaf_rn(as.x, bs.y, -p3);
+                        const float p4 = __fmul_rn(as.y, bs.x), e4 = __fmaf_rn(as.y, bs.x, -p4);
+                        float s1, t1, s2, t2;
+                        two_sum(p1, -p2, s1, t1);
+                        two_sum(p3, p4, s2, t2);
+                        df_add(rh, rl, s1, __fadd_rn(__fsub_rn(e1, e2), t1));
+                        df_add(ih, il, s2, __fadd_rn(__fadd_rn(e3, e4), t2));
+                    } else {
+                        cfma(acc, as, bs);
+                    }
                 }
             }
         }
-        for (int32_t off = S >> 1; off > 0; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        if constexpr (sizeof(T) == 4) {
+            for (int32_t off = S >> 1; off > 0; off >>= 1) {
+                const float orh = __shfl_xor_sync(0xffffffffu, rh, off), orl = __shfl_xor_sync(0xffffffffu, rl, off);
+                const float oih = __shfl_xor_sync(0xffffffffu, ih, off), oil = __shfl_xor_sync(0xffffffffu, il, off);
+                df_add(rh, rl, orh, orl);
+                df_add(ih, il, oih, oil);
+            }
+            acc = cmake(__fadd_rn(rh, rl), __fadd_rn(ih, il));   // one rounding of each sum
+        } else {
+            for (int32_t off = S >> 1; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
         }
         if (act && sub == 0) {
             Cp[o] = acc;
