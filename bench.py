@@ -142,10 +142,10 @@ def kernel_sources_sha():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three contraction kernels of one
-# run of the headline workload (k_warp 195.9 MB + k_local 321.5 MB + k_persist 3736.1 MB per
+# run of the headline workload (k_warp 195.8 MB + k_local 321.9 MB + k_persist 3736.1 MB per
 # launch, mean of two runs), from one ncu capture of `bench.py` at the default batch
 # (profiles/traffic_brickwork24_batch2432.md); valid for the kernel sources with this hash.
-TRAFFIC = {"sources_sha": "162badb9ee2bc96c", "batch": 2432, "bytes_per_run": 4253491840}
+TRAFFIC = {"sources_sha": "83f845039e7f2be6", "batch": 2432, "bytes_per_run": 4253798144}
 
 
 def measured_peaks():
