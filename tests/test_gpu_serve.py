@@ -139,3 +139,70 @@ def test_request_larger_than_pool_is_refused(tnsa):
         tnsa.tn_serve_poll(server, tk, timeout_s=10.0)
     assert ei.value.status == tnsa.TN_EBUDGET
     assert tnsa.tn_serve_get_stats(server)["rejected"] == 1
+
+
+def test_split_precision_serving_mix_equals_alone(tnsa):
+    """Continuous batching in BF16 split, with requests whose dense step runs on the tensor cores:
+    trace(A B C) of 256 x 256 matrices, a new C per request (the A B product is a tensor-core
+    step in every request), mixed with 12-qubit brickwork amplitudes.  Every result equals the
+    request computed alone bit for bit, and the exact value within the BF16 bound."""
+    d = 256
+    rng = np.random.default_rng(21)
+    A = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2 * d)
+    B = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2 * d)
+
+    class Tr:
+        pass
+    tr = Tr()
+    tr.tensors = [A, B, np.zeros((d, d), complex)]
+    tr.degrees = np.array([2, 2, 2], np.int32)
+    tr.dims = np.array([d] * 6, np.int64)
+    tr.data = np.concatenate([t.ravel() for t in tr.tensors]).astype(np.complex128).view(np.float64)
+    tr.edges = np.array([[0, 1, 1, 0], [1, 1, 2, 0], [2, 1, 0, 0]], np.int32)
+    ht = tnsa.tn_build(tr)
+    pt = tnsa.tn_plan_import(ht, [(0, 1), (2, 3)])
+    assert (tnsa.tn_plan_compile_steps(ht, pt, "bf16", -1)[:, 0] == 4).any(), "a tensor-core step"
+    c1 = tni.brickwork_1d(12, 8, seed=51)
+    net = tni.amplitude_tn(c1, [0] * 12)
+    ha = tnsa.tn_build(net)
+    pa = tnsa.tn_plan_create(ha, k=2, iterations=50, seed=1, position=net.qubit)
+    ids = tni.bra_ids(net, 12)
+
+    ctx = tnsa.tn_ctx_create(0)
+    server = tnsa.tn_serve_create(ctx, "bf16", hbm_budget_bytes=1 << 30, max_batch=16)
+    mt, ma = tnsa.tn_serve_register(server, ht, pt), tnsa.tn_serve_register(server, ha, pa)
+    reqs = []
+    for r in range(40):
+        if r % 2:
+            C = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2 * d)
+            reqs.append(("trace", C, complex(np.einsum("ik,kj,ji->", A, B, C))))
+        else:
+            bits = rng.integers(0, 2, 12)
+            reqs.append(("amp", bits, None))
+    tickets = []
+    for kind, x, _ in reqs:
+        if kind == "trace":
+            tickets.append(tnsa.tn_serve_submit(server, mt, [2], x.reshape(1, -1)))
+        else:
+            tickets.append(tnsa.tn_serve_submit(server, ma, ids, np.eye(2, dtype=np.complex128)[x]))
+    psi = sv.simulate(c1).reshape((2,) * 12)
+    for (kind, x, ref), tk in zip(reqs, tickets):
+        r = tnsa.tn_serve_poll(server, tk, timeout_s=30.0)
+        assert r is not None
+        got = complex(r[0]) * 2.0 ** r[1]
+        if kind == "trace":
+            h = tnsa.tn_build(tr)
+            tnsa.tn_net_set_tensor(h, 2, x)
+            m, e, _ = tnsa.tn_contract(ctx, h, pt, "bf16")
+            assert got == complex(m) * 2.0 ** e                   # bit for bit
+            check(got, ref, TOL["bf16"], "trace(A B C)")
+        else:
+            h = tnsa.tn_build(net)
+            for q, t in enumerate(ids):
+                tnsa.tn_net_set_tensor(h, t, np.eye(2, dtype=np.complex128)[x[q]])
+            m, e, _ = tnsa.tn_contract(ctx, h, pa, "bf16")
+            assert got == complex(m) * 2.0 ** e
+            ref = psi[tuple(int(b) for b in x)]
+            if abs(ref) >= 1e-3 * 2.0 ** -6:   # the parity tests' redraw threshold
+                check(got, ref, TOL["bf16"], f"amplitude {tuple(x)}")
+    assert tnsa.tn_serve_get_stats(server)["completed"] == len(reqs)
