@@ -214,3 +214,41 @@ def test_results_buffer_must_hold_every_job(tnsa):
     mant, e2, st = tnsa.tn_batch_results(b)
     assert len(mant) == 3 and (st == 0).all()
     b.close()
+
+
+def test_staged_updates_accumulate_and_alternate(tnsa):
+    """Tensor updates are written into two pinned staging sets used in turn: several calls before
+    one run accumulate (the run applies all of them), a rejected call stages nothing, and runs that
+    alternate between the sets (each refilled only after its previous copy completed) keep giving
+    the state vector's amplitudes."""
+    circ = tni.brickwork_1d(12, 8, seed=4)
+    psi = sv.simulate(circ).reshape((2,) * 12)
+    rng = np.random.default_rng(31)
+    x0 = [tni.random_bitstring(12, 700 + i) for i in range(6)]
+    nets = [tni.amplitude_tn(circ, x) for x in x0]
+    hs = [tnsa.tn_build(n) for n in nets]
+    plan = tnsa.tn_plan_create(hs[0], k=2, iterations=50, seed=1, position=nets[0].qubit)
+    ctx = tnsa.tn_ctx_create(0)
+    b = tnsa.tn_batch_create(ctx, hs, [plan] * len(hs), "c64")
+    tnsa.tn_batch_run(b)
+    bras = tni.bra_ids(nets[0], 12)
+    eye = np.eye(2, dtype=np.complex128)
+    cur = [list(x) for x in x0]
+    for rnd in range(5):
+        # the new bitstrings of all jobs, staged in three calls (jobs 0-1, 2-3, 4-5)
+        new = [rng.integers(0, 2, 12) for _ in range(6)]
+        for lo in (0, 2, 4):
+            jobs = np.repeat(np.arange(lo, lo + 2, dtype=np.int32), 12)
+            tens = np.tile(np.asarray(bras, np.int32), 2)
+            tnsa.tn_batch_set_tensors(b, jobs, tens, eye[np.concatenate(new[lo:lo + 2])])
+        with pytest.raises(tnsa.TnError):   # a NaN entry: rejected, nothing staged
+            tnsa.tn_batch_set_tensors(b, [0], [bras[0]], np.array([np.nan, 0.0], np.complex128))
+        tnsa.tn_batch_run(b)
+        cur = [list(x) for x in new]
+        mant, e2, st = tnsa.tn_batch_results(b)
+        assert (st == 0).all()
+        got = amps(tnsa, mant, e2)
+        for i, x in enumerate(cur):
+            ref = psi[tuple(x)]
+            if abs(ref) >= 1e-3 * 2.0 ** -6:
+                check(got[i], ref, TOL["c64"], f"round {rnd} job {i}")
