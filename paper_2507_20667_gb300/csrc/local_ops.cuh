@@ -465,17 +465,19 @@ __device__ void local_mm(const LocalStep &s, const LocalSmem &L, T sA, T sB, flo
 // inside the loop.  When k is the contiguous index of A, a thread starts its k loop at m mod K, so
 // that the threads of a warp read different banks of A (the padded B rows keep their B reads apart
 // too).
-template <typename T, int NT>
+template <typename T, int NT, int NS>
 __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx, char *scratch) {
     using C = cx_t<T>;
     constexpr int R = (sizeof(T) == 4 ? 32 : 16) / NT > 0 ? (sizeof(T) == 4 ? 32 : 16) / NT : 1;
+    // NS neighbouring threads share each row: thread g of them holds columns [g NC, g NC + NC)
+    constexpr int NC = NT / NS;
     const C *A = reinterpret_cast<const C *>(L.data) + s.a_off;
     const C *B = reinterpret_cast<const C *>(L.data) + s.b_off;
     C *Cp = reinterpret_cast<C *>(L.data) + s.c_off;
     // [K][PB] scaled B; complex64 rows are padded to an even length, so they start on 16 bytes and
     // are read two entries per load
-    constexpr bool PAIRS = sizeof(T) == 4;
-    const int32_t N = s.N, K = s.K, M = s.M, PB = PAIRS ? (N + 2) & ~1 : N + 1;
+    constexpr bool PAIRS = sizeof(T) == 4 && NC % 2 == 0;
+    const int32_t N = s.N, K = s.K, M = s.M, PB = sizeof(T) == 4 ? (N + 2) & ~1 : N + 1;
     C *Bd = reinterpret_cast<C *>(scratch);
     int32_t *kat = reinterpret_cast<int32_t *>(Bd + 16 * (NT + 2));          // [K] offsets in A
     const bool p2 = s.pow2;
@@ -488,21 +490,23 @@ __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, f
         if (n == 0) kat[k] = ka;
     }
     __syncthreads();
+    const int32_t g = (int32_t)threadIdx.x % NS, c0 = g * NC;
+    if (c0 >= N) return;   // no column of this group (the caller's barrier follows)
     const bool skew = s.nk > 0 && s.k_sa[0] == 1;
-    const int32_t step = blockDim.x;
-    for (int32_t m0 = threadIdx.x; m0 < M; m0 += step * R) {
+    const int32_t step = (int32_t)blockDim.x / NS;
+    for (int32_t m0 = (int32_t)threadIdx.x / NS; m0 < M; m0 += step * R) {
         int32_t offA[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int32_t m = m0 + r * step;
             offA[r] = m < M ? lgroup_off(s.nm, s.m_dim, s.m_str, s.m_lsb, p2, m) : -1;
         }
-        const int32_t sh = skew ? m0 % K : 0;   // step is a multiple of K when K divides 256
-        C acc[R][NT];
+        const int32_t sh = skew ? m0 % K : 0;   // rows of a warp start at different k
+        C acc[R][NC];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int n = 0; n < NT; ++n) acc[r][n] = cmake((T)0, (T)0);
+            for (int n = 0; n < NC; ++n) acc[r][n] = cmake((T)0, (T)0);
 #pragma unroll 1
         for (int32_t kk = 0; kk < K; ++kk) {
             int32_t k = kk + sh;
@@ -511,25 +515,25 @@ __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, f
             C av[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) av[r] = offA[r] >= 0 ? cscale(A[offA[r] + ko], sA) : cmake((T)0, (T)0);
-            const C *Bk = Bd + k * PB;
+            const C *Bk = Bd + k * PB + c0;
             if constexpr (PAIRS) {
                 const float4 *Bk4 = reinterpret_cast<const float4 *>(Bk);
 #pragma unroll
-                for (int n2 = 0; n2 < NT / 2; ++n2) {
-                    if (2 * n2 >= N) break;
+                for (int n2 = 0; n2 < NC / 2; ++n2) {
+                    if (c0 + 2 * n2 >= N) break;
                     const float4 bb = Bk4[n2];
                     const C b0 = cmake(bb.x, bb.y), b1 = cmake(bb.z, bb.w);
 #pragma unroll
                     for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2], av[r], b0);
-                    if (2 * n2 + 1 < N) {
+                    if (c0 + 2 * n2 + 1 < N) {
 #pragma unroll
                         for (int r = 0; r < R; ++r) cfma(acc[r][2 * n2 + 1], av[r], b1);
                     }
                 }
             } else {
 #pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    if (n >= N) break;
+                for (int n = 0; n < NC; ++n) {
+                    if (c0 + n >= N) break;
                     const C b = Bk[n];
 #pragma unroll
                     for (int r = 0; r < R; ++r) cfma(acc[r][n], av[r], b);
@@ -539,15 +543,28 @@ __device__ void local_rows(const LocalStep &s, const LocalSmem &L, T sA, T sB, f
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (offA[r] < 0) continue;
-            C *out = Cp + (m0 + r * step) * N;
+            C *out = Cp + (m0 + r * step) * N + c0;
 #pragma unroll
-            for (int n = 0; n < NT; ++n)
-                if (n < N) {
+            for (int n = 0; n < NC; ++n)
+                if (c0 + n < N) {
                     out[n] = acc[r][n];
                     mx = fmaxf(mx, absmax2(acc[r][n]));
                 }
         }
     }
+}
+
+// Narrow block-wide step: NS threads share a row when the rows alone would leave threads idle.
+template <typename T, int NT>
+__device__ __forceinline__ void local_rows_any(const LocalStep &s, const LocalSmem &L, T sA, T sB, float &mx,
+                                               char *scratch) {
+    constexpr int R = (sizeof(T) == 4 ? 32 : 16) / NT > 0 ? (sizeof(T) == 4 ? 32 : 16) / NT : 1;
+    const int32_t busy = (s.M + R - 1) / R;   // threads with a row when NS = 1
+    if constexpr (NT >= 8) {
+        if (4 * busy <= (int32_t)blockDim.x) return local_rows<T, NT, 4>(s, L, sA, sB, mx, scratch);
+    }
+    if (2 * busy <= (int32_t)blockDim.x) return local_rows<T, NT, 2>(s, L, sA, sB, mx, scratch);
+    local_rows<T, NT, 1>(s, L, sA, sB, mx, scratch);
 }
 
 // Scratch bytes of local_mm: the largest tile set (TK = 8 for complex64, 4 for complex128).
@@ -562,9 +579,9 @@ __device__ __forceinline__ void local_mm_dispatch(const LocalStep &s, const Loca
                                                   char *scratch) {
     constexpr int TK = LocalMmScratch<T>::TK;
     if (s.N <= 16 && s.K <= 16) {
-        if (s.N <= 4) local_rows<T, 4>(s, L, sA, sB, mx, scratch);
-        else if (s.N <= 8) local_rows<T, 8>(s, L, sA, sB, mx, scratch);
-        else local_rows<T, 16>(s, L, sA, sB, mx, scratch);
+        if (s.N <= 4) local_rows_any<T, 4>(s, L, sA, sB, mx, scratch);
+        else if (s.N <= 8) local_rows_any<T, 8>(s, L, sA, sB, mx, scratch);
+        else local_rows_any<T, 16>(s, L, sA, sB, mx, scratch);
     } else if (s.N <= 4) local_mm<T, 1, 256, 1, 4, TK>(s, L, sA, sB, mx, scratch);
     else if (s.N <= 8) local_mm<T, 2, 128, 2, 4, TK>(s, L, sA, sB, mx, scratch);
     else if (s.N <= 16) local_mm<T, 4, 64, 4, 4, TK>(s, L, sA, sB, mx, scratch);
