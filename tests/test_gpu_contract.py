@@ -268,6 +268,46 @@ def test_rows_steps_with_odd_width(tnsa, ctx):
     assert found >= 1
 
 
+def _split_row_steps(geo):
+    """Steps of a 256-thread block program that the narrow row kernel runs with 2 or 4 threads per
+    row: not small enough for one warp (M N > 256 or M N K > 4096), N and K <= 16, and so few rows
+    (R = 32 / NT per thread, NT = N rounded up to 4, 8 or 16) that at least half the threads would
+    hold none.  Both operand orders are considered, since the program may swap A and B."""
+    hits = []
+    for kind, M, N, K, *_ in geo:
+        for m, n in ((M, N), (N, M)):
+            if n > 16 or K > 16 or not (m * n > 256 or m * n * K > 4096):
+                continue
+            nt = 4 if n <= 4 else 8 if n <= 8 else 16
+            if 2 * -(-m // (32 // nt)) <= 256:
+                hits.append((int(m), int(n), int(K)))
+    return hits
+
+
+def test_block_row_steps_shared_between_threads(tnsa, ctx):
+    """Mixed-dimension networks (dims 3 and 5) that run entirely as subtree programs: their
+    block-wide row steps with few rows share each row between 2 or 4 threads, and odd widths leave
+    part of the last thread's columns empty.  Compared with the oracle in complex64 and
+    complex128."""
+    found = 0
+    for seed in range(40):
+        net = tni.random_network(12, 6, (3, 5), seed=seed)
+        h = tnsa.tn_build(net)
+        plan = tnsa.tn_plan_create(h, k=1)
+        hits = [s for s in _split_row_steps(tnsa.tn_plan_compile_steps(h, plan, "c64", 0)) if s[1] % 2]
+        progs = tnsa.tn_plan_compile_steps(h, plan, "c64", 64 * 1024)
+        if not hits or not all(p[0] == 5 for p in progs):
+            continue
+        found += 1
+        ref = oracle_amp(net)
+        for prec in ("c64", "c128"):
+            m, e, _ = tnsa.tn_contract(ctx, h, plan, prec)
+            check(tnsa.amplitude(m, e), ref, TOL[prec], f"seed {seed} {prec} {hits}")
+        if found == 6:
+            break
+    assert found >= 3
+
+
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_large_leaves_max_abs_across_slices(tnsa, ctx, prec):
     """Two vectors of 50000 entries (leaves above 64 entries are converted by blocks per slice of
