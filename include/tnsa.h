@@ -33,7 +33,7 @@ typedef enum {
     TN_EBUDGET = 3,       /* the plan's device footprint exceeds the context's budget */
     TN_ECUDA = 4,         /* a CUDA call failed or no usable device */
     TN_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-    TN_EUNSUPPORTED = 6   /* valid request outside what this build supports */
+    TN_EUNSUPPORTED = 6   /* valid request outside what this library supports */
 } tn_status;
 
 /* Arithmetic used for the pairwise contractions.

@@ -1826,7 +1826,7 @@ tn_status tn_ctx_create(int32_t device, void *cuda_stream, size_t hbm_budget_byt
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, device));
     if (prop.major != 10 || prop.minor != 3)
-        return fail(TN_ECUDA, "this build targets sm_103a (GB300); device is sm_" +
+        return fail(TN_ECUDA, "this library targets sm_103a (GB300); device is sm_" +
                                   std::to_string(prop.major) + std::to_string(prop.minor));
     CK(cudaSetDevice(device));
     tn_ctx *c = new (std::nothrow) tn_ctx;
