@@ -55,8 +55,3 @@ def greedy_steps(legsets: list, dims: dict) -> list:
         next_id += 1
     return steps
 
-
-def partition_tree_steps(net_leg_sets: list, dims: dict, members: list) -> list:
-    """Greedy tree for one partition; `members` are global tensor ids in increasing order.
-    Returns the steps in local ids (members[i] has local id i)."""
-    return greedy_steps([net_leg_sets[t] for t in members], dims)

@@ -6,7 +6,9 @@
     independence of the result (the contraction result does not depend on the tree, Section 2.3);
   * the cost model against hand-derived numbers (tests/golden/costs_hand.txt) and the identities
     that follow from Eq. 3.4-3.5;
-  * the greedy rule against a hand-derived sequence.
+  * the greedy rule against a hand-derived sequence;
+  * the permutation index map against index arithmetic written out with plain loops, and the
+    matrix transpose.
 """
 import math
 import os
@@ -17,6 +19,7 @@ import pytest
 from oracle import contract as oc
 from oracle import costs as ocost
 from oracle import greedy as og
+from oracle import perm as operm
 from oracle import statevector as sv
 from paper_2507_20667_gb300 import inputs as tni
 
@@ -288,3 +291,34 @@ def test_greedy_ties_and_disconnected():
     steps = og.greedy_steps(list(ocost.leaf_legs(net)), ocost.edge_dims(net))
     # tie between (0,1) and (2,3) -> (0,1) first; then (2,3); then outer product of scalars 4, 5
     assert steps == [(0, 1), (2, 3), (4, 5)]
+
+
+@pytest.mark.parametrize("dims,perm", [((2, 3, 4), (2, 0, 1)), ((3, 1, 5, 2), (3, 1, 0, 2)),
+                                       ((2, 2, 2, 2, 2), (4, 3, 2, 1, 0)), ((5,), (0,)), ((), ())])
+def test_permute_iota_brute_force(dims, perm):
+    """Output element i (row-major over the permuted shape) is the input element whose index along
+    axis perm[t] is the output's index along axis t: the map enumerated with plain loops."""
+    out = operm.permute_iota(dims, perm)
+    odims = [dims[p] for p in perm]
+    expected = []
+    for i in range(math.prod(dims)):
+        idx, r = [], i
+        for d in reversed(odims):
+            idx.append(r % d)
+            r //= d
+        idx.reverse()
+        src = [0] * len(dims)
+        for t, p in enumerate(perm):
+            src[p] = idx[t]
+        lin = 0
+        for a, d in enumerate(dims):
+            lin = lin * d + src[a]
+        expected.append(lin)
+    assert out.tolist() == expected
+
+
+def test_permute_iota_matrix_transpose():
+    """Swapping the two axes of a rows x cols matrix: element (j, i) of the result is i cols + j."""
+    rows, cols = 3, 5
+    out = operm.permute_iota((rows, cols), (1, 0))
+    assert out.tolist() == [i * cols + j for j in range(cols) for i in range(rows)]
