@@ -458,9 +458,11 @@ __device__ void local_mm(const LocalStep &s, const LocalSmem &L, T sA, T sB, flo
         }
 }
 
-// Block-wide narrow contraction (N <= NT <= 16, K <= 16) with every operand in shared memory:
-// each thread owns R rows (m, m + blockDim, ...), R = 32 / NT, with their R x N accumulators in
-// registers; per shared index it reads the rows' A entries and one row of B from a dense, scaled,
+// Block-wide narrow contraction (N <= NT <= 16, K <= 16) with every operand in shared memory.
+// NS neighbouring threads share a set of R rows (m, m + blockDim / NS, ...), R = 32 / NT (16 / NT
+// for complex128), and each of them holds the R x NT / NS accumulators of its own columns in
+// registers; NS > 1 only when the rows alone would leave at least half the block idle.  Per shared
+// index a thread reads its rows' A entries and its part of one row of B from a dense, scaled,
 // padded copy in the scratch area, and every B entry feeds R complex multiply-adds.  No barrier
 // inside the loop.  When k is the contiguous index of A, a thread starts its k loop at m mod K, so
 // that the threads of a warp read different banks of A (the padded B rows keep their B reads apart
