@@ -145,7 +145,7 @@ def kernel_sources_sha():
 # run of the headline workload (k_warp 195.8 MB + k_local 321.9 MB + k_persist 3736.1 MB per
 # launch, mean of two runs), from one ncu capture of `bench.py` at the default batch
 # (profiles/traffic_brickwork24_batch2432.md); valid for the kernel sources with this hash.
-TRAFFIC = {"sources_sha": "ea93704879c7347c", "batch": 2432, "bytes_per_run": 4253917056}
+TRAFFIC = {"sources_sha": "41dac86b20f80667", "batch": 2432, "bytes_per_run": 4253917056}
 
 
 def measured_peaks():

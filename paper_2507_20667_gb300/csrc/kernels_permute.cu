@@ -3,9 +3,10 @@
 // order are fused first.  When the innermost axis survives the permutation, the tensor is a set
 // of contiguous rows moved as wholes: a group of lanes per row, whose first lane computes the
 // row's source offset and broadcasts it with a shuffle, copies the row in 16-byte vectors when both
-// ends are 16-byte aligned (element by element otherwise).  Otherwise a 32 x 32 tile of
+// ends are 16-byte aligned (element by element otherwise).  Otherwise a tile of
 // (output-innermost, input-innermost) is staged in shared memory so that both the reads and the
-// writes are coalesced.
+// writes are coalesced: 64 x 64 for elements of up to 8 bytes (contiguous runs of 512 bytes on
+// both sides for 8-byte elements, instead of 256), 32 x 32 otherwise.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -133,54 +134,59 @@ __global__ void __launch_bounds__(256) k_perm_tile(const E *__restrict__ in, E *
 }
 
 // Grouped tile, for permutations of many short axes (the bit permutations of qubit tensors): the
-// output's innermost axes whose sizes multiply to at most 32 form group A, the input's innermost
-// axes (outside A) group B.  A block moves one PA x PB tile of (A index, B index) for one index of
-// the remaining axes through shared memory: it reads with consecutive threads along B (contiguous
-// in the input) and writes with consecutive threads along A (contiguous in the output).
+// output's innermost axes whose sizes multiply to at most 64 (or 32) form group A, the input's
+// innermost axes (outside A) group B.  A block moves PA x PB tiles of (A index, B index), each for
+// one index of the remaining axes, through shared memory: it reads with consecutive threads along B
+// (contiguous in the input) and writes with consecutive threads along A (contiguous in the output).
+constexpr int kGroupMax = 64;   // largest group: the edge of the large tile
+
 struct GroupTile {
     int32_t pa, pb;                           // sizes of the two groups (products of their dims)
     int32_t nrest;
-    int64_t in_a[32], out_a[32];              // offsets of each A index in the input / output
-    int64_t in_b[32], out_b[32];              // same for B
+    int64_t in_a[kGroupMax], out_a[kGroupMax];   // offsets of each A index in the input / output
+    int64_t in_b[kGroupMax], out_b[kGroupMax];   // same for B
     int64_t rdim[kMaxRank], rin[kMaxRank], rout[kMaxRank];   // remaining axes, outermost first
 };
 
-template <typename E>
+// TE: tile edge (groups of at most TE elements); kTiles tiles per block, TE * TE / 256 elements of
+// each per thread.
+template <typename E, int TE, int kTiles>
 __global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ in, E *__restrict__ out,
                                                          const GroupTile g, int64_t n_tiles) {
-    constexpr int kTiles = 4;   // tiles per block
-    __shared__ E tile[32][33];
-    __shared__ int64_t s_in_a[32], s_out_a[32], s_in_b[32], s_out_b[32], s_ib[kTiles], s_ob[kTiles];
+    constexpr int kPer = TE * TE / 256;
+    static_assert(kPer * 256 == TE * TE && TE <= kGroupMax && TE + kTiles <= 256, "tile split");
+    __shared__ E tile[TE][TE + 1];
+    __shared__ int64_t s_in_a[TE], s_out_a[TE], s_in_b[TE], s_out_b[TE], s_ib[kTiles], s_ob[kTiles];
     const int tid = threadIdx.x;
     // the offset tables move from the parameters to shared memory once (the arithmetic loops index
-    // them per thread), and the first kTiles threads decompose the block's tile indices
-    if (tid < 32) {
+    // them per thread), and the next kTiles threads decompose the block's tile indices
+    if (tid < TE) {
         s_in_a[tid] = tid < g.pa ? g.in_a[tid] : 0;
         s_out_a[tid] = tid < g.pa ? g.out_a[tid] : 0;
         s_in_b[tid] = tid < g.pb ? g.in_b[tid] : 0;
         s_out_b[tid] = tid < g.pb ? g.out_b[tid] : 0;
-    } else if (tid < 32 + kTiles) {
-        int64_t blk = (int64_t)blockIdx.x * kTiles + (tid - 32), ib = 0, ob = 0;
+    } else if (tid < TE + kTiles) {
+        int64_t blk = (int64_t)blockIdx.x * kTiles + (tid - TE), ib = 0, ob = 0;
         for (int32_t t = g.nrest - 1; t >= 0; --t) {
             const int64_t dgt = blk % g.rdim[t];
             blk /= g.rdim[t];
             ib += dgt * g.rin[t];
             ob += dgt * g.rout[t];
         }
-        s_ib[tid - 32] = ib;
-        s_ob[tid - 32] = ob;
+        s_ib[tid - TE] = ib;
+        s_ob[tid - TE] = ob;
     }
     __syncthreads();
-    // every read of the block's tiles is issued first (up to kTiles x 4 loads in flight per
-    // thread), then each tile goes through shared memory in turn
-    const int n = g.pa * g.pb;                       // at most 1024 = 4 per thread
+    // every read of the block's tiles is issued first (kTiles x kPer loads in flight per thread),
+    // then each tile goes through shared memory in turn
+    const int n = g.pa * g.pb;                       // at most TE * TE: kPer per thread
     int nq = kTiles;
     if ((int64_t)blockIdx.x * kTiles + nq > n_tiles) nq = (int)(n_tiles - (int64_t)blockIdx.x * kTiles);
-    E v[kTiles][4];
+    E v[kTiles][kPer];
 #pragma unroll
     for (int q = 0; q < kTiles; ++q)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kPer; ++u) {
             const int e = tid + u * 256;
             if (q < nq && e < n) {
                 const int b = e % g.pb, a = e / g.pb;
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ i
     for (int q = 0; q < kTiles; ++q) {
         if (q >= nq) break;   // block-uniform
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kPer; ++u) {
             const int e = tid + u * 256;
             if (e < n) tile[e / g.pb][e % g.pb] = v[q][u];
         }
@@ -205,13 +211,13 @@ __global__ void __launch_bounds__(256) k_perm_group_tile(const E *__restrict__ i
     }
 }
 
-// Builds the grouped tile of plan p; false when it does not apply (a single axis of 32 or more
-// innermost in the output, or groups smaller than 8 elements).
-bool group_tile(const PermPlan &p, GroupTile &g) {
+// Builds the grouped tile of plan p with groups of at most `lim` elements (lim <= kGroupMax); false
+// when it does not apply (groups smaller than 8 elements).
+bool group_tile(const PermPlan &p, GroupTile &g, int64_t lim) {
     std::vector<char> in_a(p.rank, 0), in_b(p.rank, 0);
     int64_t pa = 1, pb = 1;
     std::vector<int32_t> ga, gb;   // innermost first
-    for (int32_t t = p.rank - 1; t >= 0 && pa * p.odim[t] <= 32; --t) {
+    for (int32_t t = p.rank - 1; t >= 0 && pa * p.odim[t] <= lim; --t) {
         pa *= p.odim[t];
         ga.push_back(t);
         in_a[t] = 1;
@@ -222,7 +228,7 @@ bool group_tile(const PermPlan &p, GroupTile &g) {
     std::sort(by_in.begin(), by_in.end(), [&](int32_t x, int32_t y) { return p.istride[x] < p.istride[y]; });
     for (int32_t t : by_in) {
         if (in_a[t]) continue;
-        if (pb * p.odim[t] > 32) break;
+        if (pb * p.odim[t] > lim) break;
         pb *= p.odim[t];
         gb.push_back(t);
         in_b[t] = 1;
@@ -263,10 +269,20 @@ cudaError_t perm_launch(const void *src, void *dst, const PermPlan &p, cudaStrea
     if (p.total == 0) return cudaSuccess;
     if (p.b >= 0 && p.odim[p.a] < 32) {
         GroupTile g;
-        if (group_tile(p, g)) {
+        // the 64 x 64 tile (33 KB of shared memory for 8-byte elements) when it is at least half
+        // full, else the 32 x 32 tile, four per block
+        if constexpr (sizeof(E) <= 8) {
+            if (group_tile(p, g, 64) && (int64_t)g.pa * g.pb >= 2048) {
+                const int64_t tiles = p.total / ((int64_t)g.pa * g.pb);
+                if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+                k_perm_group_tile<E, 64, 1><<<(unsigned)tiles, 256, 0, st>>>(in, out, g, tiles);
+                return cudaGetLastError();
+            }
+        }
+        if (group_tile(p, g, 32)) {
             const int64_t tiles = p.total / ((int64_t)g.pa * g.pb), blocks = (tiles + 3) / 4;
             if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-            k_perm_group_tile<E><<<(unsigned)blocks, 256, 0, st>>>(in, out, g, tiles);
+            k_perm_group_tile<E, 32, 4><<<(unsigned)blocks, 256, 0, st>>>(in, out, g, tiles);
             return cudaGetLastError();
         }
     }
