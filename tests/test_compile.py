@@ -10,6 +10,7 @@ The algorithmic flop count is the plan's con_serial times 8 (Eq. 3.2), whatever 
 import numpy as np
 import pytest
 
+from oracle import costs as ocost
 from paper_2507_20667_gb300 import inputs as tni
 from paper_2507_20667_gb300 import tnsa
 
@@ -77,3 +78,41 @@ def test_rows_chains_link_producer_to_consumer(budget):
         assert n <= 32
     # complex128 storage never stages A in shared memory, so it has no chains
     assert tnsa.tn_plan_compile_stats(h, plan, "c128", budget)["n_chained"] == 0
+
+
+def _grid():
+    circ = tni.grid_2d(3, 4, 6, seed=4)
+    net = tni.amplitude_tn(circ, tni.random_bitstring(12, 7))
+    h = tnsa.tn_build(net)
+    return net, h, tnsa.tn_plan_create(h, k=3, iterations=100, seed=5)
+
+
+def _mixed(seed):
+    net = tni.random_network(14, 10, (1, 2, 3, 5, 6), seed=seed)
+    h = tnsa.tn_build(net)
+    return net, h, tnsa.tn_plan_create(h, k=2, iterations=50, seed=seed)
+
+
+@pytest.mark.parametrize("make", [_cfg2_like, _grid, lambda: _mixed(0), lambda: _mixed(3)],
+                         ids=["brickwork16", "grid3x4", "mixed0", "mixed3"])
+def test_step_geometry_matches_leg_sets(make):
+    """Leg analysis (Eq. 2.6, Eq. 3.3): for every pairwise step of the plan's tree, the compiled
+    M, N and K are the sizes of the two operands' free legs and of their shared legs, as the
+    oracle's leg sets give them along the exported tree.  The compiler makes the larger operand A,
+    so M and N are compared as an unordered pair; the DOTF entry of the root's DOTP + DOTF pair is
+    not a pairwise step of its own."""
+    net, h, plan = make()
+    _, psteps, _ = tnsa.tn_plan_export(plan, net.n_tensors)
+    dims = ocost.edge_dims(net)
+    legs = dict(enumerate(ocost.leaf_legs(net)))
+    want = []
+    for l, r, o in psteps:
+        a, b = legs[int(l)], legs[int(r)]
+        shared = a & b
+        legs[int(o)] = a ^ b
+        m, n = ocost.prod(dims, a - shared), ocost.prod(dims, b - shared)
+        want.append((min(m, n), max(m, n), ocost.prod(dims, shared)))
+    got = [(int(min(M, N)), int(max(M, N)), int(K))
+           for kind, M, N, K, *_ in tnsa.tn_plan_compile_steps(h, plan, "c64", 0) if kind != KIND_DOTF]
+    assert len(want) == net.n_tensors - 1
+    assert sorted(got) == sorted(want)
